@@ -1,0 +1,193 @@
+"""Seeded synthetic graph generators.
+
+These produce the *inputs* of the solver (edge lists and weights) and nothing
+else: no part of the method's arithmetic lives here.  Both the CUDA path and the
+FP64 oracle consume the same arrays, so this module is the only code the two
+sides share.
+
+The paper's own workloads (Bhoslib frb59-26-*, SNAP Amazon/DBLP/Google+, Sec. 4.2)
+are not available; these generators stand in for them with seeded graphs of
+the shapes used in the benchmarks:
+
+* ``er_graph``      -- Erdos-Renyi G(n, M): M distinct undirected edges, uniform.
+* ``chung_lu``      -- power-law expected-degree graph (exponent gamma), M edges.
+* ``grid_graph``    -- 4-neighbour W x H grid, the multiway-cut image workload.
+
+Every edge list is canonical: ``eu < ev`` elementwise, no duplicates, sorted by
+``(eu, ev)``.  Vertex ids of the random graphs are a seeded random relabelling,
+so id order carries no structure.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Graph",
+    "er_graph",
+    "chung_lu",
+    "grid_graph",
+    "int_weights",
+    "unit_interval_weights",
+    "lognormal_weights",
+    "batch_instances",
+]
+
+
+@dataclass
+class Graph:
+    """An undirected simple graph with optional vertex / edge weights."""
+
+    n: int
+    eu: np.ndarray  # int32[m], eu < ev
+    ev: np.ndarray  # int32[m]
+    w: np.ndarray | None = None  # float32[n] vertex weights (VC / IS)
+    ce: np.ndarray | None = None  # float32[m] edge weights (multiway cut)
+    terminals: np.ndarray | None = None  # int32[k] (multiway cut)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return int(self.eu.shape[0])
+
+
+def _canonical_unique(u: np.ndarray, v: np.ndarray, n: int, m: int):
+    """Canonicalise pairs, drop loops, keep the first ``m`` distinct pairs in
+    draw order.  Returns the kept keys (u*n+v) or fewer if not enough."""
+    keep = u != v
+    u, v = u[keep], v[keep]
+    lo = np.minimum(u, v).astype(np.int64)
+    hi = np.maximum(u, v).astype(np.int64)
+    key = lo * n + hi
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    return key[first[:m]]
+
+
+def _finish(keys: np.ndarray, n: int, relabel: np.ndarray | None):
+    eu = (keys // n).astype(np.int64)
+    ev = (keys % n).astype(np.int64)
+    if relabel is not None:
+        eu, ev = relabel[eu], relabel[ev]
+        lo = np.minimum(eu, ev)
+        hi = np.maximum(eu, ev)
+        eu, ev = lo, hi
+    order = np.lexsort((ev, eu))
+    return eu[order].astype(np.int32), ev[order].astype(np.int32)
+
+
+def er_graph(n: int, m: int, seed: int) -> Graph:
+    """G(n, M): ``m`` distinct edges drawn uniformly without loops."""
+    if m > n * (n - 1) // 2:
+        raise ValueError("too many edges for a simple graph")
+    rng = np.random.default_rng(seed)
+    keys = np.empty(0, np.int64)
+    need = m
+    while keys.shape[0] < m:
+        draw = int(need * 1.2) + 64
+        u = rng.integers(0, n, size=draw)
+        v = rng.integers(0, n, size=draw)
+        new = _canonical_unique(u, v, n, draw)
+        allk = np.concatenate([keys, new])
+        _, first = np.unique(allk, return_index=True)
+        first.sort()
+        keys = allk[first][:m]
+        need = m - keys.shape[0]
+    eu, ev = _finish(keys, n, None)
+    return Graph(n=n, eu=eu, ev=ev, meta={"kind": "er", "n": n, "m": m, "seed": seed})
+
+
+def chung_lu(n: int, m: int, gamma: float, seed: int) -> Graph:
+    """Chung-Lu power-law graph.
+
+    Expected degrees w_i proportional to (i+1)^(-1/(gamma-1)), scaled to mean 2m/n
+    and capped at sqrt(sum w) (the usual Chung-Lu admissibility cap).  Endpoint
+    pairs are drawn independently from w; loops and repeated pairs are dropped
+    until ``m`` distinct edges remain.  Vertex ids are randomly relabelled.
+    """
+    rng = np.random.default_rng(seed)
+    i = np.arange(n, dtype=np.float64)
+    w = (i + 1.0) ** (-1.0 / (gamma - 1.0))
+    target = 2.0 * m / n
+    for _ in range(8):
+        w *= target / w.mean()
+        cap = np.sqrt(w.sum())
+        w = np.minimum(w, cap)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    keys = np.empty(0, np.int64)
+    need = m
+    while keys.shape[0] < m:
+        draw = int(need * 1.3) + 1024
+        u = np.searchsorted(cdf, rng.random(draw), side="right")
+        v = np.searchsorted(cdf, rng.random(draw), side="right")
+        u = np.minimum(u, n - 1)
+        v = np.minimum(v, n - 1)
+        new = _canonical_unique(u, v, n, draw)
+        allk = np.concatenate([keys, new])
+        _, first = np.unique(allk, return_index=True)
+        first.sort()
+        keys = allk[first][:m]
+        need = m - keys.shape[0]
+    relabel = rng.permutation(n).astype(np.int64)
+    eu, ev = _finish(keys, n, relabel)
+    return Graph(n=n, eu=eu, ev=ev,
+                 meta={"kind": "chung_lu", "n": n, "m": m, "gamma": gamma, "seed": seed})
+
+
+def grid_graph(width: int, height: int, k: int, seed: int) -> Graph:
+    """4-neighbour grid with ``k`` distinct terminal pixels and lognormal(0,1)
+    edge weights (FP32).  Vertex id = row*width + col."""
+    n = width * height
+    idx = np.arange(n, dtype=np.int64).reshape(height, width)
+    hu = idx[:, :-1].ravel()
+    hv = idx[:, 1:].ravel()
+    vu = idx[:-1, :].ravel()
+    vv = idx[1:, :].ravel()
+    eu = np.concatenate([hu, vu])
+    ev = np.concatenate([hv, vv])
+    order = np.lexsort((ev, eu))
+    eu = eu[order].astype(np.int32)
+    ev = ev[order].astype(np.int32)
+    rng = np.random.default_rng(seed)
+    terminals = rng.choice(n, size=k, replace=False).astype(np.int32)
+    ce = lognormal_weights(eu.shape[0], rng)
+    return Graph(n=n, eu=eu, ev=ev, ce=ce, terminals=terminals,
+                 meta={"kind": "grid", "width": width, "height": height, "k": k, "seed": seed})
+
+
+def int_weights(n: int, lo: int, hi: int, rng) -> np.ndarray:
+    """Integer weights uniform in [lo, hi], stored as FP32 (exact)."""
+    return rng.integers(lo, hi + 1, size=n).astype(np.float32)
+
+
+def unit_interval_weights(n: int, rng) -> np.ndarray:
+    """Weights uniform in (0, 1] on the 2^-24 lattice, exact in FP32."""
+    return (rng.integers(1, (1 << 24) + 1, size=n).astype(np.float64) / float(1 << 24)).astype(np.float32)
+
+
+def lognormal_weights(m: int, rng) -> np.ndarray:
+    return rng.lognormal(0.0, 1.0, size=m).astype(np.float32)
+
+
+def batch_instances(count: int, n_lo: int, n_hi: int, d_lo: float, d_hi: float,
+                    w_lo: int, w_hi: int, seed: int):
+    """Batched workload: ``count`` ER instances, the first half vertex cover, the
+    second half independent set.  n ~ U[n_lo, n_hi], average degree
+    d ~ U[d_lo, d_hi], M = round(n*d/2), integer weights U[w_lo, w_hi].
+
+    Returns a list of (kind, Graph) with kind in {"vc", "is"}.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    ds = rng.uniform(d_lo, d_hi, size=count)
+    seeds = rng.integers(0, 2**62, size=count)
+    for t in range(count):
+        n = int(ns[t])
+        m = int(round(n * ds[t] / 2.0))
+        g = er_graph(n, m, int(seeds[t]))
+        g.w = int_weights(n, w_lo, w_hi, np.random.default_rng(int(seeds[t]) ^ 0x5DEECE66D))
+        out.append(("vc" if t < count // 2 else "is", g))
+    return out
