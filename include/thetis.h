@@ -1,0 +1,236 @@
+/*
+ * thetis.h -- C ABI of the GB300 (sm_103a) solver for LP relaxations by
+ * projected stochastic coordinate descent on a quadratic penalty, followed by
+ * LP rounding ("An Approximate, Efficient LP Solver for LP Rounding",
+ * Sridhar et al., arXiv 1311.2661).
+ *
+ * The problem is the paper's standard form (Sec. 3.1, eq. LP)
+ *      min c^T x   s.t.  A x = b,   lo <= x <= hi,
+ * where every inequality row (GE / LE) receives one slack column with
+ * coefficient -1 / +1 and bounds [0, +inf) (App. C.2 / C.3 slack forms).
+ * The solver minimises the regularised penalty of eq. QP (Sec. 3.2)
+ *      f(x) = c^T x - ubar^T (Ax-b) + beta/2 ||Ax-b||^2 + 1/(2 beta) ||x-xbar||^2
+ * by coordinate steps x_j <- Proj(x_j - grad_j f / L_j) (Algorithm 1, Sec. 3.3),
+ * with simplex-constrained blocks stepped and projected as a whole (App. E,
+ * multiway cut).
+ *
+ * Conventions for every call:
+ *  - Every call returns a thetis_status; nothing aborts.  On an error the
+ *    thread-local thetis_last_error() names the cause.  A CUDA error is
+ *    reported as THETIS_E_CUDA after the handle's stream is synchronised.
+ *  - Array arguments are plain pointers.  `mem` says where they live:
+ *    THETIS_MEM_HOST (pageable or pinned host memory) or THETIS_MEM_DEVICE
+ *    (device memory of the current device).  Inputs are deep-copied before
+ *    the call returns, so the caller may free them afterwards.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work of
+ *    a handle is ordered on that stream.
+ *  - A handle is used by one host thread at a time.
+ */
+#ifndef THETIS_H
+#define THETIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  THETIS_OK = 0,
+  THETIS_E_INVALID = 1,  /* bad argument, malformed sparse matrix, size overflow */
+  THETIS_E_NOMEM = 2,    /* device allocation failed */
+  THETIS_E_BUDGET = 3,   /* request exceeds the server's memory budget */
+  THETIS_E_CUDA = 4,     /* CUDA runtime or kernel error */
+  THETIS_E_TIMEOUT = 5,  /* a bounded device wait ran out */
+  THETIS_E_REPAIR = 6,   /* covering repair impossible: eps >= 1 */
+  THETIS_PENDING = 7,    /* server request not finished yet */
+  THETIS_NOT_CONVERGED = 8 /* informational: epochs ran out before rho <= tol */
+} thetis_status;
+
+typedef enum { THETIS_MEM_HOST = 0, THETIS_MEM_DEVICE = 1 } thetis_mem;
+typedef enum { THETIS_ROW_EQ = 0, THETIS_ROW_GE = 1, THETIS_ROW_LE = 2 } thetis_row_kind;
+typedef enum { THETIS_ROUND_VC = 0, THETIS_ROUND_IS = 1, THETIS_ROUND_MC = 2 } thetis_round_kind;
+typedef enum { THETIS_MODE_COLORED = 0, THETIS_MODE_ASYNC = 1 } thetis_mode;
+
+typedef struct thetis_handle thetis_handle;
+typedef struct thetis_server thetis_server;
+
+/*
+ * General sparse LP in the standard form of Sec. 3.1 (eq. LP), structural
+ * columns only; slacks are appended per GE/LE row.
+ *   m, n          rows and structural columns (n >= 1, m >= 0, both < 2^31)
+ *   csc_ptr[n+1]  int64 column pointers, csc_ptr[0] = 0, non-decreasing
+ *   csc_row[nnz]  int32 row indices in [0, m); no repeated row inside a column
+ *   csc_val[nnz]  coefficients, or NULL for all +1
+ *   b[m], c[n], lo[n], hi[n]   lo <= hi; lo == hi marks a fixed column
+ *   row_kind[m]   thetis_row_kind per row
+ *   block_k, n_blocks, block_first[n_blocks]: simplex blocks of block_k
+ *                 consecutive columns starting at block_first[t]; each block's
+ *                 coordinates stay on the probability simplex (App. E).  A
+ *                 block whose lo == hi everywhere is fixed.  block_k = 1 and
+ *                 n_blocks = 0 when there are none.
+ */
+typedef struct {
+  int64_t m, n;
+  const int64_t* csc_ptr;
+  const int32_t* csc_row;
+  const float* csc_val;
+  const float *b, *c, *lo, *hi;
+  const uint8_t* row_kind;
+  int32_t block_k;
+  int64_t n_blocks;
+  const int64_t* block_first;
+} thetis_problem_desc;
+
+/* Solve parameters (eq. QP, Algorithm 1).
+ *   beta          penalty parameter (> 0)
+ *   epochs        maximum epochs; one epoch = one step of every free coordinate
+ *   tol           stop once rho <= tol at a check (0: run all epochs)
+ *   refresh_every R: every R epochs (and after the last) r = Ax - b is
+ *                 recomputed in FP64 and the FP64 checks run
+ *   step_rule     0: L_j = beta ||a_j||^2 + 1/beta per coordinate (block: max
+ *                 over the block); 1: the global L_max of eq. Lmax
+ *   mode          THETIS_MODE_COLORED (colour classes in order: the iterates
+ *                 equal a serial sweep in that order) or THETIS_MODE_ASYNC
+ *                 (all coordinates at once with atomic residual updates, the
+ *                 asynchronous parallel scheme of Sec. 3.4)
+ *   ubar[m], xbar[n + n_slack]  eq. QP centres, NULL = 0; xbar lists the
+ *                 structural columns then the slacks in row order
+ *   x0[n]         structural starting point (NULL: 0 clipped to the bounds,
+ *                 barycentre for simplex blocks); slacks start at 0
+ *   mem           where ubar / xbar / x0 live */
+typedef struct {
+  double beta;
+  int32_t epochs;
+  double tol;
+  int32_t refresh_every;
+  int32_t step_rule;
+  int32_t mode;
+  const float* ubar;
+  const float* xbar;
+  const float* x0;
+  int32_t mem;
+} thetis_params;
+
+/* Result of a solve; all checks in FP64 on the final iterate.
+ *   rho     max over coordinates of |x_j - Proj(x_j - grad_j / L_j)| with the
+ *           per-coordinate L_j, r recomputed exactly (the stopping residual)
+ *   obj     c^T x;  infeas  ||Ax - b||_inf;  fbeta  f(x) of eq. QP */
+typedef struct {
+  int32_t epochs_run;
+  int32_t converged;
+  int32_t ncolors;
+  double rho, obj, infeas, fbeta;
+  int64_t updates; /* coordinate updates performed (blocks count k) */
+  double solve_ms; /* device time of the solve */
+} thetis_solve_info;
+
+/* Result of a rounding.
+ *   obj        objective of the integral solution in the problem's own sense
+ *              (VC: cover weight, IS: set weight, MC: cut cost)
+ *   repair     eps (VC, Lemma 1), alpha (IS, App. C.3) or 0 (MC)
+ *   best_rep   repetition that won (ties to the lowest)
+ *   near       VC: vertices with |x~ - 1/2| < 1e-4; IS: vertices whose
+ *              Bernoulli draw is within 1e-4 of x~ in the winning rep; MC: 0
+ *   valid      1 if the exact validity check passed */
+typedef struct {
+  double obj;
+  double repair;
+  int32_t best_rep;
+  int64_t near;
+  int32_t valid;
+} thetis_round_info;
+
+/* Library-wide: message of the last failed call on this thread. */
+const char* thetis_last_error(void);
+/* Library-wide: number of kernels this library has launched so far. */
+uint64_t thetis_launch_count(void);
+
+/*
+ * thetis_create -- build the standard form of `desc` on the device, colour
+ * the column-intersection graph (greedy in the order (nnz desc,
+ * splitmix64(seed, unit) desc, unit asc); Jones-Plassmann rounds that give
+ * the same colouring as the sequential greedy) and lay the problem out in
+ * colour order.  Sec. 3.1 eq. LP with the slack forms of App. C.
+ * Errors: THETIS_E_INVALID on malformed input, THETIS_E_NOMEM, THETIS_E_CUDA.
+ * *out owns all device state until thetis_destroy.
+ */
+thetis_status thetis_create(const thetis_problem_desc* desc, int32_t mem, uint64_t seed,
+                            void* stream, thetis_handle** out);
+
+/*
+ * Graph builders (mem applies to all arrays):
+ *  thetis_build_vc: vertex cover LP of Sec. 2 (eq. lp_vertex_cover): min w^T x,
+ *    x_u + x_v >= 1 per edge, 0 <= x <= 1.  Row e: x_u + x_v - s_e = 1.
+ *  thetis_build_is: independent set as set packing (App. B.2): max w^T x,
+ *    x_u + x_v <= 1, 0 <= x <= 1, stored as min -w^T x, row x_u + x_v + s_e = 1.
+ *  thetis_build_mc: multiway cut, linearised form of App. B.3: x_v on the
+ *    k-simplex, z_{e,i} in [0,1] with cost ce_e/2, rows
+ *    z - x_{u,i} + x_{v,i} - s = 0 and z + x_{u,i} - x_{v,i} - s = 0;
+ *    terminals[i] is fixed at the unit vector e_i.  2 <= k <= 32.
+ *  eu[m], ev[m]: edge endpoints in [0, n), eu != ev, no repeated edge.
+ *  w[n]: vertex weights (> 0); ce[m]: edge weights (>= 0).
+ */
+thetis_status thetis_build_vc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
+                              const float* w, int32_t mem, uint64_t seed, void* stream,
+                              thetis_handle** out);
+thetis_status thetis_build_is(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
+                              const float* w, int32_t mem, uint64_t seed, void* stream,
+                              thetis_handle** out);
+thetis_status thetis_build_mc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
+                              const float* ce, int32_t k, const int32_t* terminals, int32_t mem,
+                              uint64_t seed, void* stream, thetis_handle** out);
+
+/* Sizes of a built problem (any pointer may be NULL): rows m, structural
+ * columns n, slack columns (one per GE/LE row), free coordinates (what one
+ * epoch updates; simplex blocks count k), non-zeros of A including the slack
+ * entries, and the number of colours. */
+thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* struct_cols,
+                               int64_t* slack_cols, int64_t* free_coords, int64_t* nnz,
+                               int32_t* ncolors);
+
+/*
+ * thetis_solve -- coordinate descent on eq. QP (Algorithm 1 re-ordered as a
+ * colour-class sweep, or the asynchronous scheme of Sec. 3.4), FP32 iterate
+ * and residual, FP64 refresh of r = Ax - b every refresh_every epochs, FP64
+ * checks (Def. 2 infeasibility, objective, eq. QP value, projected-gradient
+ * step rho).  Continues from the handle's current iterate (set by create, by
+ * x0, or left by a previous solve).  Returns THETIS_OK, THETIS_NOT_CONVERGED
+ * (valid iterate, tol not reached), or an error.  info may be NULL.
+ */
+thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solve_info* info);
+
+/*
+ * thetis_round -- repair + round the current iterate (structural part).
+ *  VC: eps = max_e (1 - x_u - x_v)_+, x~ = min(1, x/(1-eps)) (Lemma
+ *      lem:infeasible:rounded:vc), label = [x~ >= 1/2] (Sec. 2); reps ignored.
+ *      THETIS_E_REPAIR if eps >= 1.
+ *  IS: alpha = max_e (x_u + x_v - 1)_+, x~ = x/(1+alpha) (App. C.3), then
+ *      Algorithm 2 of App. B.2 with theta = 1/k: pick v iff U < x~_v, drop the
+ *      larger-id end of every picked edge; best of `reps` by weight.
+ *  MC: CKR region growing (App. B.3) with radius rho ~ U[0,1) and a random
+ *      terminal order; best of `reps` by cut cost.
+ * Random draws: U(seed, rep, stream, vertex) from splitmix64.
+ * labels_out[n] (uint8, vertex order): VC/IS membership, MC label in [0,k).
+ * out_mem says where labels_out lives.  info may be NULL.
+ */
+thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_t reps,
+                           uint8_t* labels_out, int32_t out_mem, thetis_round_info* info);
+
+/* Copy the structural part of the iterate, original column order, as FP32. */
+thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem);
+/* Copy the slack part of the iterate (one value per GE/LE row, row order). */
+thetis_status thetis_get_slack(thetis_handle* h, float* out, int32_t out_mem);
+/* The colour of every coordinate unit (structural units in column order, then
+ * slack units in row order); fixed columns have no unit.  out[n_units]. */
+thetis_status thetis_get_colors(thetis_handle* h, int32_t* out, int64_t* n_units);
+/* Synchronise the handle's stream (surfaces asynchronous errors). */
+thetis_status thetis_sync(thetis_handle* h);
+thetis_status thetis_destroy(thetis_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THETIS_H */

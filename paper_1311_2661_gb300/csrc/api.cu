@@ -1,0 +1,440 @@
+// C ABI of the library (include/thetis.h).
+#include <cstring>
+#include <new>
+
+#include "problem.cuh"
+
+using namespace thetis;
+
+struct thetis_handle {
+  std::unique_ptr<Problem> P;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int64_t graph_launches = 0;  // kernels per epoch graph replay
+  // key of the captured epoch graph
+  double g_beta = 0;
+  int g_rule = -1, g_mode = -1, g_ub = -1, g_xb = -1;
+  ~thetis_handle() {
+    if (P) {
+      cudaStreamSynchronize(stream);
+      P.reset();
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (own_stream && stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
+  }
+};
+
+namespace {
+
+template <class F>
+thetis_status guard(cudaStream_t s, F&& f) {
+  try {
+    f();
+    return THETIS_OK;
+  } catch (Error& e) {
+    set_error(e.msg);
+    if (e.st == THETIS_E_CUDA || e.st == THETIS_E_NOMEM) {
+      if (s) cudaStreamSynchronize(s);
+      cudaError_t le = cudaGetLastError();
+      if (e.st == THETIS_E_CUDA && le == cudaErrorMemoryAllocation) return THETIS_E_NOMEM;
+    }
+    if (e.st == THETIS_E_CUDA && e.msg.find("out of memory") != std::string::npos) return THETIS_E_NOMEM;
+    return e.st;
+  } catch (std::bad_alloc&) {
+    set_error("host allocation failed");
+    return THETIS_E_NOMEM;
+  } catch (std::exception& e) {
+    set_error(e.what());
+    return THETIS_E_INVALID;
+  }
+}
+
+// Copy n elements to the device if they are on the host; returns a device pointer.
+template <class T>
+const T* to_dev(const T* p, int64_t n, int32_t mem, Arena& tmp, cudaStream_t s) {
+  if (!p) return nullptr;
+  if (mem == THETIS_MEM_DEVICE) return p;
+  TH_CHECK(mem == THETIS_MEM_HOST, THETIS_E_INVALID, "mem must be THETIS_MEM_HOST or THETIS_MEM_DEVICE");
+  T* d = tmp.alloc<T>(n);
+  if (n > 0) TH_CUDA(cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+template <class T>
+void from_dev(T* dst, const T* src, int64_t n, int32_t mem, cudaStream_t s) {
+  if (n <= 0) return;
+  TH_CHECK(mem == THETIS_MEM_HOST || mem == THETIS_MEM_DEVICE, THETIS_E_INVALID, "bad out_mem");
+  TH_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), mem == THETIS_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                        : cudaMemcpyDeviceToDevice, s));
+}
+
+thetis_handle* new_handle(void* stream) {
+  auto* h = new thetis_handle();
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      throw Error{THETIS_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)};
+    }
+    h->own_stream = true;
+  }
+  return h;
+}
+
+template <class T>
+T* keep_copy(Arena& mem, const T* src_dev, int64_t n, cudaStream_t s) {
+  T* d = mem.alloc<T>(n);
+  if (n > 0) TH_CUDA(cudaMemcpyAsync(d, src_dev, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  return d;
+}
+
+void finish_create(thetis_handle* h) {
+  init_iterate(*h->P);
+  TH_CUDA(cudaEventCreate(&h->ev0));
+  TH_CUDA(cudaEventCreate(&h->ev1));
+  TH_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* thetis_last_error(void) { return get_error(); }
+uint64_t thetis_launch_count(void) { return launch_count(); }
+
+thetis_status thetis_create(const thetis_problem_desc* d, int32_t mem, uint64_t seed, void* stream,
+                            thetis_handle** out) {
+  if (!d || !out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  *out = nullptr;
+  thetis_handle* h = nullptr;
+  thetis_status st = guard(nullptr, [&] {
+    TH_CHECK(d->n >= 1 && d->m >= 0, THETIS_E_INVALID, "need n >= 1 and m >= 0");
+    TH_CHECK(d->csc_ptr && d->b && d->c && d->lo && d->hi && d->row_kind, THETIS_E_INVALID, "null array in desc");
+    h = new_handle(stream);
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    int64_t nnz = 0;
+    if (mem == THETIS_MEM_HOST) {
+      nnz = d->csc_ptr[d->n];
+    } else {
+      TH_CUDA(cudaMemcpyAsync(&nnz, d->csc_ptr + d->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+    }
+    TH_CHECK(nnz >= 0, THETIS_E_INVALID, "negative nnz");
+    TH_CHECK(nnz == 0 || d->csc_row, THETIS_E_INVALID, "csc_row is null");
+    RawLP raw;
+    raw.M = d->m;
+    raw.Ns = d->n;
+    raw.nnz = nnz;
+    raw.colptr = const_cast<int64_t*>(to_dev(d->csc_ptr, d->n + 1, mem, tmp, s));
+    raw.rowidx = const_cast<int32_t*>(to_dev(d->csc_row, nnz, mem, tmp, s));
+    raw.val = const_cast<float*>(to_dev(d->csc_val, nnz, mem, tmp, s));
+    raw.b = const_cast<float*>(to_dev(d->b, d->m, mem, tmp, s));
+    raw.c = const_cast<float*>(to_dev(d->c, d->n, mem, tmp, s));
+    raw.lo = const_cast<float*>(to_dev(d->lo, d->n, mem, tmp, s));
+    raw.hi = const_cast<float*>(to_dev(d->hi, d->n, mem, tmp, s));
+    raw.row_kind = const_cast<uint8_t*>(to_dev(d->row_kind, d->m, mem, tmp, s));
+    raw.block_k = d->n_blocks > 0 ? d->block_k : 1;
+    raw.n_blocks = d->n_blocks;
+    TH_CHECK(d->n_blocks == 0 || d->block_first, THETIS_E_INVALID, "block_first is null");
+    raw.block_first = const_cast<int64_t*>(to_dev(d->block_first, d->n_blocks, mem, tmp, s));
+    h->P = build_problem(raw, KIND_GENERAL, seed, s, tmp);
+    finish_create(h);
+  });
+  if (st != THETIS_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return THETIS_OK;
+}
+
+static thetis_status build_graph(int kind, int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
+                                 const float* wv, const float* ce, int32_t k, const int32_t* term, int32_t mem,
+                                 uint64_t seed, void* stream, thetis_handle** out) {
+  if (!out) {
+    set_error("null out");
+    return THETIS_E_INVALID;
+  }
+  *out = nullptr;
+  thetis_handle* h = nullptr;
+  thetis_status st = guard(nullptr, [&] {
+    TH_CHECK(n >= 1 && m >= 0 && n < (int64_t(1) << 31) && m < (int64_t(1) << 31), THETIS_E_INVALID,
+             "need 1 <= n < 2^31 and 0 <= m < 2^31");
+    TH_CHECK(m == 0 || (eu && ev), THETIS_E_INVALID, "null edge array");
+    if (kind == KIND_MC) {
+      TH_CHECK(k >= 2 && k <= 32 && k <= n, THETIS_E_INVALID, "multiway cut needs 2 <= k <= min(32, n)");
+      TH_CHECK(term && (m == 0 || ce), THETIS_E_INVALID, "null terminals or edge weights");
+      TH_CHECK((n + m) * (int64_t)k < (int64_t(1) << 31) && 2 * m * (int64_t)k < (int64_t(1) << 31),
+               THETIS_E_INVALID, "multiway-cut LP too large");
+    } else {
+      TH_CHECK(wv != nullptr, THETIS_E_INVALID, "null vertex weights");
+    }
+    h = new_handle(stream);
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    const int32_t* deu = to_dev(eu, m, mem, tmp, s);
+    const int32_t* dev = to_dev(ev, m, mem, tmp, s);
+    RawLP raw;
+    const float *dw = nullptr, *dce = nullptr;
+    const int32_t* dterm = nullptr;
+    if (kind == KIND_MC) {
+      dce = to_dev(ce, m, mem, tmp, s);
+      dterm = to_dev(term, k, mem, tmp, s);
+      build_mc_raw(n, m, deu, dev, dce, k, dterm, raw, tmp, s);
+    } else {
+      dw = to_dev(wv, n, mem, tmp, s);
+      build_vc_is_raw(kind, n, m, deu, dev, dw, raw, tmp, s);
+    }
+    h->P = build_problem(raw, kind, seed, s, tmp);
+    Problem& P = *h->P;
+    P.nv = n;
+    P.ne = m;
+    P.eu = keep_copy(P.mem, deu, m, s);
+    P.ev = keep_copy(P.mem, dev, m, s);
+    if (kind == KIND_MC) {
+      P.ce = keep_copy(P.mem, dce, m, s);
+      P.term = keep_copy(P.mem, dterm, k, s);
+    } else {
+      P.w = keep_copy(P.mem, dw, n, s);
+    }
+    finish_create(h);
+  });
+  if (st != THETIS_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return THETIS_OK;
+}
+
+thetis_status thetis_build_vc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, const float* w,
+                              int32_t mem, uint64_t seed, void* stream, thetis_handle** out) {
+  return build_graph(KIND_VC, n, m, eu, ev, w, nullptr, 0, nullptr, mem, seed, stream, out);
+}
+thetis_status thetis_build_is(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, const float* w,
+                              int32_t mem, uint64_t seed, void* stream, thetis_handle** out) {
+  return build_graph(KIND_IS, n, m, eu, ev, w, nullptr, 0, nullptr, mem, seed, stream, out);
+}
+thetis_status thetis_build_mc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, const float* ce,
+                              int32_t k, const int32_t* terminals, int32_t mem, uint64_t seed, void* stream,
+                              thetis_handle** out) {
+  return build_graph(KIND_MC, n, m, eu, ev, nullptr, ce, k, terminals, mem, seed, stream, out);
+}
+
+thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* struct_cols, int64_t* slack_cols,
+                               int64_t* free_coords, int64_t* nnz, int32_t* ncolors) {
+  if (!h || !h->P) {
+    set_error("null handle");
+    return THETIS_E_INVALID;
+  }
+  const Problem& P = *h->P;
+  if (rows) *rows = P.M;
+  if (struct_cols) *struct_cols = P.Ns;
+  if (slack_cols) *slack_cols = P.Msl;
+  if (free_coords) *free_coords = P.free_coords;
+  if (nnz) *nnz = P.nnz + P.Msl;
+  if (ncolors) *ncolors = P.ncolors;
+  return THETIS_OK;
+}
+
+thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solve_info* info) {
+  if (!h || !h->P || !p) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  bool converged = false;
+  thetis_status st = guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    TH_CHECK(p->beta > 0 && std::isfinite(p->beta), THETIS_E_INVALID, "beta must be > 0");
+    TH_CHECK(p->epochs >= 0, THETIS_E_INVALID, "epochs must be >= 0");
+    TH_CHECK(p->step_rule == 0 || p->step_rule == 1, THETIS_E_INVALID, "step_rule must be 0 or 1");
+    TH_CHECK(p->mode == THETIS_MODE_COLORED || p->mode == THETIS_MODE_ASYNC, THETIS_E_INVALID, "bad mode");
+    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode};
+    Arena tmp(s);
+    const float* dub = to_dev(p->ubar, P.M, p->mem, tmp, s);
+    const float* dxb = to_dev(p->xbar, P.Ns + P.Msl, p->mem, tmp, s);
+    const float* dx0 = to_dev(p->x0, P.Ns, p->mem, tmp, s);
+    prepare_solve(P, dub, dxb, dx0);
+    const bool ub = dub != nullptr, xb = dxb != nullptr;
+    refresh_only(P);
+    // capture one epoch as a CUDA graph (re-captured when its arguments change)
+    bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
+                  h->g_ub == (int)ub && h->g_xb == (int)xb;
+    if (!key_ok && a.epochs > 0) {
+      if (P.epoch_graph) {
+        cudaGraphExecDestroy(P.epoch_graph);
+        P.epoch_graph = nullptr;
+      }
+      cudaGraph_t g;
+      uint64_t l0 = launch_count();
+      TH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        run_epoch(P, a, ub, xb);
+      } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        throw;
+      }
+      TH_CUDA(cudaStreamEndCapture(s, &g));
+      uint64_t l1 = launch_count();
+      h->graph_launches = (int64_t)(l1 - l0);
+      count_launch((uint64_t)0 - (l1 - l0));  // nothing ran during capture
+      cudaError_t e = cudaGraphInstantiate(&P.epoch_graph, g, 0);
+      cudaGraphDestroy(g);
+      TH_CUDA(e);
+      h->g_beta = a.beta;
+      h->g_rule = a.step_rule;
+      h->g_mode = a.mode;
+      h->g_ub = ub;
+      h->g_xb = xb;
+    }
+    TH_CUDA(cudaEventRecord(h->ev0, s));
+    CheckOut co{};
+    int ep = 0;
+    bool checked_last = false;
+    for (ep = 0; ep < a.epochs;) {
+      TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
+      count_launch((uint64_t)h->graph_launches);
+      ++ep;
+      checked_last = false;
+      if (ep % a.refresh_every == 0 || ep == a.epochs) {
+        refresh_and_check(P, a, ub, xb, co);
+        checked_last = true;
+        if (co.rho <= a.tol) {
+          converged = true;
+          break;
+        }
+      }
+    }
+    if (!checked_last) refresh_and_check(P, a, ub, xb, co);
+    if (a.epochs == 0) converged = co.rho <= a.tol;
+    TH_CUDA(cudaEventRecord(h->ev1, s));
+    TH_CUDA(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    TH_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (info) {
+      info->epochs_run = ep;
+      info->converged = converged ? 1 : 0;
+      info->ncolors = P.ncolors;
+      info->rho = co.rho;
+      info->obj = co.obj;
+      info->infeas = co.infeas;
+      info->fbeta = co.fbeta;
+      info->updates = (int64_t)ep * P.free_coords;
+      info->solve_ms = ms;
+    }
+  });
+  if (st != THETIS_OK) return st;
+  return converged ? THETIS_OK : THETIS_NOT_CONVERGED;
+}
+
+thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_t reps, uint8_t* labels_out,
+                           int32_t out_mem, thetis_round_info* info) {
+  if (!h || !h->P || !labels_out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  RoundOut ro{};
+  thetis_status st = guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    uint8_t* dl = (out_mem == THETIS_MEM_DEVICE) ? labels_out : tmp.alloc<uint8_t>(P.nv);
+    round_problem(P, kind, seed, reps, dl, ro);
+    if (ro.status == THETIS_OK && out_mem != THETIS_MEM_DEVICE) from_dev(labels_out, dl, P.nv, THETIS_MEM_HOST, s);
+    TH_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+      info->obj = ro.obj;
+      info->repair = ro.repair;
+      info->best_rep = ro.best_rep;
+      info->near = ro.near;
+      info->valid = ro.valid;
+    }
+  });
+  if (st != THETIS_OK) return st;
+  if (ro.status != THETIS_OK) {
+    set_error("covering repair impossible: eps >= 1");
+    if (info) info->repair = ro.repair;
+    return (thetis_status)ro.status;
+  }
+  return THETIS_OK;
+}
+
+thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem) {
+  if (!h || !h->P || !out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    Arena tmp(h->stream);
+    float* d = (out_mem == THETIS_MEM_DEVICE) ? out : tmp.alloc<float>(P.Ns);
+    gather_x_orig(P, d);
+    if (out_mem != THETIS_MEM_DEVICE) from_dev(out, d, P.Ns, THETIS_MEM_HOST, h->stream);
+    TH_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+__global__ void k_gather_slack(const float* s, const uint32_t* slack_orig, int64_t Msl, float* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Msl; t += (int64_t)gridDim.x * blockDim.x)
+    out[slack_orig[t]] = s[t];
+}
+
+thetis_status thetis_get_slack(thetis_handle* h, float* out, int32_t out_mem) {
+  if (!h || !h->P || !out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    if (P.Msl == 0) return;
+    Arena tmp(h->stream);
+    float* d = (out_mem == THETIS_MEM_DEVICE) ? out : tmp.alloc<float>(P.Msl);
+    k_gather_slack<<<grid_for(P.Msl, 256), 256, 0, h->stream>>>(P.s, P.slack_orig, P.Msl, d);
+    TH_LAUNCHED();
+    if (out_mem != THETIS_MEM_DEVICE) from_dev(out, d, P.Msl, THETIS_MEM_HOST, h->stream);
+    TH_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+thetis_status thetis_get_colors(thetis_handle* h, int32_t* out, int64_t* n_units) {
+  if (!h || !h->P) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    if (n_units) *n_units = P.U;
+    if (out && P.U > 0) {
+      TH_CUDA(cudaMemcpyAsync(out, P.unit_color, P.U * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+      TH_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  });
+}
+
+thetis_status thetis_sync(thetis_handle* h) {
+  if (!h) {
+    set_error("null handle");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] { TH_CUDA(cudaStreamSynchronize(h->stream)); });
+}
+
+thetis_status thetis_destroy(thetis_handle* h) {
+  if (!h) return THETIS_OK;
+  delete h;
+  return THETIS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1004 @@
+// Building a problem on the device: graph builders (Sec. 2 vertex cover,
+// App. B.2 independent set, App. B.3 multiway cut), the CSR twin, the greedy
+// colouring of the column-intersection graph (Jones-Plassmann rounds, which
+// colour exactly like the sequential greedy in the same total order), and the
+// colour-ordered internal layout.
+#include <algorithm>
+#include <cmath>
+
+#include "problem.cuh"
+
+namespace thetis {
+
+// Thresholds of the per-colour unit classes (structural units by non-zeros).
+constexpr int64_t T_BIG = 2048;  // more: one CTA per unit
+constexpr int64_t T_MED = 24;    // more: one warp per unit; else 8-lane groups
+
+static int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 32 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------------------
+// graph builders
+// ---------------------------------------------------------------------------
+__global__ void k_pairs_from_edges(const int32_t* eu, const int32_t* ev, int64_t m, uint32_t* keys,
+                                   uint32_t* vals) {
+  GSTRIDE(e, m) {
+    keys[e] = (uint32_t)eu[e];
+    vals[e] = (uint32_t)e;
+    keys[m + e] = (uint32_t)ev[e];
+    vals[m + e] = (uint32_t)e;
+  }
+}
+
+__global__ void k_count_keys(const uint32_t* keys, int64_t n, int64_t* cnt) {
+  GSTRIDE(i, n) atomicAdd((unsigned long long*)&cnt[keys[i]], 1ull);
+}
+
+__global__ void k_check_edges(const int32_t* eu, const int32_t* ev, int64_t m, int64_t n, int* err) {
+  GSTRIDE(e, m) {
+    int32_t a = eu[e], b = ev[e];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) atomicExch(err, 1);
+  }
+}
+
+__global__ void k_u32_to_i32(const uint32_t* in, int32_t* out, int64_t n) {
+  GSTRIDE(i, n) out[i] = (int32_t)in[i];
+}
+
+__global__ void k_edge_lp_vectors(int kind, const float* w, int64_t n, int64_t m, float* b, float* c,
+                                  float* lo, float* hi, uint8_t* rk, int* err) {
+  GSTRIDE(i, n > m ? n : m) {
+    if (i < n) {
+      float wv = w[i];
+      if (!(wv > 0.f) || !isfinite(wv)) atomicExch(err, 2);
+      c[i] = (kind == KIND_VC) ? wv : -wv;
+      lo[i] = 0.f;
+      hi[i] = 1.f;
+    }
+    if (i < m) {
+      b[i] = 1.f;
+      rk[i] = (kind == KIND_VC) ? THETIS_ROW_GE : THETIS_ROW_LE;
+    }
+  }
+}
+
+static int read_flag(int* d, cudaStream_t s) {
+  int h = 0;
+  TH_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+// vertex -> incident edges (stable: edges where v = eu in edge order, then v = ev)
+static void incidence(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, int64_t*& ptr,
+                      uint32_t*& edges, Arena& tmp, cudaStream_t s) {
+  uint32_t* keys = tmp.alloc<uint32_t>(2 * m);
+  edges = tmp.alloc<uint32_t>(2 * m);
+  if (m > 0) {
+    k_pairs_from_edges<<<grid_for(m, 256), 256, 0, s>>>(eu, ev, m, keys, edges);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(keys, edges, 2 * m, bits_for(n), tmp, s);
+  ptr = tmp.alloc<int64_t>(n + 1);
+  TH_CUDA(cudaMemsetAsync(ptr, 0, (n + 1) * sizeof(int64_t), s));
+  if (m > 0) {
+    k_count_keys<<<grid_for(2 * m, 256), 256, 0, s>>>(keys, 2 * m, ptr);
+    TH_LAUNCHED();
+  }
+  exclusive_scan_i64(ptr, ptr, n, tmp, s);
+}
+
+void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
+                     const float* d_w, RawLP& raw, Arena& tmp, cudaStream_t s) {
+  int* err = tmp.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (m > 0) {
+    k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(d_eu, d_ev, m, n, err);
+    TH_LAUNCHED();
+  }
+  TH_CHECK(read_flag(err, s) == 0, THETIS_E_INVALID, "edge endpoint out of range or a loop");
+  int64_t* ptr;
+  uint32_t* edges;
+  incidence(n, m, d_eu, d_ev, ptr, edges, tmp, s);
+  raw.M = m;
+  raw.Ns = n;
+  raw.nnz = 2 * m;
+  raw.colptr = ptr;
+  raw.rowidx = tmp.alloc<int32_t>(2 * m);
+  if (m > 0) {
+    k_u32_to_i32<<<grid_for(2 * m, 256), 256, 0, s>>>(edges, raw.rowidx, 2 * m);
+    TH_LAUNCHED();
+  }
+  raw.val = nullptr;
+  raw.b = tmp.alloc<float>(m);
+  raw.c = tmp.alloc<float>(n);
+  raw.lo = tmp.alloc<float>(n);
+  raw.hi = tmp.alloc<float>(n);
+  raw.row_kind = tmp.alloc<uint8_t>(m);
+  k_edge_lp_vectors<<<grid_for(std::max(n, m), 256), 256, 0, s>>>(kind, d_w, n, m, raw.b, raw.c,
+                                                                   raw.lo, raw.hi, raw.row_kind, err);
+  TH_LAUNCHED();
+  TH_CHECK(read_flag(err, s) == 0, THETIS_E_INVALID, "vertex weights must be finite and > 0");
+  raw.block_k = 1;
+  raw.n_blocks = 0;
+  raw.bounds_uniform = true;
+  raw.lo_u = 0.f;
+  raw.hi_u = 1.f;
+  raw.slack_sign_uniform = (kind == KIND_VC) ? -1 : 1;
+}
+
+// Multiway cut: x_{v,i} at v*k+i (2 deg(v) entries), z_{e,i} at n*k+e*k+i.
+__global__ void k_mc_counts(const int64_t* iptr, int64_t n, int64_t m, int32_t k, int64_t* cnt) {
+  GSTRIDE(j, n * k + m * k) {
+    if (j < n * k) {
+      int64_t v = j / k;
+      cnt[j] = 2 * (iptr[v + 1] - iptr[v]);
+    } else {
+      cnt[j] = 2;
+    }
+  }
+}
+
+__global__ void k_mc_fill(const int64_t* iptr, const uint32_t* iedge, const int32_t* eu, int64_t n,
+                          int64_t m, int32_t k, const int64_t* colptr, int32_t* rowidx, float* val) {
+  GSTRIDE(j, n * k + m * k) {
+    int64_t q = colptr[j];
+    if (j < n * k) {
+      int64_t v = j / k;
+      int32_t i = (int32_t)(j % k);
+      for (int64_t t = iptr[v]; t < iptr[v + 1]; ++t) {
+        int64_t e = iedge[t];
+        bool is_u = (eu[e] == v);
+        int64_t rp = 2 * (e * k + i);
+        rowidx[q] = (int32_t)rp;
+        val[q] = is_u ? -1.f : 1.f;
+        rowidx[q + 1] = (int32_t)(rp + 1);
+        val[q + 1] = is_u ? 1.f : -1.f;
+        q += 2;
+      }
+    } else {
+      int64_t z = j - n * k;  // e*k + i
+      rowidx[q] = (int32_t)(2 * z);
+      val[q] = 1.f;
+      rowidx[q + 1] = (int32_t)(2 * z + 1);
+      val[q + 1] = 1.f;
+    }
+  }
+}
+
+__global__ void k_mc_vectors(const float* ce, const int32_t* term, int64_t n, int64_t m, int32_t k,
+                             float* b, float* c, float* lo, float* hi, uint8_t* rk, int64_t* bfirst,
+                             int* err) {
+  int64_t Ns = n * k + m * k;
+  GSTRIDE(i, Ns > 2 * m * k ? Ns : 2 * m * k) {
+    if (i < Ns) {
+      lo[i] = 0.f;
+      hi[i] = 1.f;
+      if (i < n * k) {
+        c[i] = 0.f;
+      } else {
+        float w = ce[(i - n * k) / k];
+        if (!(w >= 0.f) || !isfinite(w)) atomicExch(err, 2);
+        c[i] = 0.5f * w;
+      }
+    }
+    if (i < 2 * m * k) {
+      b[i] = 0.f;
+      rk[i] = THETIS_ROW_GE;
+    }
+    if (i < n) bfirst[i] = i * k;
+  }
+}
+
+__global__ void k_mc_terminals(const int32_t* term, int64_t n, int32_t k, float* lo, float* hi, int* err) {
+  int t = threadIdx.x;
+  if (t >= k) return;
+  int64_t v = term[t];
+  if (v < 0 || v >= n) {
+    atomicExch(err, 3);
+    return;
+  }
+  for (int i = 0; i < k; ++i) {
+    float e = (i == t) ? 1.f : 0.f;
+    lo[v * k + i] = e;
+    hi[v * k + i] = e;
+  }
+  for (int q = 0; q < t; ++q)
+    if (term[q] == v) atomicExch(err, 4);
+}
+
+void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
+                  const float* d_ce, int32_t k, const int32_t* d_term, RawLP& raw, Arena& tmp,
+                  cudaStream_t s) {
+  int* err = tmp.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (m > 0) {
+    k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(d_eu, d_ev, m, n, err);
+    TH_LAUNCHED();
+  }
+  TH_CHECK(read_flag(err, s) == 0, THETIS_E_INVALID, "edge endpoint out of range or a loop");
+  int64_t* iptr;
+  uint32_t* iedge;
+  incidence(n, m, d_eu, d_ev, iptr, iedge, tmp, s);
+  int64_t Ns = n * k + m * k;
+  raw.M = 2 * m * k;
+  raw.Ns = Ns;
+  raw.colptr = tmp.alloc<int64_t>(Ns + 1);
+  k_mc_counts<<<grid_for(Ns, 256), 256, 0, s>>>(iptr, n, m, k, raw.colptr);
+  TH_LAUNCHED();
+  exclusive_scan_i64(raw.colptr, raw.colptr, Ns, tmp, s);
+  raw.nnz = 4 * m * k + 2 * m * k;
+  raw.rowidx = tmp.alloc<int32_t>(raw.nnz);
+  raw.val = tmp.alloc<float>(raw.nnz);
+  k_mc_fill<<<grid_for(Ns, 256), 256, 0, s>>>(iptr, iedge, d_eu, n, m, k, raw.colptr, raw.rowidx, raw.val);
+  TH_LAUNCHED();
+  raw.b = tmp.alloc<float>(raw.M);
+  raw.c = tmp.alloc<float>(Ns);
+  raw.lo = tmp.alloc<float>(Ns);
+  raw.hi = tmp.alloc<float>(Ns);
+  raw.row_kind = tmp.alloc<uint8_t>(raw.M);
+  raw.block_first = tmp.alloc<int64_t>(n);
+  k_mc_vectors<<<grid_for(std::max(Ns, 2 * m * k), 256), 256, 0, s>>>(
+      d_ce, d_term, n, m, k, raw.b, raw.c, raw.lo, raw.hi, raw.row_kind, raw.block_first, err);
+  TH_LAUNCHED();
+  k_mc_terminals<<<1, 32, 0, s>>>(d_term, n, k, raw.lo, raw.hi, err);
+  TH_LAUNCHED();
+  int f = read_flag(err, s);
+  TH_CHECK(f != 2, THETIS_E_INVALID, "edge weights must be finite and >= 0");
+  TH_CHECK(f != 3, THETIS_E_INVALID, "terminal out of range");
+  TH_CHECK(f != 4, THETIS_E_INVALID, "terminals must be distinct");
+  raw.block_k = k;
+  raw.n_blocks = n;
+  raw.bounds_uniform = false;  // terminal blocks are fixed
+  raw.slack_sign_uniform = -1;
+}
+
+// ---------------------------------------------------------------------------
+// general layout
+// ---------------------------------------------------------------------------
+__global__ void k_validate(const int64_t* colptr, const int32_t* rowidx, const float* val,
+                           const float* lo, const float* hi, const uint8_t* rk, int64_t Ns,
+                           int64_t M, int64_t nnz, int* err, int* notpm1) {
+  GSTRIDE(j, Ns) {
+    if (colptr[j + 1] < colptr[j]) atomicExch(err, 1);
+    if (!(lo[j] <= hi[j])) atomicExch(err, 2);
+  }
+  GSTRIDE(p, nnz) {
+    int32_t r = rowidx[p];
+    if (r < 0 || r >= M) atomicExch(err, 3);
+    if (val) {
+      float v = val[p];
+      if (!isfinite(v)) atomicExch(err, 4);
+      if (v != 1.f && v != -1.f) atomicExch(notpm1, 1);
+    }
+  }
+  GSTRIDE(i, M) {
+    if (rk[i] > 2) atomicExch(err, 5);
+  }
+}
+
+__global__ void k_block_claim(const int64_t* bfirst, int64_t nb, int32_t k, int64_t Ns, int32_t* blk,
+                              int* err) {
+  GSTRIDE(t, nb) {
+    int64_t f = bfirst[t];
+    if (f < 0 || f + k > Ns) {
+      atomicExch(err, 6);
+      continue;
+    }
+    for (int q = 0; q < k; ++q)
+      if (atomicCAS(&blk[f + q], -1, (int32_t)t) != -1) atomicExch(err, 7);
+  }
+}
+
+// Per structural column: is it the first column of a free unit? is it fixed?
+__global__ void k_unit_flags(const int32_t* blk, const int64_t* bfirst, int32_t k, const float* lo,
+                             const float* hi, int64_t Ns, int64_t* start_flag, int64_t* fixed_flag) {
+  GSTRIDE(j, Ns) {
+    int32_t t = blk ? blk[j] : -1;
+    bool st = false, fx = false;
+    if (t < 0) {
+      fx = !(lo[j] < hi[j]);
+      st = !fx;
+    } else {
+      int64_t f = bfirst[t];
+      bool bfixed = true;
+      for (int q = 0; q < k; ++q)
+        if (lo[f + q] < hi[f + q]) bfixed = false;
+      fx = bfixed;
+      st = (j == f) && !bfixed;
+    }
+    start_flag[j] = st ? 1 : 0;
+    fixed_flag[j] = fx ? 1 : 0;
+  }
+}
+
+// unit_of_col, unit first column, unit length
+__global__ void k_unit_ids(const int32_t* blk, const int64_t* bfirst, int32_t k, int64_t Ns,
+                           const int64_t* start_scan, const int64_t* fixed_flag, int64_t* unit_of_col,
+                           int64_t* ufirst, int32_t* ulen) {
+  GSTRIDE(j, Ns) {
+    if (fixed_flag[j]) {
+      unit_of_col[j] = -1;
+      continue;
+    }
+    int32_t t = blk ? blk[j] : -1;
+    int64_t f = (t < 0) ? j : bfirst[t];
+    int64_t u = start_scan[f];
+    unit_of_col[j] = u;
+    if (j == f) {
+      ufirst[u] = f;
+      ulen[u] = (t < 0) ? 1 : k;
+    }
+  }
+}
+
+__global__ void k_slack_flags(const uint8_t* rk, int64_t M, int64_t* has) {
+  GSTRIDE(i, M) has[i] = (rk[i] != THETIS_ROW_EQ) ? 1 : 0;
+}
+
+// (row, p) pairs for the CSC -> CSR transpose
+__global__ void k_row_pairs(const int32_t* rowidx, int64_t nnz, uint32_t* keys, uint32_t* vals) {
+  GSTRIDE(p, nnz) {
+    keys[p] = (uint32_t)rowidx[p];
+    vals[p] = (uint32_t)p;
+  }
+}
+
+__device__ __forceinline__ int64_t upper_col(const int64_t* colptr, int64_t Ns, int64_t p) {
+  // column j with colptr[j] <= p < colptr[j+1]
+  int64_t lo = 0, hi = Ns;  // invariant colptr[lo] <= p < colptr[hi]
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (colptr[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_col_of_p(const int64_t* colptr, int64_t Ns, int64_t nnz, uint32_t* colof) {
+  GSTRIDE(p, nnz) colof[p] = (uint32_t)upper_col(colptr, Ns, p);
+}
+
+__global__ void k_count_rows(const int32_t* rowidx, int64_t nnz, int64_t* cnt) {
+  GSTRIDE(p, nnz) atomicAdd((unsigned long long*)&cnt[rowidx[p]], 1ull);
+}
+
+// csr_p: positions p sorted by row (stable); check for a repeated (row, col)
+__global__ void k_csr_dupcheck(const int64_t* rowptr, const uint32_t* csr_p, const uint32_t* colof,
+                               int64_t M, int* err) {
+  GSTRIDE(i, M) {
+    for (int64_t q = rowptr[i] + 1; q < rowptr[i + 1]; ++q)
+      if (colof[csr_p[q]] == colof[csr_p[q - 1]]) atomicExch(err, 8);
+  }
+}
+
+__global__ void k_unit_keys(const int64_t* colptr, const int64_t* ufirst, const int32_t* ulen, int64_t Us,
+                            int64_t U, uint64_t seed, int64_t* unnz, uint64_t* uh) {
+  GSTRIDE(u, U) {
+    if (u < Us) {
+      int64_t f = ufirst[u];
+      unnz[u] = colptr[f + ulen[u]] - colptr[f];
+    } else {
+      unnz[u] = 1;
+    }
+    uh[u] = sm64_at(seed, (uint64_t)u);
+  }
+}
+
+struct JPView {
+  const int64_t* colptr;
+  const int32_t* rowidx;
+  const int64_t* rowptr;
+  const uint32_t* csr_p;
+  const uint32_t* colof;
+  const int64_t* unit_of_col;
+  const int64_t* slack_unit;  // per row: unit id or -1
+  const int64_t* ufirst;
+  const int32_t* ulen;
+  const int64_t* unnz;
+  const uint64_t* uh;
+  int64_t Us;
+  const int64_t* slack_row;   // slack unit s -> row
+};
+
+__device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
+  int64_t na = V.unnz[a], nb = V.unnz[b];
+  if (na != nb) return na > nb;
+  uint64_t ha = V.uh[a], hb = V.uh[b];
+  if (ha != hb) return ha > hb;
+  return a < b;
+}
+
+// Visit the conflicting units of unit u, lane-strided; f(w) for every neighbour occurrence.
+template <class F>
+__device__ __forceinline__ void for_neighbours(const JPView& V, int64_t u, int lane, F f) {
+  if (u < V.Us) {
+    int64_t f0 = V.ufirst[u];
+    int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      int64_t i = V.rowidx[p];
+      for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
+        int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
+        if (w >= 0 && w != u) f(w);
+      }
+      int64_t sw = V.slack_unit[i];
+      if (sw >= 0) f(sw);
+    }
+  } else {
+    int64_t i = V.slack_row[u - V.Us];
+    int64_t q0 = V.rowptr[i], q1 = V.rowptr[i + 1];
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
+      if (w >= 0) f(w);
+    }
+  }
+}
+
+__global__ void k_jp_round(JPView V, const uint32_t* work, const int64_t* nwork, uint32_t* next,
+                           int64_t* nnext, int32_t* color) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t nw = *nwork;
+  for (int64_t t = warp; t < nw; t += nwarps) {
+    int64_t u = work[t];
+    bool blocked = false;
+    for_neighbours(V, u, lane, [&](int64_t w) {
+      if (!blocked && color[w] < 0 && higher(V, w, u)) blocked = true;
+    });
+    if (__any_sync(0xffffffffu, blocked)) {
+      if (lane == 0) next[atomicAdd((unsigned long long*)nnext, 1ull)] = (uint32_t)u;
+      continue;
+    }
+    int base = 0;
+    int chosen = -1;
+    while (chosen < 0) {
+      unsigned long long mask = 0;
+      for_neighbours(V, u, lane, [&](int64_t w) {
+        int cw = color[w];
+        if (cw >= base && cw < base + 64) mask |= 1ull << (cw - base);
+      });
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+      if (~mask) chosen = base + __ffsll((long long)~mask) - 1;
+      base += 64;
+    }
+    if (lane == 0) color[u] = chosen;
+  }
+}
+
+__global__ void k_slack_units(const int64_t* has_scan, const int64_t* has, int64_t M, int64_t Us,
+                              int64_t* slack_unit, int64_t* slack_row) {
+  GSTRIDE(i, M) {
+    if (has[i]) {
+      int64_t s = has_scan[i];
+      slack_unit[i] = Us + s;
+      slack_row[s] = i;
+    } else {
+      slack_unit[i] = -1;
+    }
+  }
+}
+
+__global__ void k_max_i32(const int32_t* a, int64_t n, int* out) {
+  int m = -1;
+  GSTRIDE(i, n) m = max(m, a[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// sort keys for structural units: colour * 4 + class
+__global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const int64_t* unnz, int64_t Us,
+                              uint32_t* keys, uint32_t* vals, int64_t* cnt) {
+  GSTRIDE(u, Us) {
+    int cls;
+    if (ulen[u] > 1) cls = UC_BLOCK;
+    else if (unnz[u] > T_BIG) cls = UC_BIG;
+    else if (unnz[u] > T_MED) cls = UC_MED;
+    else cls = UC_SMALL;
+    uint32_t key = (uint32_t)color[u] * UC_COUNT + cls;
+    keys[u] = key;
+    vals[u] = (uint32_t)u;
+    atomicAdd((unsigned long long*)&cnt[key], 1ull);
+  }
+}
+
+__global__ void k_slack_keys(const int32_t* color, int64_t Us, int64_t Msl, const int64_t* slack_row,
+                             uint32_t* keys, uint32_t* vals, int64_t* cnt) {
+  GSTRIDE(s, Msl) {
+    uint32_t c = (uint32_t)color[Us + s];
+    keys[s] = c;
+    vals[s] = (uint32_t)slack_row[s];
+    atomicAdd((unsigned long long*)&cnt[c], 1ull);
+  }
+}
+
+__global__ void k_pos_len(const uint32_t* unit_of_pos, const int32_t* ulen, int64_t Us, int64_t* len) {
+  GSTRIDE(p, Us) len[p] = ulen[unit_of_pos[p]];
+}
+
+__global__ void k_col_maps_free(const uint32_t* unit_of_pos, const int64_t* ufirst, const int32_t* ulen,
+                                const int64_t* cstart, int64_t Us, uint32_t* col_of_orig,
+                                uint32_t* orig_of_col) {
+  GSTRIDE(p, Us) {
+    int64_t u = unit_of_pos[p];
+    int64_t f = ufirst[u];
+    for (int q = 0; q < ulen[u]; ++q) {
+      col_of_orig[f + q] = (uint32_t)(cstart[p] + q);
+      orig_of_col[cstart[p] + q] = (uint32_t)(f + q);
+    }
+  }
+}
+
+__global__ void k_col_maps_fixed(const int64_t* fixed_flag, const int64_t* fixed_scan, int64_t Ns,
+                                 int64_t Nfree, uint32_t* col_of_orig, uint32_t* orig_of_col) {
+  GSTRIDE(j, Ns) {
+    if (fixed_flag[j]) {
+      int64_t jj = Nfree + fixed_scan[j];
+      col_of_orig[j] = (uint32_t)jj;
+      orig_of_col[jj] = (uint32_t)j;
+    }
+  }
+}
+
+__global__ void k_row_maps(const uint32_t* slack_rows_sorted, int64_t Msl, const int64_t* has,
+                           const int64_t* has_scan, int64_t M, uint32_t* row_of_orig, uint32_t* orig_of_row,
+                           uint32_t* slack_orig) {
+  GSTRIDE(t, Msl) {
+    uint32_t i = slack_rows_sorted[t];
+    row_of_orig[i] = (uint32_t)t;
+    orig_of_row[t] = i;
+    slack_orig[t] = (uint32_t)has_scan[i];
+  }
+  GSTRIDE(i, M) {
+    if (!has[i]) {
+      int64_t t = Msl + (i - has_scan[i]);
+      row_of_orig[i] = (uint32_t)t;
+      orig_of_row[t] = (uint32_t)i;
+    }
+  }
+}
+
+__global__ void k_int_col_counts(const uint32_t* orig_of_col, const int64_t* colptr, int64_t N, int64_t* cnt) {
+  GSTRIDE(j, N) {
+    int64_t o = orig_of_col[j];
+    cnt[j] = colptr[o + 1] - colptr[o];
+  }
+}
+
+// one warp per internal column
+__global__ void k_int_csc_fill(const uint32_t* orig_of_col, const int64_t* ocolptr, const int32_t* orow,
+                               const float* oval, const uint32_t* row_of_orig, const int64_t* icolptr,
+                               int64_t N, bool keep_val, uint32_t* irow, float* ival, float* csq) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < N; j += nwarps) {
+    int64_t o = orig_of_col[j];
+    int64_t p0 = ocolptr[o], p1 = ocolptr[o + 1], q0 = icolptr[j];
+    float sq = 0.f;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      float v = oval ? oval[p] : 1.f;
+      uint32_t r = row_of_orig[orow[p]];
+      if (keep_val) {
+        irow[q0 + (p - p0)] = r;
+        ival[q0 + (p - p0)] = v;
+      } else {
+        irow[q0 + (p - p0)] = r | (v < 0.f ? NEG_BIT : 0u);
+      }
+      sq += v * v;
+    }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
+    if (csq && lane == 0) csq[j] = sq;
+  }
+}
+
+__global__ void k_int_row_counts(const uint32_t* orig_of_row, const int64_t* orowptr, int64_t M, int64_t* cnt) {
+  GSTRIDE(i, M) {
+    int64_t o = orig_of_row[i];
+    cnt[i] = orowptr[o + 1] - orowptr[o];
+  }
+}
+
+__global__ void k_int_csr_fill(const uint32_t* orig_of_row, const int64_t* orowptr, const uint32_t* csr_p,
+                               const uint32_t* colof, const float* oval, const uint32_t* col_of_orig,
+                               const int64_t* irowptr, int64_t M, bool keep_val, uint32_t* icol, float* ival) {
+  GSTRIDE(i, M) {
+    int64_t o = orig_of_row[i];
+    int64_t q0 = irowptr[i];
+    for (int64_t q = orowptr[o]; q < orowptr[o + 1]; ++q) {
+      uint32_t p = csr_p[q];
+      float v = oval ? oval[p] : 1.f;
+      uint32_t jc = col_of_orig[colof[p]];
+      if (keep_val) {
+        icol[q0] = jc;
+        ival[q0] = v;
+      } else {
+        icol[q0] = jc | (v < 0.f ? NEG_BIT : 0u);
+      }
+      ++q0;
+    }
+  }
+}
+
+__global__ void k_col_vectors(const uint32_t* orig_of_col, const float* oc, const float* olo, const float* ohi,
+                              int64_t N, bool per_col_bounds, float* c, float* lo, float* hi) {
+  GSTRIDE(j, N) {
+    int64_t o = orig_of_col[j];
+    c[j] = oc[o];
+    if (per_col_bounds) {
+      lo[j] = olo[o];
+      hi[j] = ohi[o];
+    }
+  }
+}
+
+__global__ void k_row_vectors(const uint32_t* orig_of_row, const float* ob, const uint8_t* rk, int64_t M,
+                              float* b, int8_t* sig) {
+  GSTRIDE(i, M) {
+    int64_t o = orig_of_row[i];
+    b[i] = ob[o];
+    uint8_t k = rk[o];
+    sig[i] = (k == THETIS_ROW_GE) ? -1 : (k == THETIS_ROW_LE ? 1 : 0);
+  }
+}
+
+__global__ void k_unit_color_copy(const int32_t* color, int64_t U, int32_t* out) {
+  GSTRIDE(u, U) out[u] = color[u];
+}
+
+__global__ void k_max_sq_free(const int64_t* colptr, const float* csq, int64_t Nfree, double* out) {
+  double m = 0.0;
+  GSTRIDE(j, Nfree) {
+    double v = csq ? (double)csq[j] : (double)(colptr[j + 1] - colptr[j]);
+    m = fmax(m, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_max_unit_nnz(const int64_t* unnz, int64_t U, unsigned long long* out) {
+  unsigned long long m = 0;
+  GSTRIDE(u, U) m = max(m, (unsigned long long)unnz[u]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cudaStream_t s, Arena& tmp) {
+  auto Pp = std::make_unique<Problem>(s);
+  Problem& P = *Pp;
+  const int64_t M = raw.M, Ns = raw.Ns, nnz = raw.nnz;
+  TH_CHECK(Ns >= 1 && M >= 0 && Ns < (int64_t(1) << 31) - 1 && M < (int64_t(1) << 31) - 1 &&
+               nnz < (int64_t(1) << 32) - 1,
+           THETIS_E_INVALID, "problem too large or empty");
+  P.kind = kind;
+  P.M = M;
+  P.Ns = Ns;
+  P.nnz = nnz;
+  P.k = raw.block_k;
+
+  // -- validation --------------------------------------------------------
+  int* err = tmp.alloc<int>(2);
+  TH_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+  k_validate<<<grid_for(std::max(std::max(Ns, M), nnz), 256), 256, 0, s>>>(
+      raw.colptr, raw.rowidx, raw.val, raw.lo, raw.hi, raw.row_kind, Ns, M, nnz, err, err + 1);
+  TH_LAUNCHED();
+  int64_t* d_tmp64 = tmp.alloc<int64_t>(2);
+  TH_CUDA(cudaMemcpyAsync(d_tmp64, raw.colptr, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  TH_CUDA(cudaMemcpyAsync(d_tmp64 + 1, raw.colptr + Ns, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  int64_t ends[2];
+  int flags[2];
+  TH_CUDA(cudaMemcpyAsync(ends, d_tmp64, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(flags, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  TH_CHECK(ends[0] == 0 && ends[1] == nnz, THETIS_E_INVALID, "csc_ptr must start at 0 and end at nnz");
+  TH_CHECK(flags[0] != 1, THETIS_E_INVALID, "csc_ptr is not non-decreasing");
+  TH_CHECK(flags[0] != 2, THETIS_E_INVALID, "lo > hi (or NaN) in a bound");
+  TH_CHECK(flags[0] != 3, THETIS_E_INVALID, "row index out of range");
+  TH_CHECK(flags[0] != 4, THETIS_E_INVALID, "non-finite coefficient");
+  TH_CHECK(flags[0] != 5, THETIS_E_INVALID, "invalid row kind");
+  P.has_val = (raw.val != nullptr) && flags[1];
+  P.bounds_uniform = raw.bounds_uniform;
+  P.lo_u = raw.lo_u;
+  P.hi_u = raw.hi_u;
+  P.slack_sign_uniform = raw.slack_sign_uniform;
+
+  // -- units ---------------------------------------------------------------
+  int32_t* blk = nullptr;
+  if (raw.n_blocks > 0) {
+    TH_CHECK(raw.block_k >= 2 && raw.block_k <= 32, THETIS_E_INVALID, "block_k must be in [2, 32]");
+    blk = tmp.alloc<int32_t>(Ns);
+    TH_CUDA(cudaMemsetAsync(blk, 0xff, Ns * sizeof(int32_t), s));
+    k_block_claim<<<grid_for(raw.n_blocks, 256), 256, 0, s>>>(raw.block_first, raw.n_blocks, raw.block_k, Ns, blk, err);
+    TH_LAUNCHED();
+    int f = read_flag(err, s);
+    TH_CHECK(f != 6, THETIS_E_INVALID, "simplex block out of range");
+    TH_CHECK(f != 7, THETIS_E_INVALID, "simplex blocks overlap");
+  } else {
+    P.k = 1;
+  }
+  int64_t* start_flag = tmp.alloc<int64_t>(Ns + 1);
+  int64_t* fixed_flag = tmp.alloc<int64_t>(Ns + 1);
+  k_unit_flags<<<grid_for(Ns, 256), 256, 0, s>>>(blk, raw.block_first, raw.block_k, raw.lo, raw.hi, Ns,
+                                                 start_flag, fixed_flag);
+  TH_LAUNCHED();
+  int64_t* start_scan = tmp.alloc<int64_t>(Ns + 1);
+  int64_t* fixed_scan = tmp.alloc<int64_t>(Ns + 1);
+  exclusive_scan_i64(start_flag, start_scan, Ns, tmp, s);
+  exclusive_scan_i64(fixed_flag, fixed_scan, Ns, tmp, s);
+  int64_t* has = tmp.alloc<int64_t>(M + 1);
+  int64_t* has_scan = tmp.alloc<int64_t>(M + 1);
+  if (M > 0) {
+    k_slack_flags<<<grid_for(M, 256), 256, 0, s>>>(raw.row_kind, M, has);
+    TH_LAUNCHED();
+  }
+  exclusive_scan_i64(has, has_scan, M, tmp, s);
+  int64_t cnts[3];
+  TH_CUDA(cudaMemcpyAsync(&cnts[0], start_scan + Ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(&cnts[1], fixed_scan + Ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(&cnts[2], has_scan + M, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  const int64_t Us = cnts[0], Nfix = cnts[1], Msl = cnts[2];
+  const int64_t U = Us + Msl;
+  P.Us = Us;
+  P.Nfix = Nfix;
+  P.Nfree = Ns - Nfix;
+  P.Msl = Msl;
+  P.U = U;
+  P.free_coords = P.Nfree + Msl;
+  TH_CHECK(U < (int64_t(1) << 32) - 1, THETIS_E_INVALID, "too many coordinate units");
+
+  int64_t* unit_of_col = tmp.alloc<int64_t>(Ns);
+  int64_t* ufirst = tmp.alloc<int64_t>(Us + 1);
+  int32_t* ulen = tmp.alloc<int32_t>(Us + 1);
+  k_unit_ids<<<grid_for(Ns, 256), 256, 0, s>>>(blk, raw.block_first, raw.block_k, Ns, start_scan, fixed_flag,
+                                               unit_of_col, ufirst, ulen);
+  TH_LAUNCHED();
+  int64_t* slack_unit = tmp.alloc<int64_t>(M + 1);
+  int64_t* slack_row = tmp.alloc<int64_t>(Msl + 1);
+  if (M > 0) {
+    k_slack_units<<<grid_for(M, 256), 256, 0, s>>>(has_scan, has, M, Us, slack_unit, slack_row);
+    TH_LAUNCHED();
+  }
+
+  // -- CSR transpose (stable by row, columns ascending inside a row) -------
+  uint32_t* rkeys = tmp.alloc<uint32_t>(nnz);
+  uint32_t* csr_p = tmp.alloc<uint32_t>(nnz);
+  if (nnz > 0) {
+    k_row_pairs<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, nnz, rkeys, csr_p);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(rkeys, csr_p, nnz, bits_for(M), tmp, s);
+  int64_t* orowptr = tmp.alloc<int64_t>(M + 1);
+  TH_CUDA(cudaMemsetAsync(orowptr, 0, (M + 1) * sizeof(int64_t), s));
+  uint32_t* colof = tmp.alloc<uint32_t>(nnz);
+  if (nnz > 0) {
+    k_count_rows<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, nnz, orowptr);
+    TH_LAUNCHED();
+    k_col_of_p<<<grid_for(nnz, 256), 256, 0, s>>>(raw.colptr, Ns, nnz, colof);
+    TH_LAUNCHED();
+  }
+  exclusive_scan_i64(orowptr, orowptr, M, tmp, s);
+  if (M > 0) {
+    k_csr_dupcheck<<<grid_for(M, 256), 256, 0, s>>>(orowptr, csr_p, colof, M, err);
+    TH_LAUNCHED();
+    TH_CHECK(read_flag(err, s) != 8, THETIS_E_INVALID, "repeated row index inside a column");
+  }
+
+  // -- colouring (Jones-Plassmann, first fit, fixed total order) -----------
+  int64_t* unnz = tmp.alloc<int64_t>(U + 1);
+  uint64_t* uh = tmp.alloc<uint64_t>(U + 1);
+  k_unit_keys<<<grid_for(U, 256), 256, 0, s>>>(raw.colptr, ufirst, ulen, Us, U, seed, unnz, uh);
+  TH_LAUNCHED();
+  int32_t* color = tmp.alloc<int32_t>(U + 1);
+  TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));
+  uint32_t* wa = tmp.alloc<uint32_t>(U + 1);
+  uint32_t* wb = tmp.alloc<uint32_t>(U + 1);
+  int64_t* cnt2 = tmp.alloc<int64_t>(2);
+  fill_iota_u32(wa, U, s);
+  TH_CUDA(cudaMemcpyAsync(cnt2, &U, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  JPView V{raw.colptr, raw.rowidx, orowptr, csr_p, colof, unit_of_col, slack_unit, ufirst, ulen, unnz, uh, Us, slack_row};
+  {
+    int64_t* na = cnt2;
+    int64_t* nb = cnt2 + 1;
+    int64_t left = U;
+    int64_t rounds = 0;
+    const int jp_grid = 152 * 16;
+    while (left > 0) {
+      for (int q = 0; q < 8; ++q) {
+        TH_CUDA(cudaMemsetAsync(nb, 0, sizeof(int64_t), s));
+        k_jp_round<<<jp_grid, 256, 0, s>>>(V, wa, na, wb, nb, color);
+        TH_LAUNCHED();
+        std::swap(wa, wb);
+        std::swap(na, nb);
+        ++rounds;
+      }
+      TH_CUDA(cudaMemcpyAsync(&left, na, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+      TH_CHECK(rounds <= U + 16, THETIS_E_CUDA, "colouring did not finish");
+    }
+  }
+  int* dmax = tmp.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(dmax, 0xff, sizeof(int), s));
+  k_max_i32<<<grid_for(U, 256), 256, 0, s>>>(color, U, dmax);
+  TH_LAUNCHED();
+  int maxc = read_flag(dmax, s);
+  const int32_t C = (U > 0) ? maxc + 1 : 0;
+  P.ncolors = C;
+  P.unit_color = P.mem.alloc<int32_t>(U);
+  if (U > 0) {
+    k_unit_color_copy<<<grid_for(U, 256), 256, 0, s>>>(color, U, P.unit_color);
+    TH_LAUNCHED();
+  }
+
+  // -- colour order --------------------------------------------------------
+  uint32_t* skeys = tmp.alloc<uint32_t>(Us + 1);
+  uint32_t* unit_of_pos = P.mem.alloc<uint32_t>(Us + 1);
+  int64_t* ccnt = tmp.alloc<int64_t>((int64_t)C * UC_COUNT + 1);
+  TH_CUDA(cudaMemsetAsync(ccnt, 0, ((int64_t)C * UC_COUNT + 1) * sizeof(int64_t), s));
+  if (Us > 0) {
+    k_struct_keys<<<grid_for(Us, 256), 256, 0, s>>>(color, ulen, unnz, Us, skeys, unit_of_pos, ccnt);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(skeys, unit_of_pos, Us, bits_for((int64_t)C * UC_COUNT + 1), tmp, s);
+  P.unit_of_pos = unit_of_pos;
+  uint32_t* slkeys = tmp.alloc<uint32_t>(Msl + 1);
+  uint32_t* slrows = tmp.alloc<uint32_t>(Msl + 1);
+  int64_t* scnt = tmp.alloc<int64_t>(C + 1);
+  TH_CUDA(cudaMemsetAsync(scnt, 0, (C + 1) * sizeof(int64_t), s));
+  if (Msl > 0) {
+    k_slack_keys<<<grid_for(Msl, 256), 256, 0, s>>>(color, Us, Msl, slack_row, slkeys, slrows, scnt);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(slkeys, slrows, Msl, bits_for(C + 1), tmp, s);
+  std::vector<int64_t> hc((size_t)C * UC_COUNT + 1), hs((size_t)C + 1);
+  TH_CUDA(cudaMemcpyAsync(hc.data(), ccnt, hc.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hs.data(), scnt, hs.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+
+  // internal columns
+  int64_t* plen = tmp.alloc<int64_t>(Us + 1);
+  int64_t* cstart = tmp.alloc<int64_t>(Us + 1);
+  if (Us > 0) {
+    k_pos_len<<<grid_for(Us, 256), 256, 0, s>>>(unit_of_pos, ulen, Us, plen);
+    TH_LAUNCHED();
+  }
+  exclusive_scan_i64(plen, cstart, Us, tmp, s);
+  P.col_of_orig = P.mem.alloc<uint32_t>(Ns);
+  uint32_t* orig_of_col = tmp.alloc<uint32_t>(Ns);
+  if (Us > 0) {
+    k_col_maps_free<<<grid_for(Us, 256), 256, 0, s>>>(unit_of_pos, ufirst, ulen, cstart, Us, P.col_of_orig, orig_of_col);
+    TH_LAUNCHED();
+  }
+  k_col_maps_fixed<<<grid_for(Ns, 256), 256, 0, s>>>(fixed_flag, fixed_scan, Ns, P.Nfree, P.col_of_orig, orig_of_col);
+  TH_LAUNCHED();
+  // internal rows
+  P.row_of_orig = P.mem.alloc<uint32_t>(M);
+  P.orig_of_row = P.mem.alloc<uint32_t>(M);
+  P.slack_orig = P.mem.alloc<uint32_t>(Msl);
+  if (M > 0) {
+    k_row_maps<<<grid_for(M, 256), 256, 0, s>>>(slrows, Msl, has, has_scan, M, P.row_of_orig, P.orig_of_row,
+                                                P.slack_orig);
+    TH_LAUNCHED();
+  }
+
+  // internal CSC
+  int64_t* icnt = tmp.alloc<int64_t>(Ns + 1);
+  k_int_col_counts<<<grid_for(Ns, 256), 256, 0, s>>>(orig_of_col, raw.colptr, Ns, icnt);
+  TH_LAUNCHED();
+  P.colptr = P.mem.alloc<int64_t>(Ns + 1);
+  exclusive_scan_i64(icnt, P.colptr, Ns, tmp, s);
+  P.rowidx = P.mem.alloc<uint32_t>(nnz);
+  if (P.has_val) {
+    P.val = P.mem.alloc<float>(nnz);
+    P.csq = P.mem.alloc<float>(Ns);
+  }
+  k_int_csc_fill<<<grid_for(Ns * 32, 256), 256, 0, s>>>(orig_of_col, raw.colptr, raw.rowidx, raw.val,
+                                                         P.row_of_orig, P.colptr, Ns, P.has_val, P.rowidx,
+                                                         P.val, P.csq);
+  TH_LAUNCHED();
+  // internal CSR (structural entries)
+  int64_t* rcnt = tmp.alloc<int64_t>(M + 1);
+  P.rowptr = P.mem.alloc<int64_t>(M + 1);
+  if (M > 0) {
+    k_int_row_counts<<<grid_for(M, 256), 256, 0, s>>>(P.orig_of_row, orowptr, M, rcnt);
+    TH_LAUNCHED();
+  }
+  exclusive_scan_i64(rcnt, P.rowptr, M, tmp, s);
+  P.colidx = P.mem.alloc<uint32_t>(nnz);
+  if (P.has_val) P.rval = P.mem.alloc<float>(nnz);
+  if (M > 0) {
+    k_int_csr_fill<<<grid_for(M, 256), 256, 0, s>>>(P.orig_of_row, orowptr, csr_p, colof, raw.val, P.col_of_orig,
+                                                    P.rowptr, M, P.has_val, P.colidx, P.rval);
+    TH_LAUNCHED();
+  }
+  // vectors
+  P.c = P.mem.alloc<float>(Ns);
+  P.x = P.mem.alloc<float>(Ns);
+  if (!P.bounds_uniform) {
+    P.lo = P.mem.alloc<float>(Ns);
+    P.hi = P.mem.alloc<float>(Ns);
+  }
+  k_col_vectors<<<grid_for(Ns, 256), 256, 0, s>>>(orig_of_col, raw.c, raw.lo, raw.hi, Ns, !P.bounds_uniform,
+                                                  P.c, P.lo, P.hi);
+  TH_LAUNCHED();
+  P.b = P.mem.alloc<float>(M);
+  P.sig = P.mem.alloc<int8_t>(M);
+  P.r = P.mem.alloc<float>(M);
+  P.s = P.mem.alloc<float>(Msl);
+  if (M > 0) {
+    k_row_vectors<<<grid_for(M, 256), 256, 0, s>>>(P.orig_of_row, raw.b, raw.row_kind, M, P.b, P.sig);
+    TH_LAUNCHED();
+  }
+  // lmax and max unit size
+  double* dsq = tmp.alloc<double>(1);
+  unsigned long long* dmu = tmp.alloc<unsigned long long>(1);
+  TH_CUDA(cudaMemsetAsync(dsq, 0, sizeof(double), s));
+  TH_CUDA(cudaMemsetAsync(dmu, 0, sizeof(unsigned long long), s));
+  if (P.Nfree > 0) {
+    k_max_sq_free<<<grid_for(P.Nfree, 256), 256, 0, s>>>(P.colptr, P.csq, P.Nfree, dsq);
+    TH_LAUNCHED();
+  }
+  k_max_unit_nnz<<<grid_for(U, 256), 256, 0, s>>>(unnz, U, dmu);
+  TH_LAUNCHED();
+  double hsq = 0.0;
+  unsigned long long hmu = 0;
+  TH_CUDA(cudaMemcpyAsync(&hsq, dsq, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(&hmu, dmu, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  P.lmax_sq = std::max(hsq, (P.Msl > 0) ? 1.0 : 0.0);
+  P.max_unit_nnz = (int64_t)hmu;
+
+  // colour plan
+  P.plan.assign(C, ColorPlan{});
+  {
+    int64_t u = 0, col = 0, srow = 0;
+    for (int c = 0; c < C; ++c) {
+      ColorPlan& cp = P.plan[c];
+      for (int cls = 0; cls < UC_COUNT; ++cls) {
+        int64_t n = hc[(size_t)c * UC_COUNT + cls];
+        if (n == 0) continue;
+        int32_t len = (cls == UC_BLOCK) ? P.k : 1;
+        cp.segs.push_back(Seg{cls, u, u + n, col, len});
+        u += n;
+        col += n * len;
+      }
+      cp.srow0 = srow;
+      srow += hs[c];
+      cp.srow1 = srow;
+    }
+    TH_CHECK(u == Us && col == P.Nfree && srow == Msl, THETIS_E_CUDA, "colour plan inconsistent");
+  }
+  // free simplex blocks (internal first columns)
+  {
+    std::vector<int64_t> bs;
+    for (auto& cp : P.plan)
+      for (auto& sg : cp.segs)
+        if (sg.cls == UC_BLOCK)
+          for (int64_t u = sg.u0; u < sg.u1; ++u) bs.push_back(sg.c0 + (u - sg.u0) * sg.len);
+    P.nblk = (int64_t)bs.size();
+    if (P.nblk > 0) {
+      P.blk_start = P.mem.alloc<int64_t>(P.nblk);
+      TH_CUDA(cudaMemcpyAsync(P.blk_start, bs.data(), P.nblk * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+
+  // solve scratch
+  P.r64 = P.mem.alloc<double>(M);
+  P.red = P.mem.alloc<double>(8 * 4096);
+  P.red_out = P.mem.alloc<double>(16);
+  TH_CUDA(cudaMallocHost((void**)&P.h_red, 16 * sizeof(double)));
+  return Pp;
+}
+
+Problem::~Problem() {
+  if (epoch_graph) cudaGraphExecDestroy(epoch_graph);
+  if (h_red) cudaFreeHost(h_red);
+}
+
+}  // namespace thetis

@@ -1,0 +1,167 @@
+// Internal, colour-ordered device layout of one LP and the kernels' views of it.
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace thetis {
+
+enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3 };
+
+// Classes of coordinate units inside one colour.  Units of a colour are stored
+// class by class, so that every class is a contiguous range of units and of
+// internal columns.
+enum UnitClass { UC_BLOCK = 0, UC_BIG = 1, UC_MED = 2, UC_SMALL = 3, UC_COUNT = 4 };
+
+struct Seg {
+  int cls;        // UnitClass
+  int64_t u0, u1; // units [u0, u1) (positions in colour order)
+  int64_t c0;     // first internal column of unit u0
+  int32_t len;    // columns per unit (k for blocks, 1 otherwise)
+};
+
+struct ColorPlan {
+  std::vector<Seg> segs;   // non-empty classes of this colour
+  int64_t srow0 = 0, srow1 = 0; // internal rows whose slack has this colour
+  int64_t nnz = 0;          // structural non-zeros of this colour
+};
+
+// Original-order input held on the device while the layout is built.
+struct RawLP {
+  int64_t M = 0, Ns = 0, nnz = 0;
+  int64_t* colptr = nullptr;   // Ns+1
+  int32_t* rowidx = nullptr;   // nnz
+  float* val = nullptr;        // nnz or null (+1)
+  float *b = nullptr, *c = nullptr, *lo = nullptr, *hi = nullptr;
+  uint8_t* row_kind = nullptr;
+  int32_t block_k = 1;
+  int64_t n_blocks = 0;
+  int64_t* block_first = nullptr;
+  // uniform-bounds hint (set by the graph builders)
+  bool bounds_uniform = false;
+  float lo_u = 0.f, hi_u = 1.f;
+  int slack_sign_uniform = 0;  // -1 / +1 if every row has a slack of that sign
+};
+
+struct Problem {
+  explicit Problem(cudaStream_t s) : stream(s), mem(s) {}
+  cudaStream_t stream;
+  Arena mem;  // lives as long as the handle
+
+  int kind = KIND_GENERAL;
+  int64_t M = 0;      // rows
+  int64_t Ns = 0;     // structural columns (original)
+  int64_t nnz = 0;    // structural non-zeros
+  int32_t k = 1;      // simplex block size
+  bool has_val = false;
+  bool bounds_uniform = false;
+  float lo_u = 0.f, hi_u = 1.f;
+  int slack_sign_uniform = 0;
+
+  // graph meta (builders)
+  int64_t nv = 0, ne = 0;
+  int32_t *eu = nullptr, *ev = nullptr, *term = nullptr;
+  float *w = nullptr, *ce = nullptr;
+
+  // units
+  int64_t U = 0;        // all units (structural free units then slack units)
+  int64_t Us = 0;       // free structural units
+  int64_t Nfree = 0;    // free structural columns
+  int64_t Nfix = 0;     // fixed structural columns
+  int64_t Msl = 0;      // rows with a slack (= slack units)
+  int32_t ncolors = 0;
+  int64_t free_coords = 0;  // Nfree + Msl
+  std::vector<ColorPlan> plan;
+
+  // internal CSC over internal structural columns [0, Nfree + Nfix)
+  int64_t* colptr = nullptr;
+  uint32_t* rowidx = nullptr;  // internal row | NEG_BIT
+  float* val = nullptr;        // if has_val
+  // internal CSR (structural entries only) for the FP64 refresh
+  int64_t* rowptr = nullptr;
+  uint32_t* colidx = nullptr;  // internal column | NEG_BIT
+  float* rval = nullptr;
+
+  // per internal structural column
+  float* x = nullptr;
+  float* c = nullptr;
+  float* lo = nullptr;  // null if bounds_uniform
+  float* hi = nullptr;
+  float* csq = nullptr; // ||a_j||^2 if has_val (else nnz)
+  // per internal row
+  float* r = nullptr;
+  float* b = nullptr;
+  float* s = nullptr;     // slack values, internal rows [0, Msl)
+  int8_t* sig = nullptr;  // slack sign per internal row (0: EQ)
+
+  // maps
+  uint32_t* col_of_orig = nullptr;  // Ns
+  uint32_t* row_of_orig = nullptr;  // M
+  uint32_t* orig_of_row = nullptr;  // M
+  int32_t* unit_color = nullptr;    // U (original unit numbering)
+  uint32_t* unit_of_pos = nullptr;  // Us: original unit id at colour position
+  uint32_t* slack_orig = nullptr;   // Msl: original slack index of internal slack row
+  int64_t* blk_start = nullptr;     // internal first column of every free simplex block
+  int64_t nblk = 0;
+  uint8_t* in_block = nullptr;      // per internal column: part of a simplex block
+
+  // solve scratch (allocated once)
+  double* r64 = nullptr;      // M
+  double* red = nullptr;      // reduction partials
+  double* red_out = nullptr;  // final check values
+  double* h_red = nullptr;    // pinned host mirror
+  float* ctil = nullptr;      // c - A^T ubar (internal order) when ubar given
+  float* cs = nullptr;        // slack linear term -sig*ubar when ubar given
+  float* ubar_int = nullptr;  // ubar in internal row order
+  float* xbar = nullptr;      // Nfree+Nfix, when given
+  float* sbar = nullptr;      // Msl, when given
+  float* xorig = nullptr;     // rounding scratch: x in vertex order (n*k)
+  double lmax_sq = 0.0;       // max ||a_j||^2 over free structural columns
+  int64_t max_unit_nnz = 0;
+
+  // CUDA graph of one epoch
+  cudaGraphExec_t epoch_graph = nullptr;
+  int graph_key = -1;
+  ~Problem();
+};
+
+// build.cu
+std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cudaStream_t s,
+                                       Arena& tmp);
+void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
+                     const float* d_w, RawLP& raw, Arena& tmp, cudaStream_t s);
+void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
+                  const float* d_ce, int32_t k, const int32_t* d_term, RawLP& raw, Arena& tmp,
+                  cudaStream_t s);
+
+// scd.cu
+struct SolveArgs {
+  double beta;
+  int32_t epochs;
+  double tol;
+  int32_t refresh_every;
+  int32_t step_rule;
+  int32_t mode;
+};
+struct CheckOut {
+  double rho, obj, infeas, fbeta;
+};
+void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const float* d_x0);
+void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar);
+void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out);
+void refresh_only(Problem& P);
+void init_iterate(Problem& P);
+
+// round.cu
+struct RoundOut {
+  double obj, repair;
+  int32_t best_rep;
+  int64_t near;
+  int32_t valid;
+  int status;
+};
+void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out);
+void gather_x_orig(Problem& P, float* d_out);
+
+}  // namespace thetis

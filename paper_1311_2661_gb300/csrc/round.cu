@@ -1,0 +1,304 @@
+// Repair of the approximate LP point and oblivious rounding (App. C, App. B):
+// vertex cover threshold (Sec. 2, Lemma lem:infeasible:rounded:vc), Bansal et
+// al. packing rounding with alterations for independent set (App. B.2,
+// Algorithm 2, theta = 1/k, tighter alpha of App. C.3), CKR region growing for
+// multiway cut (App. B.3), best of R repetitions (Sec. 4.2), exact validity.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "problem.cuh"
+
+namespace thetis {
+
+#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+constexpr int RB = 256;       // reduction blocks per repetition (fixed: deterministic sums)
+constexpr int MAX_REPS = 64;
+constexpr double NEAR_BAND = 1e-4;
+
+__global__ void k_gather_x(const float* x, const uint32_t* col_of_orig, int64_t n, float* out) {
+  GSTRIDE(j, n) out[j] = x[col_of_orig[j]];
+}
+
+void gather_x_orig(Problem& P, float* d_out) {
+  k_gather_x<<<grid_for(P.Ns, 256), 256, 0, P.stream>>>(P.x, P.col_of_orig, P.Ns, d_out);
+  TH_LAUNCHED();
+  TH_CUDA(cudaGetLastError());
+}
+
+// max over edges of f(x_u + x_v), f(t) = (1 - t)_+ (VC) or (t - 1)_+ (IS), exact in FP64
+__global__ void k_edge_violation(const float* x, const int32_t* eu, const int32_t* ev, int64_t m, int cover,
+                                 unsigned long long* out) {
+  double mx = 0.0;
+  GSTRIDE(e, m) {
+    double xu = (double)x[eu[e]], xv = (double)x[ev[e]];
+    double v = cover ? (1.0 - xu) - xv : (xu + xv) - 1.0;
+    mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// VC: x~ = min(1, x/(1-eps)); label = x~ >= 1/2; near-threshold count; weight partials
+__global__ void k_vc_label(const float* x, const float* w, int64_t n, const unsigned long long* eps_bits,
+                           uint8_t* lab, double* part, unsigned long long* near) {
+  double eps = __longlong_as_double((long long)*eps_bits);
+  double sum = 0.0;
+  unsigned long long nr = 0;
+  GSTRIDE(v, n) {
+    double xt = fmin(1.0, fmax(0.0, (double)x[v] / (1.0 - eps)));
+    uint8_t l = xt >= 0.5;
+    lab[v] = l;
+    if (fabs(xt - 0.5) < NEAR_BAND) ++nr;
+    if (l) sum += (double)w[v];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  }
+  __shared__ double sm[8];
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = sum;
+    if (nr) atomicAdd(near, nr);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
+    part[blockIdx.x] = a;
+  }
+}
+
+// IS, all repetitions: pick[r][v] = U(seed, r, 1, v) < x~_v
+__global__ void k_is_pick(const float* x, int64_t n, int reps, uint64_t seed, const unsigned long long* alpha_bits,
+                          uint8_t* pick) {
+  double alpha = __longlong_as_double((long long)*alpha_bits);
+  GSTRIDE(t, n * reps) {
+    int64_t r = t / n, v = t % n;
+    double xt = (double)x[v] / (1.0 + alpha);
+    pick[t] = rng_unif(seed, (uint64_t)r, STREAM_IS_PICK, (uint64_t)v) < xt;
+  }
+}
+
+// alteration: for every edge with both ends picked, delete the end of larger id
+__global__ void k_is_alter(const int32_t* eu, const int32_t* ev, int64_t m, int64_t n, int reps, const uint8_t* pick,
+                           uint8_t* keep) {
+  GSTRIDE(t, m * reps) {
+    int64_t r = t / m, e = t % m;
+    int32_t u = eu[e], v = ev[e];
+    const uint8_t* pr = pick + r * n;
+    if (pr[u] && pr[v]) keep[r * n + (u > v ? u : v)] = 0;
+  }
+}
+
+// per-repetition FP64 sums of w over selected vertices (VC/IS) in a fixed order
+__global__ void k_rep_weight(const uint8_t* sel, const float* w, int64_t n, double* part) {
+  int r = blockIdx.y;
+  double sum = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (sel[(int64_t)r * n + v]) sum += (double)w[v];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  __shared__ double sm[8];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
+    part[(int64_t)r * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+__global__ void k_rep_final(const double* part, int nb, int reps, double* out) {
+  int r = threadIdx.x;
+  if (r >= reps) return;
+  double a = 0.0;
+  for (int b = 0; b < nb; ++b) a += part[(int64_t)r * nb + b];
+  out[r] = a;
+}
+
+// CKR: label of every vertex in every repetition
+__global__ void k_ckr_label(const float* x, int64_t n, int k, int reps, const double* rad, const int32_t* sigma,
+                            uint8_t* lab) {
+  GSTRIDE(t, n * reps) {
+    int64_t r = t / n, v = t % n;
+    const int32_t* sg = sigma + r * k;
+    double thr = 1.0 - rad[r];
+    int l = sg[k - 1];
+    for (int q = 0; q < k - 1; ++q)
+      if ((double)x[v * k + sg[q]] >= thr) {
+        l = sg[q];
+        break;
+      }
+    lab[t] = (uint8_t)l;
+  }
+}
+
+__global__ void k_cut_cost(const uint8_t* lab, const int32_t* eu, const int32_t* ev, const float* ce, int64_t m,
+                           int64_t n, double* part) {
+  int r = blockIdx.y;
+  double sum = 0.0;
+  const uint8_t* L = lab + (int64_t)r * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    if (L[eu[e]] != L[ev[e]]) sum += (double)ce[e];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  __shared__ double sm[8];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
+    part[(int64_t)r * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// exact validity: 0 = valid
+__global__ void k_valid_edges(const uint8_t* lab, const int32_t* eu, const int32_t* ev, int64_t m, int kind,
+                              int* bad) {
+  GSTRIDE(e, m) {
+    uint8_t a = lab[eu[e]], b = lab[ev[e]];
+    if (kind == KIND_VC && !a && !b) atomicExch(bad, 1);
+    if (kind == KIND_IS && a && b) atomicExch(bad, 1);
+  }
+}
+
+__global__ void k_valid_mc(const uint8_t* lab, int64_t n, int k, const int32_t* term, int* bad) {
+  GSTRIDE(v, n) if (lab[v] >= k) atomicExch(bad, 1);
+  if (blockIdx.x == 0 && threadIdx.x < k)
+    if (lab[term[threadIdx.x]] != threadIdx.x) atomicExch(bad, 1);
+}
+
+__global__ void k_is_near(const float* x, int64_t n, int rep, uint64_t seed, const unsigned long long* alpha_bits,
+                          unsigned long long* near) {
+  double alpha = __longlong_as_double((long long)*alpha_bits);
+  unsigned long long c = 0;
+  GSTRIDE(v, n) {
+    double xt = (double)x[v] / (1.0 + alpha);
+    if (fabs(rng_unif(seed, (uint64_t)rep, STREAM_IS_PICK, (uint64_t)v) - xt) < NEAR_BAND) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(near, c);
+}
+
+void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out) {
+  cudaStream_t s = P.stream;
+  TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC, THETIS_E_INVALID,
+           "rounding needs a problem built by thetis_build_vc / _is / _mc");
+  TH_CHECK((kind == THETIS_ROUND_VC && P.kind == KIND_VC) || (kind == THETIS_ROUND_IS && P.kind == KIND_IS) ||
+               (kind == THETIS_ROUND_MC && P.kind == KIND_MC),
+           THETIS_E_INVALID, "rounding kind does not match the problem");
+  if (kind == THETIS_ROUND_VC) reps = 1;
+  TH_CHECK(reps >= 1 && reps <= MAX_REPS, THETIS_E_INVALID, "reps must be in [1, 64]");
+  const int64_t n = P.nv, m = P.ne;
+  Arena tmp(s);
+  if (!P.xorig) P.xorig = P.mem.alloc<float>(P.Ns);
+  gather_x_orig(P, P.xorig);
+  unsigned long long* dbits = tmp.alloc<unsigned long long>(4);
+  TH_CUDA(cudaMemsetAsync(dbits, 0, 4 * sizeof(unsigned long long), s));
+  int* bad = (int*)(dbits + 3);
+  double* part = tmp.alloc<double>((int64_t)RB * reps + 1);
+  double* repv = tmp.alloc<double>(reps);
+  std::vector<double> hv(reps);
+  out.best_rep = 0;
+  out.near = 0;
+  out.status = THETIS_OK;
+  if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_IS) {
+    bool cover = kind == THETIS_ROUND_VC;
+    if (m > 0) {
+      k_edge_violation<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(P.xorig, P.eu, P.ev, m, cover ? 1 : 0, dbits);
+      TH_LAUNCHED();
+    }
+    unsigned long long hb = 0;
+    TH_CUDA(cudaMemcpyAsync(&hb, dbits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    double viol;
+    memcpy(&viol, &hb, sizeof(double));
+    out.repair = viol;
+    if (cover) {
+      if (viol >= 1.0) {
+        out.status = THETIS_E_REPAIR;
+        return;
+      }
+      k_vc_label<<<RB, 256, 0, s>>>(P.xorig, P.w, n, dbits, d_labels, part, dbits + 1);
+      TH_LAUNCHED();
+      k_rep_final<<<1, 32, 0, s>>>(part, RB, 1, repv);
+      TH_LAUNCHED();
+      if (m > 0) {
+        k_valid_edges<<<grid_for(m, 256), 256, 0, s>>>(d_labels, P.eu, P.ev, m, KIND_VC, bad);
+        TH_LAUNCHED();
+      }
+    } else {
+      uint8_t* pick = tmp.alloc<uint8_t>(n * reps);
+      uint8_t* keep = tmp.alloc<uint8_t>(n * reps);
+      k_is_pick<<<grid_for(n * reps, 256), 256, 0, s>>>(P.xorig, n, reps, seed, dbits, pick);
+      TH_LAUNCHED();
+      TH_CUDA(cudaMemcpyAsync(keep, pick, n * reps, cudaMemcpyDeviceToDevice, s));
+      if (m > 0) {
+        k_is_alter<<<grid_for(m * reps, 256), 256, 0, s>>>(P.eu, P.ev, m, n, reps, pick, keep);
+        TH_LAUNCHED();
+      }
+      k_rep_weight<<<dim3(RB, reps), 256, 0, s>>>(keep, P.w, n, part);
+      TH_LAUNCHED();
+      k_rep_final<<<1, MAX_REPS, 0, s>>>(part, RB, reps, repv);
+      TH_LAUNCHED();
+      TH_CUDA(cudaMemcpyAsync(hv.data(), repv, reps * sizeof(double), cudaMemcpyDeviceToHost, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+      int best = 0;
+      for (int r = 1; r < reps; ++r)
+        if (hv[r] > hv[best]) best = r;
+      out.best_rep = best;
+      TH_CUDA(cudaMemcpyAsync(d_labels, keep + (int64_t)best * n, n, cudaMemcpyDeviceToDevice, s));
+      k_is_near<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(P.xorig, n, best, seed, dbits, dbits + 1);
+      TH_LAUNCHED();
+      if (m > 0) {
+        k_valid_edges<<<grid_for(m, 256), 256, 0, s>>>(d_labels, P.eu, P.ev, m, KIND_IS, bad);
+        TH_LAUNCHED();
+      }
+    }
+  } else {
+    const int k = P.k;
+    std::vector<double> rad(reps);
+    std::vector<int32_t> sig((size_t)reps * k);
+    for (int r = 0; r < reps; ++r) {
+      rad[r] = rng_unif(seed, (uint64_t)r, STREAM_CKR_RADIUS, 0);
+      int32_t* sg = &sig[(size_t)r * k];
+      for (int i = 0; i < k; ++i) sg[i] = i;
+      for (int i = k - 1; i >= 1; --i) {
+        int j = (int)std::floor(rng_unif(seed, (uint64_t)r, STREAM_CKR_PERM, (uint64_t)i) * (double)(i + 1));
+        std::swap(sg[i], sg[j]);
+      }
+    }
+    double* drad = tmp.alloc<double>(reps);
+    int32_t* dsig = tmp.alloc<int32_t>((int64_t)reps * k);
+    TH_CUDA(cudaMemcpyAsync(drad, rad.data(), reps * sizeof(double), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(dsig, sig.data(), sig.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    uint8_t* lab = tmp.alloc<uint8_t>(n * reps);
+    k_ckr_label<<<grid_for(n * reps, 256), 256, 0, s>>>(P.xorig, n, k, reps, drad, dsig, lab);
+    TH_LAUNCHED();
+    k_cut_cost<<<dim3(RB, reps), 256, 0, s>>>(lab, P.eu, P.ev, P.ce, m, n, part);
+    TH_LAUNCHED();
+    k_rep_final<<<1, MAX_REPS, 0, s>>>(part, RB, reps, repv);
+    TH_LAUNCHED();
+    TH_CUDA(cudaMemcpyAsync(hv.data(), repv, reps * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    int best = 0;
+    for (int r = 1; r < reps; ++r)
+      if (hv[r] < hv[best]) best = r;
+    out.best_rep = best;
+    out.repair = 0.0;
+    TH_CUDA(cudaMemcpyAsync(d_labels, lab + (int64_t)best * n, n, cudaMemcpyDeviceToDevice, s));
+    k_valid_mc<<<grid_for(n, 256), 256, 0, s>>>(d_labels, n, k, P.term, bad);
+    TH_LAUNCHED();
+  }
+  unsigned long long hn[4];
+  TH_CUDA(cudaMemcpyAsync(hn, dbits, sizeof(hn), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hv.data(), repv, reps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  out.near = (int64_t)hn[1];
+  int hbad = (int)(hn[3] & 0xffffffffu);
+  out.valid = hbad ? 0 : 1;
+  out.obj = hv[out.best_rep];
+  TH_CUDA(cudaGetLastError());
+}
+
+}  // namespace thetis

@@ -1,0 +1,728 @@
+// Coordinate descent on the quadratic-penalty QP (Sec. 3.2 eq. QP), one
+// colour class per launch: every unit of a colour touches rows no other unit
+// of that colour touches, so the parallel step equals the serial sweep over
+// the colour (Algorithm 1's update, re-ordered by colour).  Also the
+// asynchronous all-at-once mode of Sec. 3.4 (atomic residual updates), the
+// FP64 residual refresh r = Ax - b and the FP64 checks.
+#include <algorithm>
+#include <cmath>
+
+#include "problem.cuh"
+
+namespace thetis {
+
+constexpr int STEP_T = 256;        // threads per CTA of the step kernels
+constexpr int GROUP_SMALL = 8;     // lanes per unit for small units
+constexpr int CACHE = 4;           // r values a lane keeps between gather and scatter
+constexpr int CHECK_BLOCKS = 1024; // fixed grid of the check kernel (deterministic reduction)
+constexpr int NRED = 6;            // rho, obj, infeas, rr, ur, xx
+
+struct StepView {
+  const int64_t* colptr;
+  const uint32_t* rowidx;
+  const float* val;  // null: +-1 encoded in rowidx
+  const float* csq;  // ||a_j||^2 when val != null
+  float* x;
+  const float* ct;   // c - A^T ubar
+  const float* xbar; // null: 0
+  const float* lo;   // null: uniform bounds
+  const float* hi;
+  float lo_u, hi_u;
+  float* r;
+  float* s;
+  const int8_t* sig;
+  int sig_u;         // uniform slack sign or 0
+  const float* cs;   // slack linear term or null
+  const float* sbar; // null: 0
+  float beta, inv_beta;
+  float lfix;        // > 0: global L_max (step_rule 1)
+  int k;
+  int async;         // 1: atomic residual updates
+};
+
+struct SegLaunch {
+  int cls;        // UnitClass, or 4 for slacks
+  int64_t u0;     // first unit position (slacks: first internal row)
+  int64_t n;      // units (slacks: rows)
+  int64_t c0;     // first internal column
+  int64_t b0;     // first CTA of this segment
+};
+
+struct ColorLaunch {
+  SegLaunch seg[UC_COUNT + 1];
+  int nseg;
+};
+
+__device__ __forceinline__ float coef(const StepView& V, int64_t p, uint32_t e) {
+  return V.val ? V.val[p] : sgn_of(e);
+}
+__device__ __forceinline__ uint32_t rowof(const StepView& V, uint32_t e) {
+  return V.val ? e : idx_of(e);
+}
+
+__device__ __forceinline__ void r_add(const StepView& V, uint32_t row, float cached, float delta) {
+  if (V.async) atomicAdd(&V.r[row], delta);
+  else V.r[row] = cached + delta;
+}
+
+// One projected step of singleton column j by G cooperating lanes (G a power of
+// two <= 32) -- or by a whole CTA when G == STEP_T.
+template <int G>
+__device__ __forceinline__ void step_column(const StepView& V, int64_t j, int lane, float* red_smem,
+                                            bool valid = true) {
+  const int64_t p0 = valid ? V.colptr[j] : 0, p1 = valid ? V.colptr[j + 1] : 0;
+  uint32_t ce[CACHE];
+  float cr[CACHE];
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < CACHE; ++t) {
+    int64_t p = p0 + lane + (int64_t)t * G;
+    ce[t] = 0;
+    cr[t] = 0.f;
+    if (p < p1) {
+      uint32_t e = V.rowidx[p];
+      float rr = V.r[rowof(V, e)];
+      ce[t] = e;
+      cr[t] = rr;
+      acc = fmaf(coef(V, p, e), rr, acc);
+    }
+  }
+  for (int64_t p = p0 + lane + (int64_t)CACHE * G; p < p1; p += G) {
+    uint32_t e = V.rowidx[p];
+    acc = fmaf(coef(V, p, e), V.r[rowof(V, e)], acc);
+  }
+  // reduce over the G lanes
+  if (G <= 32) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float v = (threadIdx.x < G / 32) ? red_smem[threadIdx.x] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) red_smem[32] = v;
+    }
+    __syncthreads();
+    acc = red_smem[32];
+  }
+  if (!valid) {
+    if (G > 32) __syncthreads();
+    return;
+  }
+  const float xj = V.x[j];
+  const float xb = V.xbar ? V.xbar[j] : 0.f;
+  const float g = V.ct[j] + V.beta * acc + (xj - xb) * V.inv_beta;
+  const float sq = V.val ? V.csq[j] : (float)(p1 - p0);
+  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, sq, V.inv_beta);
+  const float lo = V.lo ? V.lo[j] : V.lo_u;
+  const float hi = V.hi ? V.hi[j] : V.hi_u;
+  const float xn = fminf(fmaxf(xj - g / L, lo), hi);
+  const float d = xn - xj;
+  if (lane == 0) V.x[j] = xn;
+  if (d != 0.f) {
+#pragma unroll
+    for (int t = 0; t < CACHE; ++t) {
+      int64_t p = p0 + lane + (int64_t)t * G;
+      if (p < p1) r_add(V, rowof(V, ce[t]), cr[t], coef(V, p, ce[t]) * d);
+    }
+    for (int64_t p = p0 + lane + (int64_t)CACHE * G; p < p1; p += G) {
+      uint32_t e = V.rowidx[p];
+      uint32_t row = rowof(V, e);
+      float delta = coef(V, p, e) * d;
+      if (V.async) atomicAdd(&V.r[row], delta);
+      else V.r[row] += delta;
+    }
+  }
+  if (G > 32) __syncthreads();
+}
+
+// Block step (App. E): the k columns of a simplex block, one warp.  Lanes are
+// split into k groups of S lanes (S the largest power of two <= 32/k); group q
+// computes grad_q, the block moves to Proj_simplex(x - grad/L), L = beta
+// max_q ||a_q||^2 + 1/beta.
+__device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int lane) {
+  const int k = V.k;
+  int S = 1;
+  while (S * 2 * k <= 32) S *= 2;
+  const int q = lane / S, t = lane % S;
+  const bool act = q < k;
+  const int64_t jq = j0 + (act ? q : 0);
+  const int64_t p0 = act ? V.colptr[jq] : 0, p1 = act ? V.colptr[jq + 1] : 0;
+  uint32_t ce[CACHE];
+  float cr[CACHE];
+  float acc = 0.f;
+#pragma unroll
+  for (int u = 0; u < CACHE; ++u) {
+    int64_t p = p0 + t + (int64_t)u * S;
+    ce[u] = 0;
+    cr[u] = 0.f;
+    if (p < p1) {
+      uint32_t e = V.rowidx[p];
+      float rr = V.r[rowof(V, e)];
+      ce[u] = e;
+      cr[u] = rr;
+      acc = fmaf(coef(V, p, e), rr, acc);
+    }
+  }
+  for (int64_t p = p0 + t + (int64_t)CACHE * S; p < p1; p += S) {
+    uint32_t e = V.rowidx[p];
+    acc = fmaf(coef(V, p, e), V.r[rowof(V, e)], acc);
+  }
+  for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  // per-column ||a||^2 and the block L
+  float sq = act ? (V.val ? V.csq[jq] : (float)(p1 - p0)) : 0.f;
+  float sqm = sq;
+  for (int o = 16; o > 0; o >>= 1) sqm = fmaxf(sqm, __shfl_xor_sync(0xffffffffu, sqm, o));
+  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, sqm, V.inv_beta);
+  // gather y_q into lane q
+  float gq = __shfl_sync(0xffffffffu, acc, (lane < k ? lane : 0) * S);
+  float xq = 0.f, y = -INFINITY;
+  if (lane < k) {
+    xq = V.x[j0 + lane];
+    float xb = V.xbar ? V.xbar[j0 + lane] : 0.f;
+    float g = V.ct[j0 + lane] + V.beta * gq + (xq - xb) * V.inv_beta;
+    y = xq - g / L;
+  }
+  // simplex projection: for lane j, c_j = #{i: y_i >= y_j}, S_j = sum of those y_i;
+  // theta = (S - 1)/c at the largest c whose y_j - (S_j - 1)/c_j > 0.
+  float cnt = 0.f, sum = 0.f;
+  for (int i = 0; i < k; ++i) {
+    float yi = __shfl_sync(0xffffffffu, y, i);
+    if (lane < k && yi >= y) {
+      cnt += 1.f;
+      sum += yi;
+    }
+  }
+  float theta = (lane < k) ? (sum - 1.f) / cnt : 0.f;
+  bool ok = (lane < k) && (y - theta > 0.f);
+  int key = ok ? (int)cnt : 0;
+  int best = key;
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  unsigned who = __ballot_sync(0xffffffffu, key == best && ok);
+  float th = __shfl_sync(0xffffffffu, theta, __ffs(who) - 1);
+  float xn = fmaxf(y - th, 0.f);
+  float d = xn - xq;
+  if (lane < k) V.x[j0 + lane] = xn;
+  float dq = __shfl_sync(0xffffffffu, d, act ? q : 0);
+  if (act && dq != 0.f) {
+#pragma unroll
+    for (int u = 0; u < CACHE; ++u) {
+      int64_t p = p0 + t + (int64_t)u * S;
+      if (p < p1) r_add(V, rowof(V, ce[u]), cr[u], coef(V, p, ce[u]) * dq);
+    }
+    for (int64_t p = p0 + t + (int64_t)CACHE * S; p < p1; p += S) {
+      uint32_t e = V.rowidx[p];
+      uint32_t row = rowof(V, e);
+      float delta = coef(V, p, e) * dq;
+      if (V.async) atomicAdd(&V.r[row], delta);
+      else V.r[row] += delta;
+    }
+  }
+}
+
+__device__ __forceinline__ void step_slack(const StepView& V, int64_t i) {
+  const float sv = V.s[i];
+  const float rv = V.r[i];
+  const float sg = V.sig_u ? (float)V.sig_u : (float)V.sig[i];
+  const float sb = V.sbar ? V.sbar[i] : 0.f;
+  const float lin = V.cs ? V.cs[i] : 0.f;
+  const float g = lin + V.beta * sg * rv + (sv - sb) * V.inv_beta;
+  const float L = (V.lfix > 0.f) ? V.lfix : V.beta + V.inv_beta;
+  const float sn = fmaxf(sv - g / L, 0.f);
+  const float d = sn - sv;
+  V.s[i] = sn;
+  if (d != 0.f) {
+    if (V.async) atomicAdd(&V.r[i], sg * d);
+    else V.r[i] = rv + sg * d;
+  }
+}
+
+// One colour: CTAs [seg.b0, next.b0) serve segment seg.
+__global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch CL) {
+  __shared__ float red_smem[33];
+  int si = 0;
+  while (si + 1 < CL.nseg && (int64_t)blockIdx.x >= CL.seg[si + 1].b0) ++si;
+  const SegLaunch S = CL.seg[si];
+  const int64_t b = blockIdx.x - S.b0;
+  const int lane = threadIdx.x & 31;
+  switch (S.cls) {
+    case UC_BIG: {
+      if (b < S.n) step_column<STEP_T>(V, S.c0 + b, threadIdx.x, red_smem);
+      break;
+    }
+    case UC_MED: {
+      int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
+      if (u < S.n) step_column<32>(V, S.c0 + u, lane, red_smem);
+      break;
+    }
+    case UC_SMALL: {
+      int64_t u = b * (STEP_T / GROUP_SMALL) + (threadIdx.x / GROUP_SMALL);
+      // every lane of the warp joins the group shuffles; groups past the end idle
+      bool in = u < S.n;
+      if (__any_sync(0xffffffffu, in))
+        step_column<GROUP_SMALL>(V, S.c0 + (in ? u : 0), threadIdx.x % GROUP_SMALL, red_smem, in);
+      break;
+    }
+    case UC_BLOCK: {
+      int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
+      if (u < S.n) step_block(V, S.c0 + u * V.k, lane);
+      break;
+    }
+    default: {  // slacks
+      int64_t i = b * STEP_T + threadIdx.x;
+      if (i < S.n) step_slack(V, S.u0 + i);
+      break;
+    }
+  }
+}
+
+static int64_t ctas_for(int cls, int64_t n) {
+  switch (cls) {
+    case UC_BIG: return n;
+    case UC_MED:
+    case UC_BLOCK: return (n + STEP_T / 32 - 1) / (STEP_T / 32);
+    case UC_SMALL: return (n + STEP_T / GROUP_SMALL - 1) / (STEP_T / GROUP_SMALL);
+    default: return (n + STEP_T - 1) / STEP_T;
+  }
+}
+
+static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
+  StepView V;
+  V.colptr = P.colptr;
+  V.rowidx = P.rowidx;
+  V.val = P.has_val ? P.val : nullptr;
+  V.csq = P.csq;
+  V.x = P.x;
+  V.ct = use_ubar ? P.ctil : P.c;
+  V.xbar = use_xbar ? P.xbar : nullptr;
+  V.lo = P.bounds_uniform ? nullptr : P.lo;
+  V.hi = P.bounds_uniform ? nullptr : P.hi;
+  V.lo_u = P.lo_u;
+  V.hi_u = P.hi_u;
+  V.r = P.r;
+  V.s = P.s;
+  V.sig = P.sig;
+  V.sig_u = P.slack_sign_uniform;
+  V.cs = use_ubar ? P.cs : nullptr;
+  V.sbar = use_xbar ? P.sbar : nullptr;
+  V.beta = (float)a.beta;
+  V.inv_beta = (float)(1.0 / a.beta);
+  V.lfix = (a.step_rule == 1) ? (float)(a.beta * P.lmax_sq + 1.0 / a.beta) : 0.f;
+  V.k = P.k;
+  V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
+  return V;
+}
+
+// Launches of one epoch in colour order (colored) or one launch over all
+// units (async).
+void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
+  StepView V = make_view(P, a, use_ubar, use_xbar);
+  cudaStream_t s = P.stream;
+  auto launch = [&](ColorLaunch& CL, int64_t total) {
+    if (total <= 0) return;
+    TH_CHECK(total < (int64_t(1) << 31), THETIS_E_INVALID, "colour class too large for one launch");
+    k_color_step<<<(unsigned)total, STEP_T, 0, s>>>(V, CL);
+    TH_LAUNCHED();
+  };
+  if (a.mode == THETIS_MODE_ASYNC) {
+    // every class of every colour in one launch; slack rows as one range
+    // (per-class launches keep the CTA shapes; they run back to back)
+    for (int cls = 0; cls < UC_COUNT; ++cls) {
+      ColorLaunch CL{};
+      int64_t tot = 0;
+      for (auto& cp : P.plan)
+        for (auto& sg : cp.segs)
+          if (sg.cls == cls) {
+            if (CL.nseg == UC_COUNT + 1) {
+              launch(CL, tot);
+              CL = ColorLaunch{};
+              tot = 0;
+            }
+            CL.seg[CL.nseg++] = SegLaunch{cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+            tot += ctas_for(cls, sg.u1 - sg.u0);
+          }
+      launch(CL, tot);
+    }
+    if (P.Msl > 0) {
+      ColorLaunch CL{};
+      CL.seg[0] = SegLaunch{UC_COUNT, 0, P.Msl, 0, 0};
+      CL.nseg = 1;
+      launch(CL, ctas_for(UC_COUNT, P.Msl));
+    }
+    TH_CUDA(cudaGetLastError());
+    return;
+  }
+  for (auto& cp : P.plan) {
+    ColorLaunch CL{};
+    int64_t tot = 0;
+    for (auto& sg : cp.segs) {
+      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+      tot += ctas_for(sg.cls, sg.u1 - sg.u0);
+    }
+    if (cp.srow1 > cp.srow0) {
+      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
+      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0);
+    }
+    launch(CL, tot);
+  }
+  TH_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// FP64 refresh and checks
+// ---------------------------------------------------------------------------
+#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// r = A x - b in FP64 (row by row over the internal CSR, plus the slack)
+__global__ void k_refresh(const int64_t* rowptr, const uint32_t* colidx, const float* rval, const float* x,
+                          const float* s, const int8_t* sig, const float* b, int64_t M, int64_t Msl,
+                          double* r64, float* r) {
+  GSTRIDE(i, M) {
+    double acc = 0.0;
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      uint32_t e = colidx[q];
+      double a = rval ? (double)rval[q] : (double)sgn_of(e);
+      uint32_t j = rval ? e : idx_of(e);
+      acc += a * (double)x[j];
+    }
+    if (i < Msl) acc += (double)sig[i] * (double)s[i];
+    acc -= (double)b[i];
+    r64[i] = acc;
+    r[i] = (float)acc;
+  }
+}
+
+struct CheckView {
+  const int64_t* colptr;
+  const uint32_t* rowidx;
+  const float* val;
+  const float* csq;
+  const float* x;
+  const float* c;   // original c
+  const float* ct;  // c - A^T ubar
+  const float* xbar;
+  const float* lo;
+  const float* hi;
+  float lo_u, hi_u;
+  const double* r64;
+  const float* s;
+  const int8_t* sig;
+  const float* cs;
+  const float* sbar;
+  const float* ubar;  // internal row order, or null
+  double beta;
+  int k;
+  int64_t Ncol;   // all internal structural columns
+  int64_t Nfree;
+  int64_t M, Msl;
+  const int64_t* blk_start;  // internal column where a block starts (per block), or null
+  int64_t nblk;
+  const uint8_t* in_block;   // per free internal column: 1 if part of a block
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double col_dot64(const CheckView& V, int64_t j, int lane, double* sq) {
+  double acc = 0.0, s2 = 0.0;
+  for (int64_t p = V.colptr[j] + lane; p < V.colptr[j + 1]; p += 32) {
+    uint32_t e = V.rowidx[p];
+    double a = V.val ? (double)V.val[p] : (double)sgn_of(e);
+    uint32_t row = V.val ? e : idx_of(e);
+    acc += a * V.r64[row];
+    s2 += a * a;
+  }
+  *sq = warp_sum_d(s2);
+  return warp_sum_d(acc);
+}
+
+__global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
+  // per-thread partials: rho(max), obj, infeas(max), rr, ur, xx
+  double rho = 0.0, obj = 0.0, inf = 0.0, rr = 0.0, ur = 0.0, xx = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double beta = V.beta, ib = 1.0 / beta;
+  // (a) free singleton columns, warp per column
+  for (int64_t j = warp; j < V.Nfree; j += nwarps) {
+    if (V.in_block && V.in_block[j]) continue;
+    double sq;
+    double atr = col_dot64(V, j, lane, &sq);
+    double xj = V.x[j], xb = V.xbar ? V.xbar[j] : 0.0;
+    double g = (double)V.ct[j] + beta * atr + (xj - xb) * ib;
+    double L = beta * sq + ib;
+    double lo = V.lo ? V.lo[j] : V.lo_u, hi = V.hi ? V.hi[j] : V.hi_u;
+    double xn = fmin(fmax(xj - g / L, lo), hi);
+    if (lane == 0) rho = fmax(rho, fabs(xn - xj));
+  }
+  // (b) simplex blocks, warp per block
+  for (int64_t t = warp; t < V.nblk; t += nwarps) {
+    int64_t j0 = V.blk_start[t];
+    double yq = -INFINITY, xq = 0.0, sqmax = 0.0;
+    double gl = 0.0;
+    for (int q = 0; q < V.k; ++q) {
+      double sq;
+      double atr = col_dot64(V, j0 + q, lane, &sq);
+      sqmax = fmax(sqmax, sq);
+      if (lane == q) gl = atr;
+    }
+    double L = beta * sqmax + ib;
+    if (lane < V.k) {
+      xq = V.x[j0 + lane];
+      double xb = V.xbar ? V.xbar[j0 + lane] : 0.0;
+      double g = (double)V.ct[j0 + lane] + beta * gl + (xq - xb) * ib;
+      yq = xq - g / L;
+    }
+    double cnt = 0.0, sum = 0.0;
+    for (int i = 0; i < V.k; ++i) {
+      double yi = __shfl_sync(0xffffffffu, yq, i);
+      if (lane < V.k && yi >= yq) {
+        cnt += 1.0;
+        sum += yi;
+      }
+    }
+    double theta = (lane < V.k) ? (sum - 1.0) / cnt : 0.0;
+    bool ok = (lane < V.k) && (yq - theta > 0.0);
+    int key = ok ? (int)cnt : 0;
+    int best = key;
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    unsigned who = __ballot_sync(0xffffffffu, key == best && ok);
+    double th = __shfl_sync(0xffffffffu, theta, __ffs(who) - 1);
+    if (lane < V.k) rho = fmax(rho, fabs(fmax(yq - th, 0.0) - xq));
+  }
+  // (c) objective and proximal term over all structural columns
+  GSTRIDE(j, V.Ncol) {
+    double xj = V.x[j], xb = (V.xbar) ? V.xbar[j] : 0.0;
+    obj += (double)V.c[j] * xj;
+    xx += (xj - xb) * (xj - xb);
+  }
+  // (d) rows and slacks
+  GSTRIDE(i, V.M) {
+    double ri = V.r64[i];
+    inf = fmax(inf, fabs(ri));
+    rr += ri * ri;
+    if (V.ubar) ur += (double)V.ubar[i] * ri;
+    if (i < V.Msl) {
+      double sv = V.s[i], sb = V.sbar ? V.sbar[i] : 0.0;
+      double sg = (double)V.sig[i];
+      double g = (V.cs ? (double)V.cs[i] : 0.0) + beta * sg * ri + (sv - sb) * ib;
+      double sn = fmax(sv - g / (beta + ib), 0.0);
+      rho = fmax(rho, fabs(sn - sv));
+      xx += (sv - sb) * (sv - sb);
+    }
+  }
+  // block reduction, fixed order
+  __shared__ double sm[NRED][8];
+  double vals[NRED] = {warp_max_d(rho), warp_sum_d(obj), warp_max_d(inf), warp_sum_d(rr), warp_sum_d(ur),
+                       warp_sum_d(xx)};
+  const int w = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < NRED; ++q) sm[q][w] = vals[q];
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    int q = threadIdx.x;
+    double a = sm[q][0];
+    for (int t = 1; t < 8; ++t) a = (q == 0 || q == 2) ? fmax(a, sm[q][t]) : a + sm[q][t];
+    red[(int64_t)q * CHECK_BLOCKS + blockIdx.x] = a;
+  }
+}
+
+__global__ void k_check_final(const double* red, double* out) {
+  int q = threadIdx.x;
+  if (q >= NRED) return;
+  double a = red[(int64_t)q * CHECK_BLOCKS];
+  for (int t = 1; t < CHECK_BLOCKS; ++t) {
+    double v = red[(int64_t)q * CHECK_BLOCKS + t];
+    a = (q == 0 || q == 2) ? fmax(a, v) : a + v;
+  }
+  out[q] = a;
+}
+
+// ---------------------------------------------------------------------------
+// solve preparation: ubar / xbar / x0 into internal order
+// ---------------------------------------------------------------------------
+__global__ void k_perm_rows_f(const float* src, const uint32_t* orig_of_row, int64_t M, float* dst) {
+  GSTRIDE(i, M) dst[i] = src[orig_of_row[i]];
+}
+
+__global__ void k_ctil(const int64_t* colptr, const uint32_t* rowidx, const float* val, const float* c,
+                       const float* ubar_int, int64_t N, float* ct) {
+  GSTRIDE(j, N) {
+    float acc = 0.f;
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      uint32_t e = rowidx[p];
+      float a = val ? val[p] : sgn_of(e);
+      uint32_t row = val ? e : idx_of(e);
+      acc = fmaf(a, ubar_int[row], acc);
+    }
+    ct[j] = c[j] - acc;
+  }
+}
+
+__global__ void k_cs(const float* ubar_int, const int8_t* sig, int64_t Msl, float* cs) {
+  GSTRIDE(i, Msl) cs[i] = -(float)sig[i] * ubar_int[i];
+}
+
+__global__ void k_xbar(const float* xbar, const uint32_t* col_of_orig, int64_t Ns, const uint32_t* slack_orig,
+                       int64_t Msl, float* xb, float* sb) {
+  GSTRIDE(j, Ns) xb[col_of_orig[j]] = xbar[j];
+  GSTRIDE(t, Msl) sb[t] = xbar[Ns + slack_orig[t]];
+}
+
+__global__ void k_x0(const float* x0, const uint32_t* col_of_orig, int64_t Ns, int64_t Nfree, const float* lo,
+                     const float* hi, float lo_u, float hi_u, const uint8_t* in_block, float* x) {
+  GSTRIDE(j, Ns) {
+    int64_t jj = col_of_orig[j];
+    if (jj >= Nfree) continue;  // fixed columns keep their value
+    float v = x0[j];
+    if (!(in_block && in_block[jj])) {
+      float l = lo ? lo[jj] : lo_u, h = hi ? hi[jj] : hi_u;
+      v = fminf(fmaxf(v, l), h);
+    }
+    x[jj] = v;
+  }
+}
+
+// initial point: singletons clip(0), blocks barycentre, fixed at lo; slacks 0
+__global__ void k_init_x(int64_t Ncol, int64_t Nfree, const float* lo, const float* hi, float lo_u, float hi_u,
+                         const uint8_t* in_block, int k, float* x) {
+  GSTRIDE(j, Ncol) {
+    float l = lo ? lo[j] : lo_u, h = hi ? hi[j] : hi_u;
+    float v;
+    if (j >= Nfree) v = l;
+    else if (in_block && in_block[j]) v = 1.f / (float)k;
+    else v = fminf(fmaxf(0.f, l), h);
+    x[j] = v;
+  }
+}
+
+__global__ void k_mark_blocks(const int64_t* blk_start, int64_t nblk, int k, uint8_t* in_block) {
+  GSTRIDE(t, nblk)
+  for (int q = 0; q < k; ++q) in_block[blk_start[t] + q] = 1;
+}
+
+static CheckView make_check_view(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
+  CheckView V;
+  V.colptr = P.colptr;
+  V.rowidx = P.rowidx;
+  V.val = P.has_val ? P.val : nullptr;
+  V.csq = P.csq;
+  V.x = P.x;
+  V.c = P.c;
+  V.ct = use_ubar ? P.ctil : P.c;
+  V.xbar = use_xbar ? P.xbar : nullptr;
+  V.lo = P.bounds_uniform ? nullptr : P.lo;
+  V.hi = P.bounds_uniform ? nullptr : P.hi;
+  V.lo_u = P.lo_u;
+  V.hi_u = P.hi_u;
+  V.r64 = P.r64;
+  V.s = P.s;
+  V.sig = P.sig;
+  V.cs = use_ubar ? P.cs : nullptr;
+  V.sbar = use_xbar ? P.sbar : nullptr;
+  V.ubar = use_ubar ? P.ubar_int : nullptr;
+  V.beta = a.beta;
+  V.k = P.k;
+  V.Ncol = P.Ns;
+  V.Nfree = P.Nfree;
+  V.M = P.M;
+  V.Msl = P.Msl;
+  V.blk_start = P.blk_start;
+  V.nblk = P.nblk;
+  V.in_block = P.in_block;
+  return V;
+}
+
+void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out) {
+  cudaStream_t s = P.stream;
+  if (P.M > 0) {
+    k_refresh<<<grid_for(P.M, 256, 152 * 64), 256, 0, s>>>(P.rowptr, P.colidx, P.has_val ? P.rval : nullptr, P.x,
+                                                          P.s, P.sig, P.b, P.M, P.Msl, P.r64, P.r);
+    TH_LAUNCHED();
+  }
+  k_check<<<CHECK_BLOCKS, 256, 0, s>>>(make_check_view(P, a, use_ubar, use_xbar), P.red);
+  TH_LAUNCHED();
+  k_check_final<<<1, 32, 0, s>>>(P.red, P.red_out);
+  TH_LAUNCHED();
+  TH_CUDA(cudaMemcpyAsync(P.h_red, P.red_out, NRED * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  const double* h = P.h_red;
+  out.rho = h[0];
+  out.obj = h[1];
+  out.infeas = h[2];
+  out.fbeta = h[1] - h[4] + 0.5 * a.beta * h[3] + 0.5 / a.beta * h[5];
+}
+
+// FP64 recompute of r only (start of a solve)
+void refresh_only(Problem& P) {
+  if (P.M <= 0) return;
+  k_refresh<<<grid_for(P.M, 256, 152 * 64), 256, 0, P.stream>>>(P.rowptr, P.colidx, P.has_val ? P.rval : nullptr,
+                                                                 P.x, P.s, P.sig, P.b, P.M, P.Msl, P.r64, P.r);
+  TH_LAUNCHED();
+  TH_CUDA(cudaGetLastError());
+}
+
+void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const float* d_x0) {
+  cudaStream_t s = P.stream;
+  if (d_ubar) {
+    if (!P.ubar_int) {
+      P.ubar_int = P.mem.alloc<float>(P.M);
+      P.ctil = P.mem.alloc<float>(P.Ns);
+      P.cs = P.mem.alloc<float>(P.Msl);
+    }
+    if (P.M > 0) {
+      k_perm_rows_f<<<grid_for(P.M, 256), 256, 0, s>>>(d_ubar, P.orig_of_row, P.M, P.ubar_int);
+      TH_LAUNCHED();
+    }
+    k_ctil<<<grid_for(P.Ns, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.has_val ? P.val : nullptr, P.c, P.ubar_int,
+                                               P.Ns, P.ctil);
+    TH_LAUNCHED();
+    if (P.Msl > 0) {
+      k_cs<<<grid_for(P.Msl, 256), 256, 0, s>>>(P.ubar_int, P.sig, P.Msl, P.cs);
+      TH_LAUNCHED();
+    }
+  }
+  if (d_xbar) {
+    if (!P.xbar) {
+      P.xbar = P.mem.alloc<float>(P.Ns);
+      P.sbar = P.mem.alloc<float>(P.Msl);
+    }
+    k_xbar<<<grid_for(std::max(P.Ns, P.Msl), 256), 256, 0, s>>>(d_xbar, P.col_of_orig, P.Ns, P.slack_orig, P.Msl,
+                                                                P.xbar, P.sbar);
+    TH_LAUNCHED();
+  }
+  if (d_x0) {
+    k_x0<<<grid_for(P.Ns, 256), 256, 0, s>>>(d_x0, P.col_of_orig, P.Ns, P.Nfree, P.bounds_uniform ? nullptr : P.lo,
+                                             P.bounds_uniform ? nullptr : P.hi, P.lo_u, P.hi_u, P.in_block, P.x);
+    TH_LAUNCHED();
+  }
+  TH_CUDA(cudaGetLastError());
+}
+
+void init_iterate(Problem& P) {
+  cudaStream_t s = P.stream;
+  if (P.nblk > 0 && !P.in_block) {
+    P.in_block = P.mem.alloc<uint8_t>(P.Ns);
+    TH_CUDA(cudaMemsetAsync(P.in_block, 0, P.Ns, s));
+    k_mark_blocks<<<grid_for(P.nblk, 256), 256, 0, s>>>(P.blk_start, P.nblk, P.k, P.in_block);
+    TH_LAUNCHED();
+  }
+  k_init_x<<<grid_for(P.Ns, 256), 256, 0, s>>>(P.Ns, P.Nfree, P.bounds_uniform ? nullptr : P.lo,
+                                               P.bounds_uniform ? nullptr : P.hi, P.lo_u, P.hi_u, P.in_block, P.k,
+                                               P.x);
+  TH_LAUNCHED();
+  if (P.Msl > 0) TH_CUDA(cudaMemsetAsync(P.s, 0, P.Msl * sizeof(float), s));
+  refresh_only(P);
+}
+
+}  // namespace thetis

@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libthetis.so (include/thetis.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host memory) or torch tensors
+(host or CUDA); all arrays of one call must live in the same place.  Streams
+may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or ``None``
+(the handle then owns a private stream).
+
+The functions carry the C names (``thetis_build_vc``, ``thetis_solve``, ...).
+If the library has not been built, importing this module raises: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libthetis.so")
+
+THETIS_OK, THETIS_E_INVALID, THETIS_E_NOMEM, THETIS_E_BUDGET, THETIS_E_CUDA = 0, 1, 2, 3, 4
+THETIS_E_TIMEOUT, THETIS_E_REPAIR, THETIS_PENDING, THETIS_NOT_CONVERGED = 5, 6, 7, 8
+MEM_HOST, MEM_DEVICE = 0, 1
+ROW_EQ, ROW_GE, ROW_LE = 0, 1, 2
+ROUND_VC, ROUND_IS, ROUND_MC = 0, 1, 2
+MODE_COLORED, MODE_ASYNC = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_NOMEM", 3: "E_BUDGET", 4: "E_CUDA", 5: "E_TIMEOUT",
+                6: "E_REPAIR", 7: "PENDING", 8: "NOT_CONVERGED"}
+
+
+class ThetisError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"thetis {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("csc_ptr", C.c_void_p), ("csc_row", C.c_void_p),
+                ("csc_val", C.c_void_p), ("b", C.c_void_p), ("c", C.c_void_p), ("lo", C.c_void_p),
+                ("hi", C.c_void_p), ("row_kind", C.c_void_p), ("block_k", C.c_int32),
+                ("n_blocks", C.c_int64), ("block_first", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("beta", C.c_double), ("epochs", C.c_int32), ("tol", C.c_double),
+                ("refresh_every", C.c_int32), ("step_rule", C.c_int32), ("mode", C.c_int32),
+                ("ubar", C.c_void_p), ("xbar", C.c_void_p), ("x0", C.c_void_p), ("mem", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("epochs_run", C.c_int32), ("converged", C.c_int32), ("ncolors", C.c_int32),
+                ("rho", C.c_double), ("obj", C.c_double), ("infeas", C.c_double), ("fbeta", C.c_double),
+                ("updates", C.c_int64), ("solve_ms", C.c_double)]
+
+
+class RoundInfo(C.Structure):
+    _fields_ = [("obj", C.c_double), ("repair", C.c_double), ("best_rep", C.c_int32),
+                ("near", C.c_int64), ("valid", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1311_2661_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    P, i64, i32, u64 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64
+    st = C.c_int
+    sigs = {
+        "thetis_last_error": (C.c_char_p, []),
+        "thetis_launch_count": (u64, []),
+        "thetis_create": (st, [P, i32, u64, P, P]),
+        "thetis_build_vc": (st, [i64, i64, P, P, P, i32, u64, P, P]),
+        "thetis_build_is": (st, [i64, i64, P, P, P, i32, u64, P, P]),
+        "thetis_build_mc": (st, [i64, i64, P, P, P, i32, P, i32, u64, P, P]),
+        "thetis_get_sizes": (st, [P, P, P, P, P, P, P]),
+        "thetis_solve": (st, [P, P, P]),
+        "thetis_round": (st, [P, i32, u64, i32, P, i32, P]),
+        "thetis_get_x": (st, [P, P, i32]),
+        "thetis_get_slack": (st, [P, P, i32]),
+        "thetis_get_colors": (st, [P, P, P]),
+        "thetis_sync": (st, [P]),
+        "thetis_destroy": (st, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def thetis_last_error() -> str:
+    m = _lib.thetis_last_error()
+    return m.decode() if m else ""
+
+
+def thetis_launch_count() -> int:
+    return int(_lib.thetis_launch_count())
+
+
+def _check(st, allow=(THETIS_OK,)):
+    if st not in allow:
+        raise ThetisError(st, thetis_last_error())
+    return st
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class _Args:
+    """Collects array pointers for one call and checks they share one memory space."""
+
+    def __init__(self):
+        self.keep = []
+        self.mem = None
+
+    def __call__(self, a, dtype):
+        if a is None:
+            return None
+        if _is_torch(a):
+            import torch
+
+            tdt = {np.int32: torch.int32, np.int64: torch.int64, np.float32: torch.float32,
+                   np.uint8: torch.uint8}[dtype]
+            t = a.to(tdt).contiguous()
+            mem = MEM_DEVICE if t.is_cuda else MEM_HOST
+            self.keep.append(t)
+            ptr = t.data_ptr()
+        else:
+            arr = np.ascontiguousarray(a, dtype=dtype)
+            self.keep.append(arr)
+            mem = MEM_HOST
+            ptr = arr.ctypes.data
+        if self.mem is None:
+            self.mem = mem
+        elif self.mem != mem:
+            raise ValueError("all arrays of one call must live in the same memory space")
+        return ptr
+
+    @property
+    def memspace(self):
+        return MEM_HOST if self.mem is None else self.mem
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Handle:
+    """Owns a thetis_handle; destroyed with the object."""
+
+    def __init__(self, ptr, n_vertices=None, kind=None):
+        self._h = ptr
+        self.n_vertices = n_vertices
+        self.kind = kind
+        self.sizes = thetis_get_sizes(self)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.thetis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience methods
+    def solve(self, **kw):
+        return thetis_solve(self, **kw)
+
+    def round(self, kind=None, **kw):
+        if kind is None:
+            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC}[self.kind]
+        return thetis_round(self, kind, **kw)
+
+    def get_x(self, out=None):
+        return thetis_get_x(self, out)
+
+    def get_slack(self, out=None):
+        return thetis_get_slack(self, out)
+
+    def colors(self):
+        return thetis_get_colors(self)
+
+
+def thetis_get_sizes(h: Handle):
+    vals = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()]
+    _check(_lib.thetis_get_sizes(h.ptr, *[C.byref(v) for v in vals]))
+    return dict(rows=vals[0].value, struct_cols=vals[1].value, slack_cols=vals[2].value,
+                free_coords=vals[3].value, nnz=vals[4].value, ncolors=vals[5].value)
+
+
+def _build(fn, kind, n, eu, ev, weights, seed, stream, k=None, terminals=None):
+    A = _Args()
+    m = int(eu.shape[0])
+    peu, pev = A(eu, np.int32), A(ev, np.int32)
+    pw = A(weights, np.float32)
+    out = C.c_void_p()
+    if kind == "mc":
+        pt = A(terminals, np.int32)
+        st = fn(n, m, peu, pev, pw, int(k), pt, A.memspace, seed, _stream_ptr(stream), C.byref(out))
+    else:
+        st = fn(n, m, peu, pev, pw, A.memspace, seed, _stream_ptr(stream), C.byref(out))
+    _check(st)
+    return Handle(out.value, n_vertices=n, kind=kind)
+
+
+def thetis_build_vc(n, eu, ev, w, seed=0, stream=None) -> Handle:
+    return _build(_lib.thetis_build_vc, "vc", int(n), eu, ev, w, seed, stream)
+
+
+def thetis_build_is(n, eu, ev, w, seed=0, stream=None) -> Handle:
+    return _build(_lib.thetis_build_is, "is", int(n), eu, ev, w, seed, stream)
+
+
+def thetis_build_mc(n, eu, ev, ce, k, terminals, seed=0, stream=None) -> Handle:
+    return _build(_lib.thetis_build_mc, "mc", int(n), eu, ev, ce, seed, stream, k=k, terminals=terminals)
+
+
+def thetis_create(m, n, csc_ptr, csc_row, b, c, lo, hi, row_kind, csc_val=None, block_k=1, block_first=None,
+                  seed=0, stream=None) -> Handle:
+    A = _Args()
+    d = ProblemDesc()
+    d.m, d.n = int(m), int(n)
+    d.csc_ptr = A(csc_ptr, np.int64)
+    d.csc_row = A(csc_row, np.int32)
+    d.csc_val = A(csc_val, np.float32)
+    d.b, d.c = A(b, np.float32), A(c, np.float32)
+    d.lo, d.hi = A(lo, np.float32), A(hi, np.float32)
+    d.row_kind = A(row_kind, np.uint8)
+    d.block_k = int(block_k)
+    d.n_blocks = 0 if block_first is None else int(len(block_first))
+    d.block_first = A(block_first, np.int64)
+    out = C.c_void_p()
+    _check(_lib.thetis_create(C.byref(d), A.memspace, seed, _stream_ptr(stream), C.byref(out)))
+    return Handle(out.value, kind="general")
+
+
+def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step_rule=0, mode=MODE_COLORED,
+                 ubar=None, xbar=None, x0=None):
+    A = _Args()
+    p = Params()
+    p.beta, p.epochs, p.tol = float(beta), int(epochs), float(tol)
+    p.refresh_every, p.step_rule, p.mode = int(refresh_every), int(step_rule), int(mode)
+    p.ubar, p.xbar, p.x0 = A(ubar, np.float32), A(xbar, np.float32), A(x0, np.float32)
+    p.mem = A.memspace
+    info = SolveInfo()
+    st = _check(_lib.thetis_solve(h.ptr, C.byref(p), C.byref(info)), allow=(THETIS_OK, THETIS_NOT_CONVERGED))
+    return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
+                rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
+                solve_ms=info.solve_ms)
+
+
+def thetis_round(h: Handle, kind, seed=0, reps=10, out=None):
+    """Returns (labels, info).  ``out`` may be a CUDA uint8 tensor (labels stay on the device)."""
+    info = RoundInfo()
+    if out is None:
+        lab = np.zeros(h.n_vertices, np.uint8)
+        ptr, mem = lab.ctypes.data, MEM_HOST
+    else:
+        lab = out
+        if _is_torch(out):
+            ptr, mem = out.data_ptr(), (MEM_DEVICE if out.is_cuda else MEM_HOST)
+        else:
+            ptr, mem = out.ctypes.data, MEM_HOST
+    st = _lib.thetis_round(h.ptr, int(kind), int(seed), int(reps), ptr, mem, C.byref(info))
+    if st == THETIS_E_REPAIR:
+        return None, dict(status=st, repair=info.repair, valid=False)
+    _check(st)
+    return lab, dict(status=st, obj=info.obj, repair=info.repair, best_rep=info.best_rep, near=info.near,
+                     valid=bool(info.valid))
+
+
+def _out_ptr(out):
+    if _is_torch(out):
+        return out.data_ptr(), (MEM_DEVICE if out.is_cuda else MEM_HOST)
+    return out.ctypes.data, MEM_HOST
+
+
+def thetis_get_x(h: Handle, out=None):
+    """Structural part of the iterate, original column order (FP32)."""
+    if out is None:
+        out = np.zeros(h.sizes["struct_cols"], np.float32)
+    ptr, mem = _out_ptr(out)
+    _check(_lib.thetis_get_x(h.ptr, ptr, mem))
+    return out
+
+
+def thetis_get_slack(h: Handle, out=None):
+    """Slack part of the iterate, one value per GE/LE row in row order."""
+    if out is None:
+        out = np.zeros(h.sizes["slack_cols"], np.float32)
+    ptr, mem = _out_ptr(out)
+    _check(_lib.thetis_get_slack(h.ptr, ptr, mem))
+    return out
+
+
+def thetis_get_colors(h: Handle):
+    nu = C.c_int64()
+    _check(_lib.thetis_get_colors(h.ptr, None, C.byref(nu)))
+    out = np.zeros(nu.value, np.int32)
+    _check(_lib.thetis_get_colors(h.ptr, out.ctypes.data, C.byref(nu)))
+    return out
+
+
+def thetis_sync(h: Handle):
+    _check(_lib.thetis_sync(h.ptr))
+
+
+def thetis_destroy(h: Handle):
+    h.close()
