@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Throughput of the SCD + LP-rounding hot path on one GB300 (or N replicas).
+
+One step = the whole hot path over one seeded synthetic instance whose edge
+list and weights are already resident in HBM: build the standard form on the
+device, colour the column-intersection graph, 50 colour-class SCD epochs on
+eq. QP (FP32 iterate, FP64 residual refresh and checks every 10 epochs, stop
+early at rho <= 1e-3), repair, best-of-10 rounding and exact validity.
+
+Default workload: independent-set LP on a Chung-Lu power-law graph
+(exponent 2.1, n = 2^20, m = 1.6e7 edges, weights U(0,1]).  The metric is
+coordinate updates per second over whole steps; `time_to_residual` reports the
+same pipeline run to rho <= 1e-3.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl thetis|reference]
+
+Under torchrun (N > 1) every rank solves its own instance (independent
+problems, weak scaling, no collective on the data path); rank 0 prints the
+JSON line.  `--impl reference` times the FP64 oracle (the serial CPU
+restatement of the method) on host cores for the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "is-chunglu-n2^20-m1.6e7": dict(kind="is", graph="chung_lu", n=1 << 20, m=16_000_000, gamma=2.1, seed=2,
+                                    beta=100.0, epochs=50, refresh=10, tol=1e-3, reps=10),
+    "vc-er-n2000-m8000": dict(kind="vc", graph="er", n=2000, m=8000, seed=1, beta=100.0, epochs=50, refresh=10,
+                              tol=1e-3, reps=1),
+    "mc-grid1024-k8": dict(kind="mc", graph="grid", width=1024, height=1024, k=8, seed=3, beta=100.0, epochs=50,
+                           refresh=10, tol=1e-3, reps=10),
+}
+DEFAULT = "is-chunglu-n2^20-m1.6e7"
+METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def make_graph(wl, rank=0):
+    from paper_1311_2661_gb300 import synth
+
+    seed = wl["seed"] + 1000 * rank
+    if wl["graph"] == "chung_lu":
+        g = synth.chung_lu(wl["n"], wl["m"], wl["gamma"], seed)
+    elif wl["graph"] == "er":
+        g = synth.er_graph(wl["n"], wl["m"], seed)
+    else:
+        g = synth.grid_graph(wl["width"], wl["height"], wl["k"], seed)
+    rng = np.random.default_rng(seed + 17)
+    if wl["kind"] == "is":
+        g.w = synth.unit_interval_weights(g.n, rng)
+    elif wl["kind"] == "vc":
+        g.w = synth.int_weights(g.n, 1, 10, rng)
+    return g
+
+
+def algorithmic_bytes_per_epoch(wl, g):
+    """Bytes one epoch must move with nothing cached: a structural column j moves
+    8 (column pointers) + 4 nnz_j (row ids) + 8 nnz_j (r read + write) + 8 (x read +
+    write) + 4 (c_j) = 20 + 12 nnz_j; a slack moves 8 (s) + 8 (r) = 16."""
+    n, m = g.n, g.m
+    if wl["kind"] in ("vc", "is"):
+        return 20 * n + 12 * (2 * m) + 16 * m
+    k = wl["k"]
+    nfree_blocks = n - k
+    deg = np.bincount(np.concatenate([g.eu, g.ev]), minlength=n)
+    free = np.ones(n, bool)
+    free[g.terminals] = False
+    xb = k * (20 * nfree_blocks + 12 * 2 * int(deg[free].sum()))
+    zb = m * k * (20 + 12 * 2)
+    sb = 16 * 2 * m * k
+    return xb + zb + sb
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, wl, ws, rank, local):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1311_2661_gb300 import thetis as T
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    g = make_graph(wl, rank)
+    kind = wl["kind"]
+    # inputs resident in HBM
+    eu_d = torch.from_numpy(g.eu).to(dev)
+    ev_d = torch.from_numpy(g.ev).to(dev)
+    wt = g.w if kind != "mc" else g.ce
+    w_d = torch.from_numpy(wt).to(dev)
+    term_d = torch.from_numpy(g.terminals).to(dev) if kind == "mc" else None
+    lab_d = torch.zeros(g.n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def build(eu, ev, w, term):
+        if kind == "vc":
+            return T.thetis_build_vc(g.n, eu, ev, w, seed=0, stream=stream)
+        if kind == "is":
+            return T.thetis_build_is(g.n, eu, ev, w, seed=0, stream=stream)
+        return T.thetis_build_mc(g.n, eu, ev, w, wl["k"], term, seed=0, stream=stream)
+
+    def step(eu, ev, w, term, out, epochs=wl["epochs"], tol=wl["tol"]):
+        h = build(eu, ev, w, term)
+        info = h.solve(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"])
+        lab, rinfo = h.round(seed=11, reps=wl["reps"], out=out)
+        assert rinfo["valid"], "rounded solution failed the exact validity check"
+        h.close()
+        return info, rinfo
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(eu_d, ev_d, w_d, term_d, lab_d)
+    torch.cuda.synchronize()
+
+    # timed region: device events around every step, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    l0 = T.thetis_launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+            infos.append(step(eu_d, ev_d, w_d, term_d, lab_d))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = T.thetis_launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    updates = sum(i[0]["updates"] for i in infos)
+    updates_all = sum_over_ranks(float(updates), ws, dev)
+    value = updates_all / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the colour-class step, one epoch graph)
+    bpe = algorithmic_bytes_per_epoch(wl, g)
+    ep_ms = sum(i[0]["epoch_ms"] for i in infos)
+    ep_n = sum(i[0]["epochs_run"] for i in infos)
+    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
+    pk, pk_kind = peaks()
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    eu_h = torch.from_numpy(g.eu).pin_memory()
+    ev_h = torch.from_numpy(g.ev).pin_memory()
+    w_h = torch.from_numpy(wt).pin_memory()
+    term_h = torch.from_numpy(g.terminals).pin_memory() if kind == "mc" else None
+    lab_h = torch.zeros(g.n, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    e_ms = 0.0
+    e_upd = 0
+    for i in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info, _ = step(eu_h, ev_h, w_h, term_h, lab_h)
+        b.record(stream)
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+        e_upd += info["updates"]
+    e_ms = max_over_ranks(e_ms, ws, dev)
+    e_upd_all = sum_over_ranks(float(e_upd), ws, dev)
+    h2d = g.eu.nbytes + g.ev.nbytes + wt.nbytes + (g.terminals.nbytes if kind == "mc" else 0)
+
+    # time to residual 1e-3 (same pipeline, epochs until rho <= 1e-3)
+    ttr = None
+    if args.ttr_epochs > 0:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info, _ = step(eu_d, ev_d, w_d, term_d, lab_d, epochs=args.ttr_epochs, tol=1e-3)
+        b.record(stream)
+        b.synchronize()
+        ttr = {"ms": a.elapsed_time(b), "epochs": info["epochs_run"], "rho": info["rho"],
+               "converged": info["converged"], "solve_ms": info["solve_ms"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, g, args.cpu_epochs)
+
+    info0 = infos[-1][0]
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "coord_updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP64 refresh/checks)",
+        "data": "synthetic (seeded Chung-Lu / ER / grid stand-ins for the paper's graphs)",
+        "config": {"workload": args.workload, "kind": kind, "n": g.n, "m": g.m,
+                   "free_coords": infos[-1][0]["updates"] // max(1, infos[-1][0]["epochs_run"]),
+                   "colors": info0["ncolors"], "beta": wl["beta"], "epochs": wl["epochs"],
+                   "refresh_every": wl["refresh"], "reps": wl["reps"], "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 and L2 flushed (2x129 MB write) between steps"},
+        "e2e": {"value": e_upd_all / (e_ms / 1e3), "unit": "coord_updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": g.n + 64},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "k_color_step (one epoch graph)", "bytes_per_epoch": bpe,
+                     "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
+        "cpu_baseline": cpu,
+        "time_to_residual": ttr,
+        "last_step": {"epochs_run": info0["epochs_run"], "rho": info0["rho"], "obj": info0["obj"],
+                      "infeas": info0["infeas"], "solve_ms": info0["solve_ms"],
+                      "rounded_obj": infos[-1][1]["obj"], "step_ms": step_ms[-1],
+                      "launches_per_epoch": info0["launches_per_epoch"]},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_setup(wl, g):
+    import oracle
+
+    oracle.build()
+    lp = oracle.build_problem(wl["kind"], g)
+    col, nc = lp.color(0)
+    return lp, col
+
+
+def cpu_baseline(wl, g, epochs):
+    """The FP64 oracle on one host core: `epochs` SCD epochs of the same
+    instance (standard-form build and colouring are setup, not timed)."""
+    lp, col = _oracle_setup(wl, g)
+    t = time.perf_counter()
+    x, info = lp.solve(beta=wl["beta"], epochs=epochs, refresh_every=wl["refresh"], color=col)
+    dt = time.perf_counter() - t
+    return {"value": epochs * lp.free_coords / dt, "unit": "coord_updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{epochs} FP64 serial SCD epochs of the full instance ({lp.free_coords} coordinates) "
+                      f"incl. the final exact refresh + checks; build and colouring excluded",
+            "seconds": dt}
+
+
+def run_reference(args, wl, ws, rank):
+    if rank != 0:
+        return
+    g = make_graph(wl, 0)
+    lp, col = _oracle_setup(wl, g)
+    x = lp.initial_x()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        x, info = lp.solve(beta=wl["beta"], epochs=1, refresh_every=wl["refresh"], color=col, x0=x)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = len(times) * lp.free_coords / total
+    sample = (f"1 FP64 serial SCD epoch of the full instance per step ({lp.free_coords} coordinates, incl. the "
+              f"exact refresh + checks); build and colouring untimed")
+    res = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "coord_updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total / len(times) * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "kind": wl["kind"], "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": "coord_updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "coord_updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="thetis", choices=["thetis", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--ttr-epochs", type=int, default=3000, help="epoch cap of the time-to-residual run (0: skip)")
+    ap.add_argument("--cpu-epochs", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup(args)
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, ws, rank)
+    else:
+        run_gpu(args, wl, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

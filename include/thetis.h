@@ -123,7 +123,9 @@ typedef struct {
   int32_t ncolors;
   double rho, obj, infeas, fbeta;
   int64_t updates; /* coordinate updates performed (blocks count k) */
-  double solve_ms; /* device time of the solve */
+  double solve_ms; /* device time of the solve (CUDA events on the handle's stream) */
+  double epoch_ms; /* device time inside the epoch sweeps only (no refresh / checks) */
+  int32_t launches_per_epoch; /* kernels one epoch launches */
 } thetis_solve_info;
 
 /* Result of a rounding.

@@ -10,7 +10,7 @@ struct thetis_handle {
   std::unique_ptr<Problem> P;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   int64_t graph_launches = 0;  // kernels per epoch graph replay
   // key of the captured epoch graph
   double g_beta = 0;
@@ -22,6 +22,8 @@ struct thetis_handle {
     }
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (ev2) cudaEventDestroy(ev2);
+    if (ev3) cudaEventDestroy(ev3);
     if (own_stream && stream) {
       cudaStreamSynchronize(stream);
       cudaStreamDestroy(stream);
@@ -99,6 +101,8 @@ void finish_create(thetis_handle* h) {
   init_iterate(*h->P);
   TH_CUDA(cudaEventCreate(&h->ev0));
   TH_CUDA(cudaEventCreate(&h->ev1));
+  TH_CUDA(cudaEventCreate(&h->ev2));
+  TH_CUDA(cudaEventCreate(&h->ev3));
   TH_CUDA(cudaStreamSynchronize(h->stream));
 }
 
@@ -303,13 +307,24 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     CheckOut co{};
     int ep = 0;
     bool checked_last = false;
+    double sweep_ms = 0.0;
+    bool open = false;
     for (ep = 0; ep < a.epochs;) {
+      if (!open) {
+        TH_CUDA(cudaEventRecord(h->ev2, s));
+        open = true;
+      }
       TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
       count_launch((uint64_t)h->graph_launches);
       ++ep;
       checked_last = false;
       if (ep % a.refresh_every == 0 || ep == a.epochs) {
-        refresh_and_check(P, a, ub, xb, co);
+        TH_CUDA(cudaEventRecord(h->ev3, s));
+        open = false;
+        refresh_and_check(P, a, ub, xb, co);  // synchronises the stream
+        float t = 0.f;
+        TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
+        sweep_ms += t;
         checked_last = true;
         if (co.rho <= a.tol) {
           converged = true;
@@ -333,6 +348,8 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
       info->fbeta = co.fbeta;
       info->updates = (int64_t)ep * P.free_coords;
       info->solve_ms = ms;
+      info->epoch_ms = sweep_ms;
+      info->launches_per_epoch = (int32_t)h->graph_launches;
     }
   });
   if (st != THETIS_OK) return st;

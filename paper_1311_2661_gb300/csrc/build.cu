@@ -10,9 +10,6 @@
 
 namespace thetis {
 
-// Thresholds of the per-colour unit classes (structural units by non-zeros).
-constexpr int64_t T_BIG = 2048;  // more: one CTA per unit
-constexpr int64_t T_MED = 24;    // more: one warp per unit; else 8-lane groups
 
 static int bits_for(int64_t n) {
   int b = 1;
@@ -439,36 +436,180 @@ __device__ __forceinline__ void for_neighbours(const JPView& V, int64_t u, int l
   }
 }
 
-__global__ void k_jp_round(JPView V, const uint32_t* work, const int64_t* nwork, uint32_t* next,
-                           int64_t* nnext, int32_t* color) {
+// Data-flow Jones-Plassmann over an explicit unit adjacency.  adj lists, for
+// every unit u, each occurrence of a conflicting unit w (once per shared row
+// incidence), with bit 31 set when w precedes u in the priority order.
+// cnt[u] = occurrences of higher-priority neighbours still uncoloured.  A unit
+// whose count reaches zero takes the smallest colour none of its (all
+// coloured) higher-priority neighbours holds -- exactly the sequential greedy
+// in priority order -- and releases its lower-priority neighbours.  Units of
+// one frontier are pairwise non-adjacent.
+constexpr uint32_t HIGH_BIT = 0x80000000u;
+constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA serves a unit
+
+__global__ void k_adj_count(JPView V, int64_t U, int64_t* acnt) {
   int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t nw = *nwork;
-  for (int64_t t = warp; t < nw; t += nwarps) {
-    int64_t u = work[t];
-    bool blocked = false;
-    for_neighbours(V, u, lane, [&](int64_t w) {
-      if (!blocked && color[w] < 0 && higher(V, w, u)) blocked = true;
-    });
-    if (__any_sync(0xffffffffu, blocked)) {
-      if (lane == 0) next[atomicAdd((unsigned long long*)nnext, 1ull)] = (uint32_t)u;
-      continue;
+  for (int64_t u = warp; u < U; u += nwarps) {
+    int64_t c = 0;
+    for_neighbours(V, u, lane, [&](int64_t) { ++c; });
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) acnt[u] = c;
+  }
+}
+
+// Members of row i other than unit u, as (unit, count) visited in a fixed
+// order: the structural columns of the row (CSR order), then the row's slack.
+template <class F>
+__device__ __forceinline__ void row_members(const JPView& V, int64_t i, int64_t u, F f) {
+  for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
+    int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
+    if (w >= 0 && w != u) f(w);
+  }
+  int64_t sw = V.slack_unit[i];
+  if (sw >= 0 && sw != u) f(sw);
+}
+
+__device__ __forceinline__ void jp_push(const int64_t* aptr, uint32_t w, uint32_t* next_s, int64_t* nnext_s,
+                                        uint32_t* next_b, int64_t* nnext_b) {
+  if (aptr[w + 1] - aptr[w] > JP_BIG) next_b[atomicAdd((unsigned long long*)nnext_b, 1ull)] = w;
+  else next_s[atomicAdd((unsigned long long*)nnext_s, 1ull)] = w;
+}
+
+// Fill the adjacency lists (deterministic order: the unit's rows in CSC order,
+// inside a row as row_members) and the initial counts; push the units that
+// have no higher-priority neighbour.
+__global__ void k_adj_fill(JPView V, int64_t U, const int64_t* aptr, uint32_t* adj, int32_t* cnt,
+                           uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < U; u += nwarps) {
+    int64_t off = aptr[u];
+    int hi = 0;
+    int64_t p0, p1;
+    bool slack = u >= V.Us;
+    if (!slack) {
+      int64_t f0 = V.ufirst[u];
+      p0 = V.colptr[f0];
+      p1 = V.colptr[f0 + V.ulen[u]];
+    } else {
+      int64_t i = V.slack_row[u - V.Us];
+      p0 = V.rowptr[i];
+      p1 = V.rowptr[i + 1];
     }
-    int base = 0;
-    int chosen = -1;
-    while (chosen < 0) {
-      unsigned long long mask = 0;
-      for_neighbours(V, u, lane, [&](int64_t w) {
-        int cw = color[w];
-        if (cw >= base && cw < base + 64) mask |= 1ull << (cw - base);
-      });
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+      int64_t p = pb + lane;
+      bool act = p < p1;
+      int c = 0;
+      int64_t i = 0, w1 = -1;
+      if (act) {
+        if (!slack) {
+          i = V.rowidx[p];
+          row_members(V, i, u, [&](int64_t) { ++c; });
+        } else {
+          w1 = V.unit_of_col[V.colof[V.csr_p[p]]];
+          c = (w1 >= 0) ? 1 : 0;
+        }
+      }
+      int incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int tot = __shfl_sync(0xffffffffu, incl, 31);
+      int64_t o = off + incl - c;
+      if (act) {
+        auto emit = [&](int64_t w) {
+          bool h = higher(V, w, u);
+          hi += h;
+          adj[o++] = (uint32_t)w | (h ? HIGH_BIT : 0u);
+        };
+        if (!slack) row_members(V, i, u, emit);
+        else if (w1 >= 0) emit(w1);
+      }
+      off += tot;
+    }
+    for (int s2 = 16; s2 > 0; s2 >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, s2);
+    if (lane == 0) {
+      cnt[u] = hi;
+      if (hi == 0) jp_push(aptr, (uint32_t)u, front_s, nfront_s, front_b, nfront_b);
+    }
+  }
+}
+
+// window mask of the colours of the higher-priority entries in adj[a0, a1), lane-strided by `step`
+__device__ __forceinline__ unsigned long long hi_color_mask(const uint32_t* adj, const int32_t* color, int64_t a0,
+                                                            int64_t a1, int64_t start, int step, int base) {
+  unsigned long long m = 0;
+  for (int64_t qb = a0 + start; qb < a1; qb += 4 * (int64_t)step) {
+    uint32_t e[4];
+    int cw[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
-      if (~mask) chosen = base + __ffsll((long long)~mask) - 1;
+    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) cw[t] = (e[t] & HIGH_BIT) ? color[e[t] & ~HIGH_BIT] : -1;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
+  }
+  return m;
+}
+
+__device__ __forceinline__ void release_lower(const uint32_t* adj, const int64_t* aptr, int32_t* cnt, int64_t a0,
+                                              int64_t a1, int64_t start, int step, uint32_t* next_s,
+                                              int64_t* nnext_s, uint32_t* next_b, int64_t* nnext_b) {
+  for (int64_t q = a0 + start; q < a1; q += step) {
+    uint32_t e = adj[q];
+    if (!(e & HIGH_BIT) && atomicSub(&cnt[e], 1) == 1) jp_push(aptr, e, next_s, nnext_s, next_b, nnext_b);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_jp_step(const uint32_t* adj, const int64_t* aptr, int32_t* cnt,
+                                                 int32_t* color, const uint32_t* front_s, const int64_t* nfront_s,
+                                                 const uint32_t* front_b, const int64_t* nfront_b, uint32_t* next_s,
+                                                 int64_t* nnext_s, uint32_t* next_b, int64_t* nnext_b,
+                                                 unsigned long long* done) {
+  __shared__ unsigned long long smask;
+  const int lane = threadIdx.x & 31;
+  const int64_t ns = *nfront_s, nb = *nfront_b;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ns + nb > 0) atomicAdd(done, (unsigned long long)(ns + nb));
+  // big units: one CTA each
+  for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
+    const uint32_t u = front_b[t];
+    const int64_t a0 = aptr[u], a1 = aptr[u + 1];
+    int base = 0, chosen = -1;
+    while (chosen < 0) {
+      if (threadIdx.x == 0) smask = 0;
+      __syncthreads();
+      unsigned long long m = hi_color_mask(adj, color, a0, a1, threadIdx.x, blockDim.x, base);
+      for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+      if (lane == 0 && m) atomicOr(&smask, m);
+      __syncthreads();
+      unsigned long long all = smask;
+      if (~all) chosen = base + __ffsll((long long)~all) - 1;
+      base += 64;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) color[u] = chosen;
+    release_lower(adj, aptr, cnt, a0, a1, threadIdx.x, blockDim.x, next_s, nnext_s, next_b, nnext_b);
+  }
+  // small units: one warp each
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < ns; t += nwarps) {
+    const uint32_t u = front_s[t];
+    const int64_t a0 = aptr[u], a1 = aptr[u + 1];
+    int base = 0, chosen = -1;
+    while (chosen < 0) {
+      unsigned long long m = hi_color_mask(adj, color, a0, a1, lane, 32, base);
+      for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+      if (~m) chosen = base + __ffsll((long long)~m) - 1;
       base += 64;
     }
     if (lane == 0) color[u] = chosen;
+    release_lower(adj, aptr, cnt, a0, a1, lane, 32, next_s, nnext_s, next_b, nnext_b);
   }
 }
 
@@ -498,7 +639,8 @@ __global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const i
   GSTRIDE(u, Us) {
     int cls;
     if (ulen[u] > 1) cls = UC_BLOCK;
-    else if (unnz[u] > T_BIG) cls = UC_BIG;
+    else if (unnz[u] > T_HUGE) cls = UC_HUGE;
+    else if (unnz[u] > T_LARGE) cls = UC_LARGE;
     else if (unnz[u] > T_MED) cls = UC_MED;
     else cls = UC_SMALL;
     uint32_t key = (uint32_t)color[u] * UC_COUNT + cls;
@@ -797,31 +939,53 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   TH_LAUNCHED();
   int32_t* color = tmp.alloc<int32_t>(U + 1);
   TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));
-  uint32_t* wa = tmp.alloc<uint32_t>(U + 1);
-  uint32_t* wb = tmp.alloc<uint32_t>(U + 1);
-  int64_t* cnt2 = tmp.alloc<int64_t>(2);
-  fill_iota_u32(wa, U, s);
-  TH_CUDA(cudaMemcpyAsync(cnt2, &U, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   JPView V{raw.colptr, raw.rowidx, orowptr, csr_p, colof, unit_of_col, slack_unit, ufirst, ulen, unnz, uh, Us, slack_row};
   {
-    int64_t* na = cnt2;
-    int64_t* nb = cnt2 + 1;
-    int64_t left = U;
+    const int jp_grid = 152 * 8;
+    int64_t* aptr = tmp.alloc<int64_t>(U + 1);
+    if (U > 0) {
+      k_adj_count<<<jp_grid, 256, 0, s>>>(V, U, aptr);
+      TH_LAUNCHED();
+    }
+    exclusive_scan_i64(aptr, aptr, U, tmp, s);
+    int64_t nadj = 0;
+    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    uint32_t* adj = tmp.alloc<uint32_t>(nadj + 1);
+    int32_t* jcnt = tmp.alloc<int32_t>(U + 1);
+    uint32_t* fs[2] = {tmp.alloc<uint32_t>(U + 1), tmp.alloc<uint32_t>(U + 1)};
+    uint32_t* fb[2] = {tmp.alloc<uint32_t>(U + 1), tmp.alloc<uint32_t>(U + 1)};
+    int64_t* fc = tmp.alloc<int64_t>(4);  // [s0, b0, s1, b1]
+    unsigned long long* done = tmp.alloc<unsigned long long>(1);
+    TH_CUDA(cudaMemsetAsync(fc, 0, 4 * sizeof(int64_t), s));
+    TH_CUDA(cudaMemsetAsync(done, 0, sizeof(unsigned long long), s));
+    if (U > 0) {
+      k_adj_fill<<<jp_grid, 256, 0, s>>>(V, U, aptr, adj, jcnt, fs[0], fc + 0, fb[0], fc + 1);
+      TH_LAUNCHED();
+    }
+    int cur = 0;
+    int64_t left = U > 0 ? 1 : 0;
     int64_t rounds = 0;
-    const int jp_grid = 152 * 16;
     while (left > 0) {
-      for (int q = 0; q < 8; ++q) {
-        TH_CUDA(cudaMemsetAsync(nb, 0, sizeof(int64_t), s));
-        k_jp_round<<<jp_grid, 256, 0, s>>>(V, wa, na, wb, nb, color);
+      for (int q = 0; q < 16; ++q) {
+        int nx = cur ^ 1;
+        TH_CUDA(cudaMemsetAsync(fc + 2 * nx, 0, 2 * sizeof(int64_t), s));
+        k_jp_step<<<jp_grid, 256, 0, s>>>(adj, aptr, jcnt, color, fs[cur], fc + 2 * cur, fb[cur], fc + 2 * cur + 1,
+                                          fs[nx], fc + 2 * nx, fb[nx], fc + 2 * nx + 1, done);
         TH_LAUNCHED();
-        std::swap(wa, wb);
-        std::swap(na, nb);
+        cur = nx;
         ++rounds;
       }
-      TH_CUDA(cudaMemcpyAsync(&left, na, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      int64_t hc[2];
+      TH_CUDA(cudaMemcpyAsync(hc, fc + 2 * cur, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       TH_CUDA(cudaStreamSynchronize(s));
-      TH_CHECK(rounds <= U + 16, THETIS_E_CUDA, "colouring did not finish");
+      left = hc[0] + hc[1];
+      TH_CHECK(rounds <= U + 32, THETIS_E_CUDA, "colouring did not finish");
     }
+    unsigned long long hdone = 0;
+    TH_CUDA(cudaMemcpyAsync(&hdone, done, sizeof(hdone), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    TH_CHECK((int64_t)hdone == U, THETIS_E_CUDA, "colouring left units uncoloured");
   }
   int* dmax = tmp.alloc<int>(1);
   TH_CUDA(cudaMemsetAsync(dmax, 0xff, sizeof(int), s));

@@ -12,7 +12,9 @@ enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3 };
 // Classes of coordinate units inside one colour.  Units of a colour are stored
 // class by class, so that every class is a contiguous range of units and of
 // internal columns.
-enum UnitClass { UC_BLOCK = 0, UC_BIG = 1, UC_MED = 2, UC_SMALL = 3, UC_COUNT = 4 };
+enum UnitClass { UC_BLOCK = 0, UC_HUGE = 1, UC_LARGE = 2, UC_MED = 3, UC_SMALL = 4, UC_COUNT = 5 };
+// non-zero thresholds of the singleton classes (more than T_HUGE: HUGE, ...)
+constexpr int64_t T_HUGE = 1024, T_LARGE = 128, T_MED = 32;
 
 struct Seg {
   int cls;        // UnitClass

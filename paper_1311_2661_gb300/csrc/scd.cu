@@ -66,30 +66,42 @@ __device__ __forceinline__ void r_add(const StepView& V, uint32_t row, float cac
 }
 
 // One projected step of singleton column j by G cooperating lanes (G a power of
-// two <= 32) -- or by a whole CTA when G == STEP_T.
-template <int G>
+// two <= 32) -- or by a whole CTA when G == STEP_T.  Each lane keeps the first
+// NC residual values it gathers in registers and writes them back after the
+// step; the rest (columns longer than NC*G) are gathered and re-read in
+// batches of four independent loads.
+template <int G, int NC>
 __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int lane, float* red_smem,
                                             bool valid = true) {
   const int64_t p0 = valid ? V.colptr[j] : 0, p1 = valid ? V.colptr[j + 1] : 0;
-  uint32_t ce[CACHE];
-  float cr[CACHE];
+  uint32_t ce[NC];
+  float cr[NC];
   float acc = 0.f;
 #pragma unroll
-  for (int t = 0; t < CACHE; ++t) {
+  for (int t = 0; t < NC; ++t) {
     int64_t p = p0 + lane + (int64_t)t * G;
-    ce[t] = 0;
-    cr[t] = 0.f;
-    if (p < p1) {
-      uint32_t e = V.rowidx[p];
-      float rr = V.r[rowof(V, e)];
-      ce[t] = e;
-      cr[t] = rr;
-      acc = fmaf(coef(V, p, e), rr, acc);
-    }
+    ce[t] = (p < p1) ? V.rowidx[p] : 0u;
   }
-  for (int64_t p = p0 + lane + (int64_t)CACHE * G; p < p1; p += G) {
-    uint32_t e = V.rowidx[p];
-    acc = fmaf(coef(V, p, e), V.r[rowof(V, e)], acc);
+#pragma unroll
+  for (int t = 0; t < NC; ++t) {
+    int64_t p = p0 + lane + (int64_t)t * G;
+    cr[t] = (p < p1) ? V.r[rowof(V, ce[t])] : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NC; ++t) {
+    int64_t p = p0 + lane + (int64_t)t * G;
+    if (p < p1) acc = fmaf(coef(V, p, ce[t]), cr[t], acc);
+  }
+  for (int64_t pb = p0 + lane + (int64_t)NC * G; pb < p1; pb += 4 * G) {
+    uint32_t e4[4];
+    float r4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) e4[t] = (pb + t * G < p1) ? V.rowidx[pb + t * G] : 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? V.r[rowof(V, e4[t])] : 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (pb + t * G < p1) acc = fmaf(coef(V, pb + t * G, e4[t]), r4[t], acc);
   }
   // reduce over the G lanes
   if (G <= 32) {
@@ -125,16 +137,22 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
   if (lane == 0) V.x[j] = xn;
   if (d != 0.f) {
 #pragma unroll
-    for (int t = 0; t < CACHE; ++t) {
+    for (int t = 0; t < NC; ++t) {
       int64_t p = p0 + lane + (int64_t)t * G;
       if (p < p1) r_add(V, rowof(V, ce[t]), cr[t], coef(V, p, ce[t]) * d);
     }
-    for (int64_t p = p0 + lane + (int64_t)CACHE * G; p < p1; p += G) {
-      uint32_t e = V.rowidx[p];
-      uint32_t row = rowof(V, e);
-      float delta = coef(V, p, e) * d;
-      if (V.async) atomicAdd(&V.r[row], delta);
-      else V.r[row] += delta;
+    for (int64_t pb = p0 + lane + (int64_t)NC * G; pb < p1; pb += 4 * G) {
+      uint32_t e4[4];
+      float r4[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) e4[t] = (pb + t * G < p1) ? V.rowidx[pb + t * G] : 0u;
+      if (!V.async) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? V.r[rowof(V, e4[t])] : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (pb + t * G < p1) r_add(V, rowof(V, e4[t]), r4[t], coef(V, pb + t * G, e4[t]) * d);
     }
   }
   if (G > 32) __syncthreads();
@@ -250,13 +268,17 @@ __global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch C
   const int64_t b = blockIdx.x - S.b0;
   const int lane = threadIdx.x & 31;
   switch (S.cls) {
-    case UC_BIG: {
-      if (b < S.n) step_column<STEP_T>(V, S.c0 + b, threadIdx.x, red_smem);
+    case UC_HUGE: {
+      if (b < S.n) step_column<STEP_T, 16>(V, S.c0 + b, threadIdx.x, red_smem);
+      break;
+    }
+    case UC_LARGE: {
+      if (b < S.n) step_column<STEP_T, 4>(V, S.c0 + b, threadIdx.x, red_smem);
       break;
     }
     case UC_MED: {
       int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
-      if (u < S.n) step_column<32>(V, S.c0 + u, lane, red_smem);
+      if (u < S.n) step_column<32, 4>(V, S.c0 + u, lane, red_smem);
       break;
     }
     case UC_SMALL: {
@@ -264,7 +286,7 @@ __global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch C
       // every lane of the warp joins the group shuffles; groups past the end idle
       bool in = u < S.n;
       if (__any_sync(0xffffffffu, in))
-        step_column<GROUP_SMALL>(V, S.c0 + (in ? u : 0), threadIdx.x % GROUP_SMALL, red_smem, in);
+        step_column<GROUP_SMALL, 4>(V, S.c0 + (in ? u : 0), threadIdx.x % GROUP_SMALL, red_smem, in);
       break;
     }
     case UC_BLOCK: {
@@ -282,7 +304,8 @@ __global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch C
 
 static int64_t ctas_for(int cls, int64_t n) {
   switch (cls) {
-    case UC_BIG: return n;
+    case UC_HUGE:
+    case UC_LARGE: return n;
     case UC_MED:
     case UC_BLOCK: return (n + STEP_T / 32 - 1) / (STEP_T / 32);
     case UC_SMALL: return (n + STEP_T / GROUP_SMALL - 1) / (STEP_T / GROUP_SMALL);

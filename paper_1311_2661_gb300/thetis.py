@@ -53,7 +53,8 @@ class Params(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("epochs_run", C.c_int32), ("converged", C.c_int32), ("ncolors", C.c_int32),
                 ("rho", C.c_double), ("obj", C.c_double), ("infeas", C.c_double), ("fbeta", C.c_double),
-                ("updates", C.c_int64), ("solve_ms", C.c_double)]
+                ("updates", C.c_int64), ("solve_ms", C.c_double), ("epoch_ms", C.c_double),
+                ("launches_per_epoch", C.c_int32)]
 
 
 class RoundInfo(C.Structure):
@@ -264,7 +265,7 @@ def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step
     st = _check(_lib.thetis_solve(h.ptr, C.byref(p), C.byref(info)), allow=(THETIS_OK, THETIS_NOT_CONVERGED))
     return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
                 rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
-                solve_ms=info.solve_ms)
+                solve_ms=info.solve_ms, epoch_ms=info.epoch_ms, launches_per_epoch=info.launches_per_epoch)
 
 
 def thetis_round(h: Handle, kind, seed=0, reps=10, out=None):

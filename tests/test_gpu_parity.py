@@ -23,6 +23,7 @@ CASES = [
     ("vc", lambda: vc_graph(2000, 8000, 1)),
     ("is", lambda: is_graph(3000, 20000, 2)),
     ("vc", lambda: hub_graph(5000, 12000, 2600, 3)),
+    ("is", lambda: hub_graph(6000, 9000, 4500, 6)),
     ("mc", lambda: synth.grid_graph(37, 23, 4, 4)),
     ("mc", lambda: synth.grid_graph(16, 16, 8, 5)),
 ]
