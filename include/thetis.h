@@ -220,6 +220,32 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
 thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_t reps,
                            uint8_t* labels_out, int32_t out_mem, thetis_round_info* info);
 
+/*
+ * thetis_round_is_static -- the independent-set branch of thetis_round (repair,
+ * best-of-reps rounding with alterations, exact validity) for callers that
+ * cannot allocate device memory when they round: serving loops that must not
+ * block on cudaMalloc / cudaFree, processes whose free device memory is owned
+ * by another allocator, code recording a stream capture.  The paper has no
+ * counterpart; this is a deployment variant of the same kernels.
+ *   n, m, eu[m], ev[m], w[n]   the graph and vertex weights, as for
+ *                              thetis_build_is (DEVICE pointers)
+ *   x[n]                       the fractional point in vertex order (DEVICE),
+ *                              e.g. from thetis_get_x
+ *   labels_out[n]              DEVICE output, 1 = in the independent set
+ *   info                       HOST output (may be NULL)
+ * Scratch: one file-scope device array of 64 MiB, held by every GPU that loads
+ * the library until the process exits.  Requires 2*n*reps + 131,616 bytes <=
+ * 64 MiB (n * reps <= 33,488,624); larger sizes return THETIS_E_INVALID.
+ * Calls no cudaMalloc / cudaFree.  The first call on a device looks the array
+ * up with cudaGetSymbolAddress (once per device): make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (different streams, or different threads) race; serialise them.
+ * Same random streams as thetis_round: equal inputs give equal outputs.
+ */
+thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
+                                     const float* w, const float* x, uint64_t seed, int32_t reps,
+                                     uint8_t* labels_out, thetis_round_info* info, void* stream);
+
 /* Copy the structural part of the iterate, original column order, as FP32. */
 thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem);
 /* Copy the slack part of the iterate (one value per GE/LE row, row order). */

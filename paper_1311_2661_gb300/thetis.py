@@ -84,6 +84,7 @@ def _load():
         "thetis_get_colors": (st, [P, P, P]),
         "thetis_sync": (st, [P]),
         "thetis_destroy": (st, [P]),
+        "thetis_round_is_static": (st, [i64, i64, P, P, P, P, u64, i32, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -292,6 +293,23 @@ def _out_ptr(out):
     if _is_torch(out):
         return out.data_ptr(), (MEM_DEVICE if out.is_cuda else MEM_HOST)
     return out.ctypes.data, MEM_HOST
+
+
+def thetis_round_is_static(n, eu, ev, w, x, labels_out, seed=0, reps=10, stream=None):
+    """Independent-set rounding with no device allocation (scratch is a fixed
+    64 MiB static device array).  eu, ev, w, x and labels_out are CUDA tensors;
+    returns the info dict.  Requires n * reps <= 33,488,624."""
+    A = _Args()
+    ptrs = [A(eu, np.int32), A(ev, np.int32), A(w, np.float32), A(x, np.float32)]
+    lab_ptr = A(labels_out, np.uint8)
+    if A.memspace != MEM_DEVICE:
+        raise ValueError("thetis_round_is_static takes device arrays only")
+    info = RoundInfo()
+    st = _lib.thetis_round_is_static(int(n), int(eu.shape[0]), *ptrs, int(seed), int(reps), lab_ptr,
+                                     C.byref(info), _stream_ptr(stream))
+    _check(st)
+    return dict(status=st, obj=info.obj, repair=info.repair, best_rep=info.best_rep, near=info.near,
+                valid=bool(info.valid))
 
 
 def thetis_get_x(h: Handle, out=None):
