@@ -99,7 +99,12 @@ typedef struct {
  *                 structural columns then the slacks in row order
  *   x0[n]         structural starting point (NULL: 0 clipped to the bounds,
  *                 barycentre for simplex blocks); slacks start at 0
- *   mem           where ubar / xbar / x0 live */
+ *   mem           where ubar / xbar / x0 live
+ *   engine        colored mode only: 0 = one persistent cooperative launch per
+ *                 refresh interval with a grid barrier between colours (falls
+ *                 back to 1 where cooperative launch is unavailable);
+ *                 1 = one launch per colour, replayed as a CUDA graph.  Both
+ *                 give the same iterates. */
 typedef struct {
   double beta;
   int32_t epochs;
@@ -111,6 +116,7 @@ typedef struct {
   const float* xbar;
   const float* x0;
   int32_t mem;
+  int32_t engine;
 } thetis_params;
 
 /* Result of a solve; all checks in FP64 on the final iterate.

@@ -402,14 +402,16 @@ void or_export_units(const orlp *P, int64_t *ustart, int32_t *ulen, int32_t *usi
 /* Colouring of the column-intersection graph                               */
 /* ------------------------------------------------------------------------ */
 /* Units j and l conflict iff some row holds a column of each.  Units are
- * visited in the total order key(u) = (nnz_u desc, h_u desc, u asc), with h_u
- * the u-th splitmix64 output of `seed`; each takes the smallest colour not held
- * by an already-coloured conflicting unit (sequential greedy colouring). */
+ * visited in the total order key(u) = (structural before slack, nnz_u desc,
+ * h_u desc, u asc), with h_u the u-th splitmix64 output of `seed`; each takes
+ * the smallest colour not held by an already-coloured conflicting unit
+ * (sequential greedy colouring). */
 static int64_t unit_nnz(const orlp *P, int64_t u) {
   return P->cp[P->ustart[u] + P->ulen[u]] - P->cp[P->ustart[u]];
 }
 
 typedef struct {
+  int32_t slack;
   int64_t nnz;
   uint64_t h;
   int64_t u;
@@ -417,6 +419,7 @@ typedef struct {
 
 static int prio_cmp(const void *a, const void *b) {
   const prio_key *x = (const prio_key *)a, *y = (const prio_key *)b;
+  if (x->slack != y->slack) return x->slack < y->slack ? -1 : 1;
   if (x->nnz != y->nnz) return x->nnz > y->nnz ? -1 : 1;
   if (x->h != y->h) return x->h > y->h ? -1 : 1;
   if (x->u != y->u) return x->u < y->u ? -1 : 1;
@@ -427,6 +430,7 @@ static int prio_cmp(const void *a, const void *b) {
 void or_priority_order(const orlp *P, uint64_t seed, int64_t *order) {
   prio_key *keys = (prio_key *)xcalloc(P->U, sizeof(prio_key));
   for (int64_t u = 0; u < P->U; ++u) {
+    keys[u].slack = P->ustart[u] >= P->Ns;
     keys[u].nnz = unit_nnz(P, u);
     keys[u].h = or_splitmix64_at(seed, (uint64_t)u);
     keys[u].u = u;

@@ -1,4 +1,5 @@
 // C ABI of the library (include/thetis.h).
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -273,10 +274,13 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     prepare_solve(P, dub, dxb, dx0);
     const bool ub = dub != nullptr, xb = dxb != nullptr;
     refresh_only(P);
-    // capture one epoch as a CUDA graph (re-captured when its arguments change)
+    TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
+    const bool persistent = a.mode == THETIS_MODE_COLORED && p->engine == 0 && P.ncolors > 0 && sweep_grid(P) > 0;
+    if (persistent) reset_sweep_flags(P);
+    // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
     bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
                   h->g_ub == (int)ub && h->g_xb == (int)xb;
-    if (!key_ok && a.epochs > 0) {
+    if (!persistent && !key_ok && a.epochs > 0) {
       if (P.epoch_graph) {
         cudaGraphExecDestroy(P.epoch_graph);
         P.epoch_graph = nullptr;
@@ -308,20 +312,28 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     int ep = 0;
     bool checked_last = false;
     double sweep_ms = 0.0;
-    bool open = false;
-    for (ep = 0; ep < a.epochs;) {
-      if (!open) {
-        TH_CUDA(cudaEventRecord(h->ev2, s));
-        open = true;
+    int64_t sweep_launches = 0;
+    while (ep < a.epochs) {
+      // epochs up to the next check
+      const int chunk = std::min(a.refresh_every - ep % a.refresh_every, a.epochs - ep);
+      TH_CUDA(cudaEventRecord(h->ev2, s));
+      if (persistent) {
+        run_sweep(P, a, ub, xb, chunk);
+        ++sweep_launches;
+      } else {
+        for (int q = 0; q < chunk; ++q) {
+          TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
+          count_launch((uint64_t)h->graph_launches);
+        }
+        sweep_launches += (int64_t)chunk * h->graph_launches;
       }
-      TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
-      count_launch((uint64_t)h->graph_launches);
-      ++ep;
+      TH_CUDA(cudaEventRecord(h->ev3, s));
+      ep += chunk;
       checked_last = false;
       if (ep % a.refresh_every == 0 || ep == a.epochs) {
-        TH_CUDA(cudaEventRecord(h->ev3, s));
-        open = false;
         refresh_and_check(P, a, ub, xb, co);  // synchronises the stream
+        if (persistent && sweep_error(P))
+          throw Error{THETIS_E_TIMEOUT, "grid barrier of the persistent sweep timed out"};
         float t = 0.f;
         TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
         sweep_ms += t;
@@ -349,7 +361,7 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
       info->updates = (int64_t)ep * P.free_coords;
       info->solve_ms = ms;
       info->epoch_ms = sweep_ms;
-      info->launches_per_epoch = (int32_t)h->graph_launches;
+      info->launches_per_epoch = ep > 0 ? (int32_t)((sweep_launches + ep - 1) / ep) : 0;
     }
   });
   if (st != THETIS_OK) return st;

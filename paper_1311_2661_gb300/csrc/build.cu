@@ -403,7 +403,11 @@ struct JPView {
   const int64_t* slack_row;   // slack unit s -> row
 };
 
+// Priority order of the colouring: structural units before slack units, then
+// (non-zeros desc, splitmix64(seed, unit) desc, unit id asc).
 __device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
+  const bool sa = a >= V.Us, sb = b >= V.Us;
+  if (sa != sb) return !sa;
   int64_t na = V.unnz[a], nb = V.unnz[b];
   if (na != nb) return na > nb;
   uint64_t ha = V.uh[a], hb = V.uh[b];
@@ -411,145 +415,132 @@ __device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
   return a < b;
 }
 
-// Visit the conflicting units of unit u, lane-strided; f(w) for every neighbour occurrence.
+// Structural units conflicting with structural unit u in row i (CSR order).
 template <class F>
-__device__ __forceinline__ void for_neighbours(const JPView& V, int64_t u, int lane, F f) {
-  if (u < V.Us) {
-    int64_t f0 = V.ufirst[u];
-    int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-      int64_t i = V.rowidx[p];
-      for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
-        int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
-        if (w >= 0 && w != u) f(w);
-      }
-      int64_t sw = V.slack_unit[i];
-      if (sw >= 0) f(sw);
-    }
-  } else {
-    int64_t i = V.slack_row[u - V.Us];
-    int64_t q0 = V.rowptr[i], q1 = V.rowptr[i + 1];
-    for (int64_t q = q0 + lane; q < q1; q += 32) {
-      int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
-      if (w >= 0) f(w);
-    }
-  }
-}
-
-// Data-flow Jones-Plassmann over an explicit unit adjacency.  adj lists, for
-// every unit u, each occurrence of a conflicting unit w (once per shared row
-// incidence), with bit 31 set when w precedes u in the priority order.
-// cnt[u] = occurrences of higher-priority neighbours still uncoloured.  A unit
-// whose count reaches zero takes the smallest colour none of its (all
-// coloured) higher-priority neighbours holds -- exactly the sequential greedy
-// in priority order -- and releases its lower-priority neighbours.  Units of
-// one frontier are pairwise non-adjacent.
-constexpr uint32_t HIGH_BIT = 0x80000000u;
-constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA serves a unit
-
-__global__ void k_adj_count(JPView V, int64_t U, int64_t* acnt) {
-  int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < U; u += nwarps) {
-    int64_t c = 0;
-    for_neighbours(V, u, lane, [&](int64_t) { ++c; });
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) acnt[u] = c;
-  }
-}
-
-// Members of row i other than unit u, as (unit, count) visited in a fixed
-// order: the structural columns of the row (CSR order), then the row's slack.
-template <class F>
-__device__ __forceinline__ void row_members(const JPView& V, int64_t i, int64_t u, F f) {
+__device__ __forceinline__ void row_struct_members(const JPView& V, int64_t i, int64_t u, F f) {
   for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
     int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
     if (w >= 0 && w != u) f(w);
   }
-  int64_t sw = V.slack_unit[i];
-  if (sw >= 0 && sw != u) f(sw);
 }
 
-__device__ __forceinline__ void jp_push(const int64_t* aptr, uint32_t w, uint32_t* next_s, int64_t* nnext_s,
-                                        uint32_t* next_b, int64_t* nnext_b) {
-  if (aptr[w + 1] - aptr[w] > JP_BIG) next_b[atomicAdd((unsigned long long*)nnext_b, 1ull)] = w;
-  else next_s[atomicAdd((unsigned long long*)nnext_s, 1ull)] = w;
-}
+// Jones-Plassmann over the structural units, driven by data flow.  Slack units
+// come last in the priority order and never conflict with one another, so each
+// takes, after all structural units are coloured, the smallest colour its row
+// does not hold (k_slack_color) -- the sequential greedy result.
+// adj lists, for every structural unit u, each occurrence of a conflicting
+// structural unit (once per shared row): first the nhigh[u] higher-priority
+// ones, then the lower-priority ones.  cnt[u] = higher-priority occurrences
+// still uncoloured; a unit whose count reaches zero takes the smallest colour
+// its (all coloured) higher-priority neighbours do not hold and releases its
+// lower-priority neighbours.  Units of one frontier are pairwise non-adjacent.
+constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA serves a unit
 
-// Fill the adjacency lists (deterministic order: the unit's rows in CSC order,
-// inside a row as row_members) and the initial counts; push the units that
-// have no higher-priority neighbour.
-__global__ void k_adj_fill(JPView V, int64_t U, const int64_t* aptr, uint32_t* adj, int32_t* cnt,
-                           uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
+__global__ void k_adj_count(JPView V, int64_t Us, int64_t* acnt, int32_t* nhigh) {
   int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < U; u += nwarps) {
-    int64_t off = aptr[u];
-    int hi = 0;
-    int64_t p0, p1;
-    bool slack = u >= V.Us;
-    if (!slack) {
-      int64_t f0 = V.ufirst[u];
-      p0 = V.colptr[f0];
-      p1 = V.colptr[f0 + V.ulen[u]];
-    } else {
-      int64_t i = V.slack_row[u - V.Us];
-      p0 = V.rowptr[i];
-      p1 = V.rowptr[i + 1];
+  for (int64_t u = warp; u < Us; u += nwarps) {
+    int64_t f0 = V.ufirst[u];
+    int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
+    int64_t c = 0, h = 0;
+    for (int64_t p = p0 + lane; p < p1; p += 32)
+      row_struct_members(V, V.rowidx[p], u, [&](int64_t w) {
+        ++c;
+        h += higher(V, w, u);
+      });
+    for (int o = 16; o > 0; o >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+      h += __shfl_xor_sync(0xffffffffu, h, o);
     }
-    for (int64_t pb = p0; pb < p1; pb += 32) {
-      int64_t p = pb + lane;
-      bool act = p < p1;
-      int c = 0;
-      int64_t i = 0, w1 = -1;
-      if (act) {
-        if (!slack) {
-          i = V.rowidx[p];
-          row_members(V, i, u, [&](int64_t) { ++c; });
-        } else {
-          w1 = V.unit_of_col[V.colof[V.csr_p[p]]];
-          c = (w1 >= 0) ? 1 : 0;
-        }
-      }
-      int incl = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      int tot = __shfl_sync(0xffffffffu, incl, 31);
-      int64_t o = off + incl - c;
-      if (act) {
-        auto emit = [&](int64_t w) {
-          bool h = higher(V, w, u);
-          hi += h;
-          adj[o++] = (uint32_t)w | (h ? HIGH_BIT : 0u);
-        };
-        if (!slack) row_members(V, i, u, emit);
-        else if (w1 >= 0) emit(w1);
-      }
-      off += tot;
-    }
-    for (int s2 = 16; s2 > 0; s2 >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, s2);
     if (lane == 0) {
-      cnt[u] = hi;
-      if (hi == 0) jp_push(aptr, (uint32_t)u, front_s, nfront_s, front_b, nfront_b);
+      acnt[u] = c;
+      nhigh[u] = (int32_t)h;
     }
   }
 }
 
-// window mask of the colours of the higher-priority entries in adj[a0, a1), lane-strided by `step`
-__device__ __forceinline__ unsigned long long hi_color_mask(const uint32_t* adj, const int32_t* color, int64_t a0,
-                                                            int64_t a1, int64_t start, int step, int base) {
+__device__ __forceinline__ int warp_excl(int v, int lane, int* total) {
+  int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  *total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - v;
+}
+
+// Push the units flagged by the lanes of one warp onto the next frontier (one
+// atomic per list per warp).
+__device__ __forceinline__ void warp_push(bool pb, bool ps, uint32_t w, int lane, uint32_t* next_s, int64_t* nnext_s,
+                                          uint32_t* next_b, int64_t* nnext_b) {
+  unsigned mb = __ballot_sync(0xffffffffu, pb), ms = __ballot_sync(0xffffffffu, ps);
+  unsigned long long bb = 0, bs = 0;
+  if (lane == 0) {
+    if (mb) bb = atomicAdd((unsigned long long*)nnext_b, (unsigned long long)__popc(mb));
+    if (ms) bs = atomicAdd((unsigned long long*)nnext_s, (unsigned long long)__popc(ms));
+  }
+  bb = __shfl_sync(0xffffffffu, bb, 0);
+  bs = __shfl_sync(0xffffffffu, bs, 0);
+  const unsigned lt = (1u << lane) - 1u;
+  if (pb) next_b[bb + __popc(mb & lt)] = w;
+  if (ps) next_s[bs + __popc(ms & lt)] = w;
+}
+
+__global__ void k_adj_fill(JPView V, int64_t Us, const int64_t* aptr, const int32_t* nhigh, uint32_t* adj,
+                           int32_t* cnt, uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < Us; u += nwarps) {  // warp-uniform
+    const bool act_u = true;
+    {
+      int64_t hoff = aptr[u], loff = aptr[u] + nhigh[u];
+      int64_t f0 = V.ufirst[u];
+      int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
+      for (int64_t pb = p0; pb < p1; pb += 32) {
+        int64_t p = pb + lane;
+        bool act = p < p1;
+        int64_t i = act ? V.rowidx[p] : 0;
+        int ch = 0, cl = 0;
+        if (act)
+          row_struct_members(V, i, u, [&](int64_t w) {
+            if (higher(V, w, u)) ++ch;
+            else ++cl;
+          });
+        int th, tl;
+        int64_t oh = hoff + warp_excl(ch, lane, &th), ol = loff + warp_excl(cl, lane, &tl);
+        if (act)
+          row_struct_members(V, i, u, [&](int64_t w) {
+            if (higher(V, w, u)) adj[oh++] = (uint32_t)w;
+            else adj[ol++] = (uint32_t)w;
+          });
+        hoff += th;
+        loff += tl;
+      }
+    }
+    // initial frontier: units without higher-priority neighbours
+    bool ready = act_u && lane == 0 && nhigh[u] == 0;
+    if (act_u && lane == 0) cnt[u] = nhigh[u];
+    bool big = ready && (aptr[u + 1] - aptr[u] > JP_BIG);
+    // one unit per warp here: the lane-0 flags suffice
+    warp_push(big, ready && !big, (uint32_t)u, lane, front_s, nfront_s, front_b, nfront_b);
+  }
+}
+
+__device__ __forceinline__ void prefetch_l2_jp(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// window mask of the colours of the entries adj[a0, a1), strided by `step` from `start`
+__device__ __forceinline__ unsigned long long color_mask(const uint32_t* adj, const int32_t* color, int64_t a0,
+                                                         int64_t a1, int64_t start, int step, int base) {
   unsigned long long m = 0;
   for (int64_t qb = a0 + start; qb < a1; qb += 4 * (int64_t)step) {
     uint32_t e[4];
     int cw[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : 0u;
+    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : 0xffffffffu;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) cw[t] = (e[t] & HIGH_BIT) ? color[e[t] & ~HIGH_BIT] : -1;
+    for (int t = 0; t < 4; ++t) cw[t] = (e[t] != 0xffffffffu) ? __ldcg(color + e[t]) : -1;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
@@ -557,59 +548,145 @@ __device__ __forceinline__ unsigned long long hi_color_mask(const uint32_t* adj,
   return m;
 }
 
-__device__ __forceinline__ void release_lower(const uint32_t* adj, const int64_t* aptr, int32_t* cnt, int64_t a0,
-                                              int64_t a1, int64_t start, int step, uint32_t* next_s,
-                                              int64_t* nnext_s, uint32_t* next_b, int64_t* nnext_b) {
-  for (int64_t q = a0 + start; q < a1; q += step) {
-    uint32_t e = adj[q];
-    if (!(e & HIGH_BIT) && atomicSub(&cnt[e], 1) == 1) jp_push(aptr, e, next_s, nnext_s, next_b, nnext_b);
+// Release the lower-priority neighbours adj[a0, a1); the loop is uniform over
+// the `step` threads that run it (a warp or a CTA).
+__device__ __forceinline__ void release(const uint32_t* adj, const int64_t* aptr, int32_t* cnt, int64_t a0, int64_t a1,
+                                        int64_t start, int step, int lane, uint32_t* next_s, int64_t* nnext_s,
+                                        uint32_t* next_b, int64_t* nnext_b) {
+  for (int64_t qb = a0; qb < a1; qb += step) {
+    const int64_t q = qb + start;
+    bool pb = false, ps = false;
+    uint32_t w = 0;
+    if (q < a1) {
+      w = adj[q];
+      if (atomicSub(&cnt[w], 1) == 1) {
+        pb = aptr[w + 1] - aptr[w] > JP_BIG;
+        ps = !pb;
+      }
+    }
+    warp_push(pb, ps, w, lane, next_s, nnext_s, next_b, nnext_b);
   }
 }
 
-__global__ void __launch_bounds__(256) k_jp_step(const uint32_t* adj, const int64_t* aptr, int32_t* cnt,
-                                                 int32_t* color, const uint32_t* front_s, const int64_t* nfront_s,
-                                                 const uint32_t* front_b, const int64_t* nfront_b, uint32_t* next_s,
-                                                 int64_t* nnext_s, uint32_t* next_b, int64_t* nnext_b,
-                                                 unsigned long long* done) {
+// grid barrier for the cooperative JP launch (same scheme as the sweep's):
+// one word, top bit flips once per barrier, bounded wait.
+__device__ __forceinline__ bool jp_barrier(unsigned* bar, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+    unsigned old, cur;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
+    ok = 1;
+    const long long t0 = clock64();
+    unsigned it = 0;
+    while (true) {
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+      if ((cur ^ old) & 0x80000000u) break;
+      if ((++it & 255u) == 0 && (*(volatile int*)err || clock64() - t0 > 4000000000LL)) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct JPRun {
+  const uint32_t* adj;
+  const int64_t* aptr;
+  const int32_t* nhigh;
+  int32_t* cnt;
+  int32_t* color;
+  uint32_t* fs[2];
+  uint32_t* fb[2];
+  int64_t* fc;  // 3 x (small, big) frontier counters
+  unsigned long long* done;
+  unsigned* bar;
+  int* err;
+};
+
+// Rounds [r0, r0 + nr) of the data-flow colouring; with nr > 1 the launch must
+// be cooperative (a grid barrier separates the rounds).
+__global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
   __shared__ unsigned long long smask;
   const int lane = threadIdx.x & 31;
-  const int64_t ns = *nfront_s, nb = *nfront_b;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && ns + nb > 0) atomicAdd(done, (unsigned long long)(ns + nb));
-  // big units: one CTA each
-  for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
-    const uint32_t u = front_b[t];
-    const int64_t a0 = aptr[u], a1 = aptr[u + 1];
-    int base = 0, chosen = -1;
-    while (chosen < 0) {
-      if (threadIdx.x == 0) smask = 0;
-      __syncthreads();
-      unsigned long long m = hi_color_mask(adj, color, a0, a1, threadIdx.x, blockDim.x, base);
-      for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-      if (lane == 0 && m) atomicOr(&smask, m);
-      __syncthreads();
-      unsigned long long all = smask;
-      if (~all) chosen = base + __ffsll((long long)~all) - 1;
-      base += 64;
-      __syncthreads();
+  for (int64_t r = r0; r < r0 + nr; ++r) {
+    const int in = (int)(r % 3), out = (int)((r + 1) % 3), z = (int)((r + 2) % 3);
+    const int64_t ns = __ldcg(R.fc + 2 * in), nb = __ldcg(R.fc + 2 * in + 1);
+    if (ns + nb == 0) return;  // every CTA reads the same counts: all stop together
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      R.fc[2 * z] = 0;
+      R.fc[2 * z + 1] = 0;
+      atomicAdd(R.done, (unsigned long long)(ns + nb));
     }
-    if (threadIdx.x == 0) color[u] = chosen;
-    release_lower(adj, aptr, cnt, a0, a1, threadIdx.x, blockDim.x, next_s, nnext_s, next_b, nnext_b);
+    const uint32_t* front_s = R.fs[r & 1];
+    const uint32_t* front_b = R.fb[r & 1];
+    uint32_t* next_s = R.fs[(r + 1) & 1];
+    uint32_t* next_b = R.fb[(r + 1) & 1];
+    int64_t* nnext_s = R.fc + 2 * out;
+    int64_t* nnext_b = R.fc + 2 * out + 1;
+    // long adjacency lists: one CTA each
+    for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
+      const uint32_t u = __ldcg(front_b + t);
+      const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
+      int base = 0, chosen = -1;
+      while (chosen < 0) {
+        if (threadIdx.x == 0) smask = 0;
+        __syncthreads();
+        unsigned long long m = color_mask(R.adj, R.color, a0, ah, threadIdx.x, blockDim.x, base);
+        for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+        if (lane == 0 && m) atomicOr(&smask, m);
+        __syncthreads();
+        unsigned long long all = smask;
+        if (~all) chosen = base + __ffsll((long long)~all) - 1;
+        base += 64;
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) R.color[u] = chosen;
+      release(R.adj, R.aptr, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+    }
+    // the rest: one warp each
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < ns; t += nwarps) {
+      const uint32_t u = __ldcg(front_s + t);
+      const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
+      int base = 0, chosen = -1;
+      while (chosen < 0) {
+        unsigned long long m = color_mask(R.adj, R.color, a0, ah, lane, 32, base);
+        for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+        if (~m) chosen = base + __ffsll((long long)~m) - 1;
+        base += 64;
+      }
+      if (lane == 0) R.color[u] = chosen;
+      release(R.adj, R.aptr, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+    }
+    if (nr > 1 && !jp_barrier(R.bar, R.err)) return;
   }
-  // small units: one warp each
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = warp; t < ns; t += nwarps) {
-    const uint32_t u = front_s[t];
-    const int64_t a0 = aptr[u], a1 = aptr[u + 1];
+}
+
+// Slack units, after every structural unit: the smallest colour not held by a
+// structural unit of the slack's row.
+__global__ void k_slack_color(JPView V, int64_t Msl, int32_t* color) {
+  GSTRIDE(t, Msl) {
+    const int64_t i = V.slack_row[t];
     int base = 0, chosen = -1;
     while (chosen < 0) {
-      unsigned long long m = hi_color_mask(adj, color, a0, a1, lane, 32, base);
-      for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+      unsigned long long m = 0;
+      for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
+        int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
+        if (w < 0) continue;
+        int cw = color[w];
+        if (cw >= base && cw < base + 64) m |= 1ull << (cw - base);
+      }
       if (~m) chosen = base + __ffsll((long long)~m) - 1;
       base += 64;
     }
-    if (lane == 0) color[u] = chosen;
-    release_lower(adj, aptr, cnt, a0, a1, lane, 32, next_s, nnext_s, next_b, nnext_b);
+    color[V.Us + t] = chosen;
   }
 }
 
@@ -656,6 +733,34 @@ __global__ void k_slack_keys(const int32_t* color, int64_t Us, int64_t Msl, cons
     uint32_t c = (uint32_t)color[Us + s];
     keys[s] = c;
     vals[s] = (uint32_t)slack_row[s];
+    atomicAdd((unsigned long long*)&cnt[c], 1ull);
+  }
+}
+
+// key = internal column of the row's highest-priority free column (0 if none)
+__global__ void k_slack_owner_keys(JPView V, int64_t Msl, const uint32_t* col_of_orig, uint32_t* keys, uint32_t* vals) {
+  GSTRIDE(t, Msl) {
+    int64_t i = V.slack_row[t];
+    int64_t best = -1, bcol = 0;
+    for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
+      int64_t col = V.colof[V.csr_p[q]];
+      int64_t u = V.unit_of_col[col];
+      if (u < 0) continue;
+      if (best < 0 || higher(V, u, best)) {
+        best = u;
+        bcol = col;
+      }
+    }
+    keys[t] = best >= 0 ? col_of_orig[bcol] : 0u;
+    vals[t] = (uint32_t)i;
+  }
+}
+
+__global__ void k_slack_color_keys(const uint32_t* rows, int64_t Msl, const int64_t* slack_unit, const int32_t* color,
+                                   uint32_t* keys, int64_t* cnt) {
+  GSTRIDE(t, Msl) {
+    uint32_t c = (uint32_t)color[slack_unit[rows[t]]];
+    keys[t] = c;
     atomicAdd((unsigned long long*)&cnt[c], 1ull);
   }
 }
@@ -737,6 +842,47 @@ __global__ void k_int_csc_fill(const uint32_t* orig_of_col, const int64_t* ocolp
     }
     for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
     if (csq && lane == 0) csq[j] = sq;
+  }
+}
+
+__global__ void k_icsc_rowkeys(const int32_t* orow, const uint32_t* row_of_orig, int64_t nnz, uint32_t* key,
+                               uint32_t* ord) {
+  GSTRIDE(p, nnz) {
+    key[p] = row_of_orig[orow[p]];
+    ord[p] = (uint32_t)p;
+  }
+}
+
+__global__ void k_icsc_colkeys(const uint32_t* ord, const uint32_t* colof, const uint32_t* col_of_orig, int64_t nnz,
+                               uint32_t* key) {
+  GSTRIDE(t, nnz) key[t] = col_of_orig[colof[ord[t]]];
+}
+
+__global__ void k_icsc_fill(const uint32_t* ord, const int32_t* orow, const float* oval, const uint32_t* row_of_orig,
+                            int64_t nnz, bool keep_val, uint32_t* irow, float* ival) {
+  GSTRIDE(t, nnz) {
+    uint32_t p = ord[t];
+    float v = oval ? oval[p] : 1.f;
+    uint32_t r = row_of_orig[orow[p]];
+    if (keep_val) {
+      irow[t] = r;
+      ival[t] = v;
+    } else {
+      irow[t] = r | (v < 0.f ? NEG_BIT : 0u);
+    }
+  }
+}
+
+// ||a_j||^2 per internal column (warp per column)
+__global__ void k_csq(const int64_t* colptr, const float* val, int64_t N, float* csq) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < N; j += nwarps) {
+    float sq = 0.f;
+    for (int64_t p = colptr[j] + lane; p < colptr[j + 1]; p += 32) sq += val[p] * val[p];
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) csq[j] = sq;
   }
 }
 
@@ -940,52 +1086,75 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   int32_t* color = tmp.alloc<int32_t>(U + 1);
   TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));
   JPView V{raw.colptr, raw.rowidx, orowptr, csr_p, colof, unit_of_col, slack_unit, ufirst, ulen, unnz, uh, Us, slack_row};
-  {
-    const int jp_grid = 152 * 8;
-    int64_t* aptr = tmp.alloc<int64_t>(U + 1);
-    if (U > 0) {
-      k_adj_count<<<jp_grid, 256, 0, s>>>(V, U, aptr);
-      TH_LAUNCHED();
-    }
-    exclusive_scan_i64(aptr, aptr, U, tmp, s);
+  if (Us > 0) {
+    int dev = 0, sms = 0, coop = 0, per = 0;
+    TH_CUDA(cudaGetDevice(&dev));
+    TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jp, 256, 0));
+    const int fill_grid = sms * 8;
+    int64_t* aptr = tmp.alloc<int64_t>(Us + 1);
+    int32_t* nhigh = tmp.alloc<int32_t>(Us + 1);
+    k_adj_count<<<fill_grid, 256, 0, s>>>(V, Us, aptr, nhigh);
+    TH_LAUNCHED();
+    exclusive_scan_i64(aptr, aptr, Us, tmp, s);
     int64_t nadj = 0;
-    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + Us, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaStreamSynchronize(s));
+    JPRun R;
     uint32_t* adj = tmp.alloc<uint32_t>(nadj + 1);
-    int32_t* jcnt = tmp.alloc<int32_t>(U + 1);
-    uint32_t* fs[2] = {tmp.alloc<uint32_t>(U + 1), tmp.alloc<uint32_t>(U + 1)};
-    uint32_t* fb[2] = {tmp.alloc<uint32_t>(U + 1), tmp.alloc<uint32_t>(U + 1)};
-    int64_t* fc = tmp.alloc<int64_t>(4);  // [s0, b0, s1, b1]
-    unsigned long long* done = tmp.alloc<unsigned long long>(1);
-    TH_CUDA(cudaMemsetAsync(fc, 0, 4 * sizeof(int64_t), s));
-    TH_CUDA(cudaMemsetAsync(done, 0, sizeof(unsigned long long), s));
-    if (U > 0) {
-      k_adj_fill<<<jp_grid, 256, 0, s>>>(V, U, aptr, adj, jcnt, fs[0], fc + 0, fb[0], fc + 1);
-      TH_LAUNCHED();
+    R.adj = adj;
+    R.aptr = aptr;
+    R.nhigh = nhigh;
+    R.cnt = tmp.alloc<int32_t>(Us + 1);
+    R.color = color;
+    for (int q = 0; q < 2; ++q) {
+      R.fs[q] = tmp.alloc<uint32_t>(Us + 1);
+      R.fb[q] = tmp.alloc<uint32_t>(Us + 1);
     }
-    int cur = 0;
-    int64_t left = U > 0 ? 1 : 0;
-    int64_t rounds = 0;
-    while (left > 0) {
-      for (int q = 0; q < 16; ++q) {
-        int nx = cur ^ 1;
-        TH_CUDA(cudaMemsetAsync(fc + 2 * nx, 0, 2 * sizeof(int64_t), s));
-        k_jp_step<<<jp_grid, 256, 0, s>>>(adj, aptr, jcnt, color, fs[cur], fc + 2 * cur, fb[cur], fc + 2 * cur + 1,
-                                          fs[nx], fc + 2 * nx, fb[nx], fc + 2 * nx + 1, done);
-        TH_LAUNCHED();
-        cur = nx;
-        ++rounds;
+    R.fc = tmp.alloc<int64_t>(6);
+    R.done = tmp.alloc<unsigned long long>(1);
+    R.bar = tmp.alloc<unsigned>(1);
+    R.err = tmp.alloc<int>(1);
+    TH_CUDA(cudaMemsetAsync(R.fc, 0, 6 * sizeof(int64_t), s));
+    TH_CUDA(cudaMemsetAsync(R.done, 0, sizeof(unsigned long long), s));
+    TH_CUDA(cudaMemsetAsync(R.bar, 0, sizeof(unsigned), s));
+    TH_CUDA(cudaMemsetAsync(R.err, 0, sizeof(int), s));
+    k_adj_fill<<<fill_grid, 256, 0, s>>>(V, Us, aptr, nhigh, adj, R.cnt, R.fs[0], R.fc + 0, R.fb[0], R.fc + 1);
+    TH_LAUNCHED();
+    const int64_t max_rounds = Us + 2;
+    if (coop && per > 0) {
+      // every round in one cooperative launch, a grid barrier between rounds
+      int grid = sms * per;
+      int64_t r0 = 0, nr = max_rounds;
+      void* args[] = {(void*)&R, (void*)&r0, (void*)&nr};
+      TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_jp, dim3(grid), dim3(256), args, 0, s));
+      TH_LAUNCHED();
+    } else {
+      // one launch per round; the host looks at the frontier every 16 rounds
+      int64_t r = 0;
+      while (r < max_rounds) {
+        for (int q = 0; q < 16 && r < max_rounds; ++q, ++r) {
+          k_jp<<<sms * 8, 256, 0, s>>>(R, r, 1);
+          TH_LAUNCHED();
+        }
+        int64_t hc[2];
+        TH_CUDA(cudaMemcpyAsync(hc, R.fc + 2 * (r % 3), 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        TH_CUDA(cudaStreamSynchronize(s));
+        if (hc[0] + hc[1] == 0) break;
       }
-      int64_t hc[2];
-      TH_CUDA(cudaMemcpyAsync(hc, fc + 2 * cur, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      TH_CUDA(cudaStreamSynchronize(s));
-      left = hc[0] + hc[1];
-      TH_CHECK(rounds <= U + 32, THETIS_E_CUDA, "colouring did not finish");
     }
     unsigned long long hdone = 0;
-    TH_CUDA(cudaMemcpyAsync(&hdone, done, sizeof(hdone), cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    TH_CUDA(cudaMemcpyAsync(&hdone, R.done, sizeof(hdone), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaStreamSynchronize(s));
-    TH_CHECK((int64_t)hdone == U, THETIS_E_CUDA, "colouring left units uncoloured");
+    TH_CHECK(herr == 0, THETIS_E_TIMEOUT, "colouring: grid barrier timed out");
+    TH_CHECK((int64_t)hdone == Us, THETIS_E_CUDA, "colouring left units uncoloured");
+  }
+  if (Msl > 0) {
+    k_slack_color<<<grid_for(Msl, 256), 256, 0, s>>>(V, Msl, color);
+    TH_LAUNCHED();
   }
   int* dmax = tmp.alloc<int>(1);
   TH_CUDA(cudaMemsetAsync(dmax, 0xff, sizeof(int), s));
@@ -1011,19 +1180,6 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   }
   radix_sort_pairs(skeys, unit_of_pos, Us, bits_for((int64_t)C * UC_COUNT + 1), tmp, s);
   P.unit_of_pos = unit_of_pos;
-  uint32_t* slkeys = tmp.alloc<uint32_t>(Msl + 1);
-  uint32_t* slrows = tmp.alloc<uint32_t>(Msl + 1);
-  int64_t* scnt = tmp.alloc<int64_t>(C + 1);
-  TH_CUDA(cudaMemsetAsync(scnt, 0, (C + 1) * sizeof(int64_t), s));
-  if (Msl > 0) {
-    k_slack_keys<<<grid_for(Msl, 256), 256, 0, s>>>(color, Us, Msl, slack_row, slkeys, slrows, scnt);
-    TH_LAUNCHED();
-  }
-  radix_sort_pairs(slkeys, slrows, Msl, bits_for(C + 1), tmp, s);
-  std::vector<int64_t> hc((size_t)C * UC_COUNT + 1), hs((size_t)C + 1);
-  TH_CUDA(cudaMemcpyAsync(hc.data(), ccnt, hc.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TH_CUDA(cudaMemcpyAsync(hs.data(), scnt, hs.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-
   // internal columns
   int64_t* plen = tmp.alloc<int64_t>(Us + 1);
   int64_t* cstart = tmp.alloc<int64_t>(Us + 1);
@@ -1040,6 +1196,26 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   }
   k_col_maps_fixed<<<grid_for(Ns, 256), 256, 0, s>>>(fixed_flag, fixed_scan, Ns, P.Nfree, P.col_of_orig, orig_of_col);
   TH_LAUNCHED();
+  // Slack rows ordered by (slack colour, owner column): the owner of a row is
+  // its highest-priority column, so the rows a column owns -- nearly all rows of
+  // a hub -- are consecutive and its gather / scatter of r is coalesced.
+  uint32_t* slkeys = tmp.alloc<uint32_t>(Msl + 1);
+  uint32_t* slrows = tmp.alloc<uint32_t>(Msl + 1);
+  int64_t* scnt = tmp.alloc<int64_t>(C + 1);
+  TH_CUDA(cudaMemsetAsync(scnt, 0, (C + 1) * sizeof(int64_t), s));
+  if (Msl > 0) {
+    k_slack_owner_keys<<<grid_for(Msl, 256), 256, 0, s>>>(V, Msl, P.col_of_orig, slkeys, slrows);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(slkeys, slrows, Msl, bits_for(Ns + 1), tmp, s);
+  if (Msl > 0) {
+    k_slack_color_keys<<<grid_for(Msl, 256), 256, 0, s>>>(slrows, Msl, slack_unit, color, slkeys, scnt);
+    TH_LAUNCHED();
+  }
+  radix_sort_pairs(slkeys, slrows, Msl, bits_for(C + 1), tmp, s);
+  std::vector<int64_t> hc((size_t)C * UC_COUNT + 1), hs((size_t)C + 1);
+  TH_CUDA(cudaMemcpyAsync(hc.data(), ccnt, hc.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hs.data(), scnt, hs.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   // internal rows
   P.row_of_orig = P.mem.alloc<uint32_t>(M);
   P.orig_of_row = P.mem.alloc<uint32_t>(M);
@@ -1061,10 +1237,30 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     P.val = P.mem.alloc<float>(nnz);
     P.csq = P.mem.alloc<float>(Ns);
   }
-  k_int_csc_fill<<<grid_for(Ns * 32, 256), 256, 0, s>>>(orig_of_col, raw.colptr, raw.rowidx, raw.val,
-                                                         P.row_of_orig, P.colptr, Ns, P.has_val, P.rowidx,
-                                                         P.val, P.csq);
-  TH_LAUNCHED();
+  // entries sorted by (internal column, internal row): two stable radix passes
+  {
+    uint32_t* k1 = tmp.alloc<uint32_t>(nnz + 1);
+    uint32_t* ord = tmp.alloc<uint32_t>(nnz + 1);
+    if (nnz > 0) {
+      k_icsc_rowkeys<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, P.row_of_orig, nnz, k1, ord);
+      TH_LAUNCHED();
+    }
+    radix_sort_pairs(k1, ord, nnz, bits_for(M + 1), tmp, s);
+    if (nnz > 0) {
+      k_icsc_colkeys<<<grid_for(nnz, 256), 256, 0, s>>>(ord, colof, P.col_of_orig, nnz, k1);
+      TH_LAUNCHED();
+    }
+    radix_sort_pairs(k1, ord, nnz, bits_for(Ns + 1), tmp, s);
+    if (nnz > 0) {
+      k_icsc_fill<<<grid_for(nnz, 256), 256, 0, s>>>(ord, raw.rowidx, raw.val, P.row_of_orig, nnz, P.has_val, P.rowidx,
+                                                     P.val);
+      TH_LAUNCHED();
+    }
+    if (P.has_val) {
+      k_csq<<<grid_for(Ns * 32, 256), 256, 0, s>>>(P.colptr, P.val, Ns, P.csq);
+      TH_LAUNCHED();
+    }
+  }
   // internal CSR (structural entries)
   int64_t* rcnt = tmp.alloc<int64_t>(M + 1);
   P.rowptr = P.mem.alloc<int64_t>(M + 1);

@@ -122,6 +122,13 @@ struct Problem {
   double lmax_sq = 0.0;       // max ||a_j||^2 over free structural columns
   int64_t max_unit_nnz = 0;
 
+  // persistent sweep (cooperative launch)
+  void* d_plan = nullptr;       // per-colour launch descriptors
+  int64_t* d_ntiles = nullptr;  // tiles per colour
+  unsigned* bar = nullptr;      // grid barrier state
+  int* err = nullptr;           // barrier timeout flag
+  int sweep_grid = -1;
+
   // CUDA graph of one epoch
   cudaGraphExec_t epoch_graph = nullptr;
   int graph_key = -1;
@@ -154,6 +161,10 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar);
 void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out);
 void refresh_only(Problem& P);
 void init_iterate(Problem& P);
+int sweep_grid(Problem& P);
+void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int epochs);
+int sweep_error(Problem& P);
+void reset_sweep_flags(Problem& P);
 
 // round.cu
 struct RoundOut {

@@ -60,6 +60,10 @@ __device__ __forceinline__ uint32_t rowof(const StepView& V, uint32_t e) {
   return V.val ? e : idx_of(e);
 }
 
+// r, x and s are written by other SMs between the colours of one persistent
+// launch: read them around L1 (ld.global.cg).
+__device__ __forceinline__ float ldr(const StepView& V, uint32_t row) { return __ldcg(V.r + row); }
+
 __device__ __forceinline__ void r_add(const StepView& V, uint32_t row, float cached, float delta) {
   if (V.async) atomicAdd(&V.r[row], delta);
   else V.r[row] = cached + delta;
@@ -74,6 +78,10 @@ template <int G, int NC>
 __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int lane, float* red_smem,
                                             bool valid = true) {
   const int64_t p0 = valid ? V.colptr[j] : 0, p1 = valid ? V.colptr[j + 1] : 0;
+  // loads that do not depend on r go first
+  const float xj = valid ? __ldcg(V.x + j) : 0.f;
+  const float ctj = valid ? V.ct[j] : 0.f;
+  const float xb = (valid && V.xbar) ? V.xbar[j] : 0.f;
   uint32_t ce[NC];
   float cr[NC];
   float acc = 0.f;
@@ -85,7 +93,7 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
 #pragma unroll
   for (int t = 0; t < NC; ++t) {
     int64_t p = p0 + lane + (int64_t)t * G;
-    cr[t] = (p < p1) ? V.r[rowof(V, ce[t])] : 0.f;
+    cr[t] = (p < p1) ? ldr(V, rowof(V, ce[t])) : 0.f;
   }
 #pragma unroll
   for (int t = 0; t < NC; ++t) {
@@ -98,7 +106,7 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
 #pragma unroll
     for (int t = 0; t < 4; ++t) e4[t] = (pb + t * G < p1) ? V.rowidx[pb + t * G] : 0u;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? V.r[rowof(V, e4[t])] : 0.f;
+    for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? ldr(V, rowof(V, e4[t])) : 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (pb + t * G < p1) acc = fmaf(coef(V, pb + t * G, e4[t]), r4[t], acc);
@@ -125,9 +133,7 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
     if (G > 32) __syncthreads();
     return;
   }
-  const float xj = V.x[j];
-  const float xb = V.xbar ? V.xbar[j] : 0.f;
-  const float g = V.ct[j] + V.beta * acc + (xj - xb) * V.inv_beta;
+  const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
   const float sq = V.val ? V.csq[j] : (float)(p1 - p0);
   const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, sq, V.inv_beta);
   const float lo = V.lo ? V.lo[j] : V.lo_u;
@@ -148,7 +154,7 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
       for (int t = 0; t < 4; ++t) e4[t] = (pb + t * G < p1) ? V.rowidx[pb + t * G] : 0u;
       if (!V.async) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? V.r[rowof(V, e4[t])] : 0.f;
+        for (int t = 0; t < 4; ++t) r4[t] = (pb + t * G < p1) ? ldr(V, rowof(V, e4[t])) : 0.f;
       }
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -156,6 +162,89 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
     }
   }
   if (G > 32) __syncthreads();
+}
+
+// Columns with more than T_HUGE non-zeros: one CTA stages the column's row ids
+// and residual values in shared memory with cp.async (every load in flight at
+// once, no register staging), then reduces, steps and scatters from there.
+// HUGE_CAP entries fit; the rest of a longer column goes through step_column.
+constexpr int HUGE_CAP = 5888;  // 8 bytes each: 47,104 bytes of dynamic shared memory
+constexpr int STEP_SMEM = HUGE_CAP * 8;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_cg4(void* smem, const void* gmem) {
+  // L1-bypassing variant for data other SMs write (r)
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ bool huge_path(const StepView& V, int64_t n) {
+  return n <= HUGE_CAP && !V.val && !V.async;
+}
+
+// Copy column j's row ids into shared memory and prefetch its r lines into L2
+// (used ahead of time, while the CTA waits at a barrier).
+__device__ __forceinline__ void stage_huge(const StepView& V, int64_t j, unsigned char* dyn) {
+  uint32_t* srow = (uint32_t*)dyn;
+  const int64_t p0 = V.colptr[j], p1 = V.colptr[j + 1];
+  const int64_t n = p1 - p0;
+  if (!huge_path(V, n)) return;
+  for (int t = threadIdx.x; t < n; t += STEP_T) cp_async4(srow + t, V.rowidx + p0 + t);
+  cp_async_wait_all();
+  for (int t = threadIdx.x; t < n; t += STEP_T) prefetch_l2(V.r + idx_of(srow[t]));
+}
+
+__device__ __forceinline__ void step_huge(const StepView& V, int64_t j, float* red_smem, unsigned char* dyn,
+                                          bool staged = false) {
+  uint32_t* srow = (uint32_t*)dyn;
+  float* sr = (float*)(dyn + HUGE_CAP * 4);
+  const int64_t p0 = V.colptr[j], p1 = V.colptr[j + 1];
+  const int64_t n = p1 - p0;
+  if (!huge_path(V, n)) {  // long, valued or async columns: register path
+    step_column<STEP_T, 8>(V, j, threadIdx.x, red_smem);
+    return;
+  }
+  const float xj = __ldcg(V.x + j);
+  const float ctj = V.ct[j];
+  const float xb = V.xbar ? V.xbar[j] : 0.f;
+  if (!staged) {
+    for (int t = threadIdx.x; t < n; t += STEP_T) cp_async4(srow + t, V.rowidx + p0 + t);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n; t += STEP_T) cp_async_cg4(sr + t, V.r + idx_of(srow[t]));
+  cp_async_wait_all();
+  __syncthreads();
+  float acc = 0.f;
+  for (int t = threadIdx.x; t < n; t += STEP_T) acc = fmaf(sgn_of(srow[t]), sr[t], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < STEP_T / 32) ? red_smem[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red_smem[32] = v;
+  }
+  __syncthreads();
+  acc = red_smem[32];
+  const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
+  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, (float)n, V.inv_beta);
+  const float lo = V.lo ? V.lo[j] : V.lo_u;
+  const float hi = V.hi ? V.hi[j] : V.hi_u;
+  const float xn = fminf(fmaxf(xj - g / L, lo), hi);
+  const float d = xn - xj;
+  if (threadIdx.x == 0) V.x[j] = xn;
+  if (d != 0.f)
+    for (int t = threadIdx.x; t < n; t += STEP_T) V.r[idx_of(srow[t])] = sr[t] + sgn_of(srow[t]) * d;
+  __syncthreads();
 }
 
 // Block step (App. E): the k columns of a simplex block, one warp.  Lanes are
@@ -180,7 +269,7 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
     cr[u] = 0.f;
     if (p < p1) {
       uint32_t e = V.rowidx[p];
-      float rr = V.r[rowof(V, e)];
+      float rr = ldr(V, rowof(V, e));
       ce[u] = e;
       cr[u] = rr;
       acc = fmaf(coef(V, p, e), rr, acc);
@@ -188,7 +277,7 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
   }
   for (int64_t p = p0 + t + (int64_t)CACHE * S; p < p1; p += S) {
     uint32_t e = V.rowidx[p];
-    acc = fmaf(coef(V, p, e), V.r[rowof(V, e)], acc);
+    acc = fmaf(coef(V, p, e), ldr(V, rowof(V, e)), acc);
   }
   for (int o = S / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   // per-column ||a||^2 and the block L
@@ -200,7 +289,7 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
   float gq = __shfl_sync(0xffffffffu, acc, (lane < k ? lane : 0) * S);
   float xq = 0.f, y = -INFINITY;
   if (lane < k) {
-    xq = V.x[j0 + lane];
+    xq = __ldcg(V.x + j0 + lane);
     float xb = V.xbar ? V.xbar[j0 + lane] : 0.f;
     float g = V.ct[j0 + lane] + V.beta * gq + (xq - xb) * V.inv_beta;
     y = xq - g / L;
@@ -237,43 +326,54 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
       uint32_t row = rowof(V, e);
       float delta = coef(V, p, e) * dq;
       if (V.async) atomicAdd(&V.r[row], delta);
-      else V.r[row] += delta;
+      else V.r[row] = ldr(V, row) + delta;
     }
   }
 }
 
-__device__ __forceinline__ void step_slack(const StepView& V, int64_t i) {
-  const float sv = V.s[i];
-  const float rv = V.r[i];
-  const float sg = V.sig_u ? (float)V.sig_u : (float)V.sig[i];
-  const float sb = V.sbar ? V.sbar[i] : 0.f;
-  const float lin = V.cs ? V.cs[i] : 0.f;
-  const float g = lin + V.beta * sg * rv + (sv - sb) * V.inv_beta;
+constexpr int SLACK_ROWS = 4;  // slack rows per thread (one tile = STEP_T * SLACK_ROWS rows)
+
+// Slack step of rows [i0, i0 + n) handled by this thread: row i0 + t*STEP_T + tid.
+__device__ __forceinline__ void step_slacks(const StepView& V, int64_t i0, int64_t n) {
+  float sv[SLACK_ROWS], rv[SLACK_ROWS];
+#pragma unroll
+  for (int t = 0; t < SLACK_ROWS; ++t) {
+    int64_t q = (int64_t)t * STEP_T + threadIdx.x;
+    sv[t] = (q < n) ? __ldcg(V.s + i0 + q) : 0.f;
+    rv[t] = (q < n) ? __ldcg(V.r + i0 + q) : 0.f;
+  }
   const float L = (V.lfix > 0.f) ? V.lfix : V.beta + V.inv_beta;
-  const float sn = fmaxf(sv - g / L, 0.f);
-  const float d = sn - sv;
-  V.s[i] = sn;
-  if (d != 0.f) {
-    if (V.async) atomicAdd(&V.r[i], sg * d);
-    else V.r[i] = rv + sg * d;
+#pragma unroll
+  for (int t = 0; t < SLACK_ROWS; ++t) {
+    int64_t q = (int64_t)t * STEP_T + threadIdx.x;
+    if (q >= n) continue;
+    const int64_t i = i0 + q;
+    const float sg = V.sig_u ? (float)V.sig_u : (float)V.sig[i];
+    const float sb = V.sbar ? V.sbar[i] : 0.f;
+    const float lin = V.cs ? V.cs[i] : 0.f;
+    const float g = lin + V.beta * sg * rv[t] + (sv[t] - sb) * V.inv_beta;
+    const float sn = fmaxf(sv[t] - g / L, 0.f);
+    const float d = sn - sv[t];
+    V.s[i] = sn;
+    if (d != 0.f) {
+      if (V.async) atomicAdd(&V.r[i], sg * d);
+      else V.r[i] = rv[t] + sg * d;
+    }
   }
 }
 
-// One colour: CTAs [seg.b0, next.b0) serve segment seg.
-__global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch CL) {
-  __shared__ float red_smem[33];
+// One tile of a colour: the CTA serves tile `tile` of the segment it falls in.
+__device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch* segs, int nseg, int64_t tile,
+                                             float* red_smem, unsigned char* dyn, bool staged = false) {
   int si = 0;
-  while (si + 1 < CL.nseg && (int64_t)blockIdx.x >= CL.seg[si + 1].b0) ++si;
-  const SegLaunch S = CL.seg[si];
-  const int64_t b = blockIdx.x - S.b0;
+  while (si + 1 < nseg && tile >= segs[si + 1].b0) ++si;
+  const SegLaunch S = segs[si];
+  const int64_t b = tile - S.b0;
   const int lane = threadIdx.x & 31;
   switch (S.cls) {
-    case UC_HUGE: {
-      if (b < S.n) step_column<STEP_T, 16>(V, S.c0 + b, threadIdx.x, red_smem);
-      break;
-    }
+    case UC_HUGE:
     case UC_LARGE: {
-      if (b < S.n) step_column<STEP_T, 4>(V, S.c0 + b, threadIdx.x, red_smem);
+      if (b < S.n) step_huge(V, S.c0 + b, red_smem, dyn, staged);
       break;
     }
     case UC_MED: {
@@ -295,9 +395,142 @@ __global__ void __launch_bounds__(STEP_T) k_color_step(StepView V, ColorLaunch C
       break;
     }
     default: {  // slacks
-      int64_t i = b * STEP_T + threadIdx.x;
-      if (i < S.n) step_slack(V, S.u0 + i);
+      int64_t i0 = S.u0 + b * (STEP_T * SLACK_ROWS);
+      int64_t rest = S.n - b * (STEP_T * SLACK_ROWS);
+      if (rest > 0) step_slacks(V, i0, rest < STEP_T * SLACK_ROWS ? rest : STEP_T * SLACK_ROWS);
       break;
+    }
+  }
+}
+
+// One colour per launch: CTA b serves tile b.
+__global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunch CL) {
+  __shared__ float red_smem[33];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  process_tile(V, CL.seg, CL.nseg, blockIdx.x, red_smem, dyn);
+}
+
+// Grid-wide barrier of a cooperative launch, split into arrive and wait so a CTA
+// can prefetch the next colour while the others finish.  One 32-bit word: CTA 0
+// adds 2^31 - (G - 1), every other CTA adds 1, so the top bit flips exactly once
+// per barrier.  The wait is bounded: after ~2 s (clock64) the CTA records
+// err = 1 and the launch gives up (the host reports THETIS_E_TIMEOUT).
+constexpr long long BARRIER_LIMIT_CYCLES = 4000000000LL;
+
+__device__ __forceinline__ unsigned bar_arrive(unsigned* bar) {
+  unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+  unsigned old;
+  asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned old, int* err) {
+  const long long t0 = clock64();
+  unsigned it = 0, cur;
+  while (true) {
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+    if ((cur ^ old) & 0x80000000u) return true;
+    if ((++it & 255u) == 0 && (*(volatile int*)err || clock64() - t0 > BARRIER_LIMIT_CYCLES)) {
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(64);  // keep hundreds of pollers from saturating the line's L2 slice
+  }
+}
+
+// L2 prefetch of the read-only data of one tile (column pointers, row ids, x, c)
+// or, for slack tiles, of the tile's s and r rows.  Only a hint: r lines may be
+// rewritten before use, which L2 coherence handles.
+__device__ __forceinline__ void prefetch_tile(const StepView& V, const SegLaunch* segs, int nseg, int64_t tile) {
+  int si = 0;
+  while (si + 1 < nseg && tile >= segs[si + 1].b0) ++si;
+  const SegLaunch S = segs[si];
+  const int64_t b = tile - S.b0;
+  int64_t u0, u1;
+  switch (S.cls) {
+    case UC_HUGE:
+    case UC_LARGE: u0 = b; u1 = b + 1; break;
+    case UC_MED:
+    case UC_BLOCK: u0 = b * (STEP_T / 32); u1 = u0 + STEP_T / 32; break;
+    case UC_SMALL: u0 = b * (STEP_T / GROUP_SMALL); u1 = u0 + STEP_T / GROUP_SMALL; break;
+    default: {
+      const int64_t r0 = S.u0 + b * (STEP_T * SLACK_ROWS);
+      const int64_t r1 = min(S.u0 + S.n, r0 + (int64_t)STEP_T * SLACK_ROWS);
+      for (int64_t i = r0 + (int64_t)threadIdx.x * 32; i < r1; i += (int64_t)STEP_T * 32) {
+        prefetch_l2(V.s + i);
+        prefetch_l2(V.r + i);
+      }
+      return;
+    }
+  }
+  if (u1 > S.n) u1 = S.n;
+  if (u0 >= u1) return;
+  const int len = (S.cls == UC_BLOCK) ? V.k : 1;
+  const int64_t j0 = S.c0 + u0 * len, j1 = S.c0 + u1 * len;
+  if (threadIdx.x == 0) {
+    prefetch_l2(V.colptr + j0);
+    prefetch_l2(V.colptr + j1);
+    prefetch_l2(V.x + j0);
+    prefetch_l2(V.ct + j0);
+  }
+  const int64_t p0 = V.colptr[j0], p1 = V.colptr[j1];
+  for (int64_t p = p0 + (int64_t)threadIdx.x * 32; p < p1; p += (int64_t)STEP_T * 32) prefetch_l2(V.rowidx + p);
+}
+
+// Persistent colour sweep: `epochs` epochs, every colour's tiles spread over all
+// CTAs, one grid barrier between colours.  Equivalent to one k_color_step launch
+// per colour.  While it waits at a barrier a CTA loads the next colour's launch
+// descriptor and prefetches its first tiles into L2.
+constexpr int PREFETCH_TILES = 2;
+
+__global__ void __launch_bounds__(STEP_T, 4) k_sweep(StepView V, const ColorLaunch* plan, const int64_t* ntiles,
+                                                     int ncolors, int epochs, unsigned* bar, int* err) {
+  __shared__ float red_smem[33];
+  __shared__ ColorLaunch cl[2];
+  __shared__ int ok;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  constexpr int CLW = (int)(sizeof(ColorLaunch) / 4);
+  static_assert(sizeof(ColorLaunch) % 4 == 0, "ColorLaunch copied as words");
+  if (threadIdx.x < CLW) ((unsigned*)&cl[0])[threadIdx.x] = ((const unsigned*)&plan[0])[threadIdx.x];
+  __syncthreads();
+  int cur = 0;
+  bool first_staged = false;
+  for (int e = 0; e < epochs; ++e) {
+    for (int c = 0; c < ncolors; ++c) {
+      const int64_t nt = ntiles[c];
+      for (int64_t t = blockIdx.x; t < nt; t += gridDim.x)
+        process_tile(V, cl[cur].seg, cl[cur].nseg, t, red_smem, dyn, first_staged && t == blockIdx.x);
+      const bool last = (e == epochs - 1) && (c == ncolors - 1);
+      if (last) break;
+      const int cn = (c + 1 < ncolors) ? c + 1 : 0;
+      __syncthreads();
+      unsigned old = 0;
+      if (threadIdx.x == 0) old = bar_arrive(bar);
+      // overlap the barrier: next descriptor and L2 prefetch of the next tiles
+      if (threadIdx.x < CLW) ((unsigned*)&cl[cur ^ 1])[threadIdx.x] = ((const unsigned*)&plan[cn])[threadIdx.x];
+      __syncthreads();
+      const int64_t ntn = ntiles[cn];
+      bool staged = false;
+      if ((int64_t)blockIdx.x < ntn) {
+        // a first tile that is a long column: its row ids go to shared memory now
+        const ColorLaunch& nx = cl[cur ^ 1];
+        int si = 0;
+        while (si + 1 < nx.nseg && (int64_t)blockIdx.x >= nx.seg[si + 1].b0) ++si;
+        const SegLaunch S = nx.seg[si];
+        if ((S.cls == UC_HUGE || S.cls == UC_LARGE) && (int64_t)blockIdx.x - S.b0 < S.n) {
+          stage_huge(V, S.c0 + ((int64_t)blockIdx.x - S.b0), dyn);
+          staged = true;
+        }
+      }
+      for (int q = staged ? 1 : 0; q < PREFETCH_TILES; ++q) {
+        const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
+        if (t < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, t);
+      }
+      if (threadIdx.x == 0) ok = bar_wait(bar, old, err) ? 1 : 0;
+      __syncthreads();
+      if (!ok) return;
+      cur ^= 1;
+      first_staged = staged;
     }
   }
 }
@@ -309,7 +542,7 @@ static int64_t ctas_for(int cls, int64_t n) {
     case UC_MED:
     case UC_BLOCK: return (n + STEP_T / 32 - 1) / (STEP_T / 32);
     case UC_SMALL: return (n + STEP_T / GROUP_SMALL - 1) / (STEP_T / GROUP_SMALL);
-    default: return (n + STEP_T - 1) / STEP_T;
+    default: return (n + STEP_T * SLACK_ROWS - 1) / (STEP_T * SLACK_ROWS);
   }
 }
 
@@ -348,7 +581,7 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
   auto launch = [&](ColorLaunch& CL, int64_t total) {
     if (total <= 0) return;
     TH_CHECK(total < (int64_t(1) << 31), THETIS_E_INVALID, "colour class too large for one launch");
-    k_color_step<<<(unsigned)total, STEP_T, 0, s>>>(V, CL);
+    k_color_step<<<(unsigned)total, STEP_T, STEP_SMEM, s>>>(V, CL);
     TH_LAUNCHED();
   };
   if (a.mode == THETIS_MODE_ASYNC) {
@@ -393,6 +626,81 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     launch(CL, tot);
   }
   TH_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// persistent sweep: device plan, cooperative launch
+// ---------------------------------------------------------------------------
+static void ensure_sweep_plan(Problem& P) {
+  if (P.d_plan) return;
+  const int C = P.ncolors;
+  std::vector<ColorLaunch> h(C > 0 ? C : 1);
+  std::vector<int64_t> nt(C > 0 ? C : 1, 0);
+  for (int c = 0; c < C; ++c) {
+    const ColorPlan& cp = P.plan[c];
+    ColorLaunch CL{};
+    int64_t tot = 0;
+    for (auto& sg : cp.segs) {
+      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+      tot += ctas_for(sg.cls, sg.u1 - sg.u0);
+    }
+    if (cp.srow1 > cp.srow0) {
+      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
+      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0);
+    }
+    h[c] = CL;
+    nt[c] = tot;
+  }
+  ColorLaunch* dp = P.mem.alloc<ColorLaunch>(h.size());
+  int64_t* dn = P.mem.alloc<int64_t>(nt.size());
+  TH_CUDA(cudaMemcpyAsync(dp, h.data(), h.size() * sizeof(ColorLaunch), cudaMemcpyHostToDevice, P.stream));
+  TH_CUDA(cudaMemcpyAsync(dn, nt.data(), nt.size() * sizeof(int64_t), cudaMemcpyHostToDevice, P.stream));
+  P.bar = P.mem.alloc<unsigned>(2);
+  P.err = P.mem.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), P.stream));
+  TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  P.d_plan = dp;
+  P.d_ntiles = dn;
+}
+
+// Grid of the cooperative sweep (0: not available on this device).
+int sweep_grid(Problem& P) {
+  if (P.sweep_grid >= 0) return P.sweep_grid;
+  int dev = 0, coop = 0, sms = 0, per = 0;
+  TH_CUDA(cudaGetDevice(&dev));
+  TH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep, STEP_T, STEP_SMEM));
+  P.sweep_grid = (coop && per > 0) ? sms * per : 0;
+  return P.sweep_grid;
+}
+
+void reset_sweep_flags(Problem& P) {
+  if (!P.bar) return;
+  TH_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), P.stream));
+  TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
+}
+
+void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int epochs) {
+  ensure_sweep_plan(P);
+  const int grid = sweep_grid(P);
+  TH_CHECK(grid > 0, THETIS_E_CUDA, "cooperative launch not available");
+  StepView V = make_view(P, a, use_ubar, use_xbar);
+  const ColorLaunch* plan = (const ColorLaunch*)P.d_plan;
+  const int64_t* nt = P.d_ntiles;
+  int C = P.ncolors;
+  void* args[] = {(void*)&V, (void*)&plan, (void*)&nt, (void*)&C, (void*)&epochs, (void*)&P.bar, (void*)&P.err};
+  TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep, dim3(grid), dim3(STEP_T), args, STEP_SMEM, P.stream));
+  TH_LAUNCHED();
+}
+
+int sweep_error(Problem& P) {
+  if (!P.err) return 0;
+  int h = 0;
+  TH_CUDA(cudaMemcpyAsync(&h, P.err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  return h;
 }
 
 // ---------------------------------------------------------------------------

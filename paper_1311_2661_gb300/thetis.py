@@ -47,7 +47,8 @@ class ProblemDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("beta", C.c_double), ("epochs", C.c_int32), ("tol", C.c_double),
                 ("refresh_every", C.c_int32), ("step_rule", C.c_int32), ("mode", C.c_int32),
-                ("ubar", C.c_void_p), ("xbar", C.c_void_p), ("x0", C.c_void_p), ("mem", C.c_int32)]
+                ("ubar", C.c_void_p), ("xbar", C.c_void_p), ("x0", C.c_void_p), ("mem", C.c_int32),
+                ("engine", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -255,13 +256,14 @@ def thetis_create(m, n, csc_ptr, csc_row, b, c, lo, hi, row_kind, csc_val=None, 
 
 
 def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step_rule=0, mode=MODE_COLORED,
-                 ubar=None, xbar=None, x0=None):
+                 ubar=None, xbar=None, x0=None, engine=0):
     A = _Args()
     p = Params()
     p.beta, p.epochs, p.tol = float(beta), int(epochs), float(tol)
     p.refresh_every, p.step_rule, p.mode = int(refresh_every), int(step_rule), int(mode)
     p.ubar, p.xbar, p.x0 = A(ubar, np.float32), A(xbar, np.float32), A(x0, np.float32)
     p.mem = A.memspace
+    p.engine = int(engine)
     info = SolveInfo()
     st = _check(_lib.thetis_solve(h.ptr, C.byref(p), C.byref(info)), allow=(THETIS_OK, THETIS_NOT_CONVERGED))
     return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,

@@ -42,12 +42,14 @@ def test_coloring_bit_exact(case):
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("step_rule", [0, 1])
-def test_scd_iterates_match_oracle(case, step_rule):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_scd_iterates_match_oracle(case, step_rule, engine):
+    """engine 0: persistent cooperative sweep; engine 1: one launch per colour."""
     kind, mk = CASES[case]
     g = mk()
     h, lp = _pair(kind, g, seed=5)
     beta, epochs = 100.0, 50
-    info = h.solve(beta=beta, epochs=epochs, refresh_every=10, step_rule=step_rule)
+    info = h.solve(beta=beta, epochs=epochs, refresh_every=10, step_rule=step_rule, engine=engine)
     col, _ = lp.color(5)
     x_o, info_o = lp.solve(beta=beta, epochs=epochs, refresh_every=10, step_rule=step_rule, color=col)
     x_g = gpu_full_x(h)
@@ -61,6 +63,17 @@ def test_scd_iterates_match_oracle(case, step_rule):
     assert rel(info["obj"], chk["obj"]) <= 1e-9
     assert abs(info["infeas"] - chk["infeas"]) <= 1e-6
     assert rel(info["fbeta"], chk["fbeta"]) <= 1e-9
+
+
+def test_engines_give_identical_iterates():
+    """The persistent sweep and the per-colour launches run the same tiles in the
+    same colour order, so their iterates agree to the last bit."""
+    g = is_graph(3000, 20000, 2)
+    h0, h1 = build_gpu("is", g, seed=5), build_gpu("is", g, seed=5)
+    i0 = h0.solve(beta=100.0, epochs=23, refresh_every=7, engine=0)
+    i1 = h1.solve(beta=100.0, epochs=23, refresh_every=7, engine=1)
+    assert np.array_equal(gpu_full_x(h0), gpu_full_x(h1))
+    assert i0["fbeta"] == i1["fbeta"]
 
 
 def test_stop_at_tolerance_matches_oracle():

@@ -220,10 +220,11 @@ def test_coloring_matches_networkx_greedy(oracle_mod, kind):
         lp = mk(25, g.eu, g.ev, np.ones(25))
     seed = 12345
     G, A, us, ul = _conflict_graph(lp)
-    # priority key restated here: (nnz desc, splitmix64_at(seed, u) desc, u asc)
+    # priority key restated here: (structural before slack, nnz desc, splitmix64_at(seed, u) desc, u asc)
     nnz = np.array([int(A[:, s:s + l].sum()) for s, l in zip(us, ul)])
-    keys = [(-nnz[u], -oracle_mod.splitmix64_at(seed, u), u) for u in range(lp.U)]
-    order = [k[2] for k in sorted(keys)]
+    slack = [int(s >= lp.Ns) for s in us]
+    keys = [(slack[u], -nnz[u], -oracle_mod.splitmix64_at(seed, u), u) for u in range(lp.U)]
+    order = [k[3] for k in sorted(keys)]
     assert list(lp.priority_order(seed)) == order
     ref = nx.greedy_color(G, strategy=lambda G_, colors: iter(order))
     col, nc = lp.color(seed)
