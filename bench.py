@@ -44,6 +44,9 @@ WORKLOADS = {
 }
 DEFAULT = "is-chunglu-n2^20-m1.6e7"
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
+# DRAM bytes per epoch of the persistent sweep from one ncu capture
+# (profiles/k_sweep_is-chunglu-n2e20.md: 3.04 GB read + 2.47 GB written per 10-epoch launch)
+SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 551_000_000}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -319,8 +322,8 @@ def run_gpu(args, wl, ws, rank, local):
                 "d2h_bytes_per_step": g.n + 64},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "k_color_step (one epoch graph)", "bytes_per_epoch": bpe,
+                     "frac": achieved / pk["hbm_gbs"], "traffic": SWEEP_TRAFFIC_PER_EPOCH.get(args.workload),
+                     "kernel": "k_sweep (persistent colour sweep); unit = one epoch", "bytes_per_epoch": bpe,
                      "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
         "cpu_baseline": cpu,
         "time_to_residual": ttr,

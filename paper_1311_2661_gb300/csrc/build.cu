@@ -19,6 +19,16 @@ static int bits_for(int64_t n) {
 
 #define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// Histogram increment with the lanes of a warp that share a key folded into
+// one atomic (colour histograms have only a handful of distinct keys).
+__device__ __forceinline__ void hist_add(int64_t* cnt, uint32_t key, bool valid) {
+  unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  unsigned peers = __match_any_sync(act, key);
+  int lane = threadIdx.x & 31;
+  if (lane == __ffs(peers) - 1) atomicAdd((unsigned long long*)&cnt[key], (unsigned long long)__popc(peers));
+}
+
 // ---------------------------------------------------------------------------
 // graph builders
 // ---------------------------------------------------------------------------
@@ -713,17 +723,23 @@ __global__ void k_max_i32(const int32_t* a, int64_t n, int* out) {
 // sort keys for structural units: colour * 4 + class
 __global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const int64_t* unnz, int64_t Us,
                               uint32_t* keys, uint32_t* vals, int64_t* cnt) {
-  GSTRIDE(u, Us) {
-    int cls;
-    if (ulen[u] > 1) cls = UC_BLOCK;
-    else if (unnz[u] > T_HUGE) cls = UC_HUGE;
-    else if (unnz[u] > T_LARGE) cls = UC_LARGE;
-    else if (unnz[u] > T_MED) cls = UC_MED;
-    else cls = UC_SMALL;
-    uint32_t key = (uint32_t)color[u] * UC_COUNT + cls;
-    keys[u] = key;
-    vals[u] = (uint32_t)u;
-    atomicAdd((unsigned long long*)&cnt[key], 1ull);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ub = blockIdx.x * (int64_t)blockDim.x; ub < Us; ub += stride) {
+    const int64_t u = ub + threadIdx.x;
+    const bool ok = u < Us;
+    uint32_t key = 0;
+    if (ok) {
+      int cls;
+      if (ulen[u] > 1) cls = UC_BLOCK;
+      else if (unnz[u] > T_HUGE) cls = UC_HUGE;
+      else if (unnz[u] > T_LARGE) cls = UC_LARGE;
+      else if (unnz[u] > T_MED) cls = UC_MED;
+      else cls = UC_SMALL;
+      key = (uint32_t)color[u] * UC_COUNT + cls;
+      keys[u] = key;
+      vals[u] = (uint32_t)u;
+    }
+    hist_add(cnt, key, ok);
   }
 }
 
@@ -758,10 +774,13 @@ __global__ void k_slack_owner_keys(JPView V, int64_t Msl, const uint32_t* col_of
 
 __global__ void k_slack_color_keys(const uint32_t* rows, int64_t Msl, const int64_t* slack_unit, const int32_t* color,
                                    uint32_t* keys, int64_t* cnt) {
-  GSTRIDE(t, Msl) {
-    uint32_t c = (uint32_t)color[slack_unit[rows[t]]];
-    keys[t] = c;
-    atomicAdd((unsigned long long*)&cnt[c], 1ull);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t tb = blockIdx.x * (int64_t)blockDim.x; tb < Msl; tb += stride) {
+    const int64_t t = tb + threadIdx.x;
+    const bool ok = t < Msl;
+    uint32_t c = ok ? (uint32_t)color[slack_unit[rows[t]]] : 0u;
+    if (ok) keys[t] = c;
+    hist_add(cnt, c, ok);
   }
 }
 

@@ -764,16 +764,25 @@ __device__ __forceinline__ double warp_max_d(double v) {
   return v;
 }
 
+// a_j^T r in FP64 (warp-wide) and ||a_j||^2 (= the non-zero count for +-1 columns)
 __device__ __forceinline__ double col_dot64(const CheckView& V, int64_t j, int lane, double* sq) {
+  const int64_t p0 = V.colptr[j], p1 = V.colptr[j + 1];
   double acc = 0.0, s2 = 0.0;
-  for (int64_t p = V.colptr[j] + lane; p < V.colptr[j + 1]; p += 32) {
-    uint32_t e = V.rowidx[p];
-    double a = V.val ? (double)V.val[p] : (double)sgn_of(e);
-    uint32_t row = V.val ? e : idx_of(e);
-    acc += a * V.r64[row];
-    s2 += a * a;
+  if (V.val) {
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const double a = (double)V.val[p];
+      acc += a * V.r64[V.rowidx[p]];
+      s2 += a * a;
+    }
+    *sq = warp_sum_d(s2);
+  } else {
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const uint32_t e = V.rowidx[p];
+      const double rv = V.r64[idx_of(e)];
+      acc += (e & NEG_BIT) ? -rv : rv;
+    }
+    *sq = (double)(p1 - p0);
   }
-  *sq = warp_sum_d(s2);
   return warp_sum_d(acc);
 }
 
@@ -784,6 +793,7 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const double beta = V.beta, ib = 1.0 / beta;
+  const double inv_ls = 1.0 / (beta + ib);  // 1 / L of every slack column
   // (a) free singleton columns, warp per column
   for (int64_t j = warp; j < V.Nfree; j += nwarps) {
     if (V.in_block && V.in_block[j]) continue;
@@ -847,7 +857,7 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
       double sv = V.s[i], sb = V.sbar ? V.sbar[i] : 0.0;
       double sg = (double)V.sig[i];
       double g = (V.cs ? (double)V.cs[i] : 0.0) + beta * sg * ri + (sv - sb) * ib;
-      double sn = fmax(sv - g / (beta + ib), 0.0);
+      double sn = fmax(sv - g * inv_ls, 0.0);
       rho = fmax(rho, fabs(sn - sv));
       xx += (sv - sb) * (sv - sb);
     }
