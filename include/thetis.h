@@ -252,6 +252,38 @@ thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, co
                                      const float* w, const float* x, uint64_t seed, int32_t reps,
                                      uint8_t* labels_out, thetis_round_info* info, void* stream);
 
+/*
+ * thetis_build_batch -- `count` independent vertex-cover / independent-set LPs
+ * (Sec. 2; App. B.2) as one block-diagonal LP.  Instance t has kind kinds[t]
+ * (THETIS_ROUND_VC or THETIS_ROUND_IS), vertices [vertex_offset[t],
+ * vertex_offset[t+1]) of w and edges [edge_offset[t], edge_offset[t+1]) of
+ * eu/ev, whose endpoints are LOCAL vertex ids in [0, n_t).  vertex_offset and
+ * edge_offset have count+1 entries, start at 0 and do not decrease (n_t >= 1).
+ * The colouring hashes instance-local ids, so every instance is coloured, swept
+ * and rounded exactly as thetis_build_vc / _is + thetis_solve + thetis_round
+ * would treat it alone (up to FP32 summation order).  The handle is solved with
+ * thetis_solve: one sweep advances every instance, and tol applies to the
+ * largest residual over all instances.  thetis_get_x returns the concatenated
+ * vertex values.  mem applies to every array.
+ */
+thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int64_t* vertex_offset,
+                                 const int64_t* edge_offset, const int32_t* eu, const int32_t* ev,
+                                 const float* w, int32_t mem, uint64_t seed, void* stream,
+                                 thetis_handle** out);
+
+/*
+ * thetis_round_batch -- repair + rounding of every instance of a batch handle,
+ * exactly as thetis_round does for one instance (VC threshold, IS best of `reps`
+ * with the instance-local vertex ids in the random streams).
+ *   labels_out[sum n_t]   concatenated labels (out_mem: host or device)
+ *   obj_out[count], status_out[count], best_rep_out[count]: HOST arrays (each may
+ *   be NULL); status 1 = valid, 0 = validity check failed, -1 = VC repair
+ *   impossible (eps >= 1).
+ */
+thetis_status thetis_round_batch(thetis_handle* h, uint64_t seed, int32_t reps, uint8_t* labels_out,
+                                 int32_t out_mem, double* obj_out, int32_t* status_out,
+                                 int32_t* best_rep_out);
+
 /* Copy the structural part of the iterate, original column order, as FP32. */
 thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem);
 /* Copy the slack part of the iterate (one value per GE/LE row, row order). */

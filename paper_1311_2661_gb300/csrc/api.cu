@@ -466,4 +466,94 @@ thetis_status thetis_destroy(thetis_handle* h) {
   return THETIS_OK;
 }
 
+thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int64_t* vertex_offset,
+                                 const int64_t* edge_offset, const int32_t* eu, const int32_t* ev, const float* w,
+                                 int32_t mem, uint64_t seed, void* stream, thetis_handle** out) {
+  if (!out || !kinds || !vertex_offset || !edge_offset || !w) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  *out = nullptr;
+  thetis_handle* h = nullptr;
+  thetis_status st = guard(nullptr, [&] {
+    TH_CHECK(count >= 1, THETIS_E_INVALID, "count must be >= 1");
+    h = new_handle(stream);
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    std::vector<int64_t> hn(count + 1), he(count + 1);
+    std::vector<uint8_t> hk(count);
+    TH_CUDA(cudaMemcpyAsync(hn.data(), vertex_offset, (count + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+    TH_CUDA(cudaMemcpyAsync(he.data(), edge_offset, (count + 1) * sizeof(int64_t), cudaMemcpyDefault, s));
+    TH_CUDA(cudaMemcpyAsync(hk.data(), kinds, count, cudaMemcpyDefault, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    TH_CHECK(hn[0] == 0 && he[0] == 0, THETIS_E_INVALID, "offsets must start at 0");
+    for (int32_t t = 0; t < count; ++t)
+      TH_CHECK(hn[t + 1] > hn[t] && he[t + 1] >= he[t], THETIS_E_INVALID,
+               "every instance needs n >= 1 and offsets must not decrease");
+    const int64_t Nv = hn[count], Ne = he[count];
+    TH_CHECK(Nv < (int64_t(1) << 31) && Ne < (int64_t(1) << 31) && 2 * Ne < (int64_t(1) << 32) - 1,
+             THETIS_E_INVALID, "batch too large");
+    TH_CHECK(Ne == 0 || (eu && ev), THETIS_E_INVALID, "null edge array");
+    const int32_t* deu = to_dev(eu, Ne, mem, tmp, s);
+    const int32_t* dev = to_dev(ev, Ne, mem, tmp, s);
+    const float* dw = to_dev(w, Nv, mem, tmp, s);
+    int64_t* dnoff = tmp.alloc<int64_t>(count + 1);
+    int64_t* deoff = tmp.alloc<int64_t>(count + 1);
+    uint8_t* dkind = tmp.alloc<uint8_t>(count);
+    TH_CUDA(cudaMemcpyAsync(dnoff, hn.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(deoff, he.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(dkind, hk.data(), count, cudaMemcpyHostToDevice, s));
+    RawLP raw;
+    int32_t *geu = nullptr, *gev = nullptr;
+    bool mixed = true;
+    build_batch_raw(count, dkind, dnoff, deoff, Nv, Ne, deu, dev, dw, raw, geu, gev, mixed, tmp, s);
+    h->P = build_problem(raw, KIND_BATCH, seed, s, tmp);
+    Problem& P = *h->P;
+    P.nv = Nv;
+    P.ne = Ne;
+    P.eu = keep_copy(P.mem, (const int32_t*)geu, Ne, s);
+    P.ev = keep_copy(P.mem, (const int32_t*)gev, Ne, s);
+    P.w = keep_copy(P.mem, dw, Nv, s);
+    P.nbatch = count;
+    P.bnoff = keep_copy(P.mem, (const int64_t*)dnoff, count + 1, s);
+    P.beoff = keep_copy(P.mem, (const int64_t*)deoff, count + 1, s);
+    P.bkind = keep_copy(P.mem, (const uint8_t*)dkind, count, s);
+    P.h_bkind = hk;
+    P.h_bnoff = hn;
+    P.h_beoff = he;
+    finish_create(h);
+  });
+  if (st != THETIS_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return THETIS_OK;
+}
+
+thetis_status thetis_round_batch(thetis_handle* h, uint64_t seed, int32_t reps, uint8_t* labels_out,
+                                 int32_t out_mem, double* obj_out, int32_t* status_out, int32_t* best_rep_out) {
+  if (!h || !h->P || !labels_out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    uint8_t* dl = (out_mem == THETIS_MEM_DEVICE) ? labels_out : tmp.alloc<uint8_t>(P.nv);
+    std::vector<double> obj, repair;
+    std::vector<int32_t> status, best;
+    std::vector<int64_t> near;
+    round_batch(P, seed, reps, dl, obj, status, best, repair, near);
+    if (out_mem != THETIS_MEM_DEVICE) from_dev(labels_out, dl, P.nv, THETIS_MEM_HOST, s);
+    TH_CUDA(cudaStreamSynchronize(s));
+    for (int64_t t = 0; t < P.nbatch; ++t) {
+      if (obj_out) obj_out[t] = obj[t];
+      if (status_out) status_out[t] = status[t];
+      if (best_rep_out) best_rep_out[t] = best[t];
+    }
+  });
+}
+
 }  // extern "C"

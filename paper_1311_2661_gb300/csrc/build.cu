@@ -100,6 +100,18 @@ static void incidence(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev
   exclusive_scan_i64(ptr, ptr, n, tmp, s);
 }
 
+// vertex -> incident edges as an int32 CSC (used by the batch builder)
+void incidence_csc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, int64_t*& ptr, int32_t*& rows,
+                   Arena& tmp, cudaStream_t s) {
+  uint32_t* edges;
+  incidence(n, m, eu, ev, ptr, edges, tmp, s);
+  rows = tmp.alloc<int32_t>(2 * m + 1);
+  if (m > 0) {
+    k_u32_to_i32<<<grid_for(2 * m, 256), 256, 0, s>>>(edges, rows, 2 * m);
+    TH_LAUNCHED();
+  }
+}
+
 void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
                      const float* d_w, RawLP& raw, Arena& tmp, cudaStream_t s) {
   int* err = tmp.alloc<int>(1);
@@ -385,15 +397,19 @@ __global__ void k_csr_dupcheck(const int64_t* rowptr, const uint32_t* csr_p, con
 }
 
 __global__ void k_unit_keys(const int64_t* colptr, const int64_t* ufirst, const int32_t* ulen, int64_t Us,
-                            int64_t U, uint64_t seed, int64_t* unnz, uint64_t* uh) {
+                            int64_t U, uint64_t seed, const uint32_t* prio_col, const uint32_t* prio_row,
+                            const int64_t* slack_row, int64_t* unnz, uint64_t* uh) {
   GSTRIDE(u, U) {
+    uint64_t pid = (uint64_t)u;
     if (u < Us) {
       int64_t f = ufirst[u];
       unnz[u] = colptr[f + ulen[u]] - colptr[f];
+      if (prio_col) pid = prio_col[f];
     } else {
       unnz[u] = 1;
+      if (prio_row) pid = prio_row[slack_row[u - Us]];
     }
-    uh[u] = sm64_at(seed, (uint64_t)u);
+    uh[u] = sm64_at(seed, pid);
   }
 }
 
@@ -1100,7 +1116,8 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   // -- colouring (Jones-Plassmann, first fit, fixed total order) -----------
   int64_t* unnz = tmp.alloc<int64_t>(U + 1);
   uint64_t* uh = tmp.alloc<uint64_t>(U + 1);
-  k_unit_keys<<<grid_for(U, 256), 256, 0, s>>>(raw.colptr, ufirst, ulen, Us, U, seed, unnz, uh);
+  k_unit_keys<<<grid_for(U, 256), 256, 0, s>>>(raw.colptr, ufirst, ulen, Us, U, seed, raw.prio_col, raw.prio_row,
+                                               slack_row, unnz, uh);
   TH_LAUNCHED();
   int32_t* color = tmp.alloc<int32_t>(U + 1);
   TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));

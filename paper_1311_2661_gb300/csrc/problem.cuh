@@ -7,7 +7,7 @@
 
 namespace thetis {
 
-enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3 };
+enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BATCH = 4 };
 
 // Classes of coordinate units inside one colour.  Units of a colour are stored
 // class by class, so that every class is a contiguous range of units and of
@@ -44,6 +44,11 @@ struct RawLP {
   bool bounds_uniform = false;
   float lo_u = 0.f, hi_u = 1.f;
   int slack_sign_uniform = 0;  // -1 / +1 if every row has a slack of that sign
+  // optional ids hashed into the colouring priority instead of the unit id
+  // (a batch of instances passes instance-local ids, so every instance is
+  // coloured exactly as it would be alone)
+  const uint32_t* prio_col = nullptr;  // per structural column
+  const uint32_t* prio_row = nullptr;  // per row (for its slack)
 };
 
 struct Problem {
@@ -60,6 +65,14 @@ struct Problem {
   bool bounds_uniform = false;
   float lo_u = 0.f, hi_u = 1.f;
   int slack_sign_uniform = 0;
+
+  // batch meta (thetis_build_batch): instance t owns vertices [bnoff[t], bnoff[t+1])
+  // and edges [beoff[t], beoff[t+1]) of the union
+  int64_t nbatch = 0;
+  int64_t *bnoff = nullptr, *beoff = nullptr;
+  uint8_t* bkind = nullptr;
+  std::vector<uint8_t> h_bkind;
+  std::vector<int64_t> h_bnoff, h_beoff;
 
   // graph meta (builders)
   int64_t nv = 0, ne = 0;
@@ -143,6 +156,14 @@ void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const 
 void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
                   const float* d_ce, int32_t k, const int32_t* d_term, RawLP& raw, Arena& tmp,
                   cudaStream_t s);
+
+// batch.cu
+void build_batch_raw(int64_t count, const uint8_t* d_kind, const int64_t* d_noff, const int64_t* d_eoff, int64_t Nv,
+                     int64_t Ne, const int32_t* d_eu, const int32_t* d_ev, const float* d_w, RawLP& raw,
+                     int32_t*& geu, int32_t*& gev, bool& mixed, Arena& tmp, cudaStream_t s);
+void round_batch(Problem& P, uint64_t seed, int reps, uint8_t* d_labels, std::vector<double>& obj,
+                 std::vector<int32_t>& status, std::vector<int32_t>& best_rep, std::vector<double>& repair,
+                 std::vector<int64_t>& near);
 
 // scd.cu
 struct SolveArgs {

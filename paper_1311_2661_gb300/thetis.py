@@ -86,6 +86,8 @@ def _load():
         "thetis_sync": (st, [P]),
         "thetis_destroy": (st, [P]),
         "thetis_round_is_static": (st, [i64, i64, P, P, P, P, u64, i32, P, P, P]),
+        "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
+        "thetis_round_batch": (st, [P, u64, i32, P, i32, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -295,6 +297,53 @@ def _out_ptr(out):
     if _is_torch(out):
         return out.data_ptr(), (MEM_DEVICE if out.is_cuda else MEM_HOST)
     return out.ctypes.data, MEM_HOST
+
+
+def thetis_build_batch(kinds, vertex_offset, edge_offset, eu, ev, w, seed=0, stream=None) -> Handle:
+    """A batch of independent VC / IS LPs as one handle.  kinds[t] is ROUND_VC or
+    ROUND_IS; eu / ev hold instance-local endpoints, concatenated; offsets have
+    count + 1 entries."""
+    A = _Args()
+    count = int(len(kinds))
+    pk = A(kinds, np.uint8)
+    pn, pe = A(vertex_offset, np.int64), A(edge_offset, np.int64)
+    peu, pev, pw = A(eu, np.int32), A(ev, np.int32), A(w, np.float32)
+    out = C.c_void_p()
+    _check(_lib.thetis_build_batch(count, pk, pn, pe, peu, pev, pw, A.memspace, seed, _stream_ptr(stream),
+                                   C.byref(out)))
+    nv = int(vertex_offset[-1])
+    h = Handle(out.value, n_vertices=nv, kind="batch")
+    h.count = count
+    return h
+
+
+def thetis_build_batch_graphs(items, seed=0, stream=None, device=False) -> Handle:
+    """Convenience: items = [(kind, synth.Graph), ...] with kind "vc" or "is"."""
+    kinds = np.array([ROUND_VC if k == "vc" else ROUND_IS for k, _ in items], np.uint8)
+    noff = np.concatenate([[0], np.cumsum([g.n for _, g in items])]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum([g.m for _, g in items])]).astype(np.int64)
+    eu = np.concatenate([g.eu for _, g in items]).astype(np.int32)
+    ev = np.concatenate([g.ev for _, g in items]).astype(np.int32)
+    w = np.concatenate([g.w for _, g in items]).astype(np.float32)
+    if device:
+        import torch
+
+        dv = lambda a: torch.from_numpy(a).cuda()
+        return thetis_build_batch(dv(kinds), dv(noff), dv(eoff), dv(eu), dv(ev), dv(w), seed=seed, stream=stream)
+    return thetis_build_batch(kinds, noff, eoff, eu, ev, w, seed=seed, stream=stream)
+
+
+def thetis_round_batch(h: Handle, seed=0, reps=10, out=None):
+    """Returns (labels, obj[count], status[count], best_rep[count])."""
+    count = h.count
+    obj = np.zeros(count, np.float64)
+    status = np.zeros(count, np.int32)
+    best = np.zeros(count, np.int32)
+    lab = np.zeros(h.n_vertices, np.uint8) if out is None else out
+    ptr, mem = _out_ptr(lab)
+    _check(_lib.thetis_round_batch(h.ptr, int(seed), int(reps), ptr, mem, obj.ctypes.data, status.ctypes.data,
+                                   best.ctypes.data))
+    return lab, obj, status, best
 
 
 def thetis_round_is_static(n, eu, ev, w, x, labels_out, seed=0, reps=10, stream=None):
