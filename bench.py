@@ -41,6 +41,13 @@ WORKLOADS = {
                               tol=1e-3, reps=1),
     "mc-grid1024-k8": dict(kind="mc", graph="grid", width=1024, height=1024, k=8, seed=3, beta=100.0, epochs=50,
                            refresh=10, tol=1e-3, reps=10),
+    # 4096 ER instances, half VC half IS, n ~ U[200, 20000], avg degree ~ U[4, 16], weights U[1, 10],
+    # all solved to rho <= 1e-3 as one batch
+    "batched-4096": dict(kind="batch", count=4096, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
+                         epochs=4000, refresh=20, tol=1e-3, reps=10, plain_sample=32),
+    # the same distribution, 256 instances (profiling-sized)
+    "batched-256": dict(kind="batch", count=256, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
+                        epochs=4000, refresh=20, tol=1e-3, reps=10, plain_sample=8),
 }
 DEFAULT = "is-chunglu-n2^20-m1.6e7"
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
@@ -219,8 +226,12 @@ def run_gpu(args, wl, ws, rank, local):
             return T.thetis_build_is(g.n, eu, ev, w, seed=0, stream=stream)
         return T.thetis_build_mc(g.n, eu, ev, w, wl["k"], term, seed=0, stream=stream)
 
+    shape = {}
+
     def step(eu, ev, w, term, out, epochs=wl["epochs"], tol=wl["tol"]):
         h = build(eu, ev, w, term)
+        # launch shape: timed trials on the first handle of this shape, cached afterwards
+        shape["small_group"], shape["ctas_per_sm"] = T.thetis_autotune(h, beta=wl["beta"])
         info = h.solve(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"])
         lab, rinfo = h.round(seed=11, reps=wl["reps"], out=out)
         assert rinfo["valid"], "rounded solution failed the exact validity check"
@@ -317,6 +328,7 @@ def run_gpu(args, wl, ws, rank, local):
                    "free_coords": infos[-1][0]["updates"] // max(1, infos[-1][0]["epochs_run"]),
                    "colors": info0["ncolors"], "beta": wl["beta"], "epochs": wl["epochs"],
                    "refresh_every": wl["refresh"], "reps": wl["reps"], "parallelism": f"replicas x{ws}",
+                   "launch_shape": dict(shape),
                    "l2": "inputs larger than L2 and L2 flushed (2x129 MB write) between steps"},
         "e2e": {"value": e_upd_all / (e_ms / 1e3), "unit": "coord_updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": g.n + 64},
@@ -332,6 +344,146 @@ def run_gpu(args, wl, ws, rank, local):
                       "rounded_obj": infos[-1][1]["obj"], "step_ms": step_ms[-1],
                       "launches_per_epoch": info0["launches_per_epoch"]},
         "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# batched workload: solves/s and latency against one-at-a-time GPU solves
+# ---------------------------------------------------------------------------
+def run_batched(args, wl, ws, rank, local):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1311_2661_gb300 import synth
+    from paper_1311_2661_gb300 import thetis as T
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    items = synth.batch_instances(wl["count"], wl["n_lo"], wl["n_hi"], wl["d_lo"], wl["d_hi"], 1, 10,
+                                  wl["seed"] + 1000 * rank)
+    kinds = np.array([T.ROUND_VC if k == "vc" else T.ROUND_IS for k, _ in items], np.uint8)
+    noff = np.concatenate([[0], np.cumsum([g.n for _, g in items])]).astype(np.int64)
+    eoff = np.concatenate([[0], np.cumsum([g.m for _, g in items])]).astype(np.int64)
+    host = dict(kinds=kinds, noff=noff, eoff=eoff,
+                eu=np.concatenate([g.eu for _, g in items]).astype(np.int32),
+                ev=np.concatenate([g.ev for _, g in items]).astype(np.int32),
+                w=np.concatenate([g.w for _, g in items]).astype(np.float32))
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    lab_d = torch.zeros(int(noff[-1]), dtype=torch.uint8, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    count = wl["count"]
+    bpe = sum(20 * g.n + 40 * g.m for _, g in items)
+    torch.cuda.synchronize()
+
+    shape = {}
+
+    def step(a, out):
+        h = T.thetis_build_batch(a["kinds"], a["noff"], a["eoff"], a["eu"], a["ev"], a["w"], seed=0, stream=stream)
+        shape["small_group"], shape["ctas_per_sm"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
+        info = h.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"])
+        lab, obj, status, best = T.thetis_round_batch(h, seed=11, reps=wl["reps"], out=out)
+        assert np.all(status == 1), "a rounded instance failed the validity check"
+        h.close()
+        return info
+
+    for _ in range(args.warmup):
+        step(d, lab_d)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    l0 = T.thetis_launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+            infos.append(step(d, lab_d))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = T.thetis_launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    value = sum_over_ranks(float(count * args.steps), ws, dev) / (total_ms / 1e3)
+    ep_ms = sum(i["epoch_ms"] for i in infos)
+    ep_n = sum(i["epochs_run"] for i in infos)
+    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
+    pk, pk_kind = peaks()
+
+    # e2e: host (pinned) inputs, labels back to the host
+    hp = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    lab_h = torch.zeros(int(noff[-1]), dtype=torch.uint8).pin_memory()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    step(hp, lab_h)
+    b.record(stream)
+    b.synchronize()
+    e_ms = max_over_ranks(a.elapsed_time(b), ws, dev)
+
+    # plain: the same instances one at a time through the single-instance API
+    rng = np.random.default_rng(7)
+    sample = rng.choice(count, size=min(wl["plain_sample"], count), replace=False)
+    lat = []
+    for t in sample:
+        kind, g = items[t]
+        eu_t, ev_t, w_t = (torch.from_numpy(x).to(dev) for x in (g.eu, g.ev, g.w))
+        out_t = torch.zeros(g.n, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bld = T.thetis_build_vc if kind == "vc" else T.thetis_build_is
+        h = bld(g.n, eu_t, ev_t, w_t, seed=0, stream=stream)
+        h.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"])
+        h.round(seed=11, reps=wl["reps"], out=out_t)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+        h.close()
+    lat = np.array(lat)
+    batch_lat = np.array(step_ms)
+
+    info0 = infos[-1]
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP64 refresh/checks)",
+        "data": "synthetic (seeded ER instances)",
+        "config": {"workload": args.workload, "instances": count, "sum_n": int(noff[-1]), "sum_m": int(eoff[-1]),
+                   "colors": info0["ncolors"], "beta": wl["beta"], "tol": wl["tol"],
+                   "refresh_every": wl["refresh"], "reps": wl["reps"], "parallelism": f"replicas x{ws}",
+                   "launch_shape": dict(shape),
+                   "l2": "inputs larger than L2 and L2 flushed (2x129 MB write) between steps"},
+        "e2e": {"value": count / (e_ms / 1e3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(sum(v.nbytes for v in host.values())), "d2h_bytes_per_step": int(noff[-1])},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "k_sweep (persistent colour sweep); unit = one epoch of the batch",
+                     "bytes_per_epoch": bpe, "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
+        "latency": {"batched_p50_ms": float(np.percentile(batch_lat, 50)),
+                    "batched_p99_ms": float(np.percentile(batch_lat, 99)),
+                    "plain_p50_ms": float(np.percentile(lat, 50)), "plain_p99_ms": float(np.percentile(lat, 99)),
+                    "plain_solves_per_s": float(1e3 / lat.mean()), "plain_sample": int(len(lat)),
+                    "note": "batched latency = whole-batch completion (every instance finishes together)"},
+        "last_step": {"epochs_run": info0["epochs_run"], "rho": info0["rho"], "converged": info0["converged"],
+                      "solve_ms": info0["solve_ms"], "step_ms": step_ms[-1]},
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(res), flush=True)
@@ -362,9 +514,46 @@ def cpu_baseline(wl, g, epochs):
             "seconds": dt}
 
 
+def run_reference_batch(args, wl, ws):
+    """The oracle solving instances of the batch one after another, each to
+    rho <= tol, plus rounding (one instance per step, on one core)."""
+    import oracle
+    from paper_1311_2661_gb300 import synth
+
+    oracle.build()
+    items = synth.batch_instances(wl["count"], wl["n_lo"], wl["n_hi"], wl["d_lo"], wl["d_hi"], 1, 10, wl["seed"])
+    rng = np.random.default_rng(7)
+    order = rng.permutation(len(items))
+    times = []
+    for i in range(args.warmup + args.steps):
+        kind, g = items[order[i % len(items)]]
+        t = time.perf_counter()
+        lp = oracle.build_problem(kind, g)
+        col, _ = lp.color(0)
+        x, _ = lp.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"], color=col)
+        if kind == "vc":
+            lp.round_vc(x[: g.n])
+        else:
+            lp.round_is(x[: g.n], 11, wl["reps"])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    value = len(times) / sum(times)
+    sample = f"{len(times)} instances of the batch, each built, coloured, solved to rho <= {wl['tol']} and rounded"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": wl["count"]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def run_reference(args, wl, ws, rank):
     if rank != 0:
         return
+    if wl["kind"] == "batch":
+        return run_reference_batch(args, wl, ws)
     g = make_graph(wl, 0)
     lp, col = _oracle_setup(wl, g)
     x = lp.initial_x()
@@ -415,6 +604,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, ws, rank)
+    elif wl["kind"] == "batch":
+        run_batched(args, wl, ws, rank, local)
     else:
         run_gpu(args, wl, ws, rank, local)
     if ws > 1:

@@ -253,6 +253,25 @@ thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, co
                                      uint8_t* labels_out, thetis_round_info* info, void* stream);
 
 /*
+ * thetis_autotune -- choose the launch shape of the colour sweep for this
+ * problem: the number of lanes that serve one small column (1, 2, 4 or 8; "warps
+ * per column") and the CTAs per SM of the persistent sweep (all that fit, 2 or
+ * 1; the size of the colour chunk each CTA takes).  Every pair is timed over
+ * trial_epochs epochs of the real problem (beta and step_rule from p); the
+ * iterate is saved before and restored after each trial, so the result of later
+ * solves does not depend on tuning.  The choice is cached in the process per
+ * problem shape (kind, size, mean column length, colour count) and applied to
+ * the handle; later handles of the same shape reuse it without trials.
+ * small_group_out / ctas_per_sm_out (0 = all that fit) may be NULL.
+ * This is a performance tool with no counterpart in the paper.
+ */
+thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t trial_epochs,
+                              int32_t* small_group_out, int32_t* ctas_per_sm_out);
+/* Set the launch shape by hand: small_group in {1, 2, 4, 8}, ctas_per_sm >= 0
+ * (0 = all that fit).  THETIS_E_INVALID otherwise. */
+thetis_status thetis_set_launch_shape(thetis_handle* h, int32_t small_group, int32_t ctas_per_sm);
+
+/*
  * thetis_build_batch -- `count` independent vertex-cover / independent-set LPs
  * (Sec. 2; App. B.2) as one block-diagonal LP.  Instance t has kind kinds[t]
  * (THETIS_ROUND_VC or THETIS_ROUND_IS), vertices [vertex_offset[t],

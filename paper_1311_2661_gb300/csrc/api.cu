@@ -1,7 +1,10 @@
 // C ABI of the library (include/thetis.h).
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "problem.cuh"
 
@@ -15,7 +18,7 @@ struct thetis_handle {
   int64_t graph_launches = 0;  // kernels per epoch graph replay
   // key of the captured epoch graph
   double g_beta = 0;
-  int g_rule = -1, g_mode = -1, g_ub = -1, g_xb = -1;
+  int g_rule = -1, g_mode = -1, g_ub = -1, g_xb = -1, g_small = -1;
   ~thetis_handle() {
     if (P) {
       cudaStreamSynchronize(stream);
@@ -279,7 +282,7 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     if (persistent) reset_sweep_flags(P);
     // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
     bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
-                  h->g_ub == (int)ub && h->g_xb == (int)xb;
+                  h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g;
     if (!persistent && !key_ok && a.epochs > 0) {
       if (P.epoch_graph) {
         cudaGraphExecDestroy(P.epoch_graph);
@@ -306,6 +309,7 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
       h->g_mode = a.mode;
       h->g_ub = ub;
       h->g_xb = xb;
+      h->g_small = P.small_g;
     }
     TH_CUDA(cudaEventRecord(h->ev0, s));
     CheckOut co{};
@@ -463,6 +467,121 @@ thetis_status thetis_sync(thetis_handle* h) {
 thetis_status thetis_destroy(thetis_handle* h) {
   if (!h) return THETIS_OK;
   delete h;
+  return THETIS_OK;
+}
+
+namespace {
+// In-process cache of tuned launch shapes, keyed by problem shape.
+struct TuneKey {
+  int kind, log2_coords, avg_nnz, colors_bucket;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, log2_coords, avg_nnz, colors_bucket) <
+           std::tie(o.kind, o.log2_coords, o.avg_nnz, o.colors_bucket);
+  }
+};
+std::mutex g_tune_mu;
+struct TuneChoice {
+  int small_g, per_sm;
+  bool full;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+TuneKey tune_key(const Problem& P) {
+  int l2 = 0;
+  while (l2 < 62 && (int64_t(1) << (l2 + 1)) <= P.free_coords) ++l2;
+  int avg = P.Nfree > 0 ? (int)((P.nnz + P.Nfree / 2) / P.Nfree) : 0;
+  int cb = 0;
+  while (cb < 20 && (1 << (cb + 1)) <= P.ncolors) ++cb;
+  return TuneKey{P.kind, l2, avg, cb};
+}
+}  // namespace
+
+thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t trial_epochs,
+                              int32_t* small_group_out, int32_t* ctas_per_sm_out) {
+  if (!h || !h->P || !p) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    TH_CHECK(p->beta > 0, THETIS_E_INVALID, "beta must be > 0");
+    const TuneKey key = tune_key(P);
+    TuneChoice best{P.small_g, P.sweep_per_sm, P.force_full};
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        best = it->second;
+        cached = true;
+      }
+    }
+    if (!cached) {
+      SolveArgs a{p->beta, std::max(1, trial_epochs), 0.0, 1 << 30, p->step_rule, THETIS_MODE_COLORED};
+      Arena tmp(s);
+      // the trials move the iterate: keep a copy and put it back after each one
+      float* x0 = tmp.alloc<float>(P.Ns);
+      float* s0 = tmp.alloc<float>(P.Msl);
+      float* r0 = tmp.alloc<float>(P.M);
+      TH_CUDA(cudaMemcpyAsync(x0, P.x, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      if (P.Msl) TH_CUDA(cudaMemcpyAsync(s0, P.s, P.Msl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      if (P.M) TH_CUDA(cudaMemcpyAsync(r0, P.r, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      prepare_solve(P, nullptr, nullptr, nullptr);
+      float best_ms = 1e30f;
+      const int groups[4] = {8, 4, 2, 1};
+      const int pers[3] = {0, 2, 1};
+      const int nvar = sweep_lean_possible(P) ? 2 : 1;
+      for (int vi = 0; vi < nvar; ++vi)
+      for (int gi = 0; gi < 4; ++gi)
+        for (int pi = 0; pi < 3; ++pi) {
+          P.force_full = vi == 1;
+          P.small_g = groups[gi];
+          P.sweep_per_sm = pers[pi];
+          P.sweep_grid = -1;
+          if (sweep_grid(P) <= 0) continue;
+          reset_sweep_flags(P);
+          run_sweep(P, a, false, false, 1);  // warm the plan and caches
+          TH_CUDA(cudaEventRecord(h->ev2, s));
+          run_sweep(P, a, false, false, a.epochs);
+          TH_CUDA(cudaEventRecord(h->ev3, s));
+          TH_CUDA(cudaEventSynchronize(h->ev3));
+          TH_CHECK(sweep_error(P) == 0, THETIS_E_TIMEOUT, "autotune: grid barrier timed out");
+          float ms = 0.f;
+          TH_CUDA(cudaEventElapsedTime(&ms, h->ev2, h->ev3));
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = {groups[gi], pers[pi], vi == 1};
+          }
+          TH_CUDA(cudaMemcpyAsync(P.x, x0, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+          if (P.Msl) TH_CUDA(cudaMemcpyAsync(P.s, s0, P.Msl * sizeof(float), cudaMemcpyDeviceToDevice, s));
+          if (P.M) TH_CUDA(cudaMemcpyAsync(P.r, r0, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+      TH_CUDA(cudaStreamSynchronize(s));
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = best;
+    }
+    P.small_g = best.small_g;
+    P.sweep_per_sm = best.per_sm;
+    P.force_full = best.full;
+    P.sweep_grid = -1;
+    if (small_group_out) *small_group_out = best.small_g;
+    if (ctas_per_sm_out) *ctas_per_sm_out = best.per_sm;
+  });
+}
+
+thetis_status thetis_set_launch_shape(thetis_handle* h, int32_t small_group, int32_t ctas_per_sm) {
+  if (!h || !h->P) {
+    set_error("null handle");
+    return THETIS_E_INVALID;
+  }
+  if (!(small_group == 1 || small_group == 2 || small_group == 4 || small_group == 8) || ctas_per_sm < 0) {
+    set_error("small_group must be 1, 2, 4 or 8 and ctas_per_sm >= 0");
+    return THETIS_E_INVALID;
+  }
+  h->P->small_g = small_group;
+  h->P->sweep_per_sm = ctas_per_sm;
+  h->P->sweep_grid = -1;
   return THETIS_OK;
 }
 

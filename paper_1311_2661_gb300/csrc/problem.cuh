@@ -141,6 +141,11 @@ struct Problem {
   unsigned* bar = nullptr;      // grid barrier state
   int* err = nullptr;           // barrier timeout flag
   int sweep_grid = -1;
+  // launch shape (set by thetis_autotune): lanes per SMALL unit, CTAs per SM
+  int small_g = 8;
+  int plan_g = -1;
+  int sweep_per_sm = 0;  // 0: as many as fit
+  bool force_full = false;  // use the full sweep even where the lean one applies
 
   // CUDA graph of one epoch
   cudaGraphExec_t epoch_graph = nullptr;
@@ -183,6 +188,7 @@ void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_x
 void refresh_only(Problem& P);
 void init_iterate(Problem& P);
 int sweep_grid(Problem& P);
+bool sweep_lean_possible(const Problem& P);
 void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int epochs);
 int sweep_error(Problem& P);
 void reset_sweep_flags(Problem& P);

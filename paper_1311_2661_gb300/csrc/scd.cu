@@ -12,7 +12,7 @@
 namespace thetis {
 
 constexpr int STEP_T = 256;        // threads per CTA of the step kernels
-constexpr int GROUP_SMALL = 8;     // lanes per unit for small units
+
 constexpr int CACHE = 4;           // r values a lane keeps between gather and scatter
 constexpr int CHECK_BLOCKS = 1024; // fixed grid of the check kernel (deterministic reduction)
 constexpr int NRED = 6;            // rho, obj, infeas, rr, ur, xx
@@ -38,6 +38,7 @@ struct StepView {
   float lfix;        // > 0: global L_max (step_rule 1)
   int k;
   int async;         // 1: atomic residual updates
+  int small_g;       // lanes per unit of the SMALL class: 1, 2, 4 or 8 (tuned)
 };
 
 struct SegLaunch {
@@ -178,7 +179,7 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_cg4(void* smem, const void* gmem) {
-  // L1-bypassing variant for data other SMs write (r)
+  // the same copy with a 128-byte L2 prefetch hint (used for r)
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
@@ -363,6 +364,10 @@ __device__ __forceinline__ void step_slacks(const StepView& V, int64_t i0, int64
 }
 
 // One tile of a colour: the CTA serves tile `tile` of the segment it falls in.
+// FULL = false compiles only the small / medium column and slack paths (for
+// problems without long columns or simplex blocks): fewer registers, more CTAs
+// per SM.
+template <bool FULL = true>
 __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch* segs, int nseg, int64_t tile,
                                              float* red_smem, unsigned char* dyn, bool staged = false) {
   int si = 0;
@@ -373,7 +378,9 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
   switch (S.cls) {
     case UC_HUGE:
     case UC_LARGE: {
-      if (b < S.n) step_huge(V, S.c0 + b, red_smem, dyn, staged);
+      if constexpr (FULL) {
+        if (b < S.n) step_huge(V, S.c0 + b, red_smem, dyn, staged);
+      }
       break;
     }
     case UC_MED: {
@@ -382,16 +389,26 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
       break;
     }
     case UC_SMALL: {
-      int64_t u = b * (STEP_T / GROUP_SMALL) + (threadIdx.x / GROUP_SMALL);
-      // every lane of the warp joins the group shuffles; groups past the end idle
+      // G lanes per unit (G tuned per problem); every lane of the warp joins the
+      // group shuffles, groups past the end idle
+      const int G = V.small_g;
+      int64_t u = b * (STEP_T / G) + (threadIdx.x / G);
       bool in = u < S.n;
-      if (__any_sync(0xffffffffu, in))
-        step_column<GROUP_SMALL, 4>(V, S.c0 + (in ? u : 0), threadIdx.x % GROUP_SMALL, red_smem, in);
+      if (__any_sync(0xffffffffu, in)) {
+        const int64_t j = S.c0 + (in ? u : 0);
+        const int gl = threadIdx.x % G;
+        if (G == 8) step_column<8, 4>(V, j, gl, red_smem, in);
+        else if (G == 4) step_column<4, 8>(V, j, gl, red_smem, in);
+        else if (G == 2) step_column<2, 8>(V, j, gl, red_smem, in);
+        else step_column<1, 8>(V, j, gl, red_smem, in);
+      }
       break;
     }
     case UC_BLOCK: {
-      int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
-      if (u < S.n) step_block(V, S.c0 + u * V.k, lane);
+      if constexpr (FULL) {
+        int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
+        if (u < S.n) step_block(V, S.c0 + u * V.k, lane);
+      }
       break;
     }
     default: {  // slacks
@@ -452,7 +469,7 @@ __device__ __forceinline__ void prefetch_tile(const StepView& V, const SegLaunch
     case UC_LARGE: u0 = b; u1 = b + 1; break;
     case UC_MED:
     case UC_BLOCK: u0 = b * (STEP_T / 32); u1 = u0 + STEP_T / 32; break;
-    case UC_SMALL: u0 = b * (STEP_T / GROUP_SMALL); u1 = u0 + STEP_T / GROUP_SMALL; break;
+    case UC_SMALL: u0 = b * (STEP_T / V.small_g); u1 = u0 + STEP_T / V.small_g; break;
     default: {
       const int64_t r0 = S.u0 + b * (STEP_T * SLACK_ROWS);
       const int64_t r1 = min(S.u0 + S.n, r0 + (int64_t)STEP_T * SLACK_ROWS);
@@ -483,7 +500,8 @@ __device__ __forceinline__ void prefetch_tile(const StepView& V, const SegLaunch
 // descriptor and prefetches its first tiles into L2.
 constexpr int PREFETCH_TILES = 2;
 
-__global__ void __launch_bounds__(STEP_T, 4) k_sweep(StepView V, const ColorLaunch* plan, const int64_t* ntiles,
+template <bool FULL>
+__global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, const ColorLaunch* plan, const int64_t* ntiles,
                                                      int ncolors, int epochs, unsigned* bar, int* err) {
   __shared__ float red_smem[33];
   __shared__ ColorLaunch cl[2];
@@ -499,7 +517,7 @@ __global__ void __launch_bounds__(STEP_T, 4) k_sweep(StepView V, const ColorLaun
     for (int c = 0; c < ncolors; ++c) {
       const int64_t nt = ntiles[c];
       for (int64_t t = blockIdx.x; t < nt; t += gridDim.x)
-        process_tile(V, cl[cur].seg, cl[cur].nseg, t, red_smem, dyn, first_staged && t == blockIdx.x);
+        process_tile<FULL>(V, cl[cur].seg, cl[cur].nseg, t, red_smem, dyn, first_staged && t == blockIdx.x);
       const bool last = (e == epochs - 1) && (c == ncolors - 1);
       if (last) break;
       const int cn = (c + 1 < ncolors) ? c + 1 : 0;
@@ -517,7 +535,7 @@ __global__ void __launch_bounds__(STEP_T, 4) k_sweep(StepView V, const ColorLaun
         int si = 0;
         while (si + 1 < nx.nseg && (int64_t)blockIdx.x >= nx.seg[si + 1].b0) ++si;
         const SegLaunch S = nx.seg[si];
-        if ((S.cls == UC_HUGE || S.cls == UC_LARGE) && (int64_t)blockIdx.x - S.b0 < S.n) {
+        if (FULL && (S.cls == UC_HUGE || S.cls == UC_LARGE) && (int64_t)blockIdx.x - S.b0 < S.n) {
           stage_huge(V, S.c0 + ((int64_t)blockIdx.x - S.b0), dyn);
           staged = true;
         }
@@ -535,13 +553,13 @@ __global__ void __launch_bounds__(STEP_T, 4) k_sweep(StepView V, const ColorLaun
   }
 }
 
-static int64_t ctas_for(int cls, int64_t n) {
+static int64_t ctas_for(int cls, int64_t n, int small_g) {
   switch (cls) {
     case UC_HUGE:
     case UC_LARGE: return n;
     case UC_MED:
     case UC_BLOCK: return (n + STEP_T / 32 - 1) / (STEP_T / 32);
-    case UC_SMALL: return (n + STEP_T / GROUP_SMALL - 1) / (STEP_T / GROUP_SMALL);
+    case UC_SMALL: return (n + STEP_T / small_g - 1) / (STEP_T / small_g);
     default: return (n + STEP_T * SLACK_ROWS - 1) / (STEP_T * SLACK_ROWS);
   }
 }
@@ -570,6 +588,7 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.lfix = (a.step_rule == 1) ? (float)(a.beta * P.lmax_sq + 1.0 / a.beta) : 0.f;
   V.k = P.k;
   V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
+  V.small_g = P.small_g;
   return V;
 }
 
@@ -599,7 +618,7 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
               tot = 0;
             }
             CL.seg[CL.nseg++] = SegLaunch{cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
-            tot += ctas_for(cls, sg.u1 - sg.u0);
+            tot += ctas_for(cls, sg.u1 - sg.u0, P.small_g);
           }
       launch(CL, tot);
     }
@@ -607,7 +626,7 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
       ColorLaunch CL{};
       CL.seg[0] = SegLaunch{UC_COUNT, 0, P.Msl, 0, 0};
       CL.nseg = 1;
-      launch(CL, ctas_for(UC_COUNT, P.Msl));
+      launch(CL, ctas_for(UC_COUNT, P.Msl, P.small_g));
     }
     TH_CUDA(cudaGetLastError());
     return;
@@ -617,11 +636,11 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
       CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
-      tot += ctas_for(sg.cls, sg.u1 - sg.u0);
+      tot += ctas_for(sg.cls, sg.u1 - sg.u0, P.small_g);
     }
     if (cp.srow1 > cp.srow0) {
       CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
-      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0);
+      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0, P.small_g);
     }
     launch(CL, tot);
   }
@@ -632,7 +651,7 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
 // persistent sweep: device plan, cooperative launch
 // ---------------------------------------------------------------------------
 static void ensure_sweep_plan(Problem& P) {
-  if (P.d_plan) return;
+  if (P.d_plan && P.plan_g == P.small_g) return;
   const int C = P.ncolors;
   std::vector<ColorLaunch> h(C > 0 ? C : 1);
   std::vector<int64_t> nt(C > 0 ? C : 1, 0);
@@ -642,11 +661,11 @@ static void ensure_sweep_plan(Problem& P) {
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
       CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
-      tot += ctas_for(sg.cls, sg.u1 - sg.u0);
+      tot += ctas_for(sg.cls, sg.u1 - sg.u0, P.small_g);
     }
     if (cp.srow1 > cp.srow0) {
       CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
-      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0);
+      tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0, P.small_g);
     }
     h[c] = CL;
     nt[c] = tot;
@@ -655,13 +674,33 @@ static void ensure_sweep_plan(Problem& P) {
   int64_t* dn = P.mem.alloc<int64_t>(nt.size());
   TH_CUDA(cudaMemcpyAsync(dp, h.data(), h.size() * sizeof(ColorLaunch), cudaMemcpyHostToDevice, P.stream));
   TH_CUDA(cudaMemcpyAsync(dn, nt.data(), nt.size() * sizeof(int64_t), cudaMemcpyHostToDevice, P.stream));
-  P.bar = P.mem.alloc<unsigned>(2);
-  P.err = P.mem.alloc<int>(1);
+  if (!P.bar) {
+    P.bar = P.mem.alloc<unsigned>(2);
+    P.err = P.mem.alloc<int>(1);
+  }
   TH_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), P.stream));
   TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
   TH_CUDA(cudaStreamSynchronize(P.stream));
   P.d_plan = dp;
+  P.plan_g = P.small_g;
   P.d_ntiles = dn;
+}
+
+// The lean sweep serves problems whose colours hold only small / medium
+// columns and slacks (no long columns, no simplex blocks).
+bool sweep_lean_possible(const Problem& P) {
+  for (auto& cp : P.plan)
+    for (auto& sg : cp.segs)
+      if (sg.cls == UC_HUGE || sg.cls == UC_LARGE || sg.cls == UC_BLOCK) return false;
+  return true;
+}
+
+static bool sweep_lean(const Problem& P) {
+  if (P.force_full) return false;
+  for (auto& cp : P.plan)
+    for (auto& sg : cp.segs)
+      if (sg.cls == UC_HUGE || sg.cls == UC_LARGE || sg.cls == UC_BLOCK) return false;
+  return true;
 }
 
 // Grid of the cooperative sweep (0: not available on this device).
@@ -671,7 +710,9 @@ int sweep_grid(Problem& P) {
   TH_CUDA(cudaGetDevice(&dev));
   TH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep, STEP_T, STEP_SMEM));
+  if (sweep_lean(P)) TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<false>, STEP_T, 0));
+  else TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<true>, STEP_T, STEP_SMEM));
+  if (P.sweep_per_sm > 0 && P.sweep_per_sm < per) per = P.sweep_per_sm;
   P.sweep_grid = (coop && per > 0) ? sms * per : 0;
   return P.sweep_grid;
 }
@@ -691,7 +732,11 @@ void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int
   const int64_t* nt = P.d_ntiles;
   int C = P.ncolors;
   void* args[] = {(void*)&V, (void*)&plan, (void*)&nt, (void*)&C, (void*)&epochs, (void*)&P.bar, (void*)&P.err};
-  TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep, dim3(grid), dim3(STEP_T), args, STEP_SMEM, P.stream));
+  if (sweep_lean(P))
+    TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep<false>, dim3(grid), dim3(STEP_T), args, 0, P.stream));
+  else
+    TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep<true>, dim3(grid), dim3(STEP_T), args, STEP_SMEM,
+                                        P.stream));
   TH_LAUNCHED();
 }
 

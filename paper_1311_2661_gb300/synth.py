@@ -82,19 +82,26 @@ def er_graph(n: int, m: int, seed: int) -> Graph:
     if m > n * (n - 1) // 2:
         raise ValueError("too many edges for a simple graph")
     rng = np.random.default_rng(seed)
+    # draw pairs until at least m distinct ones exist, then keep a uniformly
+    # random m-subset of the distinct pairs (uniform over m-edge graphs)
     keys = np.empty(0, np.int64)
-    need = m
-    while keys.shape[0] < m:
-        draw = int(need * 1.2) + 64
+    draw = int(m * 1.1) + 64
+    while True:
         u = rng.integers(0, n, size=draw)
         v = rng.integers(0, n, size=draw)
-        new = _canonical_unique(u, v, n, draw)
-        allk = np.concatenate([keys, new])
-        _, first = np.unique(allk, return_index=True)
-        first.sort()
-        keys = allk[first][:m]
-        need = m - keys.shape[0]
-    eu, ev = _finish(keys, n, None)
+        keep = u != v
+        lo = np.minimum(u[keep], v[keep]).astype(np.int64)
+        hi = np.maximum(u[keep], v[keep]).astype(np.int64)
+        keys = np.sort(np.concatenate([keys, lo * n + hi]))
+        if keys.shape[0] > 1:
+            keys = keys[np.concatenate([[True], keys[1:] != keys[:-1]])]
+        if keys.shape[0] >= m:
+            break
+        draw = int((m - keys.shape[0]) * 1.5) + 64
+    if keys.shape[0] > m:
+        keys = keys[np.sort(rng.choice(keys.shape[0], size=m, replace=False))]
+    eu = (keys // n).astype(np.int32)
+    ev = (keys % n).astype(np.int32)
     return Graph(n=n, eu=eu, ev=ev, meta={"kind": "er", "n": n, "m": m, "seed": seed})
 
 

@@ -87,6 +87,8 @@ def _load():
         "thetis_destroy": (st, [P]),
         "thetis_round_is_static": (st, [i64, i64, P, P, P, P, u64, i32, P, P, P]),
         "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
+        "thetis_autotune": (st, [P, P, i32, P, P]),
+        "thetis_set_launch_shape": (st, [P, i32, i32]),
         "thetis_round_batch": (st, [P, u64, i32, P, i32, P, P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -297,6 +299,19 @@ def _out_ptr(out):
     if _is_torch(out):
         return out.data_ptr(), (MEM_DEVICE if out.is_cuda else MEM_HOST)
     return out.ctypes.data, MEM_HOST
+
+
+def thetis_autotune(h: Handle, beta=1e2, step_rule=0, trial_epochs=3):
+    """Pick and apply the sweep's launch shape; returns (small_group, ctas_per_sm)."""
+    p = Params()
+    p.beta, p.step_rule, p.refresh_every = float(beta), int(step_rule), 10
+    g, k = C.c_int32(), C.c_int32()
+    _check(_lib.thetis_autotune(h.ptr, C.byref(p), int(trial_epochs), C.byref(g), C.byref(k)))
+    return g.value, k.value
+
+
+def thetis_set_launch_shape(h: Handle, small_group, ctas_per_sm=0):
+    _check(_lib.thetis_set_launch_shape(h.ptr, int(small_group), int(ctas_per_sm)))
 
 
 def thetis_build_batch(kinds, vertex_offset, edge_offset, eu, ev, w, seed=0, stream=None) -> Handle:

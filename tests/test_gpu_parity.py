@@ -287,3 +287,38 @@ def test_async_mode_converges_to_oracle_solution():
     assert info["rho"] <= 1e-5
     assert rel(info["fbeta"], info_o["fbeta"]) <= 1e-5
     assert np.max(np.abs(gpu_full_x(h) - x_o)) <= 1e-2
+
+
+def test_autotune_keeps_the_iterate_and_parity():
+    """Tuning times trial sweeps on the real problem but restores the iterate;
+    a solve after tuning still matches the oracle (the lane group only changes
+    the FP32 summation order inside small columns)."""
+    T = gpu()
+    g = is_graph(3000, 20000, 2)
+    h, lp = _pair("is", g, seed=5)
+    h.solve(beta=100.0, epochs=7)
+    x_before = gpu_full_x(h)
+    sg, per = T.thetis_autotune(h, beta=100.0, trial_epochs=2)
+    assert sg in (1, 2, 4, 8) and per in (0, 1, 2)
+    assert np.array_equal(gpu_full_x(h), x_before)
+    h.solve(beta=100.0, epochs=33)
+    x_o, _ = lp.solve(beta=100.0, epochs=40, refresh_every=10, color=lp.color(5)[0])
+    assert np.max(np.abs(gpu_full_x(h) - x_o)) <= X_TOL
+    # a second handle of the same shape takes the cached choice
+    h2 = build_gpu("is", g, seed=5)
+    assert T.thetis_autotune(h2, beta=100.0, trial_epochs=2) == (sg, per)
+
+
+@pytest.mark.parametrize("group", [1, 2, 4, 8])
+def test_every_small_group_matches_oracle(group):
+    """Each lane-group variant of the small-column step is exact to tolerance."""
+    g = vc_graph(2000, 8000, 1)
+    h, lp = _pair("vc", g, seed=5)
+    _force_group(h, group)
+    h.solve(beta=100.0, epochs=30, refresh_every=10)
+    x_o, _ = lp.solve(beta=100.0, epochs=30, refresh_every=10, color=lp.color(5)[0])
+    assert np.max(np.abs(gpu_full_x(h) - x_o)) <= X_TOL
+
+
+def _force_group(h, group):
+    gpu().thetis_set_launch_shape(h, group, 0)
