@@ -303,6 +303,63 @@ thetis_status thetis_round_batch(thetis_handle* h, uint64_t seed, int32_t reps, 
                                  int32_t out_mem, double* obj_out, int32_t* status_out,
                                  int32_t* best_rep_out);
 
+/*
+ * Request server with continuous batching (deployment layer; the paper solves
+ * one LP at a time).  Worker threads each own a CUDA stream; a free worker
+ * takes the oldest queued request and every other queued VC / IS request with
+ * the same solve parameters (up to max_batch, within the memory budget) and
+ * solves them together through thetis_build_batch, so requests arriving while
+ * others run join the next batch and different workers' work overlaps on the
+ * GPU.  MC requests are solved one per worker.  Admission: a request is started
+ * only while the estimated device bytes of the running requests plus its own
+ * stay within hbm_budget_bytes; a request larger than the whole budget is
+ * refused at submit time with THETIS_E_BUDGET.
+ * Within a batch, tol applies to the largest residual of its members: a request
+ * solved in a batch runs the batch's epoch count (at least as many as alone);
+ * with tol = 0 (a fixed epoch count) its result equals the result alone up to
+ * FP32 summation order.
+ */
+typedef struct {
+  int32_t kind;            /* THETIS_ROUND_VC, THETIS_ROUND_IS or THETIS_ROUND_MC */
+  int64_t n, m;            /* vertices, edges */
+  const int32_t *eu, *ev;  /* HOST edge endpoints [m], copied at submit */
+  const float* w;          /* VC / IS vertex weights [n] */
+  const float* ce;         /* MC edge weights [m] */
+  int32_t k;               /* MC labels */
+  const int32_t* terminals;/* MC terminals [k] */
+  double beta;             /* solve parameters as in thetis_params */
+  int32_t epochs;
+  double tol;
+  int32_t refresh_every;
+  uint64_t seed;           /* colouring and rounding seed */
+  int32_t reps;            /* rounding repetitions (IS, MC) */
+} thetis_request;
+
+typedef struct {
+  int32_t status;          /* THETIS_OK, THETIS_NOT_CONVERGED or an error of build / solve / round */
+  double obj;              /* objective of the rounded solution */
+  int32_t valid;           /* exact validity check passed */
+  int32_t epochs_run;
+  double rho;              /* residual of the solve (largest over its batch) */
+  double queue_ms, service_ms, latency_ms; /* submit->start, start->done, submit->done (host clock) */
+  int32_t batch_size;      /* requests solved together with this one */
+  char message[160];       /* error text when status is an error, else empty */
+} thetis_result;
+
+thetis_status thetis_server_create(size_t hbm_budget_bytes, int32_t workers, int32_t max_batch,
+                                   thetis_server** out);
+/* Queue a request; *id identifies it.  The arrays are copied before return. */
+thetis_status thetis_submit(thetis_server* sv, const thetis_request* req, uint64_t* id);
+/* THETIS_PENDING while the request runs; then THETIS_OK with the result, the
+ * labels (host, n bytes) and the fractional point (host, n floats; n*k for MC)
+ * copied to the non-NULL outputs.  A request's result is returned once. */
+thetis_status thetis_poll(thetis_server* sv, uint64_t id, uint8_t* labels_out, float* x_out,
+                          thetis_result* out);
+thetis_status thetis_server_stats(thetis_server* sv, int64_t* submitted, int64_t* completed,
+                                  int64_t* queued, int64_t* in_flight_bytes);
+/* Finishes every queued request, then stops the workers. */
+thetis_status thetis_server_destroy(thetis_server* sv);
+
 /* Copy the structural part of the iterate, original column order, as FP32. */
 thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem);
 /* Copy the slack part of the iterate (one value per GE/LE row, row order). */

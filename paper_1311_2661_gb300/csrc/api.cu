@@ -278,7 +278,8 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     const bool ub = dub != nullptr, xb = dxb != nullptr;
     refresh_only(P);
     TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
-    const bool persistent = a.mode == THETIS_MODE_COLORED && p->engine == 0 && P.ncolors > 0 && sweep_grid(P) > 0;
+    const bool persistent = a.mode == THETIS_MODE_COLORED && p->engine == 0 && P.ncolors > 0 && coop_allowed() &&
+                            sweep_grid(P) > 0;
     if (persistent) reset_sweep_flags(P);
     // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
     bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&

@@ -643,12 +643,15 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
   for (int64_t r = r0; r < r0 + nr; ++r) {
     const int in = (int)(r % 3), out = (int)((r + 1) % 3), z = (int)((r + 2) % 3);
     const int64_t ns = __ldcg(R.fc + 2 * in), nb = __ldcg(R.fc + 2 * in + 1);
-    if (ns + nb == 0) return;  // every CTA reads the same counts: all stop together
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+      // slot z is nobody's input this round; clearing it even when the
+      // frontier is empty keeps rounds launched past the end (one launch per
+      // round) from reading a stale count three rounds later
       R.fc[2 * z] = 0;
       R.fc[2 * z + 1] = 0;
-      atomicAdd(R.done, (unsigned long long)(ns + nb));
+      if (ns + nb) atomicAdd(R.done, (unsigned long long)(ns + nb));
     }
+    if (ns + nb == 0) return;  // every CTA reads the same counts: all stop together
     const uint32_t* front_s = R.fs[r & 1];
     const uint32_t* front_b = R.fb[r & 1];
     uint32_t* next_s = R.fs[(r + 1) & 1];
@@ -1159,7 +1162,7 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     k_adj_fill<<<fill_grid, 256, 0, s>>>(V, Us, aptr, nhigh, adj, R.cnt, R.fs[0], R.fc + 0, R.fb[0], R.fc + 1);
     TH_LAUNCHED();
     const int64_t max_rounds = Us + 2;
-    if (coop && per > 0) {
+    if (coop && per > 0 && coop_allowed()) {
       // every round in one cooperative launch, a grid barrier between rounds
       int grid = sms * per;
       int64_t r0 = 0, nr = max_rounds;

@@ -40,6 +40,12 @@ struct Error {
 
 // Count of kernel launches made by this library (all threads).
 void count_launch(uint64_t n = 1);
+
+// Per host thread: when set, this thread's calls use no cooperative launches
+// (the server's worker threads share the GPU through several streams, where
+// ordinary launches are the safe choice).
+bool coop_allowed();
+void set_coop_allowed(bool on);
 uint64_t launch_count();
 
 #define TH_LAUNCHED() ::thetis::count_launch(1)

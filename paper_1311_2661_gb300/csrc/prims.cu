@@ -12,6 +12,10 @@ static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 const char* get_error() { return g_err.c_str(); }
 
+static thread_local bool g_coop = true;
+bool coop_allowed() { return g_coop; }
+void set_coop_allowed(bool on) { g_coop = on; }
+
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }

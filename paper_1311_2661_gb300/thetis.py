@@ -89,6 +89,11 @@ def _load():
         "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
         "thetis_autotune": (st, [P, P, i32, P, P]),
         "thetis_set_launch_shape": (st, [P, i32, i32]),
+        "thetis_server_create": (st, [C.c_size_t, i32, i32, P]),
+        "thetis_submit": (st, [P, P, P]),
+        "thetis_poll": (st, [P, u64, P, P, P]),
+        "thetis_server_stats": (st, [P, P, P, P, P]),
+        "thetis_server_destroy": (st, [P]),
         "thetis_round_batch": (st, [P, u64, i32, P, i32, P, P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -308,6 +313,103 @@ def thetis_autotune(h: Handle, beta=1e2, step_rule=0, trial_epochs=3):
     g, k = C.c_int32(), C.c_int32()
     _check(_lib.thetis_autotune(h.ptr, C.byref(p), int(trial_epochs), C.byref(g), C.byref(k)))
     return g.value, k.value
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int64), ("m", C.c_int64), ("eu", C.c_void_p), ("ev", C.c_void_p),
+                ("w", C.c_void_p), ("ce", C.c_void_p), ("k", C.c_int32), ("terminals", C.c_void_p),
+                ("beta", C.c_double), ("epochs", C.c_int32), ("tol", C.c_double), ("refresh_every", C.c_int32),
+                ("seed", C.c_uint64), ("reps", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("obj", C.c_double), ("valid", C.c_int32), ("epochs_run", C.c_int32),
+                ("rho", C.c_double), ("queue_ms", C.c_double), ("service_ms", C.c_double),
+                ("latency_ms", C.c_double), ("batch_size", C.c_int32), ("message", C.c_char * 160)]
+
+
+class Server:
+    """thetis_server: continuous-batching request server (host arrays only)."""
+
+    def __init__(self, budget_bytes=120 << 30, workers=4, max_batch=64):
+        h = C.c_void_p()
+        _check(_lib.thetis_server_create(int(budget_bytes), int(workers), int(max_batch), C.byref(h)))
+        self._h = h.value
+        self._sizes = {}
+
+    def submit(self, kind, g, beta=1e2, epochs=1000, tol=1e-3, refresh_every=10, seed=0, reps=10):
+        """kind in {"vc", "is", "mc"}; g a synth.Graph.  Returns the request id."""
+        q = Request()
+        q.kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC}[kind]
+        q.n, q.m = int(g.n), int(g.m)
+        keep = [np.ascontiguousarray(g.eu, np.int32), np.ascontiguousarray(g.ev, np.int32)]
+        q.eu, q.ev = keep[0].ctypes.data, keep[1].ctypes.data
+        if kind == "mc":
+            ce = np.ascontiguousarray(g.ce, np.float32)
+            t = np.ascontiguousarray(g.terminals, np.int32)
+            keep += [ce, t]
+            q.ce, q.terminals, q.k = ce.ctypes.data, t.ctypes.data, int(len(t))
+        else:
+            w = np.ascontiguousarray(g.w, np.float32)
+            keep.append(w)
+            q.w = w.ctypes.data
+        q.beta, q.epochs, q.tol, q.refresh_every = float(beta), int(epochs), float(tol), int(refresh_every)
+        q.seed, q.reps = int(seed), int(reps)
+        rid = C.c_uint64()
+        _check(_lib.thetis_submit(self._h, C.byref(q), C.byref(rid)))
+        self._sizes[rid.value] = (int(g.n), int(g.n) * (q.k if kind == "mc" else 1))
+        return rid.value
+
+    def poll(self, rid):
+        """None while pending; else (labels, x, result dict)."""
+        n, nx = self._sizes[rid]
+        lab = np.zeros(n, np.uint8)
+        x = np.zeros(nx, np.float32)
+        res = Result()
+        st = _lib.thetis_poll(self._h, C.c_uint64(rid), lab.ctypes.data, x.ctypes.data, C.byref(res))
+        if st == THETIS_PENDING:
+            return None
+        _check(st)
+        del self._sizes[rid]
+        info = {f: getattr(res, f) for f, _ in Result._fields_}
+        info["message"] = res.message.decode(errors="replace")
+        return lab, x, info
+
+    def stats(self):
+        v = [C.c_int64() for _ in range(4)]
+        _check(_lib.thetis_server_stats(self._h, *[C.byref(a) for a in v]))
+        return dict(submitted=v[0].value, completed=v[1].value, queued=v[2].value, in_flight_bytes=v[3].value)
+
+    def close(self):
+        if self._h:
+            _lib.thetis_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def thetis_server_create(budget_bytes=120 << 30, workers=4, max_batch=64):
+    return Server(budget_bytes, workers, max_batch)
+
+
+def thetis_submit(server: Server, kind, g, **kw):
+    return server.submit(kind, g, **kw)
+
+
+def thetis_poll(server: Server, rid):
+    return server.poll(rid)
+
+
+def thetis_server_stats(server: Server):
+    return server.stats()
+
+
+def thetis_server_destroy(server: Server):
+    server.close()
 
 
 def thetis_set_launch_shape(h: Handle, small_group, ctas_per_sm=0):

@@ -1,0 +1,114 @@
+"""The request server: continuous batching, admission by memory budget, and
+every result the same alone and in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_2661_gb300 import synth
+from tests.gpu_common import OBJ_RTOL, X_TOL, build_gpu, gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        r = rng.random()
+        if r < 0.4 or r < 0.8:
+            kind = "vc" if r < 0.4 else "is"
+            n = int(np.exp(rng.uniform(np.log(50), np.log(3000))))
+            m = int(n * rng.uniform(2, 8) / 2)
+            g = synth.er_graph(n, min(m, n * (n - 1) // 2), int(rng.integers(1 << 30)))
+            g.w = synth.int_weights(n, 1, 10, rng)
+        else:
+            kind = "mc"
+            side = int(rng.integers(6, 24))
+            g = synth.grid_graph(side, side, 4, int(rng.integers(1 << 30)))
+        out.append((kind, g))
+    return out
+
+
+def _wait(sv, ids, timeout=300):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(ids):
+        for i in ids:
+            if i in res:
+                continue
+            r = sv.poll(i)
+            if r is not None:
+                res[i] = r
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.002)
+    return res
+
+
+def test_mix_equals_alone_and_oracle():
+    """Fixed epoch count (tol = 0): each request solved in the mix gives the
+    same labels and iterate as solved alone (single-instance API) and as the
+    FP64 oracle, within the stated tolerances."""
+    T = gpu()
+    reqs = _requests(24, 5)
+    sv = T.Server(budget_bytes=4 << 30, workers=3, max_batch=8)
+    ids = []
+    for t, (kind, g) in enumerate(reqs):
+        ids.append(sv.submit(kind, g, beta=100.0, epochs=40, tol=0.0, refresh_every=10, seed=7, reps=10))
+        if t % 5 == 4:
+            time.sleep(0.01)  # later requests arrive while earlier ones run
+    res = _wait(sv, ids)
+    batched = 0
+    for (kind, g), i in zip(reqs, ids):
+        lab, x, info = res[i]
+        assert info["status"] in (T.THETIS_NOT_CONVERGED, T.THETIS_OK), info["message"]
+        assert info["valid"]
+        batched += info["batch_size"] > 1
+        h = build_gpu(kind, g, seed=7)
+        h.solve(beta=100.0, epochs=40, refresh_every=10)
+        lab_a, info_a = h.round(seed=7, reps=10)
+        xa = h.get_x()
+        nx = len(x)
+        assert np.max(np.abs(x - xa[:nx])) <= X_TOL
+        lp = oracle.build_problem(kind, g)
+        x_o, _ = lp.solve(beta=100.0, epochs=40, refresh_every=10, color=lp.color(7)[0])
+        assert np.max(np.abs(x.astype(np.float64) - x_o[:nx])) <= X_TOL
+        # the rounding is a function of x: compare it on the server's own iterate
+        xv = x.astype(np.float64)
+        r = lp.round_vc(xv) if kind == "vc" else (lp.round_is(xv, 7, 10) if kind == "is" else lp.round_mc(xv, 7, 10))
+        assert np.array_equal(lab, r["labels"])
+        assert rel(info["obj"], r["obj"]) <= 1e-12
+    assert batched > 0, "no request was batched with another"
+    sv.close()
+
+
+def test_budget_and_overflow():
+    T = gpu()
+    sv = T.Server(budget_bytes=64 << 20, workers=2, max_batch=4)
+    big = synth.er_graph(200000, 1000000, 1)
+    big.w = np.ones(big.n, np.float32)
+    with pytest.raises(T.ThetisError) as ei:
+        sv.submit("vc", big, epochs=5)
+    assert ei.value.status == T.THETIS_E_BUDGET
+    # many requests, each fitting the budget alone: all complete
+    reqs = _requests(12, 9)
+    ids = [sv.submit(k, g, beta=50.0, epochs=10, tol=0.0, seed=1) for k, g in reqs]
+    res = _wait(sv, ids)
+    assert all(r[2]["valid"] for r in res.values())
+    st = sv.stats()
+    assert st["completed"] == 12 and st["in_flight_bytes"] == 0 and st["queued"] == 0
+    sv.close()
+
+
+def test_to_tolerance_in_batches():
+    """With tol > 0 every request finishes at rho <= tol (the batch's largest)."""
+    T = gpu()
+    reqs = [(k, g) for k, g in _requests(10, 3) if k != "mc"]
+    sv = T.Server(budget_bytes=8 << 30, workers=2, max_batch=16)
+    ids = [sv.submit(k, g, beta=100.0, epochs=5000, tol=1e-3, refresh_every=10, seed=2) for k, g in reqs]
+    res = _wait(sv, ids)
+    for (kind, g), i in zip(reqs, ids):
+        lab, x, info = res[i]
+        assert info["status"] == T.THETIS_OK and info["rho"] <= 1e-3 and info["valid"]
+    sv.close()
