@@ -198,3 +198,46 @@ def batch_instances(count: int, n_lo: int, n_hi: int, d_lo: float, d_hi: float,
         g.w = int_weights(n, w_lo, w_hi, np.random.default_rng(int(seeds[t]) ^ 0x5DEECE66D))
         out.append(("vc" if t < count // 2 else "is", g))
     return out
+
+
+def serving_pool(count: int, seed: int, n_lo: float = 1e3, n_hi: float = 1e6, d_lo: float = 4.0,
+                 d_hi: float = 16.0, side_lo: int = 64, side_hi: int = 512, k: int = 4,
+                 mix=(0.4, 0.4, 0.2)):
+    """Request pool of the serving workload: ``count`` graphs whose kinds follow
+    ``mix`` (vertex cover, independent set, multiway cut) in proportion.  VC/IS:
+    ER with n log-uniform in [n_lo, n_hi], average degree U[d_lo, d_hi],
+    integer weights U[1, 10].  MC: a side x side 4-neighbour grid, side
+    U[side_lo, side_hi], ``k`` terminals, lognormal(0, 1) edge weights.
+
+    Returns a list of (kind, Graph)."""
+    rng = np.random.default_rng(seed)
+    n_vc = int(round(count * mix[0]))
+    n_is = int(round(count * mix[1]))
+    kinds = ["vc"] * n_vc + ["is"] * n_is + ["mc"] * (count - n_vc - n_is)
+    out = []
+    for kind in kinds:
+        s = int(rng.integers(0, 2**62))
+        if kind == "mc":
+            side = int(rng.integers(side_lo, side_hi + 1))
+            out.append((kind, grid_graph(side, side, k, s)))
+            continue
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        m = int(round(n * rng.uniform(d_lo, d_hi) / 2.0))
+        g = er_graph(n, m, s)
+        g.w = int_weights(n, 1, 10, np.random.default_rng(s ^ 0x5DEECE66D))
+        out.append((kind, g))
+    return out
+
+
+def poisson_trace(rate: float, count: int, kinds, seed: int, mix=(0.4, 0.4, 0.2)):
+    """Open-loop arrival trace: ``count`` arrival times (seconds from the start)
+    of a Poisson process with ``rate`` per second, and for each arrival the
+    index of a pool entry: the kind is drawn from ``mix``, then an entry of that
+    kind uniformly.  ``kinds`` lists the pool's kinds."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    by_kind = {c: np.flatnonzero(np.asarray(kinds) == c) for c in ("vc", "is", "mc")}
+    names = np.array(["vc", "is", "mc"])
+    pick = names[rng.choice(3, size=count, p=np.asarray(mix, np.float64) / np.sum(mix))]
+    idx = np.array([by_kind[c][rng.integers(len(by_kind[c]))] for c in pick], np.int64)
+    return t, idx

@@ -363,8 +363,8 @@ class Server:
     def poll(self, rid):
         """None while pending; else (labels, x, result dict)."""
         n, nx = self._sizes[rid]
-        lab = np.zeros(n, np.uint8)
-        x = np.zeros(nx, np.float32)
+        lab = np.empty(n, np.uint8)
+        x = np.empty(nx, np.float32)
         res = Result()
         st = _lib.thetis_poll(self._h, C.c_uint64(rid), lab.ctypes.data, x.ctypes.data, C.byref(res))
         if st == THETIS_PENDING:
