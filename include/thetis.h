@@ -281,14 +281,27 @@ thetis_status thetis_set_launch_shape(thetis_handle* h, int32_t small_group, int
  * The colouring hashes instance-local ids, so every instance is coloured, swept
  * and rounded exactly as thetis_build_vc / _is + thetis_solve + thetis_round
  * would treat it alone (up to FP32 summation order).  The handle is solved with
- * thetis_solve: one sweep advances every instance, and tol applies to the
- * largest residual over all instances.  thetis_get_x returns the concatenated
- * vertex values.  mem applies to every array.
+ * thetis_solve: one sweep advances every unfinished instance.  tol applies to
+ * each instance separately: at every check (every refresh_every epochs) an
+ * instance whose own rho <= tol stops -- it is no longer swept -- which is
+ * exactly where a solve of it alone stops; the solve ends when every instance
+ * has stopped or after `epochs`.  The returned rho is the largest rho any
+ * instance stopped at; thetis_batch_info gives each instance's epochs and rho.
+ * thetis_get_x returns the concatenated vertex values.  mem applies to every
+ * array.
  */
 thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int64_t* vertex_offset,
                                  const int64_t* edge_offset, const int32_t* eu, const int32_t* ev,
                                  const float* w, int32_t mem, uint64_t seed, void* stream,
                                  thetis_handle** out);
+
+/*
+ * thetis_batch_info -- per-instance outcome of the last thetis_solve of a batch
+ * handle: epochs_out[count] (epochs the instance was swept) and rho_out[count]
+ * (its residual when it stopped), HOST arrays, each may be NULL.
+ * THETIS_E_INVALID for a handle that is not a batch.
+ */
+thetis_status thetis_batch_info(const thetis_handle* h, int32_t* epochs_out, double* rho_out);
 
 /*
  * thetis_round_batch -- repair + rounding of every instance of a batch handle,
@@ -340,7 +353,7 @@ typedef struct {
   double obj;              /* objective of the rounded solution */
   int32_t valid;           /* exact validity check passed */
   int32_t epochs_run;
-  double rho;              /* residual of the solve (largest over its batch) */
+  double rho;              /* residual where this request stopped (its own, also in a batch) */
   double queue_ms, service_ms, latency_ms; /* submit->start, start->done, submit->done (host clock) */
   int32_t batch_size;      /* requests solved together with this one */
   char message[160];       /* error text when status is an error, else empty */

@@ -281,6 +281,7 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     const bool persistent = a.mode == THETIS_MODE_COLORED && p->engine == 0 && P.ncolors > 0 && coop_allowed() &&
                             sweep_grid(P) > 0;
     if (persistent) reset_sweep_flags(P);
+    batch_begin_solve(P);
     // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
     bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
                   h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g;
@@ -343,14 +344,22 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
         TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
         sweep_ms += t;
         checked_last = true;
-        if (co.rho <= a.tol) {
+        // a batch converges instance by instance (each against tol)
+        if (P.nbatch > 0 ? batch_after_check(P, a.tol, ep) : co.rho <= a.tol) {
           converged = true;
           break;
         }
       }
     }
-    if (!checked_last) refresh_and_check(P, a, ub, xb, co);
-    if (a.epochs == 0) converged = co.rho <= a.tol;
+    if (!checked_last) {
+      refresh_and_check(P, a, ub, xb, co);
+      converged = (P.nbatch > 0) ? batch_after_check(P, a.tol, ep) : co.rho <= a.tol;
+    }
+    if (P.nbatch > 0) {
+      batch_end_solve(P, ep);
+      co.rho = 0.0;  // the largest rho any instance stopped at
+      for (double v : P.h_brho) co.rho = std::max(co.rho, v);
+    }
     TH_CUDA(cudaEventRecord(h->ev1, s));
     TH_CUDA(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
@@ -641,6 +650,7 @@ thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int6
     P.h_bkind = hk;
     P.h_bnoff = hn;
     P.h_beoff = he;
+    batch_index(P);
     finish_create(h);
   });
   if (st != THETIS_OK) {
@@ -648,6 +658,23 @@ thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int6
     return st;
   }
   *out = h;
+  return THETIS_OK;
+}
+
+thetis_status thetis_batch_info(const thetis_handle* h, int32_t* epochs_out, double* rho_out) {
+  if (!h || !h->P) {
+    set_error("null handle");
+    return THETIS_E_INVALID;
+  }
+  const Problem& P = *h->P;
+  if (P.kind != KIND_BATCH) {
+    set_error("thetis_batch_info needs a handle from thetis_build_batch");
+    return THETIS_E_INVALID;
+  }
+  for (int64_t t = 0; t < P.nbatch; ++t) {
+    if (epochs_out) epochs_out[t] = P.h_bepochs[t];
+    if (rho_out) rho_out[t] = P.h_brho[t];
+  }
   return THETIS_OK;
 }
 

@@ -10,6 +10,7 @@
 // rounding (Sec. 2, App. B.2, App. C) are done per instance here.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "problem.cuh"
@@ -278,6 +279,81 @@ void round_batch(Problem& P, uint64_t seed, int reps, uint8_t* d_labels, std::ve
     if (vc && a >= 1.0) status[t] = -1;
     else status[t] = hbad[t] ? 0 : 1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// per-instance convergence
+// ---------------------------------------------------------------------------
+__global__ void k_binst(const uint32_t* col_of_orig, const uint32_t* orig_of_row, const int64_t* noff,
+                        const int64_t* eoff, int64_t count, int64_t Ns, int64_t M, int32_t* inst_col,
+                        int32_t* inst_row) {
+  GSTRIDE(i, Ns > M ? Ns : M) {
+    if (i < Ns) inst_col[col_of_orig[i]] = (int32_t)seg_of(noff, count, i);
+    if (i < M) inst_row[i] = (int32_t)seg_of(eoff, count, (int64_t)orig_of_row[i]);
+  }
+}
+
+void batch_index(Problem& P) {
+  cudaStream_t s = P.stream;
+  const int64_t count = P.nbatch;
+  P.binst_col = P.mem.alloc<int32_t>(P.Ns + 1);
+  P.binst_row = P.mem.alloc<int32_t>(P.M + 1);
+  P.bfrozen = P.mem.alloc<uint8_t>(count);
+  P.brho = P.mem.alloc<unsigned long long>(count);
+  TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, count, s));
+  TH_CUDA(cudaMemsetAsync(P.brho, 0, count * sizeof(unsigned long long), s));
+  const int64_t n = std::max(P.Ns, P.M);
+  if (n > 0) {
+    k_binst<<<grid_for(n, 256), 256, 0, s>>>(P.col_of_orig, P.orig_of_row, P.bnoff, P.beoff, count, P.Ns, P.M,
+                                              P.binst_col, P.binst_row);
+    TH_LAUNCHED();
+  }
+  P.h_bfrozen.assign(count, 0);
+  P.h_bepochs.assign(count, 0);
+  P.h_brho.assign(count, 0.0);
+}
+
+void batch_begin_solve(Problem& P) {
+  if (P.nbatch == 0) return;
+  std::fill(P.h_bfrozen.begin(), P.h_bfrozen.end(), 0);
+  std::fill(P.h_bepochs.begin(), P.h_bepochs.end(), 0);
+  std::fill(P.h_brho.begin(), P.h_brho.end(), 0.0);
+  TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, P.nbatch, P.stream));
+}
+
+// After a check (the stream is synchronised): record every active instance's
+// rho and freeze those at or below tol -- the test a solve of the instance
+// alone makes at the same check.
+bool batch_after_check(Problem& P, double tol, int epoch) {
+  const int64_t count = P.nbatch;
+  std::vector<unsigned long long> bits(count);
+  TH_CUDA(cudaMemcpyAsync(bits.data(), P.brho, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  bool changed = false, all = true;
+  for (int64_t t = 0; t < count; ++t) {
+    if (P.h_bfrozen[t]) continue;
+    double rho;
+    memcpy(&rho, &bits[t], sizeof(double));
+    P.h_brho[t] = rho;
+    P.h_bepochs[t] = epoch;
+    if (rho <= tol) {
+      P.h_bfrozen[t] = 1;
+      changed = true;
+    } else {
+      all = false;
+    }
+  }
+  if (changed)
+    TH_CUDA(cudaMemcpyAsync(P.bfrozen, P.h_bfrozen.data(), count, cudaMemcpyHostToDevice, P.stream));
+  // the host vector must outlive the copy
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  return all;
+}
+
+void batch_end_solve(Problem& P, int epoch) {
+  for (int64_t t = 0; t < P.nbatch; ++t)
+    if (!P.h_bfrozen[t]) P.h_bepochs[t] = epoch;
 }
 
 }  // namespace thetis

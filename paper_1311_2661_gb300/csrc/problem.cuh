@@ -73,6 +73,16 @@ struct Problem {
   uint8_t* bkind = nullptr;
   std::vector<uint8_t> h_bkind;
   std::vector<int64_t> h_bnoff, h_beoff;
+  // per-instance convergence: the instance of every internal column and row;
+  // an instance whose rho reaches tol at a check is frozen (no longer swept),
+  // so it ends exactly where a solve of it alone stops
+  int32_t* binst_col = nullptr;        // Ns
+  int32_t* binst_row = nullptr;        // M
+  uint8_t* bfrozen = nullptr;          // nbatch
+  unsigned long long* brho = nullptr;  // nbatch: rho of the last check (FP64 bits, >= 0)
+  std::vector<uint8_t> h_bfrozen;
+  std::vector<int32_t> h_bepochs;      // epochs each instance ran in the last solve
+  std::vector<double> h_brho;          // its rho when it stopped
 
   // graph meta (builders)
   int64_t nv = 0, ne = 0;
@@ -169,6 +179,13 @@ void build_batch_raw(int64_t count, const uint8_t* d_kind, const int64_t* d_noff
 void round_batch(Problem& P, uint64_t seed, int reps, uint8_t* d_labels, std::vector<double>& obj,
                  std::vector<int32_t>& status, std::vector<int32_t>& best_rep, std::vector<double>& repair,
                  std::vector<int64_t>& near);
+// per-instance convergence of a batch: index columns / rows by instance (after
+// the layout is built), clear the frozen flags at the start of a solve, and
+// after each check freeze every instance whose rho <= tol (true: all frozen)
+void batch_index(Problem& P);
+void batch_begin_solve(Problem& P);
+bool batch_after_check(Problem& P, double tol, int epoch);
+void batch_end_solve(Problem& P, int epoch);
 
 // scd.cu
 struct SolveArgs {

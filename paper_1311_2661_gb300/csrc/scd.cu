@@ -39,7 +39,20 @@ struct StepView {
   int k;
   int async;         // 1: atomic residual updates
   int small_g;       // lanes per unit of the SMALL class: 1, 2, 4 or 8 (tuned)
+  // batches: instance of every internal column / row and the frozen flags
+  // (null for a single problem)
+  const int32_t* inst_col;
+  const int32_t* inst_row;
+  const uint8_t* frozen;
 };
+
+// A column / slack row of a frozen batch instance is not stepped.
+__device__ __forceinline__ bool col_frozen(const StepView& V, int64_t j) {
+  return V.frozen && V.frozen[V.inst_col[j]];
+}
+__device__ __forceinline__ bool row_frozen(const StepView& V, int64_t i) {
+  return V.frozen && V.frozen[V.inst_row[i]];
+}
 
 struct SegLaunch {
   int cls;        // UnitClass, or 4 for slacks
@@ -337,17 +350,19 @@ constexpr int SLACK_ROWS = 4;  // slack rows per thread (one tile = STEP_T * SLA
 // Slack step of rows [i0, i0 + n) handled by this thread: row i0 + t*STEP_T + tid.
 __device__ __forceinline__ void step_slacks(const StepView& V, int64_t i0, int64_t n) {
   float sv[SLACK_ROWS], rv[SLACK_ROWS];
+  bool on[SLACK_ROWS];
 #pragma unroll
   for (int t = 0; t < SLACK_ROWS; ++t) {
     int64_t q = (int64_t)t * STEP_T + threadIdx.x;
-    sv[t] = (q < n) ? __ldcg(V.s + i0 + q) : 0.f;
-    rv[t] = (q < n) ? __ldcg(V.r + i0 + q) : 0.f;
+    on[t] = q < n && !row_frozen(V, i0 + q);
+    sv[t] = on[t] ? __ldcg(V.s + i0 + q) : 0.f;
+    rv[t] = on[t] ? __ldcg(V.r + i0 + q) : 0.f;
   }
   const float L = (V.lfix > 0.f) ? V.lfix : V.beta + V.inv_beta;
 #pragma unroll
   for (int t = 0; t < SLACK_ROWS; ++t) {
     int64_t q = (int64_t)t * STEP_T + threadIdx.x;
-    if (q >= n) continue;
+    if (!on[t]) continue;
     const int64_t i = i0 + q;
     const float sg = V.sig_u ? (float)V.sig_u : (float)V.sig[i];
     const float sb = V.sbar ? V.sbar[i] : 0.f;
@@ -379,13 +394,13 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
     case UC_HUGE:
     case UC_LARGE: {
       if constexpr (FULL) {
-        if (b < S.n) step_huge(V, S.c0 + b, red_smem, dyn, staged);
+        if (b < S.n && !col_frozen(V, S.c0 + b)) step_huge(V, S.c0 + b, red_smem, dyn, staged);
       }
       break;
     }
     case UC_MED: {
       int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
-      if (u < S.n) step_column<32, 4>(V, S.c0 + u, lane, red_smem);
+      if (u < S.n && !col_frozen(V, S.c0 + u)) step_column<32, 4>(V, S.c0 + u, lane, red_smem);
       break;
     }
     case UC_SMALL: {
@@ -393,7 +408,7 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
       // group shuffles, groups past the end idle
       const int G = V.small_g;
       int64_t u = b * (STEP_T / G) + (threadIdx.x / G);
-      bool in = u < S.n;
+      bool in = u < S.n && !col_frozen(V, S.c0 + u);
       if (__any_sync(0xffffffffu, in)) {
         const int64_t j = S.c0 + (in ? u : 0);
         const int gl = threadIdx.x % G;
@@ -589,6 +604,10 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.k = P.k;
   V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
   V.small_g = P.small_g;
+  const bool batch = P.nbatch > 0 && P.bfrozen;
+  V.inst_col = batch ? P.binst_col : nullptr;
+  V.inst_row = batch ? P.binst_row : nullptr;
+  V.frozen = batch ? P.bfrozen : nullptr;
   return V;
 }
 
@@ -798,7 +817,20 @@ struct CheckView {
   const int64_t* blk_start;  // internal column where a block starts (per block), or null
   int64_t nblk;
   const uint8_t* in_block;   // per free internal column: 1 if part of a block
+  // batches: per-instance rho (FP64 bit patterns, atomic max); frozen
+  // instances are skipped (their iterate no longer changes)
+  const int32_t* inst_col;
+  const int32_t* inst_row;
+  const uint8_t* frozen;
+  unsigned long long* inst_rho;
 };
+
+// max of non-negative doubles through their bit patterns (same order)
+__device__ __forceinline__ void rho_max(unsigned long long* p, double v) {
+  if (!(v > 0.0)) return;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if (b > __ldcg(p)) atomicMax(p, b);
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -842,6 +874,8 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
   // (a) free singleton columns, warp per column
   for (int64_t j = warp; j < V.Nfree; j += nwarps) {
     if (V.in_block && V.in_block[j]) continue;
+    const int32_t inst = V.frozen ? V.inst_col[j] : 0;
+    if (V.frozen && V.frozen[inst]) continue;
     double sq;
     double atr = col_dot64(V, j, lane, &sq);
     double xj = V.x[j], xb = V.xbar ? V.xbar[j] : 0.0;
@@ -849,7 +883,10 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
     double L = beta * sq + ib;
     double lo = V.lo ? V.lo[j] : V.lo_u, hi = V.hi ? V.hi[j] : V.hi_u;
     double xn = fmin(fmax(xj - g / L, lo), hi);
-    if (lane == 0) rho = fmax(rho, fabs(xn - xj));
+    if (lane == 0) {
+      rho = fmax(rho, fabs(xn - xj));
+      if (V.frozen) rho_max(V.inst_rho + inst, fabs(xn - xj));
+    }
   }
   // (b) simplex blocks, warp per block
   for (int64_t t = warp; t < V.nblk; t += nwarps) {
@@ -903,7 +940,12 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
       double sg = (double)V.sig[i];
       double g = (V.cs ? (double)V.cs[i] : 0.0) + beta * sg * ri + (sv - sb) * ib;
       double sn = fmax(sv - g * inv_ls, 0.0);
-      rho = fmax(rho, fabs(sn - sv));
+      if (!V.frozen) {
+        rho = fmax(rho, fabs(sn - sv));
+      } else if (!V.frozen[V.inst_row[i]]) {
+        rho = fmax(rho, fabs(sn - sv));
+        rho_max(V.inst_rho + V.inst_row[i], fabs(sn - sv));
+      }
       xx += (sv - sb) * (sv - sb);
     }
   }
@@ -1026,6 +1068,11 @@ static CheckView make_check_view(Problem& P, const SolveArgs& a, bool use_ubar, 
   V.blk_start = P.blk_start;
   V.nblk = P.nblk;
   V.in_block = P.in_block;
+  const bool batch = P.nbatch > 0 && P.bfrozen;
+  V.inst_col = batch ? P.binst_col : nullptr;
+  V.inst_row = batch ? P.binst_row : nullptr;
+  V.frozen = batch ? P.bfrozen : nullptr;
+  V.inst_rho = batch ? P.brho : nullptr;
   return V;
 }
 
@@ -1036,6 +1083,8 @@ void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_x
                                                           P.s, P.sig, P.b, P.M, P.Msl, P.r64, P.r);
     TH_LAUNCHED();
   }
+  if (P.nbatch > 0 && P.brho)
+    TH_CUDA(cudaMemsetAsync(P.brho, 0, P.nbatch * sizeof(unsigned long long), s));
   k_check<<<CHECK_BLOCKS, 256, 0, s>>>(make_check_view(P, a, use_ubar, use_xbar), P.red);
   TH_LAUNCHED();
   k_check_final<<<1, 32, 0, s>>>(P.red, P.red_out);

@@ -184,12 +184,17 @@ void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
   for (Req* r : batch) fail(r, rs);
   std::vector<float> xs(noff[count]);
   thetis_get_x(h, xs.data(), THETIS_MEM_HOST);
+  std::vector<int32_t> iep(count, si.epochs_run);
+  std::vector<double> irho(count, si.rho);
+  thetis_batch_info(h, iep.data(), irho.data());
   for (int32_t t = 0; t < count; ++t) {
     Req* r = batch[t];
     if (r->res.message[0] == 0) r->res.status = st;
     if (status[t] == -1) r->res.status = THETIS_E_REPAIR;
-    r->res.epochs_run = si.epochs_run;
-    r->res.rho = si.rho;
+    // each instance stops at its own check: its status is its own
+    if (r->res.message[0] == 0 && st == THETIS_NOT_CONVERGED && irho[t] <= q.tol) r->res.status = THETIS_OK;
+    r->res.epochs_run = iep[t];
+    r->res.rho = irho[t];
     r->res.obj = obj[t];
     r->res.valid = status[t] == 1;
     r->labels.assign(lab.begin() + noff[t], lab.begin() + noff[t + 1]);

@@ -95,6 +95,7 @@ def _load():
         "thetis_server_stats": (st, [P, P, P, P, P]),
         "thetis_server_destroy": (st, [P]),
         "thetis_round_batch": (st, [P, u64, i32, P, i32, P, P, P]),
+        "thetis_batch_info": (st, [P, P, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -461,6 +462,14 @@ def thetis_round_batch(h: Handle, seed=0, reps=10, out=None):
     _check(_lib.thetis_round_batch(h.ptr, int(seed), int(reps), ptr, mem, obj.ctypes.data, status.ctypes.data,
                                    best.ctypes.data))
     return lab, obj, status, best
+
+
+def thetis_batch_info(h: Handle):
+    """Per-instance (epochs, rho) of the last solve of a batch handle."""
+    ep = np.zeros(h.count, np.int32)
+    rho = np.zeros(h.count, np.float64)
+    _check(_lib.thetis_batch_info(h.ptr, ep.ctypes.data, rho.ctypes.data))
+    return ep, rho
 
 
 def thetis_round_is_static(n, eu, ev, w, x, labels_out, seed=0, reps=10, stream=None):

@@ -102,3 +102,33 @@ def test_batch_rejects_bad_input():
     with pytest.raises(T.ThetisError):  # bad kind
         T.thetis_build_batch(np.array([7], np.uint8), np.array([0, 2]), np.array([0, 1]),
                              np.array([0], np.int32), np.array([1], np.int32), np.ones(2, np.float32))
+
+
+def test_batch_instances_stop_where_alone_stops():
+    """tol applies per instance: each instance stops at the first check where its
+    own rho <= tol -- the same check, iterate and rho as its solve alone -- and
+    is no longer swept while the rest of the batch continues."""
+    T = gpu()
+    items = _batch(count=20, seed=12, nmax=500)
+    hb = T.thetis_build_batch_graphs(items, seed=3)
+    info = hb.solve(beta=100.0, epochs=3000, tol=1e-3, refresh_every=10)
+    ep, rho = T.thetis_batch_info(hb)
+    assert info["converged"] and info["rho"] == rho.max() and info["epochs_run"] == ep.max()
+    x, s = hb.get_x().astype(np.float64), hb.get_slack().astype(np.float64)
+    noff, eoff = _slices(items)
+    assert len(set(ep.tolist())) > 1, "every instance stopped at the same check"
+    for t, (kind, g) in enumerate(items):
+        b = T.thetis_build_vc if kind == "vc" else T.thetis_build_is
+        h = b(g.n, g.eu, g.ev, g.w, seed=3)
+        ia = h.solve(beta=100.0, epochs=3000, tol=1e-3, refresh_every=10)
+        assert ia["epochs_run"] == ep[t], t
+        assert abs(ia["rho"] - rho[t]) <= 1e-9 + 1e-6 * rho[t], t
+        xa = np.concatenate([h.get_x(), h.get_slack()]).astype(np.float64)
+        mine = np.concatenate([x[noff[t]:noff[t + 1]], s[eoff[t]:eoff[t + 1]]])
+        assert np.max(np.abs(mine - xa)) <= X_TOL, t
+        # and the FP64 oracle, run to the same epoch count in the same colour order
+        lp = oracle.build_problem(kind, g)
+        col, _ = lp.color(3)
+        x_o, _ = lp.solve(beta=100.0, epochs=int(ep[t]), refresh_every=10, color=col)
+        assert np.max(np.abs(mine - x_o)) <= X_TOL, t
+        assert lp.checks(mine, 100.0)["rho"] <= 1e-3 + 1e-6

@@ -110,5 +110,10 @@ def test_to_tolerance_in_batches():
     res = _wait(sv, ids)
     for (kind, g), i in zip(reqs, ids):
         lab, x, info = res[i]
-        assert info["status"] == T.THETIS_OK and info["rho"] <= 1e-3 and info["valid"]
+        assert info["status"] == T.THETIS_OK and info["rho"] <= 1e-3 and info["valid"], info["message"]
+        # the request stops where its solve alone stops, batched or not
+        h = build_gpu(kind, g, seed=2)
+        ia = h.solve(beta=100.0, epochs=5000, tol=1e-3, refresh_every=10)
+        assert info["epochs_run"] == ia["epochs_run"]
+        assert np.max(np.abs(x - h.get_x()[:len(x)])) <= X_TOL
     sv.close()
