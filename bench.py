@@ -275,7 +275,10 @@ def run_gpu(args, wl, ws, rank, local):
     bpe = algorithmic_bytes_per_epoch(wl, g)
     ep_ms = sum(i[0]["epoch_ms"] for i in infos)
     ep_n = sum(i[0]["epochs_run"] for i in infos)
-    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
+    # an instance stops being swept at the check where its rho reaches tol:
+    # only its own epochs move its bytes
+    moved = sum(float(bpe_inst @ i["inst_epochs"]) for i in infos)
+    achieved = moved / (ep_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -383,7 +386,8 @@ def run_batched(args, wl, ws, rank, local):
     lab_d = torch.zeros(int(noff[-1]), dtype=torch.uint8, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     count = wl["count"]
-    bpe = sum(20 * g.n + 40 * g.m for _, g in items)
+    bpe_inst = np.array([20 * g.n + 40 * g.m for _, g in items], np.float64)
+    bpe = float(bpe_inst.sum())
     torch.cuda.synchronize()
 
     shape = {}
@@ -392,6 +396,7 @@ def run_batched(args, wl, ws, rank, local):
         h = T.thetis_build_batch(a["kinds"], a["noff"], a["eoff"], a["eu"], a["ev"], a["w"], seed=0, stream=stream)
         shape["small_group"], shape["ctas_per_sm"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
         info = h.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"])
+        info["inst_epochs"] = T.thetis_batch_info(h)[0]
         lab, obj, status, best = T.thetis_round_batch(h, seed=11, reps=wl["reps"], out=out)
         assert np.all(status == 1), "a rounded instance failed the validity check"
         h.close()
@@ -480,7 +485,8 @@ def run_batched(args, wl, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": None,
                      "kernel": "k_sweep (persistent colour sweep); unit = one epoch of the batch",
-                     "bytes_per_epoch": bpe, "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
+                     "bytes_per_epoch": bpe, "bytes_per_step": moved / len(infos),
+                     "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
         "latency": {"batched_p50_ms": float(np.percentile(batch_lat, 50)),
                     "batched_p99_ms": float(np.percentile(batch_lat, 99)),
                     "plain_p50_ms": float(np.percentile(lat, 50)), "plain_p99_ms": float(np.percentile(lat, 99)),
