@@ -61,6 +61,7 @@ METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs
 # (profiles/k_sweep_is-chunglu-n2e20.md: 3.04 GB read + 2.47 GB written per 10-epoch launch)
 SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 551_000_000}
 L2_BYTES = 129 * 1024 * 1024
+SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
 
 
 def make_graph(wl, rank=0):
@@ -275,10 +276,7 @@ def run_gpu(args, wl, ws, rank, local):
     bpe = algorithmic_bytes_per_epoch(wl, g)
     ep_ms = sum(i[0]["epoch_ms"] for i in infos)
     ep_n = sum(i[0]["epochs_run"] for i in infos)
-    # an instance stops being swept at the check where its rho reaches tol:
-    # only its own epochs move its bytes
-    moved = sum(float(bpe_inst @ i["inst_epochs"]) for i in infos)
-    achieved = moved / (ep_ms / 1e3) / 1e9
+    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -425,7 +423,10 @@ def run_batched(args, wl, ws, rank, local):
     value = sum_over_ranks(float(count * args.steps), ws, dev) / (total_ms / 1e3)
     ep_ms = sum(i["epoch_ms"] for i in infos)
     ep_n = sum(i["epochs_run"] for i in infos)
-    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
+    # an instance stops being swept at the check where its rho reaches tol:
+    # only its own epochs move its bytes
+    moved = sum(float(bpe_inst @ i["inst_epochs"]) for i in infos)
+    achieved = moved / (ep_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
 
     # e2e: host (pinned) inputs, labels back to the host
@@ -497,6 +498,9 @@ def run_batched(args, wl, ws, rank, local):
         "clocks": clk.summary(),
         "cpu_baseline": None,
     }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        order = np.random.default_rng(7).permutation(count)
+        res["cpu_baseline"] = cpu_baseline_instances(wl, items, order, 15.0, "random instances of the batch")
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -657,6 +661,11 @@ def run_serving(args, wl, ws, rank, local):
         "clocks": clk.summary(),
         "cpu_baseline": None,
     }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        small = [int(j) for j in trace(0)[1] if pool[j][1].n <= SERVE_ORACLE_N_CAP]
+        res["cpu_baseline"] = cpu_baseline_instances(
+            wl, pool, small, 15.0, f"requests of the trace with n <= {SERVE_ORACLE_N_CAP} (the oracle needs minutes "
+                                   f"for the largest)")
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -684,6 +693,40 @@ def cpu_baseline(wl, g, epochs):
             "sample": f"{epochs} FP64 serial SCD epochs of the full instance ({lp.free_coords} coordinates) "
                       f"incl. the final exact refresh + checks; build and colouring excluded",
             "seconds": dt}
+
+
+def _oracle_solve_round(kind, g, wl, seed=11):
+    """Build, colour, solve to rho <= tol and round one instance on the oracle."""
+    import oracle
+
+    lp = oracle.build_problem(kind, g)
+    col, _ = lp.color(seed)
+    x, _ = lp.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"], color=col)
+    if kind == "vc":
+        lp.round_vc(x[: g.n])
+    elif kind == "is":
+        lp.round_is(x[: g.n], seed, wl["reps"])
+    else:
+        lp.round_mc(x[: g.n * len(g.terminals)], seed, wl["reps"])
+
+
+def cpu_baseline_instances(wl, items, order, seconds, what):
+    """The oracle on one host core, solving instances in `order` one after
+    another (each to rho <= tol, then rounded) for about `seconds`."""
+    import oracle
+
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    for j in order:
+        kind, g = items[j]
+        _oracle_solve_round(kind, g, wl)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} {what}, each built, coloured, solved to rho <= {wl['tol']} and rounded by the FP64 "
+                      f"oracle on one core ({dt:.1f} s)"}
 
 
 def run_reference_batch(args, wl, ws):
@@ -722,22 +765,13 @@ def run_reference_batch(args, wl, ws):
 
 
 def _oracle_request(job):
-    """One serving request on the oracle: build, colour, solve to rho <= tol,
-    round (runs in a spawned worker process)."""
+    """One serving request on the oracle (runs in a spawned worker process)."""
     import oracle
 
     kind, g, wl = job
     oracle.build()
     t = time.perf_counter()
-    lp = oracle.build_problem(kind, g)
-    col, _ = lp.color(11)
-    x, info = lp.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"], color=col)
-    if kind == "vc":
-        lp.round_vc(x[: g.n])
-    elif kind == "is":
-        lp.round_is(x[: g.n], 11, wl["reps"])
-    else:
-        lp.round_mc(x[: g.n * len(g.terminals)], 11, wl["reps"])
+    _oracle_solve_round(kind, g, wl)
     return time.perf_counter() - t
 
 
@@ -750,7 +784,7 @@ def run_reference_serving(args, wl, ws):
 
     from paper_1311_2661_gb300 import synth
 
-    n_cap = 20000
+    n_cap = SERVE_ORACLE_N_CAP
     pool, kinds = _serving_inputs(wl, 0)
     t_arr, idx = synth.poisson_trace(wl["rate"], 4096, kinds, wl["seed"] * 7919)
     small = [int(j) for j in idx if pool[j][1].n <= n_cap]
