@@ -753,7 +753,11 @@ __global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const i
       else if (unnz[u] > T_HUGE) cls = UC_HUGE;
       else if (unnz[u] > T_LARGE) cls = UC_LARGE;
       else if (unnz[u] > T_MED) cls = UC_MED;
-      else cls = UC_SMALL;
+      else if (unnz[u] > 16) cls = UC_S32;
+      else if (unnz[u] > 8) cls = UC_S16;
+      else if (unnz[u] > 4) cls = UC_S8;
+      else if (unnz[u] > 2) cls = UC_S4;
+      else cls = UC_S2;
       key = (uint32_t)color[u] * UC_COUNT + cls;
       keys[u] = key;
       vals[u] = (uint32_t)u;
@@ -993,6 +997,30 @@ __global__ void k_max_unit_nnz(const int64_t* unnz, int64_t U, unsigned long lon
   GSTRIDE(u, U) m = max(m, (unsigned long long)unnz[u]);
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ELL copy of the small classes: column j of small segment t (first column
+// c0[t], n[t] columns, width w[t], first slot e0[t]) writes its row slots.
+__global__ void k_ell_fill(const int64_t* colptr, const uint32_t* rowidx, const float* val, const int64_t* c0,
+                           const int64_t* n, const int64_t* e0, const int32_t* w, int64_t nseg, int64_t Nfree,
+                           uint32_t* ell, float* ellv) {
+  GSTRIDE(j, Nfree) {
+    int64_t lo = 0, hi = nseg;  // last segment with c0 <= j
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (c0[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    if (j < c0[lo] || j >= c0[lo] + n[lo]) continue;
+    const int64_t p = j - c0[lo];
+    const int W = w[lo];
+    const int64_t base = e0[lo] + (p >> 5) * 32 * W + (p & 31);
+    const int64_t q0 = colptr[j], q1 = colptr[j + 1];
+    for (int64_t q = q0; q < q1 && q - q0 < W; ++q) {
+      ell[base + (q - q0) * 32] = rowidx[q];
+      if (ellv) ellv[base + (q - q0) * 32] = val[q];
+    }
+  }
 }
 
 std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cudaStream_t s, Arena& tmp) {
@@ -1362,7 +1390,12 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
         int64_t n = hc[(size_t)c * UC_COUNT + cls];
         if (n == 0) continue;
         int32_t len = (cls == UC_BLOCK) ? P.k : 1;
-        cp.segs.push_back(Seg{cls, u, u + n, col, len});
+        Seg sg{cls, u, u + n, col, len};
+        if (is_small_class(cls)) {
+          sg.e0 = P.ell_size;
+          P.ell_size += (n + 31) / 32 * 32 * small_width(cls);
+        }
+        cp.segs.push_back(sg);
         u += n;
         col += n * len;
       }
@@ -1371,6 +1404,35 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
       cp.srow1 = srow;
     }
     TH_CHECK(u == Us && col == P.Nfree && srow == Msl, THETIS_E_CUDA, "colour plan inconsistent");
+  }
+  // ELL copy of the small classes' row ids
+  {
+    std::vector<int64_t> sc0, sn, se0;
+    std::vector<int32_t> sw;
+    for (auto& cp : P.plan)
+      for (auto& sg : cp.segs)
+        if (is_small_class(sg.cls)) {
+          sc0.push_back(sg.c0);
+          sn.push_back(sg.u1 - sg.u0);
+          se0.push_back(sg.e0);
+          sw.push_back(small_width(sg.cls));
+        }
+    const int64_t ns = (int64_t)sc0.size();
+    P.ell = P.mem.alloc<uint32_t>(P.ell_size + 1);
+    if (P.has_val) P.ellv = P.mem.alloc<float>(P.ell_size + 1);
+    if (ns > 0) {
+      TH_CUDA(cudaMemsetAsync(P.ell, 0xff, P.ell_size * sizeof(uint32_t), s));
+      int64_t* d64 = tmp.alloc<int64_t>(3 * ns);
+      int32_t* dw = tmp.alloc<int32_t>(ns);
+      TH_CUDA(cudaMemcpyAsync(d64, sc0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaMemcpyAsync(d64 + ns, sn.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaMemcpyAsync(d64 + 2 * ns, se0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaMemcpyAsync(dw, sw.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      k_ell_fill<<<grid_for(P.Nfree, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.has_val ? P.val : nullptr, d64,
+                                                        d64 + ns, d64 + 2 * ns, dw, ns, P.Nfree, P.ell, P.ellv);
+      TH_LAUNCHED();
+      TH_CUDA(cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
+    }
   }
   // free simplex blocks (internal first columns)
   {

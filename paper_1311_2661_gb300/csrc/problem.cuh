@@ -11,16 +11,29 @@ enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BA
 
 // Classes of coordinate units inside one colour.  Units of a colour are stored
 // class by class, so that every class is a contiguous range of units and of
-// internal columns.
-enum UnitClass { UC_BLOCK = 0, UC_HUGE = 1, UC_LARGE = 2, UC_MED = 3, UC_SMALL = 4, UC_COUNT = 5 };
+// internal columns.  Singleton columns with at most 32 non-zeros form the
+// small classes S32 ... S2 by their row-slot width W (the smallest power of two
+// >= nnz, at least 2); their row ids are also kept in ELL form.
+enum UnitClass {
+  UC_BLOCK = 0, UC_HUGE = 1, UC_LARGE = 2, UC_MED = 3,
+  UC_S32 = 4, UC_S16 = 5, UC_S8 = 6, UC_S4 = 7, UC_S2 = 8,
+  UC_COUNT = 9
+};
 // non-zero thresholds of the singleton classes (more than T_HUGE: HUGE, ...)
 constexpr int64_t T_HUGE = 1024, T_LARGE = 128, T_MED = 32;
+__host__ __device__ constexpr bool is_small_class(int cls) { return cls >= UC_S32 && cls <= UC_S2; }
+__host__ __device__ constexpr int small_width(int cls) { return 32 >> (cls - UC_S32); }
+// ELL form of a small class of width W: column p of the segment keeps its row
+// slot q at e0 + (p / 32) * 32 * W + q * 32 + p % 32 (32-column panels, slot
+// major), unused slots hold ELL_PAD
+constexpr uint32_t ELL_PAD = 0xffffffffu;
 
 struct Seg {
   int cls;        // UnitClass
   int64_t u0, u1; // units [u0, u1) (positions in colour order)
   int64_t c0;     // first internal column of unit u0
   int32_t len;    // columns per unit (k for blocks, 1 otherwise)
+  int64_t e0 = 0; // small classes: first ELL slot of the segment
 };
 
 struct ColorPlan {
@@ -98,6 +111,11 @@ struct Problem {
   int32_t ncolors = 0;
   int64_t free_coords = 0;  // Nfree + Msl
   std::vector<ColorPlan> plan;
+
+  // ELL row ids (and values, if has_val) of the small classes
+  uint32_t* ell = nullptr;
+  float* ellv = nullptr;
+  int64_t ell_size = 0;
 
   // internal CSC over internal structural columns [0, Nfree + Nfix)
   int64_t* colptr = nullptr;

@@ -38,7 +38,9 @@ struct StepView {
   float lfix;        // > 0: global L_max (step_rule 1)
   int k;
   int async;         // 1: atomic residual updates
-  int small_g;       // lanes per unit of the SMALL class: 1, 2, 4 or 8 (tuned)
+  int small_g;       // small classes: 8 / small_g row slots per lane (small_g = 1, 2, 4 or 8, tuned)
+  const uint32_t* ell;  // ELL row ids of the small classes
+  const float* ellv;    // ELL values (null: +-1 encoded in ell)
   // batches: instance of every internal column / row and the frozen flags
   // (null for a single problem)
   const int32_t* inst_col;
@@ -55,12 +57,20 @@ __device__ __forceinline__ bool row_frozen(const StepView& V, int64_t i) {
 }
 
 struct SegLaunch {
-  int cls;        // UnitClass, or 4 for slacks
+  int cls;        // UnitClass, or UC_COUNT for slacks
   int64_t u0;     // first unit position (slacks: first internal row)
   int64_t n;      // units (slacks: rows)
   int64_t c0;     // first internal column
   int64_t b0;     // first CTA of this segment
+  int64_t e0;     // small classes: first ELL slot
 };
+
+// Lanes per column of a small class of width W: each lane holds 8 / small_g
+// of the W row slots.
+__host__ __device__ __forceinline__ int small_lanes(int W, int small_g) {
+  const int per = 8 / small_g;
+  return W > per ? W / per : 1;
+}
 
 struct ColorLaunch {
   SegLaunch seg[UC_COUNT + 1];
@@ -176,6 +186,72 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
     }
   }
   if (G > 32) __syncthreads();
+}
+
+// One projected step of small column j (ELL position p in its segment, first
+// slot e0) by G lanes: lane gl holds slots gl, gl + G, ... of the W slots.  The
+// slot addresses follow from p alone, and the 32 columns of a panel read one
+// slot row as one coalesced line; padding slots are skipped.
+template <int W, int G>
+__device__ __forceinline__ void step_ell(const StepView& V, int64_t e0, int64_t j, int64_t p, int gl, bool valid) {
+  constexpr int E = W / G;
+  const int64_t base = e0 + (p >> 5) * (32 * W) + (p & 31);
+  const float xj = valid ? __ldcg(V.x + j) : 0.f;
+  const float ctj = valid ? V.ct[j] : 0.f;
+  const float xb = (valid && V.xbar) ? V.xbar[j] : 0.f;
+  uint32_t ce[E];
+  float cv[E], cr[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) ce[i] = valid ? V.ell[base + (int64_t)(gl + G * i) * 32] : ELL_PAD;
+#pragma unroll
+  for (int i = 0; i < E; ++i)
+    cv[i] = (ce[i] == ELL_PAD) ? 0.f : (V.ellv ? V.ellv[base + (int64_t)(gl + G * i) * 32] : sgn_of(ce[i]));
+#pragma unroll
+  for (int i = 0; i < E; ++i) cr[i] = (ce[i] != ELL_PAD) ? ldr(V, V.ellv ? ce[i] : idx_of(ce[i])) : 0.f;
+  float acc = 0.f, sq = 0.f;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    acc = fmaf(cv[i], cr[i], acc);
+    sq = fmaf(cv[i], cv[i], sq);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o, G);
+  }
+  if (!valid) return;
+  const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
+  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, V.ellv ? V.csq[j] : sq, V.inv_beta);
+  const float lo = V.lo ? V.lo[j] : V.lo_u;
+  const float hi = V.hi ? V.hi[j] : V.hi_u;
+  const float xn = fminf(fmaxf(xj - g / L, lo), hi);
+  const float d = xn - xj;
+  if (gl == 0) V.x[j] = xn;
+  if (d != 0.f) {
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      if (ce[i] != ELL_PAD) r_add(V, V.ellv ? ce[i] : idx_of(ce[i]), cr[i], cv[i] * d);
+  }
+}
+
+// Small class of width W: tile b of the segment, G lanes per column.
+template <int W, int G>
+__device__ __forceinline__ void small_tile(const StepView& V, const SegLaunch& S, int64_t b) {
+  const int64_t p = b * (STEP_T / G) + threadIdx.x / G;
+  const bool in = p < S.n && !col_frozen(V, S.c0 + p);
+  if (__any_sync(0xffffffffu, in)) step_ell<W, G>(V, S.e0, S.c0 + (in ? p : 0), in ? p : 0, threadIdx.x % G, in);
+}
+
+template <int W>
+__device__ __forceinline__ void small_tile_w(const StepView& V, const SegLaunch& S, int64_t b) {
+  switch (small_lanes(W, V.small_g)) {
+    case 1: if constexpr (W <= 8) small_tile<W, 1>(V, S, b); break;
+    case 2: if constexpr (W >= 2 && W <= 16) small_tile<W, 2>(V, S, b); break;
+    case 4: if constexpr (W >= 4) small_tile<W, 4>(V, S, b); break;
+    case 8: if constexpr (W >= 8) small_tile<W, 8>(V, S, b); break;
+    case 16: if constexpr (W >= 16) small_tile<W, 16>(V, S, b); break;
+    default: if constexpr (W >= 32) small_tile<W, 32>(V, S, b); break;
+  }
 }
 
 // Columns with more than T_HUGE non-zeros: one CTA stages the column's row ids
@@ -403,22 +479,11 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
       if (u < S.n && !col_frozen(V, S.c0 + u)) step_column<32, 4>(V, S.c0 + u, lane, red_smem);
       break;
     }
-    case UC_SMALL: {
-      // G lanes per unit (G tuned per problem); every lane of the warp joins the
-      // group shuffles, groups past the end idle
-      const int G = V.small_g;
-      int64_t u = b * (STEP_T / G) + (threadIdx.x / G);
-      bool in = u < S.n && !col_frozen(V, S.c0 + u);
-      if (__any_sync(0xffffffffu, in)) {
-        const int64_t j = S.c0 + (in ? u : 0);
-        const int gl = threadIdx.x % G;
-        if (G == 8) step_column<8, 4>(V, j, gl, red_smem, in);
-        else if (G == 4) step_column<4, 8>(V, j, gl, red_smem, in);
-        else if (G == 2) step_column<2, 8>(V, j, gl, red_smem, in);
-        else step_column<1, 8>(V, j, gl, red_smem, in);
-      }
-      break;
-    }
+    case UC_S32: small_tile_w<32>(V, S, b); break;
+    case UC_S16: small_tile_w<16>(V, S, b); break;
+    case UC_S8: small_tile_w<8>(V, S, b); break;
+    case UC_S4: small_tile_w<4>(V, S, b); break;
+    case UC_S2: small_tile_w<2>(V, S, b); break;
     case UC_BLOCK: {
       if constexpr (FULL) {
         int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
@@ -484,7 +549,25 @@ __device__ __forceinline__ void prefetch_tile(const StepView& V, const SegLaunch
     case UC_LARGE: u0 = b; u1 = b + 1; break;
     case UC_MED:
     case UC_BLOCK: u0 = b * (STEP_T / 32); u1 = u0 + STEP_T / 32; break;
-    case UC_SMALL: u0 = b * (STEP_T / V.small_g); u1 = u0 + STEP_T / V.small_g; break;
+    case UC_S32:
+    case UC_S16:
+    case UC_S8:
+    case UC_S4:
+    case UC_S2: {
+      // the tile's ELL panels are one contiguous range
+      const int W = small_width(S.cls);
+      const int per = STEP_T / small_lanes(W, V.small_g);
+      const int64_t p0 = b * per, p1 = min(S.n, p0 + per);
+      if (p0 >= p1) return;
+      const int64_t e1 = S.e0 + ((p1 + 31) >> 5) * 32 * W;
+      for (int64_t e = S.e0 + (p0 >> 5) * 32 * W + (int64_t)threadIdx.x * 32; e < e1; e += (int64_t)STEP_T * 32)
+        prefetch_l2(V.ell + e);
+      if (threadIdx.x == 0) {
+        prefetch_l2(V.x + S.c0 + p0);
+        prefetch_l2(V.ct + S.c0 + p0);
+      }
+      return;
+    }
     default: {
       const int64_t r0 = S.u0 + b * (STEP_T * SLACK_ROWS);
       const int64_t r1 = min(S.u0 + S.n, r0 + (int64_t)STEP_T * SLACK_ROWS);
@@ -574,8 +657,11 @@ static int64_t ctas_for(int cls, int64_t n, int small_g) {
     case UC_LARGE: return n;
     case UC_MED:
     case UC_BLOCK: return (n + STEP_T / 32 - 1) / (STEP_T / 32);
-    case UC_SMALL: return (n + STEP_T / small_g - 1) / (STEP_T / small_g);
-    default: return (n + STEP_T * SLACK_ROWS - 1) / (STEP_T * SLACK_ROWS);
+    case UC_COUNT: return (n + STEP_T * SLACK_ROWS - 1) / (STEP_T * SLACK_ROWS);
+    default: {  // small classes
+      const int per = STEP_T / small_lanes(small_width(cls), small_g);
+      return (n + per - 1) / per;
+    }
   }
 }
 
@@ -604,6 +690,8 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.k = P.k;
   V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
   V.small_g = P.small_g;
+  V.ell = P.ell;
+  V.ellv = P.has_val ? P.ellv : nullptr;
   const bool batch = P.nbatch > 0 && P.bfrozen;
   V.inst_col = batch ? P.binst_col : nullptr;
   V.inst_row = batch ? P.binst_row : nullptr;
@@ -636,14 +724,14 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
               CL = ColorLaunch{};
               tot = 0;
             }
-            CL.seg[CL.nseg++] = SegLaunch{cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+            CL.seg[CL.nseg++] = SegLaunch{cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot, sg.e0};
             tot += ctas_for(cls, sg.u1 - sg.u0, P.small_g);
           }
       launch(CL, tot);
     }
     if (P.Msl > 0) {
       ColorLaunch CL{};
-      CL.seg[0] = SegLaunch{UC_COUNT, 0, P.Msl, 0, 0};
+      CL.seg[0] = SegLaunch{UC_COUNT, 0, P.Msl, 0, 0, 0};
       CL.nseg = 1;
       launch(CL, ctas_for(UC_COUNT, P.Msl, P.small_g));
     }
@@ -654,11 +742,11 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     ColorLaunch CL{};
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
-      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot, sg.e0};
       tot += ctas_for(sg.cls, sg.u1 - sg.u0, P.small_g);
     }
     if (cp.srow1 > cp.srow0) {
-      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
+      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot, 0};
       tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0, P.small_g);
     }
     launch(CL, tot);
@@ -679,11 +767,11 @@ static void ensure_sweep_plan(Problem& P) {
     ColorLaunch CL{};
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
-      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot};
+      CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot, sg.e0};
       tot += ctas_for(sg.cls, sg.u1 - sg.u0, P.small_g);
     }
     if (cp.srow1 > cp.srow0) {
-      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot};
+      CL.seg[CL.nseg++] = SegLaunch{UC_COUNT, cp.srow0, cp.srow1 - cp.srow0, 0, tot, 0};
       tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0, P.small_g);
     }
     h[c] = CL;
