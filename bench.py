@@ -45,6 +45,9 @@ WORKLOADS = {
     # all solved to rho <= 1e-3 as one batch
     "batched-4096": dict(kind="batch", count=4096, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
                          epochs=4000, refresh=20, tol=1e-3, reps=10, plain_sample=32),
+    # the same distribution, 1024 instances (profiling-sized, r larger than L2)
+    "batched-1024": dict(kind="batch", count=1024, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
+                         epochs=4000, refresh=20, tol=1e-3, reps=10, plain_sample=8),
     # the same distribution, 256 instances (profiling-sized)
     "batched-256": dict(kind="batch", count=256, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
                         epochs=4000, refresh=20, tol=1e-3, reps=10, plain_sample=8),
