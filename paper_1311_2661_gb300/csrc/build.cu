@@ -1405,34 +1405,55 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     }
     TH_CHECK(u == Us && col == P.Nfree && srow == Msl, THETIS_E_CUDA, "colour plan inconsistent");
   }
-  // ELL copy of the small classes' row ids
+  // ELL copy of the small classes' row ids, and the segment tables
   {
-    std::vector<int64_t> sc0, sn, se0;
+    std::vector<int64_t> sc0, sstart{0}, se0, bc0, bstart{0};
     std::vector<int32_t> sw;
     for (auto& cp : P.plan)
-      for (auto& sg : cp.segs)
+      for (auto& sg : cp.segs) {
+        const int64_t n = sg.u1 - sg.u0;
         if (is_small_class(sg.cls)) {
           sc0.push_back(sg.c0);
-          sn.push_back(sg.u1 - sg.u0);
+          sstart.push_back(sstart.back() + n);
           se0.push_back(sg.e0);
           sw.push_back(small_width(sg.cls));
+        } else if (sg.cls != UC_BLOCK) {
+          bc0.push_back(sg.c0);
+          bstart.push_back(bstart.back() + n);
         }
-    const int64_t ns = (int64_t)sc0.size();
+      }
+    const int64_t ns = (int64_t)sc0.size(), nb = (int64_t)bc0.size();
+    P.nss = ns;
+    P.nsmall = sstart.back();
+    P.nbs = nb;
+    P.nbig = bstart.back();
+    P.ss_start = P.mem.alloc<int64_t>(ns + 1);
+    P.ss_c0 = P.mem.alloc<int64_t>(ns + 1);
+    P.ss_e0 = P.mem.alloc<int64_t>(ns + 1);
+    P.ss_w = P.mem.alloc<int32_t>(ns + 1);
+    P.bs_start = P.mem.alloc<int64_t>(nb + 1);
+    P.bs_c0 = P.mem.alloc<int64_t>(nb + 1);
+    TH_CUDA(cudaMemcpyAsync(P.ss_start, sstart.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(P.bs_start, bstart.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (ns > 0) {
+      TH_CUDA(cudaMemcpyAsync(P.ss_c0, sc0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaMemcpyAsync(P.ss_e0, se0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TH_CUDA(cudaMemcpyAsync(P.ss_w, sw.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    if (nb > 0) TH_CUDA(cudaMemcpyAsync(P.bs_c0, bc0.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     P.ell = P.mem.alloc<uint32_t>(P.ell_size + 1);
     if (P.has_val) P.ellv = P.mem.alloc<float>(P.ell_size + 1);
     if (ns > 0) {
       TH_CUDA(cudaMemsetAsync(P.ell, 0xff, P.ell_size * sizeof(uint32_t), s));
-      int64_t* d64 = tmp.alloc<int64_t>(3 * ns);
-      int32_t* dw = tmp.alloc<int32_t>(ns);
-      TH_CUDA(cudaMemcpyAsync(d64, sc0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-      TH_CUDA(cudaMemcpyAsync(d64 + ns, sn.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-      TH_CUDA(cudaMemcpyAsync(d64 + 2 * ns, se0.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-      TH_CUDA(cudaMemcpyAsync(dw, sw.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      k_ell_fill<<<grid_for(P.Nfree, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.has_val ? P.val : nullptr, d64,
-                                                        d64 + ns, d64 + 2 * ns, dw, ns, P.Nfree, P.ell, P.ellv);
+      std::vector<int64_t> sn(ns);
+      for (int64_t t = 0; t < ns; ++t) sn[t] = sstart[t + 1] - sstart[t];
+      int64_t* dn = tmp.alloc<int64_t>(ns);
+      TH_CUDA(cudaMemcpyAsync(dn, sn.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      k_ell_fill<<<grid_for(P.Nfree, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.has_val ? P.val : nullptr, P.ss_c0,
+                                                        dn, P.ss_e0, P.ss_w, ns, P.Nfree, P.ell, P.ellv);
       TH_LAUNCHED();
-      TH_CUDA(cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
     }
+    TH_CUDA(cudaStreamSynchronize(s));  // the host vectors above must outlive the copies
   }
   // free simplex blocks (internal first columns)
   {

@@ -116,6 +116,13 @@ struct Problem {
   uint32_t* ell = nullptr;
   float* ellv = nullptr;
   int64_t ell_size = 0;
+  // segment tables for the checks: small segments (start in the flat index of
+  // all small columns, first column, first ELL slot, width) and the other
+  // singleton segments (start, first column)
+  int64_t nss = 0, nsmall = 0, nbs = 0, nbig = 0;
+  int64_t *ss_start = nullptr, *ss_c0 = nullptr, *ss_e0 = nullptr;
+  int32_t* ss_w = nullptr;
+  int64_t *bs_start = nullptr, *bs_c0 = nullptr;
 
   // internal CSC over internal structural columns [0, Nfree + Nfix)
   int64_t* colptr = nullptr;

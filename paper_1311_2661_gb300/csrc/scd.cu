@@ -14,7 +14,7 @@ namespace thetis {
 constexpr int STEP_T = 256;        // threads per CTA of the step kernels
 
 constexpr int CACHE = 4;           // r values a lane keeps between gather and scatter
-constexpr int CHECK_BLOCKS = 1024; // fixed grid of the check kernel (deterministic reduction)
+constexpr int CHECK_BLOCKS = 2432; // fixed grid of the check kernel (deterministic reduction)
 constexpr int NRED = 6;            // rho, obj, infeas, rr, ur, xx
 
 struct StepView {
@@ -911,7 +911,31 @@ struct CheckView {
   const int32_t* inst_row;
   const uint8_t* frozen;
   unsigned long long* inst_rho;
+  // small columns through the ELL (thread per column), the other singleton
+  // columns by segment (warp per column)
+  const uint32_t* ell;
+  const float* ellv;
+  const int64_t* ss_start;
+  const int64_t* ss_c0;
+  const int64_t* ss_e0;
+  const int32_t* ss_w;
+  int64_t nss, nsmall;
+  const int64_t* bs_start;
+  const int64_t* bs_c0;
+  int64_t nbs, nbig;
 };
+
+// segment t of a table of segment starts (start[0] = 0, n segments) holding
+// flat index i: the last t with start[t] <= i
+__device__ __forceinline__ int64_t seg_find(const int64_t* start, int64_t n, int64_t i) {
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (start[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // max of non-negative doubles through their bit patterns (same order)
 __device__ __forceinline__ void rho_max(unsigned long long* p, double v) {
@@ -959,9 +983,57 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const double beta = V.beta, ib = 1.0 / beta;
   const double inv_ls = 1.0 / (beta + ib);  // 1 / L of every slack column
-  // (a) free singleton columns, warp per column
-  for (int64_t j = warp; j < V.Nfree; j += nwarps) {
-    if (V.in_block && V.in_block[j]) continue;
+  // (a1) small columns, thread per column through the ELL; a warp's columns
+  // are consecutive (nearly always one batch instance: one atomic per warp)
+  {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t tb = gt - lane; tb < V.nsmall; tb += gs) {
+      const int64_t t = tb + lane;
+      bool act = t < V.nsmall;
+      double d = 0.0;
+      int32_t inst = -1;
+      if (act) {
+        const int64_t k = seg_find(V.ss_start, V.nss, t);
+        const int64_t p = t - V.ss_start[k], j = V.ss_c0[k] + p;
+        const int W = V.ss_w[k];
+        inst = V.frozen ? V.inst_col[j] : 0;
+        if (V.frozen && V.frozen[inst]) {
+          act = false;
+          inst = -1;
+        } else {
+          const int64_t base = V.ss_e0[k] + (p >> 5) * 32 * W + (p & 31);
+          double acc = 0.0, sq = 0.0;
+          for (int q = 0; q < W; ++q) {
+            const uint32_t e = V.ell[base + (int64_t)q * 32];
+            if (e == ELL_PAD) break;  // slots fill from the front
+            const double a = V.ellv ? (double)V.ellv[base + (int64_t)q * 32] : (double)sgn_of(e);
+            acc += a * V.r64[V.ellv ? e : idx_of(e)];
+            sq += a * a;
+          }
+          const double xj = V.x[j], xb = V.xbar ? V.xbar[j] : 0.0;
+          const double g = (double)V.ct[j] + beta * acc + (xj - xb) * ib;
+          const double L = beta * sq + ib;
+          const double lo = V.lo ? V.lo[j] : V.lo_u, hi = V.hi ? V.hi[j] : V.hi_u;
+          d = fabs(fmin(fmax(xj - g / L, lo), hi) - xj);
+          rho = fmax(rho, d);
+        }
+      }
+      if (V.frozen) {
+        const int32_t i0 = __shfl_sync(0xffffffffu, inst, 0);
+        if (__all_sync(0xffffffffu, inst == i0)) {
+          const double m = warp_max_d(d);
+          if (lane == 0 && i0 >= 0) rho_max(V.inst_rho + i0, m);
+        } else if (act) {
+          rho_max(V.inst_rho + inst, d);
+        }
+      }
+    }
+  }
+  // (a2) the other singleton columns, warp per column
+  for (int64_t t = warp; t < V.nbig; t += nwarps) {
+    const int64_t k = seg_find(V.bs_start, V.nbs, t);
+    const int64_t j = V.bs_c0[k] + (t - V.bs_start[k]);
     const int32_t inst = V.frozen ? V.inst_col[j] : 0;
     if (V.frozen && V.frozen[inst]) continue;
     double sq;
@@ -1161,6 +1233,18 @@ static CheckView make_check_view(Problem& P, const SolveArgs& a, bool use_ubar, 
   V.inst_row = batch ? P.binst_row : nullptr;
   V.frozen = batch ? P.bfrozen : nullptr;
   V.inst_rho = batch ? P.brho : nullptr;
+  V.ell = P.ell;
+  V.ellv = P.has_val ? P.ellv : nullptr;
+  V.ss_start = P.ss_start;
+  V.ss_c0 = P.ss_c0;
+  V.ss_e0 = P.ss_e0;
+  V.ss_w = P.ss_w;
+  V.nss = P.nss;
+  V.nsmall = P.nsmall;
+  V.bs_start = P.bs_start;
+  V.bs_c0 = P.bs_c0;
+  V.nbs = P.nbs;
+  V.nbig = P.nbig;
   return V;
 }
 
