@@ -319,6 +319,7 @@ void batch_begin_solve(Problem& P) {
   std::fill(P.h_bepochs.begin(), P.h_bepochs.end(), 0);
   std::fill(P.h_brho.begin(), P.h_brho.end(), 0.0);
   TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, P.nbatch, P.stream));
+  batch_active_tiles(P);
 }
 
 // After a check (the stream is synchronised): record every active instance's
@@ -344,8 +345,10 @@ bool batch_after_check(Problem& P, double tol, int epoch) {
       all = false;
     }
   }
-  if (changed)
+  if (changed) {
     TH_CUDA(cudaMemcpyAsync(P.bfrozen, P.h_bfrozen.data(), count, cudaMemcpyHostToDevice, P.stream));
+    if (!all) batch_active_tiles(P);  // later sweeps skip the tiles of finished instances
+  }
   // the host vector must outlive the copy
   TH_CUDA(cudaStreamSynchronize(P.stream));
   return all;

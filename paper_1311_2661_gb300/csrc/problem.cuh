@@ -96,6 +96,16 @@ struct Problem {
   std::vector<uint8_t> h_bfrozen;
   std::vector<int32_t> h_bepochs;      // epochs each instance ran in the last solve
   std::vector<double> h_brho;          // its rho when it stopped
+  // active tiles: per colour, the sweep tiles holding a unit of an unfinished
+  // instance (built for launch shape act_g; recomputed when instances stop)
+  int32_t* act_tiles = nullptr;
+  int64_t* act_off = nullptr;
+  int64_t* act_n = nullptr;
+  int64_t* act_cnt = nullptr;     // per flat tile: 1 if active (scan input)
+  int64_t* act_pos = nullptr;     // its exclusive scan
+  int64_t* tile_start = nullptr;  // per colour: first flat tile (C + 1)
+  int64_t tiles_total = 0;
+  int act_g = -1;
 
   // graph meta (builders)
   int64_t nv = 0, ne = 0;
@@ -211,6 +221,8 @@ void batch_index(Problem& P);
 void batch_begin_solve(Problem& P);
 bool batch_after_check(Problem& P, double tol, int epoch);
 void batch_end_solve(Problem& P, int epoch);
+// (scd.cu) rebuild the active-tile lists from the frozen flags
+void batch_active_tiles(Problem& P);
 
 // scd.cu
 struct SolveArgs {

@@ -17,6 +17,20 @@ constexpr int CACHE = 4;           // r values a lane keeps between gather and s
 constexpr int CHECK_BLOCKS = 2432; // fixed grid of the check kernel (deterministic reduction)
 constexpr int NRED = 6;            // rho, obj, infeas, rr, ur, xx
 
+#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// segment t of a table of segment starts (start[0] = 0, n segments) holding
+// flat index i: the last t with start[t] <= i
+__device__ __forceinline__ int64_t seg_find(const int64_t* start, int64_t n, int64_t i) {
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (start[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 struct StepView {
   const int64_t* colptr;
   const uint32_t* rowidx;
@@ -46,6 +60,11 @@ struct StepView {
   const int32_t* inst_col;
   const int32_t* inst_row;
   const uint8_t* frozen;
+  // batches: per colour, the tiles holding a unit of an unfinished instance
+  // (act_tiles[act_off[c] .. + act_n[c]]); null for a single problem
+  const int32_t* act_tiles;
+  const int64_t* act_off;
+  const int64_t* act_n;
 };
 
 // A column / slack row of a frozen batch instance is not stepped.
@@ -75,6 +94,7 @@ __host__ __device__ __forceinline__ int small_lanes(int W, int small_g) {
 struct ColorLaunch {
   SegLaunch seg[UC_COUNT + 1];
   int nseg;
+  int color;
 };
 
 __device__ __forceinline__ float coef(const StepView& V, int64_t p, uint32_t e) {
@@ -504,7 +524,12 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
 __global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunch CL) {
   __shared__ float red_smem[33];
   extern __shared__ __align__(16) unsigned char dyn[];
-  process_tile(V, CL.seg, CL.nseg, blockIdx.x, red_smem, dyn);
+  int64_t t = blockIdx.x;
+  if (V.act_tiles) {  // batches: only the active tiles of the colour (grid sized for all)
+    if (t >= V.act_n[CL.color]) return;
+    t = V.act_tiles[V.act_off[CL.color] + t];
+  }
+  process_tile(V, CL.seg, CL.nseg, t, red_smem, dyn);
 }
 
 // Grid-wide barrier of a cooperative launch, split into arrive and wait so a CTA
@@ -611,11 +636,15 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
   __syncthreads();
   int cur = 0;
   bool first_staged = false;
+  // tile q of colour c (batches: through the active-tile list)
+  auto tile_of = [&](int c, int64_t q) -> int64_t { return V.act_tiles ? V.act_tiles[V.act_off[c] + q] : q; };
+  auto count_of = [&](int c) -> int64_t { return V.act_tiles ? V.act_n[c] : ntiles[c]; };
   for (int e = 0; e < epochs; ++e) {
     for (int c = 0; c < ncolors; ++c) {
-      const int64_t nt = ntiles[c];
-      for (int64_t t = blockIdx.x; t < nt; t += gridDim.x)
-        process_tile<FULL>(V, cl[cur].seg, cl[cur].nseg, t, red_smem, dyn, first_staged && t == blockIdx.x);
+      const int64_t nt = count_of(c);
+      for (int64_t q = blockIdx.x; q < nt; q += gridDim.x)
+        process_tile<FULL>(V, cl[cur].seg, cl[cur].nseg, tile_of(c, q), red_smem, dyn,
+                           first_staged && q == blockIdx.x);
       const bool last = (e == epochs - 1) && (c == ncolors - 1);
       if (last) break;
       const int cn = (c + 1 < ncolors) ? c + 1 : 0;
@@ -625,22 +654,23 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
       // overlap the barrier: next descriptor and L2 prefetch of the next tiles
       if (threadIdx.x < CLW) ((unsigned*)&cl[cur ^ 1])[threadIdx.x] = ((const unsigned*)&plan[cn])[threadIdx.x];
       __syncthreads();
-      const int64_t ntn = ntiles[cn];
+      const int64_t ntn = count_of(cn);
       bool staged = false;
       if ((int64_t)blockIdx.x < ntn) {
         // a first tile that is a long column: its row ids go to shared memory now
+        const int64_t t0 = tile_of(cn, blockIdx.x);
         const ColorLaunch& nx = cl[cur ^ 1];
         int si = 0;
-        while (si + 1 < nx.nseg && (int64_t)blockIdx.x >= nx.seg[si + 1].b0) ++si;
+        while (si + 1 < nx.nseg && t0 >= nx.seg[si + 1].b0) ++si;
         const SegLaunch S = nx.seg[si];
-        if (FULL && (S.cls == UC_HUGE || S.cls == UC_LARGE) && (int64_t)blockIdx.x - S.b0 < S.n) {
-          stage_huge(V, S.c0 + ((int64_t)blockIdx.x - S.b0), dyn);
+        if (FULL && (S.cls == UC_HUGE || S.cls == UC_LARGE) && t0 - S.b0 < S.n) {
+          stage_huge(V, S.c0 + (t0 - S.b0), dyn);
           staged = true;
         }
       }
       for (int q = staged ? 1 : 0; q < PREFETCH_TILES; ++q) {
-        const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
-        if (t < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, t);
+        const int64_t qq = blockIdx.x + (int64_t)q * gridDim.x;
+        if (qq < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, tile_of(cn, qq));
       }
       if (threadIdx.x == 0) ok = bar_wait(bar, old, err) ? 1 : 0;
       __syncthreads();
@@ -696,6 +726,10 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.inst_col = batch ? P.binst_col : nullptr;
   V.inst_row = batch ? P.binst_row : nullptr;
   V.frozen = batch ? P.bfrozen : nullptr;
+  const bool act = batch && P.act_tiles && P.act_g == P.small_g;
+  V.act_tiles = act ? P.act_tiles : nullptr;
+  V.act_off = act ? P.act_off : nullptr;
+  V.act_n = act ? P.act_n : nullptr;
   return V;
 }
 
@@ -711,6 +745,9 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     TH_LAUNCHED();
   };
   if (a.mode == THETIS_MODE_ASYNC) {
+    V.act_tiles = nullptr;  // the launches below merge colours: no per-colour tile lists
+    V.act_off = nullptr;
+    V.act_n = nullptr;
     // every class of every colour in one launch; slack rows as one range
     // (per-class launches keep the CTA shapes; they run back to back)
     for (int cls = 0; cls < UC_COUNT; ++cls) {
@@ -738,8 +775,10 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     TH_CUDA(cudaGetLastError());
     return;
   }
-  for (auto& cp : P.plan) {
+  for (int c = 0; c < (int)P.plan.size(); ++c) {
+    const ColorPlan& cp = P.plan[c];
     ColorLaunch CL{};
+    CL.color = c;
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
       CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot, sg.e0};
@@ -765,6 +804,7 @@ static void ensure_sweep_plan(Problem& P) {
   for (int c = 0; c < C; ++c) {
     const ColorPlan& cp = P.plan[c];
     ColorLaunch CL{};
+    CL.color = c;
     int64_t tot = 0;
     for (auto& sg : cp.segs) {
       CL.seg[CL.nseg++] = SegLaunch{sg.cls, sg.u0, sg.u1 - sg.u0, sg.c0, tot, sg.e0};
@@ -830,6 +870,104 @@ void reset_sweep_flags(Problem& P) {
   TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
 }
 
+// ---------------------------------------------------------------------------
+// active tiles of a batch
+// ---------------------------------------------------------------------------
+// One warp per flat tile: 1 if any unit of the tile belongs to an unfinished
+// instance (simplex blocks, absent from batches, always count as active).
+__global__ void k_tile_flags(StepView V, const ColorLaunch* plan, const int64_t* tstart, int C, int64_t T,
+                             int64_t* cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp; f < T; f += nwarps) {
+    const int c = (int)seg_find(tstart, C, f);
+    const int64_t t = f - tstart[c];
+    const ColorLaunch& CL = plan[c];
+    int si = 0;
+    while (si + 1 < CL.nseg && t >= CL.seg[si + 1].b0) ++si;
+    const SegLaunch& S = CL.seg[si];
+    const int64_t b = t - S.b0;
+    int64_t u0 = 0, u1 = 0;
+    bool rows = false, always = false;
+    switch (S.cls) {
+      case UC_HUGE:
+      case UC_LARGE: u0 = b; u1 = b + 1; break;
+      case UC_MED: u0 = b * (STEP_T / 32); u1 = u0 + STEP_T / 32; break;
+      case UC_BLOCK: always = true; break;
+      case UC_COUNT: u0 = b * (STEP_T * SLACK_ROWS); u1 = u0 + STEP_T * SLACK_ROWS; rows = true; break;
+      default: {
+        const int per = STEP_T / small_lanes(small_width(S.cls), V.small_g);
+        u0 = b * per;
+        u1 = u0 + per;
+      }
+    }
+    if (u1 > S.n) u1 = S.n;
+    bool any = always;
+    for (int64_t u = u0 + lane; u < u1 && !any; u += 32) {
+      const int32_t inst = rows ? V.inst_row[S.u0 + u] : V.inst_col[S.c0 + u];
+      any = !V.frozen[inst];
+    }
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) cnt[f] = any ? 1 : 0;
+  }
+}
+
+__global__ void k_tile_compact(const int64_t* cnt, const int64_t* pos, const int64_t* tstart, int C, int64_t T,
+                               int32_t* act_tiles, int64_t* act_off, int64_t* act_n) {
+  GSTRIDE(f, T) {
+    if (cnt[f]) {
+      const int c = (int)seg_find(tstart, C, f);
+      act_tiles[pos[f]] = (int32_t)(f - tstart[c]);
+    }
+  }
+  GSTRIDE(c, C) {
+    act_off[c] = pos[tstart[c]];
+    act_n[c] = pos[tstart[c + 1]] - pos[tstart[c]];
+  }
+}
+
+void batch_active_tiles(Problem& P) {
+  if (P.nbatch == 0 || P.ncolors == 0) return;
+  ensure_sweep_plan(P);
+  cudaStream_t s = P.stream;
+  const int C = P.ncolors;
+  if (P.act_g != P.small_g || !P.act_tiles) {
+    std::vector<int64_t> nt(C), ts(C + 1, 0);
+    TH_CUDA(cudaMemcpyAsync(nt.data(), P.d_ntiles, C * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < C; ++c) ts[c + 1] = ts[c] + nt[c];
+    TH_CHECK(ts[C] < (int64_t(1) << 31), THETIS_E_INVALID, "too many tiles for the active-tile lists");
+    P.tiles_total = ts[C];
+    P.tile_start = P.mem.alloc<int64_t>(C + 1);
+    P.act_tiles = P.mem.alloc<int32_t>(P.tiles_total + 1);
+    P.act_off = P.mem.alloc<int64_t>(C);
+    P.act_n = P.mem.alloc<int64_t>(C);
+    P.act_cnt = P.mem.alloc<int64_t>(P.tiles_total + 1);
+    P.act_pos = P.mem.alloc<int64_t>(P.tiles_total + 1);
+    TH_CUDA(cudaMemcpyAsync(P.tile_start, ts.data(), (C + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaStreamSynchronize(s));  // ts must outlive the copy
+    P.act_g = P.small_g;
+  }
+  // the view's instance arrays (the step parameters do not matter here)
+  StepView V{};
+  V.inst_col = P.binst_col;
+  V.inst_row = P.binst_row;
+  V.frozen = P.bfrozen;
+  V.small_g = P.small_g;
+  const int64_t T = P.tiles_total;
+  if (T > 0) {
+    k_tile_flags<<<grid_for(T * 32, 256), 256, 0, s>>>(V, (const ColorLaunch*)P.d_plan, P.tile_start, C, T,
+                                                       P.act_cnt);
+    TH_LAUNCHED();
+  }
+  Arena tmp(s);
+  exclusive_scan_i64(P.act_cnt, P.act_pos, T, tmp, s);
+  k_tile_compact<<<grid_for(std::max<int64_t>(T, C), 256), 256, 0, s>>>(P.act_cnt, P.act_pos, P.tile_start, C, T,
+                                                                        P.act_tiles, P.act_off, P.act_n);
+  TH_LAUNCHED();
+}
+
 void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int epochs) {
   ensure_sweep_plan(P);
   const int grid = sweep_grid(P);
@@ -858,7 +996,6 @@ int sweep_error(Problem& P) {
 // ---------------------------------------------------------------------------
 // FP64 refresh and checks
 // ---------------------------------------------------------------------------
-#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 // r = A x - b in FP64 (row by row over the internal CSR, plus the slack)
 __global__ void k_refresh(const int64_t* rowptr, const uint32_t* colidx, const float* rval, const float* x,
@@ -925,17 +1062,7 @@ struct CheckView {
   int64_t nbs, nbig;
 };
 
-// segment t of a table of segment starts (start[0] = 0, n segments) holding
-// flat index i: the last t with start[t] <= i
-__device__ __forceinline__ int64_t seg_find(const int64_t* start, int64_t n, int64_t i) {
-  int64_t lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (start[mid] <= i) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
+
 
 // max of non-negative doubles through their bit patterns (same order)
 __device__ __forceinline__ void rho_max(unsigned long long* p, double v) {
