@@ -14,6 +14,9 @@ Parity status of each function (the pins are in tests/test_oracle_*.py):
                                    enumeration of x(beta), Thm. 1 bounds,
                                    monotone f_beta, LCP)
   checks                           pinned (through solve pins and closed forms)
+  solve_al                         pinned (convergence to LP optima and strong
+                                   duality on closed-form / HiGHS instances,
+                                   infeasibility far below the fixed-beta penalty)
   round_vc / round_is / round_mc   pinned (validity, 2x bound, exact selection
                                    probabilities, CKR expectation for k=2)
   rng                              pinned (published splitmix64 outputs)
@@ -253,6 +256,27 @@ class OracleLP:
         return x, dict(epochs_run=info.epochs_run, ncolors=info.ncolors, converged=bool(info.converged),
                        rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta,
                        trace=trace[: nt.value].copy())
+
+    def solve_al(self, beta=1e2, epochs=50, tol=0.0, refresh_every=10, outer=5, beta_growth=1.0, step_rule=0,
+                 seed=0, color=None, ubar=None, xbar=None, x0=None):
+        """Augmented-Lagrangian outer loop of Sec. 3.4 (a proximal method of
+        multipliers): solve eq. QP at (ubar, xbar, beta) from the previous
+        iterate, then ubar <- ubar - beta (A x - b), xbar <- x and
+        beta <- beta * beta_growth.  Returns (x, ubar after the last update,
+        per-outer list of the inner solve's info with its beta)."""
+        ub = np.zeros(self.M) if ubar is None else np.array(ubar, np.float64, copy=True)
+        xb = np.zeros(self.N) if xbar is None else np.array(xbar, np.float64, copy=True)
+        x = x0
+        hist = []
+        for _ in range(outer):
+            x, info = self.solve(beta=beta, epochs=epochs, tol=tol, refresh_every=refresh_every,
+                                 step_rule=step_rule, seed=seed, color=color, ubar=ub, xbar=xb, x0=x)
+            info["beta"] = beta
+            hist.append(info)
+            ub = ub - beta * self.residual(x)
+            xb = x.copy()
+            beta *= beta_growth
+        return x, ub, hist
 
     def fbeta_steps(self, x, beta, color, step_rule=0):
         x = np.array(x, np.float64, copy=True)
