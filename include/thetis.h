@@ -210,6 +210,34 @@ thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* s
 thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solve_info* info);
 
 /*
+ * thetis_solve_al -- the augmented-Lagrangian outer loop of Sec. 3.4 (a
+ * proximal method of multipliers around eq. QP): `outer` times, solve eq. QP
+ * at (ubar, xbar, beta) as thetis_solve does (same p: epochs, tol,
+ * refresh_every, step_rule, mode, engine), continuing from the current
+ * iterate, then ubar <- ubar - beta (A x - b) (A x - b from the FP64 refresh
+ * that ended the solve), xbar <- x (slacks included) and beta <- beta *
+ * beta_growth.  p->ubar / p->xbar (original row / column order, slacks after
+ * the structural columns, p->mem) give the starting multiplier and centre, or
+ * zero when NULL; p->x0 as in thetis_solve.  The multiplier estimate after
+ * the last update is read with thetis_get_duals.
+ *   outer >= 1, beta_growth >= 1 (1 keeps beta); a batch handle is refused.
+ *   info: the last inner solve (epochs_run and updates summed over all);
+ *   infeas_out / obj_out / rho_out[outer]: HOST arrays (each may be NULL) with
+ *   ||Ax - b||_inf, c'x and rho at the end of every inner solve.
+ * Returns the last inner solve's THETIS_OK / THETIS_NOT_CONVERGED, or an error.
+ */
+thetis_status thetis_solve_al(thetis_handle* h, const thetis_params* p, int32_t outer, double beta_growth,
+                              thetis_solve_info* info, double* infeas_out, double* obj_out, double* rho_out);
+
+/*
+ * thetis_get_duals -- the multiplier estimate ubar (FP32, original row order,
+ * m entries) held by the handle: after thetis_solve_al, the estimate after its
+ * last update; after thetis_solve with p->ubar, that ubar.  out_mem says where
+ * `out` lives.  THETIS_E_INVALID if the handle holds no multiplier.
+ */
+thetis_status thetis_get_duals(thetis_handle* h, float* out, int32_t out_mem);
+
+/*
  * thetis_round -- repair + round the current iterate (structural part).
  *  VC: eps = max_e (1 - x_u - x_v)_+, x~ = min(1, x/(1-eps)) (Lemma
  *      lem:infeasible:rounded:vc), label = [x~ >= 1/2] (Sec. 2); reps ignored.

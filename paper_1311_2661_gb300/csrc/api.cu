@@ -256,130 +256,219 @@ thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* s
   return THETIS_OK;
 }
 
+namespace {
+
+// One solve of eq. QP on the handle's current iterate and (ubar, xbar) state:
+// sweeps of refresh_every epochs, each followed by the FP64 refresh + checks,
+// until rho <= tol (per instance for batches) or the epoch cap.
+struct SolveRun {
+  bool converged = false;
+  int ep = 0;
+  double sweep_ms = 0.0;
+  int64_t sweep_launches = 0;
+  CheckOut co{};
+};
+
+void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engine, SolveRun& R) {
+  Problem& P = *h->P;
+  cudaStream_t s = h->stream;
+  const bool persistent = a.mode == THETIS_MODE_COLORED && engine == 0 && P.ncolors > 0 && coop_allowed() &&
+                          sweep_grid(P) > 0;
+  if (persistent) reset_sweep_flags(P);
+  batch_begin_solve(P);
+  // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
+  bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
+                h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g;
+  if (!persistent && !key_ok && a.epochs > 0) {
+    if (P.epoch_graph) {
+      cudaGraphExecDestroy(P.epoch_graph);
+      P.epoch_graph = nullptr;
+    }
+    cudaGraph_t g;
+    uint64_t l0 = launch_count();
+    TH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      run_epoch(P, a, ub, xb);
+    } catch (...) {
+      cudaStreamEndCapture(s, &g);
+      throw;
+    }
+    TH_CUDA(cudaStreamEndCapture(s, &g));
+    uint64_t l1 = launch_count();
+    h->graph_launches = (int64_t)(l1 - l0);
+    count_launch((uint64_t)0 - (l1 - l0));  // nothing ran during capture
+    cudaError_t e = cudaGraphInstantiate(&P.epoch_graph, g, 0);
+    cudaGraphDestroy(g);
+    TH_CUDA(e);
+    h->g_beta = a.beta;
+    h->g_rule = a.step_rule;
+    h->g_mode = a.mode;
+    h->g_ub = ub;
+    h->g_xb = xb;
+    h->g_small = P.small_g;
+  }
+  bool checked_last = false;
+  while (R.ep < a.epochs) {
+    // epochs up to the next check
+    const int chunk = std::min(a.refresh_every - R.ep % a.refresh_every, a.epochs - R.ep);
+    TH_CUDA(cudaEventRecord(h->ev2, s));
+    if (persistent) {
+      run_sweep(P, a, ub, xb, chunk);
+      ++R.sweep_launches;
+    } else {
+      for (int q = 0; q < chunk; ++q) {
+        TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
+        count_launch((uint64_t)h->graph_launches);
+      }
+      R.sweep_launches += (int64_t)chunk * h->graph_launches;
+    }
+    TH_CUDA(cudaEventRecord(h->ev3, s));
+    R.ep += chunk;
+    checked_last = false;
+    if (R.ep % a.refresh_every == 0 || R.ep == a.epochs) {
+      refresh_and_check(P, a, ub, xb, R.co);  // synchronises the stream
+      if (persistent && sweep_error(P)) throw Error{THETIS_E_TIMEOUT, "grid barrier of the persistent sweep timed out"};
+      float t = 0.f;
+      TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
+      R.sweep_ms += t;
+      checked_last = true;
+      // a batch converges instance by instance (each against tol)
+      if (P.nbatch > 0 ? batch_after_check(P, a.tol, R.ep) : R.co.rho <= a.tol) {
+        R.converged = true;
+        break;
+      }
+    }
+  }
+  if (!checked_last) {
+    refresh_and_check(P, a, ub, xb, R.co);
+    R.converged = (P.nbatch > 0) ? batch_after_check(P, a.tol, R.ep) : R.co.rho <= a.tol;
+  }
+  if (P.nbatch > 0) {
+    batch_end_solve(P, R.ep);
+    R.co.rho = 0.0;  // the largest rho any instance stopped at
+    for (double v : P.h_brho) R.co.rho = std::max(R.co.rho, v);
+  }
+}
+
+void check_params(const thetis_params* p) {
+  TH_CHECK(p->beta > 0 && std::isfinite(p->beta), THETIS_E_INVALID, "beta must be > 0");
+  TH_CHECK(p->epochs >= 0, THETIS_E_INVALID, "epochs must be >= 0");
+  TH_CHECK(p->step_rule == 0 || p->step_rule == 1, THETIS_E_INVALID, "step_rule must be 0 or 1");
+  TH_CHECK(p->mode == THETIS_MODE_COLORED || p->mode == THETIS_MODE_ASYNC, THETIS_E_INVALID, "bad mode");
+  TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
+}
+
+void fill_info(const Problem& P, const SolveRun& R, float ms, thetis_solve_info* info) {
+  if (!info) return;
+  info->epochs_run = R.ep;
+  info->converged = R.converged ? 1 : 0;
+  info->ncolors = P.ncolors;
+  info->rho = R.co.rho;
+  info->obj = R.co.obj;
+  info->infeas = R.co.infeas;
+  info->fbeta = R.co.fbeta;
+  info->updates = (int64_t)R.ep * P.free_coords;
+  info->solve_ms = ms;
+  info->epoch_ms = R.sweep_ms;
+  info->launches_per_epoch = R.ep > 0 ? (int32_t)((R.sweep_launches + R.ep - 1) / R.ep) : 0;
+}
+
+}  // namespace
+
 thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solve_info* info) {
   if (!h || !h->P || !p) {
     set_error("null argument");
     return THETIS_E_INVALID;
   }
-  bool converged = false;
+  SolveRun R;
   thetis_status st = guard(h->stream, [&] {
     Problem& P = *h->P;
     cudaStream_t s = h->stream;
-    TH_CHECK(p->beta > 0 && std::isfinite(p->beta), THETIS_E_INVALID, "beta must be > 0");
-    TH_CHECK(p->epochs >= 0, THETIS_E_INVALID, "epochs must be >= 0");
-    TH_CHECK(p->step_rule == 0 || p->step_rule == 1, THETIS_E_INVALID, "step_rule must be 0 or 1");
-    TH_CHECK(p->mode == THETIS_MODE_COLORED || p->mode == THETIS_MODE_ASYNC, THETIS_E_INVALID, "bad mode");
+    check_params(p);
     SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode};
     Arena tmp(s);
     const float* dub = to_dev(p->ubar, P.M, p->mem, tmp, s);
     const float* dxb = to_dev(p->xbar, P.Ns + P.Msl, p->mem, tmp, s);
     const float* dx0 = to_dev(p->x0, P.Ns, p->mem, tmp, s);
     prepare_solve(P, dub, dxb, dx0);
-    const bool ub = dub != nullptr, xb = dxb != nullptr;
     refresh_only(P);
-    TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
-    const bool persistent = a.mode == THETIS_MODE_COLORED && p->engine == 0 && P.ncolors > 0 && coop_allowed() &&
-                            sweep_grid(P) > 0;
-    if (persistent) reset_sweep_flags(P);
-    batch_begin_solve(P);
-    // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
-    bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
-                  h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g;
-    if (!persistent && !key_ok && a.epochs > 0) {
-      if (P.epoch_graph) {
-        cudaGraphExecDestroy(P.epoch_graph);
-        P.epoch_graph = nullptr;
-      }
-      cudaGraph_t g;
-      uint64_t l0 = launch_count();
-      TH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      try {
-        run_epoch(P, a, ub, xb);
-      } catch (...) {
-        cudaStreamEndCapture(s, &g);
-        throw;
-      }
-      TH_CUDA(cudaStreamEndCapture(s, &g));
-      uint64_t l1 = launch_count();
-      h->graph_launches = (int64_t)(l1 - l0);
-      count_launch((uint64_t)0 - (l1 - l0));  // nothing ran during capture
-      cudaError_t e = cudaGraphInstantiate(&P.epoch_graph, g, 0);
-      cudaGraphDestroy(g);
-      TH_CUDA(e);
-      h->g_beta = a.beta;
-      h->g_rule = a.step_rule;
-      h->g_mode = a.mode;
-      h->g_ub = ub;
-      h->g_xb = xb;
-      h->g_small = P.small_g;
-    }
     TH_CUDA(cudaEventRecord(h->ev0, s));
-    CheckOut co{};
-    int ep = 0;
-    bool checked_last = false;
-    double sweep_ms = 0.0;
-    int64_t sweep_launches = 0;
-    while (ep < a.epochs) {
-      // epochs up to the next check
-      const int chunk = std::min(a.refresh_every - ep % a.refresh_every, a.epochs - ep);
-      TH_CUDA(cudaEventRecord(h->ev2, s));
-      if (persistent) {
-        run_sweep(P, a, ub, xb, chunk);
-        ++sweep_launches;
-      } else {
-        for (int q = 0; q < chunk; ++q) {
-          TH_CUDA(cudaGraphLaunch(P.epoch_graph, s));
-          count_launch((uint64_t)h->graph_launches);
-        }
-        sweep_launches += (int64_t)chunk * h->graph_launches;
-      }
-      TH_CUDA(cudaEventRecord(h->ev3, s));
-      ep += chunk;
-      checked_last = false;
-      if (ep % a.refresh_every == 0 || ep == a.epochs) {
-        refresh_and_check(P, a, ub, xb, co);  // synchronises the stream
-        if (persistent && sweep_error(P))
-          throw Error{THETIS_E_TIMEOUT, "grid barrier of the persistent sweep timed out"};
-        float t = 0.f;
-        TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
-        sweep_ms += t;
-        checked_last = true;
-        // a batch converges instance by instance (each against tol)
-        if (P.nbatch > 0 ? batch_after_check(P, a.tol, ep) : co.rho <= a.tol) {
-          converged = true;
-          break;
-        }
-      }
+    solve_run(h, a, dub != nullptr, dxb != nullptr, p->engine, R);
+    TH_CUDA(cudaEventRecord(h->ev1, s));
+    TH_CUDA(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    TH_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    fill_info(P, R, ms, info);
+  });
+  if (st != THETIS_OK) return st;
+  return R.converged ? THETIS_OK : THETIS_NOT_CONVERGED;
+}
+
+thetis_status thetis_solve_al(thetis_handle* h, const thetis_params* p, int32_t outer, double beta_growth,
+                              thetis_solve_info* info, double* infeas_out, double* obj_out, double* rho_out) {
+  if (!h || !h->P || !p) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  SolveRun R;
+  thetis_status st = guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    check_params(p);
+    TH_CHECK(outer >= 1, THETIS_E_INVALID, "outer must be >= 1");
+    TH_CHECK(beta_growth >= 1.0 && std::isfinite(beta_growth), THETIS_E_INVALID, "beta_growth must be >= 1");
+    TH_CHECK(P.nbatch == 0, THETIS_E_INVALID, "thetis_solve_al takes a single problem");
+    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode};
+    Arena tmp(s);
+    // ubar and xbar start from the caller's values or from zero
+    const float* dub = to_dev(p->ubar, P.M, p->mem, tmp, s);
+    const float* dxb = to_dev(p->xbar, P.Ns + P.Msl, p->mem, tmp, s);
+    const float* dx0 = to_dev(p->x0, P.Ns, p->mem, tmp, s);
+    float* z = nullptr;
+    if (!dub || !dxb) {
+      z = tmp.alloc<float>(std::max<int64_t>(P.M, P.Ns + P.Msl) + 1);
+      TH_CUDA(cudaMemsetAsync(z, 0, (std::max<int64_t>(P.M, P.Ns + P.Msl) + 1) * sizeof(float), s));
     }
-    if (!checked_last) {
-      refresh_and_check(P, a, ub, xb, co);
-      converged = (P.nbatch > 0) ? batch_after_check(P, a.tol, ep) : co.rho <= a.tol;
-    }
-    if (P.nbatch > 0) {
-      batch_end_solve(P, ep);
-      co.rho = 0.0;  // the largest rho any instance stopped at
-      for (double v : P.h_brho) co.rho = std::max(co.rho, v);
+    prepare_solve(P, dub ? dub : z, dxb ? dxb : z, dx0);
+    refresh_only(P);
+    TH_CUDA(cudaEventRecord(h->ev0, s));
+    int total = 0;
+    for (int k = 0; k < outer; ++k) {
+      R = SolveRun{};
+      solve_run(h, a, true, true, p->engine, R);
+      total += R.ep;
+      if (infeas_out) infeas_out[k] = R.co.infeas;
+      if (obj_out) obj_out[k] = R.co.obj;
+      if (rho_out) rho_out[k] = R.co.rho;
+      al_update(P, a.beta);  // ubar -= beta (Ax - b), xbar <- x, from the last exact refresh
+      a.beta *= beta_growth;
     }
     TH_CUDA(cudaEventRecord(h->ev1, s));
     TH_CUDA(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
     TH_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    if (info) {
-      info->epochs_run = ep;
-      info->converged = converged ? 1 : 0;
-      info->ncolors = P.ncolors;
-      info->rho = co.rho;
-      info->obj = co.obj;
-      info->infeas = co.infeas;
-      info->fbeta = co.fbeta;
-      info->updates = (int64_t)ep * P.free_coords;
-      info->solve_ms = ms;
-      info->epoch_ms = sweep_ms;
-      info->launches_per_epoch = ep > 0 ? (int32_t)((sweep_launches + ep - 1) / ep) : 0;
-    }
+    R.ep = total;
+    fill_info(P, R, ms, info);
+    if (info) info->updates = (int64_t)total * P.free_coords;
   });
   if (st != THETIS_OK) return st;
-  return converged ? THETIS_OK : THETIS_NOT_CONVERGED;
+  return R.converged ? THETIS_OK : THETIS_NOT_CONVERGED;
+}
+
+thetis_status thetis_get_duals(thetis_handle* h, float* out, int32_t out_mem) {
+  if (!h || !h->P || !out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  return guard(h->stream, [&] {
+    Problem& P = *h->P;
+    TH_CHECK(P.ubar_int != nullptr, THETIS_E_INVALID, "no multiplier estimate: solve with ubar or thetis_solve_al first");
+    Arena tmp(h->stream);
+    float* d = (out_mem == THETIS_MEM_DEVICE) ? out : tmp.alloc<float>(P.M);
+    gather_duals(P, d);
+    if (out_mem != THETIS_MEM_DEVICE) from_dev(out, d, P.M, THETIS_MEM_HOST, h->stream);
+    TH_CUDA(cudaStreamSynchronize(h->stream));
+  });
 }
 
 thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_t reps, uint8_t* labels_out,

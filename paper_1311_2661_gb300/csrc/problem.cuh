@@ -240,6 +240,11 @@ void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const f
 void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar);
 void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out);
 void refresh_only(Problem& P);
+// Sec. 3.4 multiplier step: ubar <- ubar - beta (A x - b) from the last FP64
+// refresh, xbar <- x (slacks included); c - A'ubar and the slack terms follow
+void al_update(Problem& P, double beta);
+// the multiplier estimate ubar in original row order
+void gather_duals(Problem& P, float* out);
 void init_iterate(Problem& P);
 int sweep_grid(Problem& P);
 bool sweep_lean_possible(const Problem& P);

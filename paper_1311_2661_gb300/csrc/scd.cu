@@ -1443,6 +1443,43 @@ void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const f
   TH_CUDA(cudaGetLastError());
 }
 
+__global__ void k_al_update(float* ubar, const double* r64, int64_t M, double beta, float* xbar, const float* x,
+                            int64_t Ns, float* sbar, const float* s, int64_t Msl) {
+  GSTRIDE(i, M > Ns ? M : Ns) {
+    if (i < M) ubar[i] = (float)((double)ubar[i] - beta * r64[i]);
+    if (i < Ns) xbar[i] = x[i];
+    if (i < Msl) sbar[i] = s[i];
+  }
+}
+
+void al_update(Problem& P, double beta) {
+  cudaStream_t s = P.stream;
+  TH_CHECK(P.ubar_int && P.xbar, THETIS_E_INVALID, "multiplier step without ubar / xbar state");
+  const int64_t n = std::max(P.M, P.Ns);
+  if (n > 0) {
+    k_al_update<<<grid_for(n, 256), 256, 0, s>>>(P.ubar_int, P.r64, P.M, beta, P.xbar, P.x, P.Ns, P.sbar, P.s,
+                                                 P.Msl);
+    TH_LAUNCHED();
+  }
+  k_ctil<<<grid_for(P.Ns, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.has_val ? P.val : nullptr, P.c, P.ubar_int, P.Ns,
+                                             P.ctil);
+  TH_LAUNCHED();
+  if (P.Msl > 0) {
+    k_cs<<<grid_for(P.Msl, 256), 256, 0, s>>>(P.ubar_int, P.sig, P.Msl, P.cs);
+    TH_LAUNCHED();
+  }
+}
+
+__global__ void k_gather_rows_f(const float* src_int, const uint32_t* row_of_orig, int64_t M, float* dst) {
+  GSTRIDE(i, M) dst[i] = src_int[row_of_orig[i]];
+}
+
+void gather_duals(Problem& P, float* out) {
+  if (P.M <= 0) return;
+  k_gather_rows_f<<<grid_for(P.M, 256), 256, 0, P.stream>>>(P.ubar_int, P.row_of_orig, P.M, out);
+  TH_LAUNCHED();
+}
+
 void init_iterate(Problem& P) {
   cudaStream_t s = P.stream;
   if (P.nblk > 0 && !P.in_block) {

@@ -96,6 +96,8 @@ def _load():
         "thetis_server_destroy": (st, [P]),
         "thetis_round_batch": (st, [P, u64, i32, P, i32, P, P, P]),
         "thetis_batch_info": (st, [P, P, P]),
+        "thetis_solve_al": (st, [P, P, i32, C.c_double, P, P, P, P]),
+        "thetis_get_duals": (st, [P, P, i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -197,6 +199,12 @@ class Handle:
     def solve(self, **kw):
         return thetis_solve(self, **kw)
 
+    def solve_al(self, **kw):
+        return thetis_solve_al(self, **kw)
+
+    def duals(self):
+        return thetis_get_duals(self)
+
     def round(self, kind=None, **kw):
         if kind is None:
             kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC}[self.kind]
@@ -279,6 +287,36 @@ def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step
     return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
                 rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
                 solve_ms=info.solve_ms, epoch_ms=info.epoch_ms, launches_per_epoch=info.launches_per_epoch)
+
+
+def thetis_solve_al(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, outer=5, beta_growth=1.0,
+                    step_rule=0, mode=MODE_COLORED, ubar=None, xbar=None, x0=None, engine=0):
+    """Augmented-Lagrangian outer loop; returns (info of the last inner solve,
+    dict of per-outer arrays infeas / obj / rho)."""
+    A = _Args()
+    p = Params()
+    p.beta, p.epochs, p.tol = float(beta), int(epochs), float(tol)
+    p.refresh_every, p.step_rule, p.mode = int(refresh_every), int(step_rule), int(mode)
+    p.ubar, p.xbar, p.x0 = A(ubar, np.float32), A(xbar, np.float32), A(x0, np.float32)
+    p.mem = A.memspace
+    p.engine = int(engine)
+    info = SolveInfo()
+    hist = {k: np.zeros(int(outer), np.float64) for k in ("infeas", "obj", "rho")}
+    st = _check(_lib.thetis_solve_al(h.ptr, C.byref(p), int(outer), float(beta_growth), C.byref(info),
+                                     hist["infeas"].ctypes.data, hist["obj"].ctypes.data, hist["rho"].ctypes.data),
+                allow=(THETIS_OK, THETIS_NOT_CONVERGED))
+    return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
+                rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
+                solve_ms=info.solve_ms, epoch_ms=info.epoch_ms), hist
+
+
+def thetis_get_duals(h: Handle, out=None):
+    """The multiplier estimate ubar (original row order)."""
+    m = thetis_get_sizes(h)["rows"]
+    o = np.zeros(m, np.float32) if out is None else out
+    ptr, mem = _out_ptr(o)
+    _check(_lib.thetis_get_duals(h.ptr, ptr, mem))
+    return o
 
 
 def thetis_round(h: Handle, kind, seed=0, reps=10, out=None):
