@@ -41,6 +41,13 @@ WORKLOADS = {
                               tol=1e-3, reps=1),
     "mc-grid1024-k8": dict(kind="mc", graph="grid", width=1024, height=1024, k=8, seed=3, beta=100.0, epochs=50,
                            refresh=10, tol=1e-3, reps=10),
+    # the IS config under the augmented-Lagrangian outer loop: 5 solves of 50 epochs, multiplier step between
+    "al-is-chunglu-n2^20-m1.6e7": dict(kind="is", graph="chung_lu", n=1 << 20, m=16_000_000, gamma=2.1, seed=2,
+                                       beta=100.0, epochs=50, refresh=10, tol=0.0, reps=10, al_outer=5),
+    # asynchronous mode (Sec. 3.4) vs concurrency: VC on ER n=1e6, avg degree 8, each level solved to rho <= 1e-3
+    "async-study-vc-er-n1e6": dict(kind="vc", graph="er", n=1_000_000, m=4_000_000, seed=4, beta=100.0,
+                                   epochs=1500, refresh=10, tol=1e-3, reps=1, study=True,
+                                   levels=[16, 64, 152, 608, 2432, 0]),
     # 4096 ER instances, half VC half IS, n ~ U[200, 20000], avg degree ~ U[4, 16], weights U[1, 10],
     # all solved to rho <= 1e-3 as one batch
     "batched-4096": dict(kind="batch", count=4096, n_lo=200, n_hi=20000, d_lo=4.0, d_hi=16.0, seed=5, beta=100.0,
@@ -242,7 +249,14 @@ def run_gpu(args, wl, ws, rank, local):
         h = build(eu, ev, w, term)
         # launch shape: timed trials on the first handle of this shape, cached afterwards
         shape["small_group"], shape["ctas_per_sm"] = T.thetis_autotune(h, beta=wl["beta"])
-        info = h.solve(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"])
+        if wl.get("al_outer"):
+            # augmented-Lagrangian outer loop (Sec. 3.4): al_outer solves of `epochs` epochs each
+            info, hist = h.solve_al(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"],
+                                    outer=wl["al_outer"])
+            info["al_infeas"] = hist["infeas"].tolist()
+            info["al_obj"] = hist["obj"].tolist()
+        else:
+            info = h.solve(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"])
         lab, rinfo = h.round(seed=11, reps=wl["reps"], out=out)
         assert rinfo["valid"], "rounded solution failed the exact validity check"
         h.close()
@@ -307,7 +321,7 @@ def run_gpu(args, wl, ws, rank, local):
 
     # time to residual 1e-3 (same pipeline, epochs until rho <= 1e-3)
     ttr = None
-    if args.ttr_epochs > 0:
+    if args.ttr_epochs > 0 and not wl.get("al_outer"):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         info, _ = step(eu_d, ev_d, w_d, term_d, lab_d, epochs=args.ttr_epochs, tol=1e-3)
@@ -352,7 +366,9 @@ def run_gpu(args, wl, ws, rank, local):
         "last_step": {"epochs_run": info0["epochs_run"], "rho": info0["rho"], "obj": info0["obj"],
                       "infeas": info0["infeas"], "solve_ms": info0["solve_ms"],
                       "rounded_obj": infos[-1][1]["obj"], "step_ms": step_ms[-1],
-                      "launches_per_epoch": info0["launches_per_epoch"]},
+                      "launches_per_epoch": info0["launches_per_epoch"],
+                      **({"al_infeas_per_outer": info0["al_infeas"], "al_obj_per_outer": info0["al_obj"]}
+                         if "al_infeas" in info0 else {})},
         "clocks": clk.summary(),
     }
     if rank == 0:
@@ -504,6 +520,81 @@ def run_batched(args, wl, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         order = np.random.default_rng(7).permutation(count)
         res["cpu_baseline"] = cpu_baseline_instances(wl, items, order, 15.0, "random instances of the batch")
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def run_async_study(args, wl, ws, rank, local):
+    """Convergence of the asynchronous scheme (Sec. 3.4: every coordinate at
+    once, atomic residual updates) against its concurrency -- at most `L` CTAs of
+    256 threads stepping at a time -- beside the colour-class sweep, each run
+    from the same start to rho <= tol.  The value is the coordinate-update rate
+    of the uncapped asynchronous solve."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1311_2661_gb300 import thetis as T
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    g = make_graph(wl, rank)
+    eu, ev, w = (torch.from_numpy(a).to(dev) for a in (g.eu, g.ev, g.w))
+    bpe = algorithmic_bytes_per_epoch(wl, g)
+    kw = dict(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"])
+
+    def solve(**extra):
+        # every run from the same start: a fresh handle (x = 0, slacks 0); build time is not in solve_ms
+        h = T.thetis_build_vc(g.n, eu, ev, w, seed=0, stream=stream)
+        info = h.solve(**kw, **extra)
+        h.close()
+        torch.cuda.synchronize()
+        return info
+
+    for _ in range(args.warmup):
+        solve(mode=T.MODE_ASYNC)
+    l0 = T.thetis_launch_count()
+    barrier(ws)
+    infos = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            infos.append(solve(mode=T.MODE_ASYNC))
+    launches = T.thetis_launch_count() - l0
+    total_ms = max_over_ranks(sum(i["solve_ms"] for i in infos), ws, dev)
+    updates = sum_over_ranks(float(sum(i["updates"] for i in infos)), ws, dev)
+    study = []
+    for L in wl["levels"]:
+        i = solve(mode=T.MODE_ASYNC, async_ctas=L)
+        study.append({"ctas": L if L else "all", "epochs": i["epochs_run"], "converged": i["converged"],
+                      "rho": i["rho"], "solve_ms": i["solve_ms"], "ms_per_epoch": i["epoch_ms"] / max(i["epochs_run"], 1),
+                      "updates_per_s": i["updates"] / (i["solve_ms"] / 1e3)})
+    col = solve()
+    pk, pk_kind = peaks()
+    ep_ms = sum(i["epoch_ms"] for i in infos)
+    ep_n = sum(i["epochs_run"] for i in infos)
+    achieved = bpe * ep_n / (ep_ms / 1e3) / 1e9
+    res = {
+        "metric": METRIC, "value": updates / (total_ms / 1e3), "unit": "coord_updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refresh/checks)",
+        "data": "synthetic (seeded ER graph)",
+        "config": {"workload": args.workload, "kind": "vc", "n": g.n, "m": g.m, "beta": wl["beta"], "tol": wl["tol"],
+                   "mode": "async, uncapped", "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2; each step a full solve to tol"},
+        "e2e": None,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "k_color_step (async: all units per class launch, atomic r)",
+                     "bytes_per_epoch": bpe, "peak_kind": f"{pk_kind} hbm_gbs"},
+        "async_study": study,
+        "colored": {"epochs": col["epochs_run"], "solve_ms": col["solve_ms"], "rho": col["rho"],
+                    "ms_per_epoch": col["epoch_ms"] / max(col["epochs_run"], 1)},
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -881,6 +972,8 @@ def main():
         run_batched(args, wl, ws, rank, local)
     elif wl["kind"] == "serve":
         run_serving(args, wl, ws, rank, local)
+    elif wl.get("study"):
+        run_async_study(args, wl, ws, rank, local)
     else:
         run_gpu(args, wl, ws, rank, local)
     if ws > 1:

@@ -104,7 +104,11 @@ typedef struct {
  *                 refresh interval with a grid barrier between colours (falls
  *                 back to 1 where cooperative launch is unavailable);
  *                 1 = one launch per colour, replayed as a CUDA graph.  Both
- *                 give the same iterates. */
+ *                 give the same iterates.
+ *   async_ctas    async mode only: at most this many CTAs (256 threads) step
+ *                 coordinates at once, each taking tiles in turn (0 = one CTA
+ *                 per tile, as many as the GPU runs); the concurrency of the
+ *                 asynchronous scheme. */
 typedef struct {
   double beta;
   int32_t epochs;
@@ -117,6 +121,7 @@ typedef struct {
   const float* x0;
   int32_t mem;
   int32_t engine;
+  int32_t async_ctas;
 } thetis_params;
 
 /* Result of a solve; all checks in FP64 on the final iterate.
@@ -221,7 +226,7 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
  * zero when NULL; p->x0 as in thetis_solve.  The multiplier estimate after
  * the last update is read with thetis_get_duals.
  *   outer >= 1, beta_growth >= 1 (1 keeps beta); a batch handle is refused.
- *   info: the last inner solve (epochs_run and updates summed over all);
+ *   info: the last inner solve (epochs_run, updates and epoch_ms summed over all);
  *   infeas_out / obj_out / rho_out[outer]: HOST arrays (each may be NULL) with
  *   ||Ax - b||_inf, c'x and rho at the end of every inner solve.
  * Returns the last inner solve's THETIS_OK / THETIS_NOT_CONVERGED, or an error.

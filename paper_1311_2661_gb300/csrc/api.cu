@@ -18,7 +18,7 @@ struct thetis_handle {
   int64_t graph_launches = 0;  // kernels per epoch graph replay
   // key of the captured epoch graph
   double g_beta = 0;
-  int g_rule = -1, g_mode = -1, g_ub = -1, g_xb = -1, g_small = -1;
+  int g_rule = -1, g_mode = -1, g_ub = -1, g_xb = -1, g_small = -1, g_async = -1;
   ~thetis_handle() {
     if (P) {
       cudaStreamSynchronize(stream);
@@ -278,7 +278,7 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
   batch_begin_solve(P);
   // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
   bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
-                h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g;
+                h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g && h->g_async == a.async_ctas;
   if (!persistent && !key_ok && a.epochs > 0) {
     if (P.epoch_graph) {
       cudaGraphExecDestroy(P.epoch_graph);
@@ -306,6 +306,7 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
     h->g_ub = ub;
     h->g_xb = xb;
     h->g_small = P.small_g;
+    h->g_async = a.async_ctas;
   }
   bool checked_last = false;
   while (R.ep < a.epochs) {
@@ -356,6 +357,7 @@ void check_params(const thetis_params* p) {
   TH_CHECK(p->step_rule == 0 || p->step_rule == 1, THETIS_E_INVALID, "step_rule must be 0 or 1");
   TH_CHECK(p->mode == THETIS_MODE_COLORED || p->mode == THETIS_MODE_ASYNC, THETIS_E_INVALID, "bad mode");
   TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
+  TH_CHECK(p->async_ctas >= 0, THETIS_E_INVALID, "async_ctas must be >= 0");
 }
 
 void fill_info(const Problem& P, const SolveRun& R, float ms, thetis_solve_info* info) {
@@ -385,7 +387,8 @@ thetis_status thetis_solve(thetis_handle* h, const thetis_params* p, thetis_solv
     Problem& P = *h->P;
     cudaStream_t s = h->stream;
     check_params(p);
-    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode};
+    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode,
+                p->async_ctas};
     Arena tmp(s);
     const float* dub = to_dev(p->ubar, P.M, p->mem, tmp, s);
     const float* dxb = to_dev(p->xbar, P.Ns + P.Msl, p->mem, tmp, s);
@@ -418,7 +421,8 @@ thetis_status thetis_solve_al(thetis_handle* h, const thetis_params* p, int32_t 
     TH_CHECK(outer >= 1, THETIS_E_INVALID, "outer must be >= 1");
     TH_CHECK(beta_growth >= 1.0 && std::isfinite(beta_growth), THETIS_E_INVALID, "beta_growth must be >= 1");
     TH_CHECK(P.nbatch == 0, THETIS_E_INVALID, "thetis_solve_al takes a single problem");
-    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode};
+    SolveArgs a{p->beta, p->epochs, p->tol, p->refresh_every > 0 ? p->refresh_every : 10, p->step_rule, p->mode,
+                p->async_ctas};
     Arena tmp(s);
     // ubar and xbar start from the caller's values or from zero
     const float* dub = to_dev(p->ubar, P.M, p->mem, tmp, s);
@@ -433,10 +437,14 @@ thetis_status thetis_solve_al(thetis_handle* h, const thetis_params* p, int32_t 
     refresh_only(P);
     TH_CUDA(cudaEventRecord(h->ev0, s));
     int total = 0;
+    double sweep_total = 0.0;
+    int64_t launches_total = 0;
     for (int k = 0; k < outer; ++k) {
       R = SolveRun{};
       solve_run(h, a, true, true, p->engine, R);
       total += R.ep;
+      sweep_total += R.sweep_ms;
+      launches_total += R.sweep_launches;
       if (infeas_out) infeas_out[k] = R.co.infeas;
       if (obj_out) obj_out[k] = R.co.obj;
       if (rho_out) rho_out[k] = R.co.rho;
@@ -448,6 +456,8 @@ thetis_status thetis_solve_al(thetis_handle* h, const thetis_params* p, int32_t 
     float ms = 0.f;
     TH_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     R.ep = total;
+    R.sweep_ms = sweep_total;
+    R.sweep_launches = launches_total;
     fill_info(P, R, ms, info);
     if (info) info->updates = (int64_t)total * P.free_coords;
   });

@@ -232,6 +232,7 @@ struct SolveArgs {
   int32_t refresh_every;
   int32_t step_rule;
   int32_t mode;
+  int32_t async_ctas = 0;  // async mode: CTA cap (0: one per tile)
 };
 struct CheckOut {
   double rho, obj, infeas, fbeta;

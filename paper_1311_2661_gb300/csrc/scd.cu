@@ -95,6 +95,7 @@ struct ColorLaunch {
   SegLaunch seg[UC_COUNT + 1];
   int nseg;
   int color;
+  int64_t ntiles;  // tiles of the launch (per-colour engine)
 };
 
 __device__ __forceinline__ float coef(const StepView& V, int64_t p, uint32_t e) {
@@ -524,12 +525,13 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
 __global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunch CL) {
   __shared__ float red_smem[33];
   extern __shared__ __align__(16) unsigned char dyn[];
-  int64_t t = blockIdx.x;
   if (V.act_tiles) {  // batches: only the active tiles of the colour (grid sized for all)
-    if (t >= V.act_n[CL.color]) return;
-    t = V.act_tiles[V.act_off[CL.color] + t];
+    if ((int64_t)blockIdx.x >= V.act_n[CL.color]) return;
+    process_tile(V, CL.seg, CL.nseg, V.act_tiles[V.act_off[CL.color] + blockIdx.x], red_smem, dyn);
+    return;
   }
-  process_tile(V, CL.seg, CL.nseg, t, red_smem, dyn);
+  // one tile per CTA, or CTAs taking tiles in turn when the grid is capped (async concurrency)
+  for (int64_t t = blockIdx.x; t < CL.ntiles; t += gridDim.x) process_tile(V, CL.seg, CL.nseg, t, red_smem, dyn);
 }
 
 // Grid-wide barrier of a cooperative launch, split into arrive and wait so a CTA
@@ -741,7 +743,10 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
   auto launch = [&](ColorLaunch& CL, int64_t total) {
     if (total <= 0) return;
     TH_CHECK(total < (int64_t(1) << 31), THETIS_E_INVALID, "colour class too large for one launch");
-    k_color_step<<<(unsigned)total, STEP_T, STEP_SMEM, s>>>(V, CL);
+    CL.ntiles = total;
+    const int64_t grid = (a.mode == THETIS_MODE_ASYNC && a.async_ctas > 0) ? std::min<int64_t>(total, a.async_ctas)
+                                                                         : total;
+    k_color_step<<<(unsigned)grid, STEP_T, STEP_SMEM, s>>>(V, CL);
     TH_LAUNCHED();
   };
   if (a.mode == THETIS_MODE_ASYNC) {

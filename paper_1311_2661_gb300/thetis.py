@@ -48,7 +48,7 @@ class Params(C.Structure):
     _fields_ = [("beta", C.c_double), ("epochs", C.c_int32), ("tol", C.c_double),
                 ("refresh_every", C.c_int32), ("step_rule", C.c_int32), ("mode", C.c_int32),
                 ("ubar", C.c_void_p), ("xbar", C.c_void_p), ("x0", C.c_void_p), ("mem", C.c_int32),
-                ("engine", C.c_int32)]
+                ("engine", C.c_int32), ("async_ctas", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -274,7 +274,7 @@ def thetis_create(m, n, csc_ptr, csc_row, b, c, lo, hi, row_kind, csc_val=None, 
 
 
 def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step_rule=0, mode=MODE_COLORED,
-                 ubar=None, xbar=None, x0=None, engine=0):
+                 ubar=None, xbar=None, x0=None, engine=0, async_ctas=0):
     A = _Args()
     p = Params()
     p.beta, p.epochs, p.tol = float(beta), int(epochs), float(tol)
@@ -282,6 +282,7 @@ def thetis_solve(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, step
     p.ubar, p.xbar, p.x0 = A(ubar, np.float32), A(xbar, np.float32), A(x0, np.float32)
     p.mem = A.memspace
     p.engine = int(engine)
+    p.async_ctas = int(async_ctas)
     info = SolveInfo()
     st = _check(_lib.thetis_solve(h.ptr, C.byref(p), C.byref(info)), allow=(THETIS_OK, THETIS_NOT_CONVERGED))
     return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
@@ -307,7 +308,8 @@ def thetis_solve_al(h: Handle, beta=1e2, epochs=50, tol=0.0, refresh_every=10, o
                 allow=(THETIS_OK, THETIS_NOT_CONVERGED))
     return dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
                 rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
-                solve_ms=info.solve_ms, epoch_ms=info.epoch_ms), hist
+                solve_ms=info.solve_ms, epoch_ms=info.epoch_ms,
+                launches_per_epoch=info.launches_per_epoch), hist
 
 
 def thetis_get_duals(h: Handle, out=None):

@@ -289,6 +289,19 @@ def test_async_mode_converges_to_oracle_solution():
     assert np.max(np.abs(gpu_full_x(h) - x_o)) <= 1e-2
 
 
+@pytest.mark.parametrize("ctas", [1, 4, 64])
+def test_async_mode_capped_concurrency_converges(ctas):
+    """The asynchronous scheme with at most `ctas` CTAs stepping at once reaches
+    the same solution (objective within 1e-5, rho <= tol)."""
+    g = vc_graph(1000, 3000, 12)
+    h, lp = _pair("vc", g)
+    info = h.solve(beta=20.0, epochs=4000, tol=1e-5, refresh_every=20, mode=gpu().MODE_ASYNC, async_ctas=ctas)
+    x_o, info_o = lp.solve(beta=20.0, epochs=100000, tol=1e-9, refresh_every=50, color=lp.color(0)[0])
+    assert info["rho"] <= 1e-5
+    assert rel(info["fbeta"], info_o["fbeta"]) <= 1e-5
+    assert np.max(np.abs(gpu_full_x(h) - x_o)) <= 1e-2
+
+
 def test_autotune_keeps_the_iterate_and_parity():
     """Tuning times trial sweeps on the real problem but restores the iterate;
     a solve after tuning still matches the oracle (the lane group only changes
