@@ -19,6 +19,10 @@ Parity status of each function (the pins are in tests/test_oracle_*.py):
                                    infeasibility far below the fixed-beta penalty)
   round_vc / round_is / round_mc   pinned (validity, 2x bound, exact selection
                                    probabilities, CKR expectation for k=2)
+  set_cover, round_sc(_rand)       pinned (equal to the VC rounding when every
+                                   element lies in two sets, f-approximation
+                                   against LP* / brute-force IP*, pick
+                                   frequencies, validity)
   rng                              pinned (published splitmix64 outputs)
 """
 from __future__ import annotations
@@ -95,6 +99,11 @@ def _load():
             "or_round_mc": (C.c_int, [P, P, u64, i32, P, P, P]),
             "or_mc_cut_cost": (dbl, [P, P]),
             "or_valid": (C.c_int, [P, P]),
+            "or_sc_frequency": (C.c_int32, [P]),
+            "or_round_sc": (C.c_int, [P, P, P, P, P, P, C.c_double]),
+            "or_round_sc_rand_rep": (None, [P, P, u64, i32, P]),
+            "or_round_sc_rand": (C.c_int, [P, P, u64, i32, P, P, P, P]),
+            "or_valid_sc": (C.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -326,6 +335,46 @@ class OracleLP:
     def mc_cut_cost(self, labels):
         labels = np.ascontiguousarray(labels, np.uint8)
         return float(_load().or_mc_cut_cost(self._h, _p(labels)))
+
+    # -- set cover (App. B.1); x = the set columns, original order ------------
+    @classmethod
+    def set_cover(cls, n_elements, set_ptr, set_elems, cost):
+        """Covering LP of a set system: min c'x, sum_{s holds a} x_s >= 1 for
+        every element a, 0 <= x <= 1 (rows = elements, columns = sets)."""
+        set_ptr = np.ascontiguousarray(set_ptr, np.int64)
+        k = set_ptr.shape[0] - 1
+        lp = cls.general(int(n_elements), set_ptr, set_elems, None, np.ones(n_elements), np.asarray(cost, np.float64),
+                         np.zeros(k), np.ones(k), np.full(n_elements, ROW_GE, np.int32))
+        lp.n_sets = k
+        return lp
+
+    def sc_frequency(self):
+        return int(_load().or_sc_frequency(self._h))
+
+    def round_sc(self, x, band=1e-4):
+        x = np.ascontiguousarray(x, np.float64)
+        lab = np.zeros(self.n_sets, np.uint8)
+        eps = C.c_double(); obj = C.c_double(); near = C.c_int64()
+        st = _load().or_round_sc(self._h, _p(x), _p(lab), C.byref(eps), C.byref(obj), C.byref(near), band)
+        return dict(status=st, labels=lab, eps=eps.value, obj=obj.value, near=near.value)
+
+    def round_sc_rand_rep(self, xt, seed, rep):
+        xt = np.ascontiguousarray(xt, np.float64)
+        take = np.zeros(self.n_sets, np.uint8)
+        _load().or_round_sc_rand_rep(self._h, _p(xt), int(seed), int(rep), _p(take))
+        return take
+
+    def round_sc_rand(self, x, seed, reps=10):
+        x = np.ascontiguousarray(x, np.float64)
+        lab = np.zeros(self.n_sets, np.uint8)
+        eps = C.c_double(); obj = C.c_double(); br = C.c_int32()
+        st = _load().or_round_sc_rand(self._h, _p(x), int(seed), int(reps), _p(lab), C.byref(eps), C.byref(obj),
+                                      C.byref(br))
+        return dict(status=st, labels=lab, eps=eps.value, obj=obj.value, best_rep=br.value)
+
+    def valid_sc(self, labels):
+        labels = np.ascontiguousarray(labels, np.uint8)
+        return bool(_load().or_valid_sc(self._h, _p(labels)))
 
     def valid(self, labels):
         labels = np.ascontiguousarray(labels, np.uint8)

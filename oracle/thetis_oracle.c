@@ -81,6 +81,7 @@ double or_rng_uniform(uint64_t seed, uint64_t rep, uint64_t stream, uint64_t idx
 #define STREAM_IS_PICK 1
 #define STREAM_CKR_RADIUS 2
 #define STREAM_CKR_PERM 3
+#define STREAM_SC_PICK 4
 
 /* ------------------------------------------------------------------------ */
 /* The standard-form LP                                                     */
@@ -878,6 +879,127 @@ int or_round_mc(const orlp *P, const double *x, uint64_t seed, int32_t reps, uin
 }
 
 /* Exact validity of an integral solution: 1 if valid, 0 if not. */
+/*
+ * Set cover (App. B.1) on a covering LP made by or_create: rows = elements,
+ * structural columns = sets (coefficient 1 where the set holds the element),
+ * every row sum_{s in a} x_s - z_a = 1 with slack z_a >= 0, costs c.
+ * Covering repair (App. C.2 lemma; q(P) = 1 for 0/1 data):
+ * eps = max_a (1 - sum_{s in a} x_s)_+ , x~ = min(1, x / (1 - eps)).
+ * Returns eps (>= 1: repair impossible).
+ */
+static double sc_repair(const orlp *P, const double *x, double *xt) {
+  double eps = 0.0;
+  for (int64_t a = 0; a < P->M; ++a) {
+    double cov = 0.0;
+    for (int64_t q = P->rp[a]; q < P->rp[a + 1]; ++q)
+      if (P->ci[q] < P->Ns) cov += P->rv[q] * x[P->ci[q]];
+    eps = fmax(eps, 1.0 - cov);
+  }
+  for (int64_t j = 0; j < P->Ns; ++j) xt[j] = fmin(1.0, fmax(0.0, x[j] / (1.0 - eps)));
+  return eps;
+}
+
+/* f = the largest number of sets holding one element */
+int32_t or_sc_frequency(const orlp *P) {
+  int32_t f = 0;
+  for (int64_t a = 0; a < P->M; ++a) {
+    int32_t k = 0;
+    for (int64_t q = P->rp[a]; q < P->rp[a + 1]; ++q) k += P->ci[q] < P->Ns;
+    if (k > f) f = k;
+  }
+  return f;
+}
+
+/* f-threshold rounding (Hochbaum): take every set with x~_s >= 1/f (FP64;
+ * |x~_s - 1/f| < band counted as near-threshold). Status 6 if eps >= 1. */
+int or_round_sc(const orlp *P, const double *x, uint8_t *label, double *eps_out, double *obj, int64_t *near,
+                double band) {
+  double *xt = (double *)xcalloc((size_t)P->Ns, sizeof(double));
+  double eps = sc_repair(P, x, xt);
+  if (eps_out) *eps_out = eps;
+  if (eps >= 1.0) {
+    free(xt);
+    return 6;
+  }
+  const double thr = 1.0 / (double)or_sc_frequency(P);
+  double cost = 0.0;
+  int64_t nr = 0;
+  for (int64_t j = 0; j < P->Ns; ++j) {
+    label[j] = xt[j] >= thr;
+    if (fabs(xt[j] - thr) < band) ++nr;
+    if (label[j]) cost += P->c[j];
+  }
+  if (obj) *obj = cost;
+  if (near) *near = nr;
+  free(xt);
+  return 0;
+}
+
+/* One repetition of randomized rounding (Srinivasan): set s is taken with
+ * probability x~_s; then every element the picks leave uncovered adds its
+ * set of largest x~ (ties: lowest set id) -- marks computed on the picks, then
+ * added together -- so the result is always a cover. */
+void or_round_sc_rand_rep(const orlp *P, const double *xt, uint64_t seed, int32_t rep, uint8_t *take) {
+  uint8_t *pick = (uint8_t *)xcalloc((size_t)P->Ns, 1);
+  for (int64_t j = 0; j < P->Ns; ++j)
+    pick[j] = or_rng_uniform(seed, (uint64_t)rep, STREAM_SC_PICK, (uint64_t)j) < xt[j];
+  memcpy(take, pick, (size_t)P->Ns);
+  for (int64_t a = 0; a < P->M; ++a) {
+    int covered = 0;
+    int64_t best = -1;
+    for (int64_t q = P->rp[a]; q < P->rp[a + 1]; ++q) {
+      const int64_t j = P->ci[q];
+      if (j >= P->Ns) continue;
+      if (pick[j]) covered = 1;
+      if (best < 0 || xt[j] > xt[best] || (xt[j] == xt[best] && j < best)) best = j;
+    }
+    if (!covered && best >= 0) take[best] = 1;
+  }
+  free(pick);
+}
+
+/* Best of `reps` repetitions by cost, ties to the lowest rep. */
+int or_round_sc_rand(const orlp *P, const double *x, uint64_t seed, int32_t reps, uint8_t *label, double *eps_out,
+                     double *obj, int32_t *best_rep) {
+  double *xt = (double *)xcalloc((size_t)P->Ns, sizeof(double));
+  double eps = sc_repair(P, x, xt);
+  if (eps_out) *eps_out = eps;
+  if (eps >= 1.0) {
+    free(xt);
+    return 6;
+  }
+  uint8_t *take = (uint8_t *)xcalloc((size_t)P->Ns, 1);
+  double best = INFINITY;
+  int32_t br = 0;
+  for (int32_t rep = 0; rep < reps; ++rep) {
+    or_round_sc_rand_rep(P, xt, seed, rep, take);
+    double cost = 0.0;
+    for (int64_t j = 0; j < P->Ns; ++j)
+      if (take[j]) cost += P->c[j];
+    if (cost < best) {
+      best = cost;
+      br = rep;
+      memcpy(label, take, (size_t)P->Ns);
+    }
+  }
+  if (obj) *obj = best;
+  if (best_rep) *best_rep = br;
+  free(take);
+  free(xt);
+  return 0;
+}
+
+/* every element covered by a taken set */
+int or_valid_sc(const orlp *P, const uint8_t *label) {
+  for (int64_t a = 0; a < P->M; ++a) {
+    int covered = 0;
+    for (int64_t q = P->rp[a]; q < P->rp[a + 1]; ++q)
+      if (P->ci[q] < P->Ns && label[P->ci[q]]) covered = 1;
+    if (!covered) return 0;
+  }
+  return 1;
+}
+
 int or_valid(const orlp *P, const uint8_t *label) {
   if (P->kind == KIND_VC) {
     for (int64_t e = 0; e < P->m; ++e)
