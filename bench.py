@@ -41,6 +41,10 @@ WORKLOADS = {
                               tol=1e-3, reps=1),
     "mc-grid1024-k8": dict(kind="mc", graph="grid", width=1024, height=1024, k=8, seed=3, beta=100.0, epochs=50,
                            refresh=10, tol=1e-3, reps=10),
+    # set cover (App. B.1): 2^20 elements, each in U[2, 8] of 2^18 random sets, costs U[1, 10];
+    # randomized rounding (best of 10, completed to a cover)
+    "sc-n2^20-k2^18": dict(kind="sc", graph="setsys", n_elements=1 << 20, n_sets=1 << 18, f_lo=2, f_hi=8, seed=6,
+                           beta=100.0, epochs=50, refresh=10, tol=1e-3, reps=10, round=4),
     # the IS config under the augmented-Lagrangian outer loop: 5 solves of 50 epochs, multiplier step between
     "al-is-chunglu-n2^20-m1.6e7": dict(kind="is", graph="chung_lu", n=1 << 20, m=16_000_000, gamma=2.1, seed=2,
                                        beta=100.0, epochs=50, refresh=10, tol=0.0, reps=10, al_outer=5),
@@ -78,6 +82,14 @@ def make_graph(wl, rank=0):
     from paper_1311_2661_gb300 import synth
 
     seed = wl["seed"] + 1000 * rank
+    if wl["graph"] == "setsys":
+        # set cover: the set lists stand in for the edge arrays (eu = set_ptr,
+        # ev = set_elems, w = costs; n = sets, m = non-zeros)
+        from types import SimpleNamespace
+
+        ss = synth.set_cover_instance(wl["n_elements"], wl["n_sets"], wl["f_lo"], wl["f_hi"], seed)
+        return SimpleNamespace(n=ss.n_sets, m=int(ss.ptr[-1]), eu=ss.ptr, ev=ss.elems, w=ss.cost,
+                               n_elements=ss.n_elements, terminals=None)
     if wl["graph"] == "chung_lu":
         g = synth.chung_lu(wl["n"], wl["m"], wl["gamma"], seed)
     elif wl["graph"] == "er":
@@ -99,6 +111,8 @@ def algorithmic_bytes_per_epoch(wl, g):
     n, m = g.n, g.m
     if wl["kind"] in ("vc", "is"):
         return 20 * n + 12 * (2 * m) + 16 * m
+    if wl["kind"] == "sc":  # n sets, m non-zeros, one slack per element
+        return 20 * n + 12 * m + 16 * g.n_elements
     k = wl["k"]
     nfree_blocks = n - k
     deg = np.bincount(np.concatenate([g.eu, g.ev]), minlength=n)
@@ -237,6 +251,8 @@ def run_gpu(args, wl, ws, rank, local):
     torch.cuda.synchronize()
 
     def build(eu, ev, w, term):
+        if kind == "sc":
+            return T.thetis_build_sc(g.n_elements, eu, ev, w, seed=0, stream=stream)
         if kind == "vc":
             return T.thetis_build_vc(g.n, eu, ev, w, seed=0, stream=stream)
         if kind == "is":
@@ -257,7 +273,7 @@ def run_gpu(args, wl, ws, rank, local):
             info["al_obj"] = hist["obj"].tolist()
         else:
             info = h.solve(beta=wl["beta"], epochs=epochs, tol=tol, refresh_every=wl["refresh"])
-        lab, rinfo = h.round(seed=11, reps=wl["reps"], out=out)
+        lab, rinfo = h.round(kind=wl.get("round"), seed=11, reps=wl["reps"], out=out)
         assert rinfo["valid"], "rounded solution failed the exact validity check"
         h.close()
         return info, rinfo
@@ -771,7 +787,10 @@ def _oracle_setup(wl, g):
     import oracle
 
     oracle.build()
-    lp = oracle.build_problem(wl["kind"], g)
+    if wl["kind"] == "sc":
+        lp = oracle.OracleLP.set_cover(g.n_elements, g.eu, g.ev, g.w.astype(np.float64))
+    else:
+        lp = oracle.build_problem(wl["kind"], g)
     col, nc = lp.color(0)
     return lp, col
 

@@ -50,7 +50,13 @@ typedef enum {
 
 typedef enum { THETIS_MEM_HOST = 0, THETIS_MEM_DEVICE = 1 } thetis_mem;
 typedef enum { THETIS_ROW_EQ = 0, THETIS_ROW_GE = 1, THETIS_ROW_LE = 2 } thetis_row_kind;
-typedef enum { THETIS_ROUND_VC = 0, THETIS_ROUND_IS = 1, THETIS_ROUND_MC = 2 } thetis_round_kind;
+typedef enum {
+  THETIS_ROUND_VC = 0,      /* vertex cover threshold (Sec. 2) */
+  THETIS_ROUND_IS = 1,      /* independent set, Bansal et al. with alterations (App. B.2) */
+  THETIS_ROUND_MC = 2,      /* multiway cut, CKR (App. B.3) */
+  THETIS_ROUND_SC = 3,      /* set cover, f-threshold (App. B.1) */
+  THETIS_ROUND_SC_RAND = 4  /* set cover, randomized rounding + fix-up (App. B.1) */
+} thetis_round_kind;
 typedef enum { THETIS_MODE_COLORED = 0, THETIS_MODE_ASYNC = 1 } thetis_mode;
 
 typedef struct thetis_handle thetis_handle;
@@ -194,6 +200,24 @@ thetis_status thetis_build_is(int64_t n, int64_t m, const int32_t* eu, const int
 thetis_status thetis_build_mc(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
                               const float* ce, int32_t k, const int32_t* terminals, int32_t mem,
                               uint64_t seed, void* stream, thetis_handle** out);
+
+/*
+ * thetis_build_sc -- set cover (App. B.1) as the covering LP
+ *   min sum_s c_s x_s  s.t.  sum_{s holds a} x_s - z_a = 1 (z_a >= 0) for every
+ *   element a,  0 <= x_s <= 1.
+ * Sets are the columns, elements the rows.  set_ptr[n_sets + 1] (int64,
+ * set_ptr[0] = 0, non-decreasing) and set_elems[set_ptr[n_sets]] (int32,
+ * element ids in [0, n_elements), strictly increasing inside a set) list the
+ * sets; cost[n_sets] > 0.  Every element must lie in some set (else the LP is
+ * infeasible: THETIS_E_INVALID).  Round with THETIS_ROUND_SC (take every set
+ * with x~_s >= 1/f, f = the largest number of sets holding one element) or
+ * THETIS_ROUND_SC_RAND (best of `reps` randomized roundings, each completed so
+ * that it covers); labels_out[n_sets] marks the chosen sets.  Both first apply
+ * the covering repair x~ = min(1, x / (1 - eps)), eps = max_a (1 - sum x)_+
+ * (App. C.2; THETIS_E_REPAIR if eps >= 1).  Arrays live in `mem`.
+ */
+thetis_status thetis_build_sc(int64_t n_elements, int64_t n_sets, const int64_t* set_ptr, const int32_t* set_elems,
+                              const float* cost, int32_t mem, uint64_t seed, void* stream, thetis_handle** out);
 
 /* Sizes of a built problem (any pointer may be NULL): rows m, structural
  * columns n, slack columns (one per GE/LE row), free coordinates (what one

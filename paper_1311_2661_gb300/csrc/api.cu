@@ -240,6 +240,54 @@ thetis_status thetis_build_mc(int64_t n, int64_t m, const int32_t* eu, const int
   return build_graph(KIND_MC, n, m, eu, ev, nullptr, ce, k, terminals, mem, seed, stream, out);
 }
 
+thetis_status thetis_build_sc(int64_t n_elements, int64_t n_sets, const int64_t* set_ptr, const int32_t* set_elems,
+                              const float* cost, int32_t mem, uint64_t seed, void* stream, thetis_handle** out) {
+  if (!out || !set_ptr || !cost) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  *out = nullptr;
+  thetis_handle* h = nullptr;
+  thetis_status st = guard(nullptr, [&] {
+    TH_CHECK(n_elements >= 1 && n_sets >= 1 && n_elements < (int64_t(1) << 31) && n_sets < (int64_t(1) << 31),
+             THETIS_E_INVALID, "need 1 <= n_elements, n_sets < 2^31");
+    h = new_handle(stream);
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    int64_t ends[2] = {0, 0};
+    TH_CUDA(cudaMemcpyAsync(&ends[0], set_ptr, sizeof(int64_t), cudaMemcpyDefault, s));
+    TH_CUDA(cudaMemcpyAsync(&ends[1], set_ptr + n_sets, sizeof(int64_t), cudaMemcpyDefault, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    const int64_t nnz = ends[1];
+    TH_CHECK(ends[0] == 0 && nnz >= 0 && nnz < (int64_t(1) << 31), THETIS_E_INVALID,
+             "set_ptr must start at 0 and hold < 2^31 entries");
+    TH_CHECK(nnz == 0 || set_elems, THETIS_E_INVALID, "null set_elems");
+    const int64_t* dptr = to_dev(set_ptr, n_sets + 1, mem, tmp, s);
+    const int32_t* delems = to_dev(set_elems, nnz, mem, tmp, s);
+    const float* dcost = to_dev(cost, n_sets, mem, tmp, s);
+    RawLP raw;
+    int64_t* eptr = nullptr;
+    int32_t* esets = nullptr;
+    int32_t f = 0;
+    build_sc_raw(n_elements, n_sets, nnz, dptr, delems, dcost, raw, eptr, esets, f, tmp, tmp, s);
+    h->P = build_problem(raw, KIND_SC, seed, s, tmp);
+    Problem& P = *h->P;
+    P.nv = n_sets;
+    P.ne = n_elements;
+    P.sc_f = f;
+    P.sc_eptr = keep_copy(P.mem, (const int64_t*)eptr, n_elements + 1, s);
+    P.sc_esets = keep_copy(P.mem, (const int32_t*)esets, nnz, s);
+    P.w = keep_copy(P.mem, dcost, n_sets, s);
+    finish_create(h);
+  });
+  if (st != THETIS_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return THETIS_OK;
+}
+
 thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* struct_cols, int64_t* slack_cols,
                                int64_t* free_coords, int64_t* nnz, int32_t* ncolors) {
   if (!h || !h->P) {

@@ -151,6 +151,107 @@ void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const 
   raw.slack_sign_uniform = (kind == KIND_VC) ? -1 : 1;
 }
 
+// Set cover: validate the set lists (elements in range and strictly
+// increasing inside a set, costs finite and > 0) and count every element's sets.
+__global__ void k_sc_check(const int64_t* ptr, const int32_t* elems, const float* cost, int64_t n_sets,
+                           int64_t n_elem, int64_t* ecount, int* err) {
+  GSTRIDE(j, n_sets) {
+    const int64_t q0 = ptr[j], q1 = ptr[j + 1];
+    if (q1 < q0) {
+      atomicExch(err, 1);
+      continue;
+    }
+    if (!(cost[j] > 0.f) || !isfinite(cost[j])) atomicExch(err, 2);
+    for (int64_t q = q0; q < q1; ++q) {
+      const int32_t a = elems[q];
+      if (a < 0 || a >= n_elem || (q > q0 && elems[q - 1] >= a)) {
+        atomicExch(err, 1);
+        break;
+      }
+      atomicAdd((unsigned long long*)&ecount[a], 1ull);
+    }
+  }
+}
+
+__global__ void k_sc_vectors(const float* cost, int64_t n_sets, int64_t n_elem, float* b, float* c, float* lo,
+                             float* hi, uint8_t* rk, const int64_t* ecount, int* err, int* fmax) {
+  GSTRIDE(i, n_sets > n_elem ? n_sets : n_elem) {
+    if (i < n_sets) {
+      c[i] = cost[i];
+      lo[i] = 0.f;
+      hi[i] = 1.f;
+    }
+    if (i < n_elem) {
+      b[i] = 1.f;
+      rk[i] = THETIS_ROW_GE;
+      if (ecount[i] == 0) atomicExch(err, 3);
+      atomicMax(fmax, (int)min(ecount[i], (int64_t)INT32_MAX));
+    }
+  }
+}
+
+// (element, set) pairs in set-major order, so a stable sort by element keeps
+// every element's sets in increasing id
+__global__ void k_sc_pairs(const int64_t* ptr, const int32_t* elems, int64_t n_sets, uint32_t* keys, uint32_t* vals) {
+  GSTRIDE(j, n_sets)
+  for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) {
+    keys[q] = (uint32_t)elems[q];
+    vals[q] = (uint32_t)j;
+  }
+}
+
+void build_sc_raw(int64_t n_elem, int64_t n_sets, int64_t nnz, const int64_t* d_ptr, const int32_t* d_elems,
+                  const float* d_cost, RawLP& raw, int64_t*& eptr, int32_t*& esets, int32_t& f, Arena& keep,
+                  Arena& tmp, cudaStream_t s) {
+  int* err = tmp.alloc<int>(2);
+  TH_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+  int64_t* ecount = tmp.alloc<int64_t>(n_elem + 1);
+  TH_CUDA(cudaMemsetAsync(ecount, 0, (n_elem + 1) * sizeof(int64_t), s));
+  k_sc_check<<<grid_for(n_sets, 256), 256, 0, s>>>(d_ptr, d_elems, d_cost, n_sets, n_elem, ecount, err);
+  TH_LAUNCHED();
+  int e1 = read_flag(err, s);
+  TH_CHECK(e1 != 1, THETIS_E_INVALID, "set lists must hold element ids in [0, n_elements), increasing inside a set");
+  TH_CHECK(e1 != 2, THETIS_E_INVALID, "set costs must be finite and > 0");
+  raw.M = n_elem;
+  raw.Ns = n_sets;
+  raw.nnz = nnz;
+  raw.colptr = const_cast<int64_t*>(d_ptr);
+  raw.rowidx = const_cast<int32_t*>(d_elems);
+  raw.val = nullptr;
+  raw.b = tmp.alloc<float>(n_elem);
+  raw.c = tmp.alloc<float>(n_sets);
+  raw.lo = tmp.alloc<float>(n_sets);
+  raw.hi = tmp.alloc<float>(n_sets);
+  raw.row_kind = tmp.alloc<uint8_t>(n_elem);
+  k_sc_vectors<<<grid_for(std::max(n_sets, n_elem), 256), 256, 0, s>>>(d_cost, n_sets, n_elem, raw.b, raw.c, raw.lo,
+                                                                       raw.hi, raw.row_kind, ecount, err, err + 1);
+  TH_LAUNCHED();
+  int hf[2];
+  TH_CUDA(cudaMemcpyAsync(hf, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  TH_CHECK(hf[0] != 3, THETIS_E_INVALID, "an element lies in no set: the covering LP is infeasible");
+  f = hf[1];
+  raw.block_k = 1;
+  raw.n_blocks = 0;
+  raw.bounds_uniform = true;
+  raw.lo_u = 0.f;
+  raw.hi_u = 1.f;
+  raw.slack_sign_uniform = -1;
+  // element -> sets lists (original ids) for the repair and the rounding
+  uint32_t* keys = tmp.alloc<uint32_t>(nnz + 1);
+  uint32_t* vals = tmp.alloc<uint32_t>(nnz + 1);
+  k_sc_pairs<<<grid_for(n_sets, 256), 256, 0, s>>>(d_ptr, d_elems, n_sets, keys, vals);
+  TH_LAUNCHED();
+  radix_sort_pairs(keys, vals, nnz, bits_for(n_elem + 1), tmp, s);
+  eptr = keep.alloc<int64_t>(n_elem + 1);
+  exclusive_scan_i64(ecount, eptr, n_elem, tmp, s);
+  esets = keep.alloc<int32_t>(nnz + 1);
+  if (nnz > 0) {
+    k_u32_to_i32<<<grid_for(nnz, 256), 256, 0, s>>>(vals, esets, nnz);
+    TH_LAUNCHED();
+  }
+}
+
 // Multiway cut: x_{v,i} at v*k+i (2 deg(v) entries), z_{e,i} at n*k+e*k+i.
 __global__ void k_mc_counts(const int64_t* iptr, int64_t n, int64_t m, int32_t k, int64_t* cnt) {
   GSTRIDE(j, n * k + m * k) {

@@ -71,7 +71,7 @@ __host__ __device__ __forceinline__ double rng_unif(uint64_t seed, uint64_t rep,
                                                    uint64_t idx) {
   return (double)(rng_u64(seed, rep, stream, idx) >> 11) * (1.0 / 9007199254740992.0);
 }
-enum : uint64_t { STREAM_IS_PICK = 1, STREAM_CKR_RADIUS = 2, STREAM_CKR_PERM = 3 };
+enum : uint64_t { STREAM_IS_PICK = 1, STREAM_CKR_RADIUS = 2, STREAM_CKR_PERM = 3, STREAM_SC_PICK = 4 };
 
 // Row index encoding in the internal CSC / CSR of +-1 matrices: bit 31 set means
 // the coefficient is -1.

@@ -7,7 +7,7 @@
 
 namespace thetis {
 
-enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BATCH = 4 };
+enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BATCH = 4, KIND_SC = 5 };
 
 // Classes of coordinate units inside one colour.  Units of a colour are stored
 // class by class, so that every class is a contiguous range of units and of
@@ -106,6 +106,12 @@ struct Problem {
   int64_t* tile_start = nullptr;  // per colour: first flat tile (C + 1)
   int64_t tiles_total = 0;
   int act_g = -1;
+
+  // set cover meta: the sets holding each element, in increasing set id
+  // (elements = rows, sets = columns, original order), and f = max frequency
+  int64_t* sc_eptr = nullptr;
+  int32_t* sc_esets = nullptr;
+  int32_t sc_f = 0;
 
   // graph meta (builders)
   int64_t nv = 0, ne = 0;
@@ -206,6 +212,12 @@ void build_vc_is_raw(int kind, int64_t n, int64_t m, const int32_t* d_eu, const 
 void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev,
                   const float* d_ce, int32_t k, const int32_t* d_term, RawLP& raw, Arena& tmp,
                   cudaStream_t s);
+
+// set cover (App. B.1): covering LP of a set system (sets = columns, elements
+// = rows, sum_{s holds a} x_s - z_a = 1, 0 <= x <= 1), plus the element lists
+void build_sc_raw(int64_t n_elem, int64_t n_sets, int64_t nnz, const int64_t* d_ptr, const int32_t* d_elems,
+                  const float* d_cost, RawLP& raw, int64_t*& eptr, int32_t*& esets, int32_t& f, Arena& keep,
+                  Arena& tmp, cudaStream_t s);
 
 // batch.cu
 void build_batch_raw(int64_t count, const uint8_t* d_kind, const int64_t* d_noff, const int64_t* d_eoff, int64_t Nv,

@@ -2,7 +2,9 @@
 // vertex cover threshold (Sec. 2, Lemma lem:infeasible:rounded:vc), Bansal et
 // al. packing rounding with alterations for independent set (App. B.2,
 // Algorithm 2, theta = 1/k, tighter alpha of App. C.3), CKR region growing for
-// multiway cut (App. B.3), best of R repetitions (Sec. 4.2), exact validity.
+// multiway cut (App. B.3), set cover by f-threshold or randomized rounding
+// (App. B.1) after the covering repair, best of R repetitions (Sec. 4.2),
+// exact validity.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -117,6 +119,103 @@ __global__ void k_rep_final(const double* part, int nb, int reps, double* out) {
   out[r] = a;
 }
 
+// Set cover (App. B.1).  eps = max_a (1 - sum_{s holds a} x_s)_+ with the sum
+// over the element's sets in increasing id (FP64, the order of the plain
+// definition), the covering repair of App. C.2 (q(P) = 1).
+__global__ void k_sc_eps(const float* x, const int64_t* eptr, const int32_t* esets, int64_t n_elem,
+                         unsigned long long* out) {
+  double mx = 0.0;
+  GSTRIDE(a, n_elem) {
+    double cov = 0.0;
+    for (int64_t q = eptr[a]; q < eptr[a + 1]; ++q) cov += (double)x[esets[q]];
+    mx = fmax(mx, 1.0 - cov);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+__device__ __forceinline__ double sc_xt(const float* x, int64_t j, double eps) {
+  return fmin(1.0, fmax(0.0, (double)x[j] / (1.0 - eps)));
+}
+
+// f-threshold: take s iff x~_s >= 1/f; near-threshold count; cost partials
+__global__ void k_sc_threshold(const float* x, const float* c, int64_t n_sets, double thr,
+                               const unsigned long long* eps_bits, uint8_t* lab, double* part,
+                               unsigned long long* near) {
+  const double eps = __longlong_as_double((long long)*eps_bits);
+  double sum = 0.0;
+  unsigned long long nr = 0;
+  GSTRIDE(j, n_sets) {
+    const double xt = sc_xt(x, j, eps);
+    const uint8_t l = xt >= thr;
+    lab[j] = l;
+    if (fabs(xt - thr) < NEAR_BAND) ++nr;
+    if (l) sum += (double)c[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  }
+  __shared__ double sm[8];
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = sum;
+    if (nr) atomicAdd(near, nr);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
+    part[blockIdx.x] = a;
+  }
+}
+
+// randomized rounding, all repetitions: pick[r][s] = U(seed, r, 4, s) < x~_s
+__global__ void k_sc_pick(const float* x, int64_t n_sets, int reps, uint64_t seed, const unsigned long long* eps_bits,
+                          uint8_t* pick) {
+  const double eps = __longlong_as_double((long long)*eps_bits);
+  GSTRIDE(t, n_sets * reps) {
+    const int64_t r = t / n_sets, j = t % n_sets;
+    pick[t] = rng_unif(seed, (uint64_t)r, STREAM_SC_PICK, (uint64_t)j) < sc_xt(x, j, eps);
+  }
+}
+
+// fix-up: an element the picks of repetition r leave uncovered adds its set of
+// largest x~ (ties: lowest id); marks read only the picks, so their order does
+// not matter
+__global__ void k_sc_fixup(const float* x, const int64_t* eptr, const int32_t* esets, int64_t n_elem, int64_t n_sets,
+                           int reps, const unsigned long long* eps_bits, const uint8_t* pick, uint8_t* take) {
+  const double eps = __longlong_as_double((long long)*eps_bits);
+  GSTRIDE(t, n_elem * reps) {
+    const int64_t r = t / n_elem, a = t % n_elem;
+    const uint8_t* pr = pick + r * n_sets;
+    bool covered = false;
+    int64_t best = -1;
+    double bx = 0.0;
+    for (int64_t q = eptr[a]; q < eptr[a + 1]; ++q) {
+      const int64_t j = esets[q];
+      if (pr[j]) {
+        covered = true;
+        break;
+      }
+      const double xt = sc_xt(x, j, eps);
+      if (best < 0 || xt > bx) {  // sets come in increasing id: ties keep the lowest
+        best = j;
+        bx = xt;
+      }
+    }
+    if (!covered && best >= 0) take[r * n_sets + best] = 1;
+  }
+}
+
+// every element covered by a taken set
+__global__ void k_sc_valid(const uint8_t* lab, const int64_t* eptr, const int32_t* esets, int64_t n_elem, int* bad) {
+  GSTRIDE(a, n_elem) {
+    bool covered = false;
+    for (int64_t q = eptr[a]; q < eptr[a + 1] && !covered; ++q) covered = lab[esets[q]] != 0;
+    if (!covered) atomicExch(bad, 1);
+  }
+}
+
 // CKR: label of every vertex in every repetition
 __global__ void k_ckr_label(const float* x, int64_t n, int k, int reps, const double* rad, const int32_t* sigma,
                             uint8_t* lab) {
@@ -182,12 +281,13 @@ __global__ void k_is_near(const float* x, int64_t n, int rep, uint64_t seed, con
 
 void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out) {
   cudaStream_t s = P.stream;
-  TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC, THETIS_E_INVALID,
-           "rounding needs a problem built by thetis_build_vc / _is / _mc");
+  TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC || P.kind == KIND_SC, THETIS_E_INVALID,
+           "rounding needs a problem built by thetis_build_vc / _is / _mc / _sc");
   TH_CHECK((kind == THETIS_ROUND_VC && P.kind == KIND_VC) || (kind == THETIS_ROUND_IS && P.kind == KIND_IS) ||
-               (kind == THETIS_ROUND_MC && P.kind == KIND_MC),
+               (kind == THETIS_ROUND_MC && P.kind == KIND_MC) ||
+               ((kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) && P.kind == KIND_SC),
            THETIS_E_INVALID, "rounding kind does not match the problem");
-  if (kind == THETIS_ROUND_VC) reps = 1;
+  if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_SC) reps = 1;
   TH_CHECK(reps >= 1 && reps <= MAX_REPS, THETIS_E_INVALID, "reps must be in [1, 64]");
   const int64_t n = P.nv, m = P.ne;
   Arena tmp(s);
@@ -202,7 +302,55 @@ void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_lab
   out.best_rep = 0;
   out.near = 0;
   out.status = THETIS_OK;
-  if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_IS) {
+  if (kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) {
+    const int64_t ns = P.Ns, ne_ = P.M;  // sets, elements
+    if (ne_ > 0) {
+      k_sc_eps<<<grid_for(ne_, 256, 152 * 8), 256, 0, s>>>(P.xorig, P.sc_eptr, P.sc_esets, ne_, dbits);
+      TH_LAUNCHED();
+    }
+    unsigned long long hb = 0;
+    TH_CUDA(cudaMemcpyAsync(&hb, dbits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    double eps;
+    memcpy(&eps, &hb, sizeof(double));
+    out.repair = eps;
+    if (eps >= 1.0) {
+      out.status = THETIS_E_REPAIR;
+      return;
+    }
+    if (kind == THETIS_ROUND_SC) {
+      k_sc_threshold<<<RB, 256, 0, s>>>(P.xorig, P.w, ns, 1.0 / (double)P.sc_f, dbits, d_labels, part, dbits + 1);
+      TH_LAUNCHED();
+      k_rep_final<<<1, 32, 0, s>>>(part, RB, 1, repv);
+      TH_LAUNCHED();
+    } else {
+      uint8_t* pick = tmp.alloc<uint8_t>(ns * reps);
+      uint8_t* take = tmp.alloc<uint8_t>(ns * reps);
+      k_sc_pick<<<grid_for(ns * reps, 256), 256, 0, s>>>(P.xorig, ns, reps, seed, dbits, pick);
+      TH_LAUNCHED();
+      TH_CUDA(cudaMemcpyAsync(take, pick, ns * reps, cudaMemcpyDeviceToDevice, s));
+      if (ne_ > 0) {
+        k_sc_fixup<<<grid_for(ne_ * reps, 256), 256, 0, s>>>(P.xorig, P.sc_eptr, P.sc_esets, ne_, ns, reps, dbits,
+                                                             pick, take);
+        TH_LAUNCHED();
+      }
+      k_rep_weight<<<dim3(RB, reps), 256, 0, s>>>(take, P.w, ns, part);
+      TH_LAUNCHED();
+      k_rep_final<<<1, MAX_REPS, 0, s>>>(part, RB, reps, repv);
+      TH_LAUNCHED();
+      TH_CUDA(cudaMemcpyAsync(hv.data(), repv, reps * sizeof(double), cudaMemcpyDeviceToHost, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+      int best = 0;
+      for (int r = 1; r < reps; ++r)
+        if (hv[r] < hv[best]) best = r;
+      out.best_rep = best;
+      TH_CUDA(cudaMemcpyAsync(d_labels, take + (int64_t)best * ns, ns, cudaMemcpyDeviceToDevice, s));
+    }
+    if (ne_ > 0) {
+      k_sc_valid<<<grid_for(ne_, 256), 256, 0, s>>>(d_labels, P.sc_eptr, P.sc_esets, ne_, bad);
+      TH_LAUNCHED();
+    }
+  } else if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_IS) {
     bool cover = kind == THETIS_ROUND_VC;
     if (m > 0) {
       k_edge_violation<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(P.xorig, P.eu, P.ev, m, cover ? 1 : 0, dbits);

@@ -241,3 +241,38 @@ def poisson_trace(rate: float, count: int, kinds, seed: int, mix=(0.4, 0.4, 0.2)
     pick = names[rng.choice(3, size=count, p=np.asarray(mix, np.float64) / np.sum(mix))]
     idx = np.array([by_kind[c][rng.integers(len(by_kind[c]))] for c in pick], np.int64)
     return t, idx
+
+
+class SetSystem:
+    """A set system for set cover: set j holds elems[ptr[j]:ptr[j+1]]
+    (increasing element ids); cost[j] integer-valued FP32."""
+
+    def __init__(self, n_elements, ptr, elems, cost):
+        self.n_elements = int(n_elements)
+        self.ptr = ptr
+        self.elems = elems
+        self.cost = cost
+
+    @property
+    def n_sets(self):
+        return int(self.ptr.shape[0]) - 1
+
+
+def set_cover_instance(n_elements: int, n_sets: int, f_lo: int, f_hi: int, seed: int) -> SetSystem:
+    """Every element is put in f ~ U[f_lo, f_hi] distinct random sets (draws
+    that repeat a set for the same element are dropped, so a few elements get
+    fewer); set costs integer U[1, 10]."""
+    rng = np.random.default_rng(seed)
+    f = rng.integers(f_lo, f_hi + 1, size=n_elements)
+    cand = rng.integers(0, n_sets, size=(n_elements, f_hi))
+    cand = np.sort(np.where(np.arange(f_hi)[None, :] < f[:, None], cand, n_sets), axis=1)
+    keep = cand < n_sets
+    keep[:, 1:] &= cand[:, 1:] != cand[:, :-1]
+    elem = np.repeat(np.arange(n_elements, dtype=np.int64), f_hi)[keep.ravel()]
+    sets = cand.ravel()[keep.ravel()].astype(np.int64)
+    order = np.lexsort((elem, sets))
+    sets, elem = sets[order], elem[order]
+    ptr = np.zeros(n_sets + 1, np.int64)
+    np.cumsum(np.bincount(sets, minlength=n_sets), out=ptr[1:])
+    cost = rng.integers(1, 11, size=n_sets).astype(np.float32)
+    return SetSystem(n_elements, ptr, elem.astype(np.int32), cost)

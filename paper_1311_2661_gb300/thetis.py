@@ -24,7 +24,7 @@ THETIS_OK, THETIS_E_INVALID, THETIS_E_NOMEM, THETIS_E_BUDGET, THETIS_E_CUDA = 0,
 THETIS_E_TIMEOUT, THETIS_E_REPAIR, THETIS_PENDING, THETIS_NOT_CONVERGED = 5, 6, 7, 8
 MEM_HOST, MEM_DEVICE = 0, 1
 ROW_EQ, ROW_GE, ROW_LE = 0, 1, 2
-ROUND_VC, ROUND_IS, ROUND_MC = 0, 1, 2
+ROUND_VC, ROUND_IS, ROUND_MC, ROUND_SC, ROUND_SC_RAND = 0, 1, 2, 3, 4
 MODE_COLORED, MODE_ASYNC = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_NOMEM", 3: "E_BUDGET", 4: "E_CUDA", 5: "E_TIMEOUT",
@@ -77,6 +77,7 @@ def _load():
         "thetis_build_vc": (st, [i64, i64, P, P, P, i32, u64, P, P]),
         "thetis_build_is": (st, [i64, i64, P, P, P, i32, u64, P, P]),
         "thetis_build_mc": (st, [i64, i64, P, P, P, i32, P, i32, u64, P, P]),
+        "thetis_build_sc": (st, [i64, i64, P, P, P, i32, u64, P, P]),
         "thetis_get_sizes": (st, [P, P, P, P, P, P, P]),
         "thetis_solve": (st, [P, P, P]),
         "thetis_round": (st, [P, i32, u64, i32, P, i32, P]),
@@ -207,7 +208,7 @@ class Handle:
 
     def round(self, kind=None, **kw):
         if kind is None:
-            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC}[self.kind]
+            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC, "sc": ROUND_SC}[self.kind]
         return thetis_round(self, kind, **kw)
 
     def get_x(self, out=None):
@@ -252,6 +253,19 @@ def thetis_build_is(n, eu, ev, w, seed=0, stream=None) -> Handle:
 
 def thetis_build_mc(n, eu, ev, ce, k, terminals, seed=0, stream=None) -> Handle:
     return _build(_lib.thetis_build_mc, "mc", int(n), eu, ev, ce, seed, stream, k=k, terminals=terminals)
+
+
+def thetis_build_sc(n_elements, set_ptr, set_elems, cost, seed=0, stream=None) -> Handle:
+    """Set cover (sets = columns, elements = rows); labels of a rounding mark sets."""
+    A = _Args()
+    pp = A(set_ptr, np.int64)
+    pe = A(set_elems, np.int32)
+    pc = A(cost, np.float32)
+    n_sets = int(set_ptr.shape[0]) - 1
+    out = C.c_void_p()
+    _check(_lib.thetis_build_sc(int(n_elements), n_sets, pp, pe, pc, A.memspace, seed, _stream_ptr(stream),
+                                C.byref(out)))
+    return Handle(out.value, n_vertices=n_sets, kind="sc")
 
 
 def thetis_create(m, n, csc_ptr, csc_row, b, c, lo, hi, row_kind, csc_val=None, block_k=1, block_first=None,
