@@ -19,6 +19,9 @@ Parity status of each function (the pins are in tests/test_oracle_*.py):
                                    infeasibility far below the fixed-beta penalty)
   round_vc / round_is / round_mc   pinned (validity, 2x bound, exact selection
                                    probabilities, CKR expectation for k=2)
+  map_lp, round_map                pinned (LP tight = Viterbi on chains,
+                                   brute force on one edge / small cycles,
+                                   relaxation bound, AL + rounding = MAP)
   set_cover, round_sc(_rand)       pinned (equal to the VC rounding when every
                                    element lies in two sets, f-approximation
                                    against LP* / brute-force IP*, pick
@@ -375,6 +378,55 @@ class OracleLP:
     def valid_sc(self, labels):
         labels = np.ascontiguousarray(labels, np.uint8)
         return bool(_load().or_valid_sc(self._h, _p(labels)))
+
+    # -- pairwise MAP (Sec. 4.1, the local-polytope LP with node rounding) ---
+    @classmethod
+    def map_lp(cls, n, k, eu, ev, theta_node, theta_edge):
+        """Local-polytope LP of pairwise MAP, as a minimisation: node marginals
+        mu_i(a) (column i*k + a, one simplex block per variable) and edge
+        marginals mu_e(a, b) (column n*k + e*k*k + a*k + b, in [0, 1]); for
+        every edge e = (u, v) and label a the rows
+          sum_b mu_e(a, b) - mu_u(a) = 0     (row 2*e*k + a)
+          sum_a mu_e(a, b) - mu_v(b) = 0     (row 2*e*k + k + b);
+        costs -theta (the score is maximised)."""
+        eu = np.asarray(eu, np.int64); ev = np.asarray(ev, np.int64)
+        E = eu.shape[0]
+        th_n = np.asarray(theta_node, np.float64).reshape(n, k)
+        th_e = np.asarray(theta_edge, np.float64).reshape(E, k, k)
+        Ns, M = n * k + E * k * k, 2 * E * k
+        cols = [[] for _ in range(Ns)]
+        for e in range(E):
+            u, v = eu[e], ev[e]
+            for a in range(k):
+                cols[u * k + a].append((2 * e * k + a, -1.0))
+                cols[v * k + a].append((2 * e * k + k + a, -1.0))
+                for b in range(k):
+                    j = n * k + e * k * k + a * k + b
+                    cols[j].append((2 * e * k + a, 1.0))
+                    cols[j].append((2 * e * k + k + b, 1.0))
+        colptr = np.zeros(Ns + 1, np.int64)
+        colptr[1:] = np.cumsum([len(c) for c in cols])
+        rowidx = np.array([r for c in cols for r, _ in c], np.int32)
+        val = np.array([v for c in cols for _, v in c], np.float64)
+        c = np.concatenate([-th_n.ravel(), -th_e.ravel()])
+        lp = cls.general(M, colptr, rowidx, val, np.zeros(M), c, np.zeros(Ns), np.ones(Ns),
+                         np.zeros(M, np.int32), block_k=k, block_first=np.arange(n, dtype=np.int64) * k)
+        lp.map_meta = (n, k, eu, ev, th_n, th_e)
+        return lp
+
+    def round_map(self, x):
+        """Node rounding: every variable takes the label of its largest node
+        marginal (ties: lowest label).  Returns labels and the LP objective of
+        the integral point (minus the score)."""
+        n, k, eu, ev, th_n, th_e = self.map_meta
+        mu = np.asarray(x[: n * k], np.float64).reshape(n, k)
+        lab = np.argmax(mu, axis=1).astype(np.uint8)
+        return dict(labels=lab, obj=self.map_energy(lab))
+
+    def map_energy(self, lab):
+        n, k, eu, ev, th_n, th_e = self.map_meta
+        lab = np.asarray(lab, np.int64)
+        return -(th_n[np.arange(n), lab].sum() + th_e[np.arange(len(eu)), lab[eu], lab[ev]].sum())
 
     def valid(self, labels):
         labels = np.ascontiguousarray(labels, np.uint8)
