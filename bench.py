@@ -45,6 +45,10 @@ WORKLOADS = {
     # randomized rounding (best of 10, completed to a cover)
     "sc-n2^20-k2^18": dict(kind="sc", graph="setsys", n_elements=1 << 20, n_sets=1 << 18, f_lo=2, f_hi=8, seed=6,
                            beta=100.0, epochs=50, refresh=10, tol=1e-3, reps=10, round=4),
+    # pairwise MAP (Sec. 4.1) on a skip-chain-CRF-shaped factor graph the size of the paper's text-chunking
+    # LP: 47,000 variables with 23 labels, 24-token sentences, 5 % skip factors (26.2 M columns, 52.3 M non-zeros)
+    "map-skipchain-n47k-k23": dict(kind="map", graph="skipchain", n=47_000, k=23, sent_len=24, skip_frac=0.05,
+                                   seed=7, beta=100.0, epochs=50, refresh=10, tol=1e-3, reps=1, cpu_sample_n=4700),
     # the IS config under the augmented-Lagrangian outer loop: 5 solves of 50 epochs, multiplier step between
     "al-is-chunglu-n2^20-m1.6e7": dict(kind="is", graph="chung_lu", n=1 << 20, m=16_000_000, gamma=2.1, seed=2,
                                        beta=100.0, epochs=50, refresh=10, tol=0.0, reps=10, al_outer=5),
@@ -90,6 +94,13 @@ def make_graph(wl, rank=0):
         ss = synth.set_cover_instance(wl["n_elements"], wl["n_sets"], wl["f_lo"], wl["f_hi"], seed)
         return SimpleNamespace(n=ss.n_sets, m=int(ss.ptr[-1]), eu=ss.ptr, ev=ss.elems, w=ss.cost,
                                n_elements=ss.n_elements, terminals=None)
+    if wl["graph"] == "skipchain":
+        # pairwise MAP: w = node scores, te = factor scores
+        from types import SimpleNamespace
+
+        f = synth.skip_chain_crf(wl["n"], wl["k"], wl["sent_len"], wl["skip_frac"], seed)
+        return SimpleNamespace(n=f.n, m=f.m, eu=f.eu, ev=f.ev, w=f.theta_node.ravel(), te=f.theta_edge.ravel(),
+                               terminals=None)
     if wl["graph"] == "chung_lu":
         g = synth.chung_lu(wl["n"], wl["m"], wl["gamma"], seed)
     elif wl["graph"] == "er":
@@ -113,6 +124,9 @@ def algorithmic_bytes_per_epoch(wl, g):
         return 20 * n + 12 * (2 * m) + 16 * m
     if wl["kind"] == "sc":  # n sets, m non-zeros, one slack per element
         return 20 * n + 12 * m + 16 * g.n_elements
+    if wl["kind"] == "map":  # n*k node columns (2mk non-zeros), m*k*k edge columns (2 each), no slacks
+        k = wl["k"]
+        return 20 * (n * k + m * k * k) + 12 * (2 * m * k + 2 * m * k * k)
     k = wl["k"]
     nfree_blocks = n - k
     deg = np.bincount(np.concatenate([g.eu, g.ev]), minlength=n)
@@ -246,11 +260,15 @@ def run_gpu(args, wl, ws, rank, local):
     wt = g.w if kind != "mc" else g.ce
     w_d = torch.from_numpy(wt).to(dev)
     term_d = torch.from_numpy(g.terminals).to(dev) if kind == "mc" else None
+    if kind == "map":
+        term_d = torch.from_numpy(g.te).to(dev)  # factor scores ride in the terminals slot
     lab_d = torch.zeros(g.n, dtype=torch.uint8, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
     def build(eu, ev, w, term):
+        if kind == "map":
+            return T.thetis_build_map(g.n, wl["k"], eu, ev, w, term, seed=0, stream=stream)
         if kind == "sc":
             return T.thetis_build_sc(g.n_elements, eu, ev, w, seed=0, stream=stream)
         if kind == "vc":
@@ -317,6 +335,8 @@ def run_gpu(args, wl, ws, rank, local):
     ev_h = torch.from_numpy(g.ev).pin_memory()
     w_h = torch.from_numpy(wt).pin_memory()
     term_h = torch.from_numpy(g.terminals).pin_memory() if kind == "mc" else None
+    if kind == "map":
+        term_h = torch.from_numpy(g.te).pin_memory()
     lab_h = torch.zeros(g.n, dtype=torch.uint8).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     e_ms = 0.0
@@ -333,7 +353,8 @@ def run_gpu(args, wl, ws, rank, local):
         e_upd += info["updates"]
     e_ms = max_over_ranks(e_ms, ws, dev)
     e_upd_all = sum_over_ranks(float(e_upd), ws, dev)
-    h2d = g.eu.nbytes + g.ev.nbytes + wt.nbytes + (g.terminals.nbytes if kind == "mc" else 0)
+    h2d = g.eu.nbytes + g.ev.nbytes + wt.nbytes + (g.terminals.nbytes if kind == "mc" else 0) + \
+        (g.te.nbytes if kind == "map" else 0)
 
     # time to residual 1e-3 (same pipeline, epochs until rho <= 1e-3)
     ttr = None
@@ -789,6 +810,8 @@ def _oracle_setup(wl, g):
     oracle.build()
     if wl["kind"] == "sc":
         lp = oracle.OracleLP.set_cover(g.n_elements, g.eu, g.ev, g.w.astype(np.float64))
+    elif wl["kind"] == "map":
+        lp = oracle.OracleLP.map_lp(g.n, wl["k"], g.eu, g.ev, g.w.astype(np.float64), g.te.astype(np.float64))
     else:
         lp = oracle.build_problem(wl["kind"], g)
     col, nc = lp.color(0)
@@ -797,13 +820,19 @@ def _oracle_setup(wl, g):
 
 def cpu_baseline(wl, g, epochs):
     """The FP64 oracle on one host core: `epochs` SCD epochs of the same
-    instance (standard-form build and colouring are setup, not timed)."""
+    instance (standard-form build and colouring are setup, not timed) -- or,
+    where the workload names `cpu_sample_n`, of a smaller instance of the same
+    generator (the oracle's serial colouring of the full one takes minutes)."""
+    what = "the full instance"
+    if wl.get("cpu_sample_n"):
+        g = make_graph(dict(wl, n=wl["cpu_sample_n"]), 0)
+        what = f"an instance of the same generator with n = {wl['cpu_sample_n']}"
     lp, col = _oracle_setup(wl, g)
     t = time.perf_counter()
     x, info = lp.solve(beta=wl["beta"], epochs=epochs, refresh_every=wl["refresh"], color=col)
     dt = time.perf_counter() - t
     return {"value": epochs * lp.free_coords / dt, "unit": "coord_updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{epochs} FP64 serial SCD epochs of the full instance ({lp.free_coords} coordinates) "
+            "sample": f"{epochs} FP64 serial SCD epochs of {what} ({lp.free_coords} coordinates) "
                       f"incl. the final exact refresh + checks; build and colouring excluded",
             "seconds": dt}
 
@@ -937,7 +966,7 @@ def run_reference(args, wl, ws, rank):
         return run_reference_batch(args, wl, ws)
     if wl["kind"] == "serve":
         return run_reference_serving(args, wl, ws)
-    g = make_graph(wl, 0)
+    g = make_graph(dict(wl, n=wl["cpu_sample_n"]) if wl.get("cpu_sample_n") else wl, 0)
     lp, col = _oracle_setup(wl, g)
     x = lp.initial_x()
     times = []

@@ -55,7 +55,8 @@ typedef enum {
   THETIS_ROUND_IS = 1,      /* independent set, Bansal et al. with alterations (App. B.2) */
   THETIS_ROUND_MC = 2,      /* multiway cut, CKR (App. B.3) */
   THETIS_ROUND_SC = 3,      /* set cover, f-threshold (App. B.1) */
-  THETIS_ROUND_SC_RAND = 4  /* set cover, randomized rounding + fix-up (App. B.1) */
+  THETIS_ROUND_SC_RAND = 4, /* set cover, randomized rounding + fix-up (App. B.1) */
+  THETIS_ROUND_MAP = 5      /* pairwise MAP, node rounding (Sec. 4.1) */
 } thetis_round_kind;
 typedef enum { THETIS_MODE_COLORED = 0, THETIS_MODE_ASYNC = 1 } thetis_mode;
 
@@ -218,6 +219,23 @@ thetis_status thetis_build_mc(int64_t n, int64_t m, const int32_t* eu, const int
  */
 thetis_status thetis_build_sc(int64_t n_elements, int64_t n_sets, const int64_t* set_ptr, const int32_t* set_elems,
                               const float* cost, int32_t mem, uint64_t seed, void* stream, thetis_handle** out);
+
+/*
+ * thetis_build_map -- MAP inference on a pairwise factor graph (Sec. 4.1) as
+ * the local-polytope LP (the relaxation whose rounding the paper takes from
+ * Ravikumar et al.): n variables with k labels each (2 <= k <= 32), m pairwise
+ * factors eu[e] -- ev[e] (0-based, no loops), scores theta_node[n*k] (row-major
+ * by variable) and theta_edge[m*k*k] (factor e, label of eu[e], label of
+ * ev[e]).  Columns: node marginals mu_i(a) at i*k + a (one simplex block per
+ * variable) then edge marginals mu_e(a, b) at n*k + e*k*k + a*k + b in [0, 1];
+ * rows 2*e*k + a: sum_b mu_e(a, b) - mu_u(a) = 0 and 2*e*k + k + b:
+ * sum_a mu_e(a, b) - mu_v(b) = 0; costs -theta (the score is maximised).
+ * Round with THETIS_ROUND_MAP: labels_out[n] = argmax_a mu_i(a) (ties: lowest
+ * label); info.obj = -(score of the labelling).  Arrays live in `mem`.
+ */
+thetis_status thetis_build_map(int64_t n, int64_t m, int32_t k, const int32_t* eu, const int32_t* ev,
+                               const float* theta_node, const float* theta_edge, int32_t mem, uint64_t seed,
+                               void* stream, thetis_handle** out);
 
 /* Sizes of a built problem (any pointer may be NULL): rows m, structural
  * columns n, slack columns (one per GE/LE row), free coordinates (what one

@@ -394,20 +394,25 @@ class OracleLP:
         th_n = np.asarray(theta_node, np.float64).reshape(n, k)
         th_e = np.asarray(theta_edge, np.float64).reshape(E, k, k)
         Ns, M = n * k + E * k * k, 2 * E * k
-        cols = [[] for _ in range(Ns)]
-        for e in range(E):
-            u, v = eu[e], ev[e]
-            for a in range(k):
-                cols[u * k + a].append((2 * e * k + a, -1.0))
-                cols[v * k + a].append((2 * e * k + k + a, -1.0))
-                for b in range(k):
-                    j = n * k + e * k * k + a * k + b
-                    cols[j].append((2 * e * k + a, 1.0))
-                    cols[j].append((2 * e * k + k + b, 1.0))
+        a = np.arange(k)
+        # node entries: incidence t = (vertex, edge, side), every label a
+        vert = np.concatenate([eu, ev]); edge = np.concatenate([np.arange(E), np.arange(E)])
+        side = np.concatenate([np.zeros(E, np.int64), np.ones(E, np.int64)])
+        ncol = (vert[:, None] * k + a[None, :]).ravel()
+        nrow = (2 * edge[:, None] * k + side[:, None] * k + a[None, :]).ravel()
+        # edge entries: column (e, a, b) in rows 2ek + a and 2ek + k + b
+        e3 = np.arange(E)[:, None, None]
+        ecol = (n * k + e3 * k * k + a[None, :, None] * k + a[None, None, :]).ravel()
+        erow_u = (2 * e3 * k + a[None, :, None] + 0 * a[None, None, :]).ravel()
+        erow_v = (2 * e3 * k + k + a[None, None, :] + 0 * a[None, :, None]).ravel()
+        col = np.concatenate([ncol, ecol, ecol])
+        row = np.concatenate([nrow, erow_u, erow_v])
+        val = np.concatenate([-np.ones(ncol.shape[0]), np.ones(2 * ecol.shape[0])])
+        order = np.argsort(col, kind="stable")
         colptr = np.zeros(Ns + 1, np.int64)
-        colptr[1:] = np.cumsum([len(c) for c in cols])
-        rowidx = np.array([r for c in cols for r, _ in c], np.int32)
-        val = np.array([v for c in cols for _, v in c], np.float64)
+        np.cumsum(np.bincount(col, minlength=Ns), out=colptr[1:])
+        rowidx = row[order].astype(np.int32)
+        val = val[order]
         c = np.concatenate([-th_n.ravel(), -th_e.ravel()])
         lp = cls.general(M, colptr, rowidx, val, np.zeros(M), c, np.zeros(Ns), np.ones(Ns),
                          np.zeros(M, np.int32), block_k=k, block_first=np.arange(n, dtype=np.int64) * k)

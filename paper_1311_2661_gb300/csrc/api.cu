@@ -288,6 +288,47 @@ thetis_status thetis_build_sc(int64_t n_elements, int64_t n_sets, const int64_t*
   return THETIS_OK;
 }
 
+thetis_status thetis_build_map(int64_t n, int64_t m, int32_t k, const int32_t* eu, const int32_t* ev,
+                               const float* theta_node, const float* theta_edge, int32_t mem, uint64_t seed,
+                               void* stream, thetis_handle** out) {
+  if (!out || !theta_node) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  *out = nullptr;
+  thetis_handle* h = nullptr;
+  thetis_status st = guard(nullptr, [&] {
+    TH_CHECK(n >= 1 && m >= 0 && k >= 2 && k <= 32, THETIS_E_INVALID, "need n >= 1, m >= 0, 2 <= k <= 32");
+    TH_CHECK(m == 0 || (eu && ev && theta_edge), THETIS_E_INVALID, "null edge array");
+    TH_CHECK(n * (int64_t)k + m * (int64_t)k * k < (int64_t(1) << 31) && 2 * m * (int64_t)k < (int64_t(1) << 31),
+             THETIS_E_INVALID, "MAP LP too large");
+    h = new_handle(stream);
+    cudaStream_t s = h->stream;
+    Arena tmp(s);
+    const int32_t* deu = to_dev(eu, m, mem, tmp, s);
+    const int32_t* dev = to_dev(ev, m, mem, tmp, s);
+    const float* dtn = to_dev(theta_node, n * (int64_t)k, mem, tmp, s);
+    const float* dte = to_dev(theta_edge, m * (int64_t)k * k, mem, tmp, s);
+    RawLP raw;
+    build_map_raw(n, m, k, deu, dev, dtn, dte, raw, tmp, s);
+    h->P = build_problem(raw, KIND_MAP, seed, s, tmp);
+    Problem& P = *h->P;
+    P.nv = n;
+    P.ne = m;
+    P.eu = keep_copy(P.mem, deu, m, s);
+    P.ev = keep_copy(P.mem, dev, m, s);
+    P.map_tn = keep_copy(P.mem, dtn, n * (int64_t)k, s);
+    P.map_te = keep_copy(P.mem, dte, m * (int64_t)k * k, s);
+    finish_create(h);
+  });
+  if (st != THETIS_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return THETIS_OK;
+}
+
 thetis_status thetis_get_sizes(const thetis_handle* h, int64_t* rows, int64_t* struct_cols, int64_t* slack_cols,
                                int64_t* free_coords, int64_t* nnz, int32_t* ncolors) {
   if (!h || !h->P) {

@@ -378,6 +378,98 @@ void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev
   raw.slack_sign_uniform = -1;
 }
 
+// Pairwise MAP: node column (i, a) at i*k + a holds -1 in row 2*e*k + a of every
+// edge e with eu[e] = i and in row 2*e*k + k + a of every edge with ev[e] = i;
+// edge column (e, a, b) at n*k + e*k*k + a*k + b holds +1 in rows 2*e*k + a and
+// 2*e*k + k + b.
+__global__ void k_map_counts(const int64_t* iptr, int64_t n, int64_t m, int32_t k, int64_t* cnt) {
+  GSTRIDE(j, n * k + m * (int64_t)k * k) cnt[j] = (j < n * k) ? iptr[j / k + 1] - iptr[j / k] : 2;
+}
+
+__global__ void k_map_fill(const int64_t* iptr, const uint32_t* iedge, const int32_t* eu, int64_t n, int64_t m,
+                           int32_t k, const int64_t* colptr, int32_t* rowidx, float* val) {
+  GSTRIDE(j, n * k + m * (int64_t)k * k) {
+    int64_t q = colptr[j];
+    if (j < n * k) {
+      const int64_t v = j / k;
+      const int32_t a = (int32_t)(j % k);
+      for (int64_t t = iptr[v]; t < iptr[v + 1]; ++t) {
+        const int64_t e = iedge[t];
+        rowidx[q] = (int32_t)(2 * e * k + (eu[e] == v ? 0 : k) + a);
+        val[q++] = -1.f;
+      }
+    } else {
+      const int64_t t = j - n * k, e = t / ((int64_t)k * k);
+      const int32_t a = (int32_t)((t / k) % k), b = (int32_t)(t % k);
+      rowidx[q] = (int32_t)(2 * e * k + a);
+      val[q] = 1.f;
+      rowidx[q + 1] = (int32_t)(2 * e * k + k + b);
+      val[q + 1] = 1.f;
+    }
+  }
+}
+
+__global__ void k_map_vectors(const float* tn, const float* te, int64_t n, int64_t m, int32_t k, float* b, float* c,
+                              float* lo, float* hi, uint8_t* rk, int64_t* bfirst, int* err) {
+  const int64_t Ns = n * k + m * (int64_t)k * k, M = 2 * m * (int64_t)k;
+  GSTRIDE(i, Ns > M ? Ns : M) {
+    if (i < Ns) {
+      const float t = (i < n * k) ? tn[i] : te[i - n * k];
+      if (!isfinite(t)) atomicExch(err, 2);
+      c[i] = -t;
+      lo[i] = 0.f;
+      hi[i] = 1.f;
+    }
+    if (i < M) {
+      b[i] = 0.f;
+      rk[i] = THETIS_ROW_EQ;
+    }
+    if (i < n) bfirst[i] = i * k;
+  }
+}
+
+void build_map_raw(int64_t n, int64_t m, int32_t k, const int32_t* d_eu, const int32_t* d_ev, const float* d_tn,
+                   const float* d_te, RawLP& raw, Arena& tmp, cudaStream_t s) {
+  int* err = tmp.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (m > 0) {
+    k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(d_eu, d_ev, m, n, err);
+    TH_LAUNCHED();
+  }
+  TH_CHECK(read_flag(err, s) == 0, THETIS_E_INVALID, "edge endpoint out of range or a loop");
+  int64_t* iptr;
+  uint32_t* iedge;
+  incidence(n, m, d_eu, d_ev, iptr, iedge, tmp, s);
+  const int64_t Ns = n * k + m * (int64_t)k * k;
+  raw.M = 2 * m * (int64_t)k;
+  raw.Ns = Ns;
+  raw.colptr = tmp.alloc<int64_t>(Ns + 1);
+  k_map_counts<<<grid_for(Ns, 256), 256, 0, s>>>(iptr, n, m, k, raw.colptr);
+  TH_LAUNCHED();
+  exclusive_scan_i64(raw.colptr, raw.colptr, Ns, tmp, s);
+  raw.nnz = 2 * m * (int64_t)k + 2 * m * (int64_t)k * k;
+  raw.rowidx = tmp.alloc<int32_t>(raw.nnz + 1);
+  raw.val = tmp.alloc<float>(raw.nnz + 1);
+  k_map_fill<<<grid_for(Ns, 256), 256, 0, s>>>(iptr, iedge, d_eu, n, m, k, raw.colptr, raw.rowidx, raw.val);
+  TH_LAUNCHED();
+  raw.b = tmp.alloc<float>(raw.M + 1);
+  raw.c = tmp.alloc<float>(Ns);
+  raw.lo = tmp.alloc<float>(Ns);
+  raw.hi = tmp.alloc<float>(Ns);
+  raw.row_kind = tmp.alloc<uint8_t>(raw.M + 1);
+  raw.block_first = tmp.alloc<int64_t>(n);
+  k_map_vectors<<<grid_for(std::max(Ns, raw.M), 256), 256, 0, s>>>(d_tn, d_te, n, m, k, raw.b, raw.c, raw.lo, raw.hi,
+                                                                   raw.row_kind, raw.block_first, err);
+  TH_LAUNCHED();
+  TH_CHECK(read_flag(err, s) == 0, THETIS_E_INVALID, "scores must be finite");
+  raw.block_k = k;
+  raw.n_blocks = n;
+  raw.bounds_uniform = true;
+  raw.lo_u = 0.f;
+  raw.hi_u = 1.f;
+  raw.slack_sign_uniform = 0;
+}
+
 // ---------------------------------------------------------------------------
 // general layout
 // ---------------------------------------------------------------------------

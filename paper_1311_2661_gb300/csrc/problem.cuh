@@ -7,7 +7,7 @@
 
 namespace thetis {
 
-enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BATCH = 4, KIND_SC = 5 };
+enum ProbKind { KIND_GENERAL = 0, KIND_VC = 1, KIND_IS = 2, KIND_MC = 3, KIND_BATCH = 4, KIND_SC = 5, KIND_MAP = 6 };
 
 // Classes of coordinate units inside one colour.  Units of a colour are stored
 // class by class, so that every class is a contiguous range of units and of
@@ -112,6 +112,10 @@ struct Problem {
   int64_t* sc_eptr = nullptr;
   int32_t* sc_esets = nullptr;
   int32_t sc_f = 0;
+
+  // pairwise MAP meta: node and edge scores (n*k, m*k*k)
+  float* map_tn = nullptr;
+  float* map_te = nullptr;
 
   // graph meta (builders)
   int64_t nv = 0, ne = 0;
@@ -218,6 +222,12 @@ void build_mc_raw(int64_t n, int64_t m, const int32_t* d_eu, const int32_t* d_ev
 void build_sc_raw(int64_t n_elem, int64_t n_sets, int64_t nnz, const int64_t* d_ptr, const int32_t* d_elems,
                   const float* d_cost, RawLP& raw, int64_t*& eptr, int32_t*& esets, int32_t& f, Arena& keep,
                   Arena& tmp, cudaStream_t s);
+
+// pairwise MAP (Sec. 4.1): the local-polytope LP of an MRF with k labels per
+// variable (node marginals on simplex blocks, edge marginals in [0, 1],
+// marginalisation rows), costs -theta
+void build_map_raw(int64_t n, int64_t m, int32_t k, const int32_t* d_eu, const int32_t* d_ev, const float* d_tn,
+                   const float* d_te, RawLP& raw, Arena& tmp, cudaStream_t s);
 
 // batch.cu
 void build_batch_raw(int64_t count, const uint8_t* d_kind, const int64_t* d_noff, const int64_t* d_eoff, int64_t Nv,

@@ -216,6 +216,45 @@ __global__ void k_sc_valid(const uint8_t* lab, const int64_t* eptr, const int32_
   }
 }
 
+// Pairwise MAP node rounding (Sec. 4.1): every variable takes the label of its
+// largest node marginal, ties to the lowest label.
+__global__ void k_map_label(const float* x, int64_t n, int k, uint8_t* lab) {
+  GSTRIDE(i, n) {
+    int best = 0;
+    float bx = x[i * k];
+    for (int a = 1; a < k; ++a)
+      if (x[i * k + a] > bx) {
+        bx = x[i * k + a];
+        best = a;
+      }
+    lab[i] = (uint8_t)best;
+  }
+}
+
+// objective of the integral point, -(sum_i theta_i(l_i) + sum_e theta_e(l_u, l_v)),
+// in fixed-order FP64 partials
+__global__ void k_map_energy(const uint8_t* lab, const float* tn, const float* te, const int32_t* eu,
+                             const int32_t* ev, int64_t n, int64_t m, int k, double* part) {
+  double sum = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n + m; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < n) {
+      sum -= (double)tn[t * k + lab[t]];
+    } else {
+      const int64_t e = t - n;
+      sum -= (double)te[e * k * k + (int64_t)lab[eu[e]] * k + lab[ev[e]]];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  __shared__ double sm[8];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sm[q];
+    part[blockIdx.x] = a;
+  }
+}
+
 // CKR: label of every vertex in every repetition
 __global__ void k_ckr_label(const float* x, int64_t n, int k, int reps, const double* rad, const int32_t* sigma,
                             uint8_t* lab) {
@@ -281,13 +320,14 @@ __global__ void k_is_near(const float* x, int64_t n, int rep, uint64_t seed, con
 
 void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out) {
   cudaStream_t s = P.stream;
-  TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC || P.kind == KIND_SC, THETIS_E_INVALID,
-           "rounding needs a problem built by thetis_build_vc / _is / _mc / _sc");
+  TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC || P.kind == KIND_SC || P.kind == KIND_MAP,
+           THETIS_E_INVALID, "rounding needs a problem built by thetis_build_vc / _is / _mc / _sc / _map");
   TH_CHECK((kind == THETIS_ROUND_VC && P.kind == KIND_VC) || (kind == THETIS_ROUND_IS && P.kind == KIND_IS) ||
                (kind == THETIS_ROUND_MC && P.kind == KIND_MC) ||
-               ((kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) && P.kind == KIND_SC),
+               ((kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) && P.kind == KIND_SC) ||
+               (kind == THETIS_ROUND_MAP && P.kind == KIND_MAP),
            THETIS_E_INVALID, "rounding kind does not match the problem");
-  if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_SC) reps = 1;
+  if (kind == THETIS_ROUND_VC || kind == THETIS_ROUND_SC || kind == THETIS_ROUND_MAP) reps = 1;
   TH_CHECK(reps >= 1 && reps <= MAX_REPS, THETIS_E_INVALID, "reps must be in [1, 64]");
   const int64_t n = P.nv, m = P.ne;
   Arena tmp(s);
@@ -302,7 +342,15 @@ void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_lab
   out.best_rep = 0;
   out.near = 0;
   out.status = THETIS_OK;
-  if (kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) {
+  if (kind == THETIS_ROUND_MAP) {
+    k_map_label<<<grid_for(n, 256), 256, 0, s>>>(P.xorig, n, P.k, d_labels);
+    TH_LAUNCHED();
+    k_map_energy<<<RB, 256, 0, s>>>(d_labels, P.map_tn, P.map_te, P.eu, P.ev, n, m, P.k, part);
+    TH_LAUNCHED();
+    k_rep_final<<<1, 32, 0, s>>>(part, RB, 1, repv);
+    TH_LAUNCHED();
+    out.repair = 0.0;
+  } else if (kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) {
     const int64_t ns = P.Ns, ne_ = P.M;  // sets, elements
     if (ne_ > 0) {
       k_sc_eps<<<grid_for(ne_, 256, 152 * 8), 256, 0, s>>>(P.xorig, P.sc_eptr, P.sc_esets, ne_, dbits);

@@ -276,3 +276,44 @@ def set_cover_instance(n_elements: int, n_sets: int, f_lo: int, f_hi: int, seed:
     np.cumsum(np.bincount(sets, minlength=n_sets), out=ptr[1:])
     cost = rng.integers(1, 11, size=n_sets).astype(np.float32)
     return SetSystem(n_elements, ptr, elem.astype(np.int32), cost)
+
+
+class PairwiseMRF:
+    """Pairwise factor graph: n variables with k labels, edges eu[e] -- ev[e],
+    scores theta_node (n, k) and theta_edge (m, k, k), FP32."""
+
+    def __init__(self, n, k, eu, ev, theta_node, theta_edge):
+        self.n, self.k = int(n), int(k)
+        self.eu, self.ev = eu, ev
+        self.theta_node, self.theta_edge = theta_node, theta_edge
+
+    @property
+    def m(self):
+        return int(self.eu.shape[0])
+
+
+def skip_chain_crf(n: int, k: int, sent_len: int, skip_frac: float, seed: int) -> PairwiseMRF:
+    """Skip-chain-CRF-shaped MRF (the shape of the paper's text-chunking factor
+    graph): the variables form sentences of `sent_len` consecutive tokens with a
+    chain factor between neighbours; a `skip_frac` share of tokens also gets a
+    skip factor to a random earlier token within 500 positions.  Unary scores
+    N(0, 1); chain factors share one transition matrix N(0, 0.5) (tied CRF
+    weights); skip factors reward equal labels by a weight U(0, 1)."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n - 1)
+    chain = i[(i + 1) % sent_len != 0]
+    cu, cv = chain, chain + 1
+    src = np.flatnonzero(rng.random(n) < skip_frac)
+    src = src[src > 0]
+    dst = np.maximum(0, src - rng.integers(2, 501, size=src.shape[0]))
+    ok = dst < src - 1  # not a chain neighbour
+    su, sv = dst[ok], src[ok]
+    eu = np.concatenate([cu, su]).astype(np.int32)
+    ev = np.concatenate([cv, sv]).astype(np.int32)
+    tn = rng.normal(size=(n, k)).astype(np.float32)
+    trans = rng.normal(scale=0.5, size=(k, k)).astype(np.float32)
+    te = np.empty((eu.shape[0], k, k), np.float32)
+    te[: cu.shape[0]] = trans
+    lam = rng.random(su.shape[0]).astype(np.float32)
+    te[cu.shape[0]:] = lam[:, None, None] * np.eye(k, dtype=np.float32)[None]
+    return PairwiseMRF(n, k, eu, ev, tn, te)

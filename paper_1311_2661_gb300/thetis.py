@@ -24,7 +24,7 @@ THETIS_OK, THETIS_E_INVALID, THETIS_E_NOMEM, THETIS_E_BUDGET, THETIS_E_CUDA = 0,
 THETIS_E_TIMEOUT, THETIS_E_REPAIR, THETIS_PENDING, THETIS_NOT_CONVERGED = 5, 6, 7, 8
 MEM_HOST, MEM_DEVICE = 0, 1
 ROW_EQ, ROW_GE, ROW_LE = 0, 1, 2
-ROUND_VC, ROUND_IS, ROUND_MC, ROUND_SC, ROUND_SC_RAND = 0, 1, 2, 3, 4
+ROUND_VC, ROUND_IS, ROUND_MC, ROUND_SC, ROUND_SC_RAND, ROUND_MAP = 0, 1, 2, 3, 4, 5
 MODE_COLORED, MODE_ASYNC = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_NOMEM", 3: "E_BUDGET", 4: "E_CUDA", 5: "E_TIMEOUT",
@@ -78,6 +78,7 @@ def _load():
         "thetis_build_is": (st, [i64, i64, P, P, P, i32, u64, P, P]),
         "thetis_build_mc": (st, [i64, i64, P, P, P, i32, P, i32, u64, P, P]),
         "thetis_build_sc": (st, [i64, i64, P, P, P, i32, u64, P, P]),
+        "thetis_build_map": (st, [i64, i64, i32, P, P, P, P, i32, u64, P, P]),
         "thetis_get_sizes": (st, [P, P, P, P, P, P, P]),
         "thetis_solve": (st, [P, P, P]),
         "thetis_round": (st, [P, i32, u64, i32, P, i32, P]),
@@ -208,7 +209,7 @@ class Handle:
 
     def round(self, kind=None, **kw):
         if kind is None:
-            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC, "sc": ROUND_SC}[self.kind]
+            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC, "sc": ROUND_SC, "map": ROUND_MAP}[self.kind]
         return thetis_round(self, kind, **kw)
 
     def get_x(self, out=None):
@@ -266,6 +267,18 @@ def thetis_build_sc(n_elements, set_ptr, set_elems, cost, seed=0, stream=None) -
     _check(_lib.thetis_build_sc(int(n_elements), n_sets, pp, pe, pc, A.memspace, seed, _stream_ptr(stream),
                                 C.byref(out)))
     return Handle(out.value, n_vertices=n_sets, kind="sc")
+
+
+def thetis_build_map(n, k, eu, ev, theta_node, theta_edge, seed=0, stream=None) -> Handle:
+    """Pairwise MAP as the local-polytope LP; labels of a rounding are variable labels."""
+    A = _Args()
+    m = int(eu.shape[0])
+    peu, pev = A(eu, np.int32), A(ev, np.int32)
+    ptn, pte = A(theta_node, np.float32), A(theta_edge, np.float32)
+    out = C.c_void_p()
+    _check(_lib.thetis_build_map(int(n), m, int(k), peu, pev, ptn, pte, A.memspace, seed, _stream_ptr(stream),
+                                 C.byref(out)))
+    return Handle(out.value, n_vertices=int(n), kind="map")
 
 
 def thetis_create(m, n, csc_ptr, csc_row, b, c, lo, hi, row_kind, csc_val=None, block_k=1, block_first=None,
