@@ -365,6 +365,7 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
                           sweep_grid(P) > 0;
   if (persistent) reset_sweep_flags(P);
   batch_begin_solve(P);
+  if (a.mode == THETIS_MODE_COLORED) ensure_tail(P);
   // per-colour engine: capture one epoch as a CUDA graph (re-captured when its arguments change)
   bool key_ok = P.epoch_graph && h->g_beta == a.beta && h->g_rule == a.step_rule && h->g_mode == a.mode &&
                 h->g_ub == (int)ub && h->g_xb == (int)xb && h->g_small == P.small_g && h->g_async == a.async_ctas;

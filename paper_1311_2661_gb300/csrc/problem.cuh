@@ -202,6 +202,20 @@ struct Problem {
   int sweep_per_sm = 0;  // 0: as many as fit
   bool force_full = false;  // use the full sweep even where the lean one applies
 
+  // tail colours: the last colours, holding only a few singleton columns each,
+  // run as three phases (tail_T = first tail colour, tail_n units in colour
+  // order, tail_coff per tail colour); every tail unit's entries are split into
+  // rows shared with another tail unit (tptr / trow) and the rest (hptr / hrow)
+  int tail_T = -1;            // -1: not built yet; == ncolors: no tail
+  int64_t tail_n = 0;
+  int tail_ncol = 0;
+  int tail_ctas = 0;          // CTAs of the tail colour chain (one per unit)
+  int64_t* tail_col = nullptr;
+  int64_t* tail_coff = nullptr;
+  int64_t *tail_hptr = nullptr, *tail_tptr = nullptr;
+  uint32_t *tail_hrow = nullptr, *tail_trow = nullptr;
+  float *tail_h = nullptr, *tail_d = nullptr;
+
   // CUDA graph of one epoch
   cudaGraphExec_t epoch_graph = nullptr;
   int graph_key = -1;
@@ -270,7 +284,10 @@ void al_update(Problem& P, double beta);
 void gather_duals(Problem& P, float* out);
 void init_iterate(Problem& P);
 int sweep_grid(Problem& P);
-bool sweep_lean_possible(const Problem& P);
+bool sweep_lean_possible(Problem& P);
+// select the tail colours and split their columns' rows (once per problem;
+// before any stream capture of an epoch)
+void ensure_tail(Problem& P);
 void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int epochs);
 int sweep_error(Problem& P);
 void reset_sweep_flags(Problem& P);

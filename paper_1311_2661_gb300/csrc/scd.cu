@@ -521,6 +521,161 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tail colours.  The last colours hold only a few singleton columns each (the
+// hubs of a power-law graph); their order is a chain, so each colour costs a
+// grid barrier plus one column's latency.  A tail column's rows are split
+// into those shared with another tail column (T rows) and the rest (H rows).
+// No unit touches an H row between the end of the head colours and that
+// column's own step, so the three phases
+//   P (all CTAs): h_u = a_u^T r over the H rows,
+//   T (one CTA per unit, colours in order, a barrier of those few CTAs
+//     between colours): the step of every tail column from h_u plus its T
+//     rows, scattering the T rows,
+//   S (all CTAs): r += a_u d_u on the H rows,
+// leave x and r as the colour-by-colour sweep does (each r entry is updated
+// once, from the value it had); only the FP32 order of the dot changes.
+// ---------------------------------------------------------------------------
+struct TailView {
+  int64_t n;           // tail units
+  int ncol;            // tail colours
+  const int64_t* col;  // internal column of each unit, colour order
+  const int64_t* coff; // first unit of each tail colour (ncol + 1)
+  const int64_t* hptr;
+  const uint32_t* hrow;
+  const int64_t* tptr;
+  const uint32_t* trow;
+  float* h;            // partial dot over the H rows
+  float* d;            // step of the unit
+  int ctas;            // CTAs of phase T: the most units of any tail colour (one CTA per unit)
+};
+
+
+__device__ __noinline__ void tail_partial(const StepView& V, const TailView& T, int64_t u, float* red_smem) {
+  const int64_t q0 = T.hptr[u], q1 = T.hptr[u + 1];
+  float acc = 0.f;
+  for (int64_t qb = q0 + threadIdx.x; qb < q1; qb += 4 * STEP_T) {
+    uint32_t e4[4];
+    float r4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) e4[t] = (qb + t * STEP_T < q1) ? T.hrow[qb + t * STEP_T] : 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) r4[t] = (qb + t * STEP_T < q1) ? ldr(V, idx_of(e4[t])) : 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (qb + t * STEP_T < q1) acc = fmaf(sgn_of(e4[t]), r4[t], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < STEP_T / 32) ? red_smem[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) T.h[u] = v;
+  }
+  __syncthreads();
+}
+
+// The step of tail unit u by the whole CTA: its T rows gathered four at a
+// time per thread, block-reduced, added to the H-row partial; the T rows
+// scattered.  (The tail functions are not inlined: the sweep's hot loop keeps
+// its registers.)
+__device__ __noinline__ void tail_unit(const StepView& V, const TailView& T, int64_t u, float* red_smem) {
+  const int64_t j = T.col[u];
+  const int64_t q0 = T.tptr[u], q1 = T.tptr[u + 1];
+  const float xj = __ldcg(V.x + j);
+  const float ctj = V.ct[j];
+  const float xb = V.xbar ? V.xbar[j] : 0.f;
+  const float hj = T.h[u];
+  uint32_t ce[4];
+  float cr[4];
+  const int64_t qf = q0 + threadIdx.x;  // first batch: kept for the scatter
+#pragma unroll
+  for (int t = 0; t < 4; ++t) ce[t] = (qf + t * STEP_T < q1) ? T.trow[qf + t * STEP_T] : 0u;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) cr[t] = (qf + t * STEP_T < q1) ? ldr(V, idx_of(ce[t])) : 0.f;
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (qf + t * STEP_T < q1) acc = fmaf(sgn_of(ce[t]), cr[t], acc);
+  for (int64_t qb = qf + 4 * STEP_T; qb < q1; qb += 4 * STEP_T) {
+    uint32_t e4[4];
+    float r4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) e4[t] = (qb + t * STEP_T < q1) ? T.trow[qb + t * STEP_T] : 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) r4[t] = (qb + t * STEP_T < q1) ? ldr(V, idx_of(e4[t])) : 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (qb + t * STEP_T < q1) acc = fmaf(sgn_of(e4[t]), r4[t], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < STEP_T / 32) ? red_smem[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      const float tot = hj + v;
+      const float nnz = (float)((T.hptr[u + 1] - T.hptr[u]) + (q1 - q0));
+      const float g = ctj + V.beta * tot + (xj - xb) * V.inv_beta;
+      const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, nnz, V.inv_beta);
+      const float lo = V.lo ? V.lo[j] : V.lo_u;
+      const float hi = V.hi ? V.hi[j] : V.hi_u;
+      const float xn = fminf(fmaxf(xj - g / L, lo), hi);
+      V.x[j] = xn;
+      T.d[u] = xn - xj;
+      red_smem[32] = xn - xj;
+    }
+  }
+  __syncthreads();
+  const float d = red_smem[32];
+  __syncthreads();  // red_smem is reused by the next unit
+  if (d == 0.f) return;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (qf + t * STEP_T < q1) V.r[idx_of(ce[t])] = cr[t] + sgn_of(ce[t]) * d;
+  for (int64_t qb = qf + 4 * STEP_T; qb < q1; qb += 4 * STEP_T) {
+    uint32_t e4[4];
+    float r4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) e4[t] = (qb + t * STEP_T < q1) ? T.trow[qb + t * STEP_T] : 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) r4[t] = (qb + t * STEP_T < q1) ? ldr(V, idx_of(e4[t])) : 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (qb + t * STEP_T < q1) V.r[idx_of(e4[t])] = r4[t] + sgn_of(e4[t]) * d;
+  }
+}
+
+__device__ __noinline__ void tail_scatter(const StepView& V, const TailView& T, int64_t u) {
+  const float d = T.d[u];
+  if (d == 0.f) return;
+  for (int64_t q = T.hptr[u] + threadIdx.x; q < T.hptr[u + 1]; q += STEP_T) {
+    const uint32_t e = T.hrow[q];
+    V.r[idx_of(e)] = ldr(V, idx_of(e)) + sgn_of(e) * d;
+  }
+}
+
+// the three phases as separate launches (per-colour engine)
+__global__ void __launch_bounds__(STEP_T) k_tail_partial(StepView V, TailView T) {
+  __shared__ float red_smem[33];
+  for (int64_t u = blockIdx.x; u < T.n; u += gridDim.x) tail_partial(V, T, u, red_smem);
+}
+// one tail colour per launch, one CTA per unit
+__global__ void __launch_bounds__(STEP_T) k_tail_colour(StepView V, TailView T, int tc) {
+  __shared__ float red_smem[33];
+  const int64_t u = T.coff[tc] + blockIdx.x;
+  if (u < T.coff[tc + 1]) tail_unit(V, T, u, red_smem);
+}
+__global__ void __launch_bounds__(STEP_T) k_tail_scatter(StepView V, TailView T) {
+  for (int64_t u = blockIdx.x; u < T.n; u += gridDim.x) tail_scatter(V, T, u);
+}
+
 // One colour per launch: CTA b serves tile b.
 __global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunch CL) {
   __shared__ float red_smem[33];
@@ -541,8 +696,9 @@ __global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunc
 // err = 1 and the launch gives up (the host reports THETIS_E_TIMEOUT).
 constexpr long long BARRIER_LIMIT_CYCLES = 4000000000LL;
 
-__device__ __forceinline__ unsigned bar_arrive(unsigned* bar) {
-  unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+__device__ __forceinline__ unsigned bar_arrive(unsigned* bar, unsigned participants = 0) {
+  const unsigned n = participants ? participants : gridDim.x;  // CTAs 0 .. n-1 take part
+  unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (n - 1)) : 1u;
   unsigned old;
   asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
   return old;
@@ -627,7 +783,7 @@ constexpr int PREFETCH_TILES = 2;
 
 template <bool FULL>
 __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, const ColorLaunch* plan, const int64_t* ntiles,
-                                                     int ncolors, int epochs, unsigned* bar, int* err) {
+                                                     int ncolors, int epochs, unsigned* bar, int* err, TailView TV) {
   __shared__ float red_smem[33];
   __shared__ ColorLaunch cl[2];
   __shared__ int ok;
@@ -641,44 +797,85 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
   // tile q of colour c (batches: through the active-tile list)
   auto tile_of = [&](int c, int64_t q) -> int64_t { return V.act_tiles ? V.act_tiles[V.act_off[c] + q] : q; };
   auto count_of = [&](int c) -> int64_t { return V.act_tiles ? V.act_n[c] : ntiles[c]; };
+  // grid barrier that also loads colour cn's descriptor, stages its first long
+  // column and prefetches its first tiles while waiting
+  auto advance = [&](int cn) -> bool {
+    __syncthreads();
+    unsigned old = 0;
+    if (threadIdx.x == 0) old = bar_arrive(bar);
+    if (threadIdx.x < CLW) ((unsigned*)&cl[cur ^ 1])[threadIdx.x] = ((const unsigned*)&plan[cn])[threadIdx.x];
+    __syncthreads();
+    const int64_t ntn = count_of(cn);
+    bool staged = false;
+    if ((int64_t)blockIdx.x < ntn) {
+      // a first tile that is a long column: its row ids go to shared memory now
+      const int64_t t0 = tile_of(cn, blockIdx.x);
+      const ColorLaunch& nx = cl[cur ^ 1];
+      int si = 0;
+      while (si + 1 < nx.nseg && t0 >= nx.seg[si + 1].b0) ++si;
+      const SegLaunch S = nx.seg[si];
+      if (FULL && (S.cls == UC_HUGE || S.cls == UC_LARGE) && t0 - S.b0 < S.n) {
+        stage_huge(V, S.c0 + (t0 - S.b0), dyn);
+        staged = true;
+      }
+    }
+    for (int q = staged ? 1 : 0; q < PREFETCH_TILES; ++q) {
+      const int64_t qq = blockIdx.x + (int64_t)q * gridDim.x;
+      if (qq < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, tile_of(cn, qq));
+    }
+    if (threadIdx.x == 0) ok = bar_wait(bar, old, err) ? 1 : 0;
+    __syncthreads();
+    cur ^= 1;
+    first_staged = staged;
+    return ok != 0;
+  };
+  // plain grid barrier (between the tail phases)
+  auto sync = [&]() -> bool {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned old = bar_arrive(bar);
+      ok = bar_wait(bar, old, err) ? 1 : 0;
+    }
+    __syncthreads();
+    return ok != 0;
+  };
   for (int e = 0; e < epochs; ++e) {
+    const bool last_epoch = e == epochs - 1;
     for (int c = 0; c < ncolors; ++c) {
       const int64_t nt = count_of(c);
       for (int64_t q = blockIdx.x; q < nt; q += gridDim.x)
         process_tile<FULL>(V, cl[cur].seg, cl[cur].nseg, tile_of(c, q), red_smem, dyn,
                            first_staged && q == blockIdx.x);
-      const bool last = (e == epochs - 1) && (c == ncolors - 1);
-      if (last) break;
-      const int cn = (c + 1 < ncolors) ? c + 1 : 0;
-      __syncthreads();
-      unsigned old = 0;
-      if (threadIdx.x == 0) old = bar_arrive(bar);
-      // overlap the barrier: next descriptor and L2 prefetch of the next tiles
-      if (threadIdx.x < CLW) ((unsigned*)&cl[cur ^ 1])[threadIdx.x] = ((const unsigned*)&plan[cn])[threadIdx.x];
-      __syncthreads();
-      const int64_t ntn = count_of(cn);
-      bool staged = false;
-      if ((int64_t)blockIdx.x < ntn) {
-        // a first tile that is a long column: its row ids go to shared memory now
-        const int64_t t0 = tile_of(cn, blockIdx.x);
-        const ColorLaunch& nx = cl[cur ^ 1];
-        int si = 0;
-        while (si + 1 < nx.nseg && t0 >= nx.seg[si + 1].b0) ++si;
-        const SegLaunch S = nx.seg[si];
-        if (FULL && (S.cls == UC_HUGE || S.cls == UC_LARGE) && t0 - S.b0 < S.n) {
-          stage_huge(V, S.c0 + (t0 - S.b0), dyn);
-          staged = true;
+      if (c + 1 < ncolors) {
+        if (!advance(c + 1)) return;
+      } else if (TV.n > 0) {
+        if (!sync()) return;
+      } else if (!last_epoch) {
+        if (!advance(0)) return;
+      }
+    }
+    if (TV.n > 0) {
+      for (int64_t u = blockIdx.x; u < TV.n; u += gridDim.x) tail_partial(V, TV, u, red_smem);
+      if (!sync()) return;
+      const int nT = min(TV.ctas, (int)gridDim.x);
+      if ((int)blockIdx.x < nT) {
+        // colours in order, one CTA per unit, a barrier of the nT CTAs between colours
+        for (int tc = 0; tc < TV.ncol; ++tc) {
+          for (int64_t u = TV.coff[tc] + blockIdx.x; u < TV.coff[tc + 1]; u += nT) tail_unit(V, TV, u, red_smem);
+          if (tc + 1 < TV.ncol) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+              const unsigned old = bar_arrive(bar + 32, (unsigned)nT);
+              ok = bar_wait(bar + 32, old, err) ? 1 : 0;
+            }
+            __syncthreads();
+            if (!ok) return;
+          }
         }
       }
-      for (int q = staged ? 1 : 0; q < PREFETCH_TILES; ++q) {
-        const int64_t qq = blockIdx.x + (int64_t)q * gridDim.x;
-        if (qq < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, tile_of(cn, qq));
-      }
-      if (threadIdx.x == 0) ok = bar_wait(bar, old, err) ? 1 : 0;
-      __syncthreads();
-      if (!ok) return;
-      cur ^= 1;
-      first_staged = staged;
+      if (!sync()) return;
+      for (int64_t u = blockIdx.x; u < TV.n; u += gridDim.x) tail_scatter(V, TV, u);
+      if (!last_epoch && !advance(0)) return;
     }
   }
 }
@@ -735,6 +932,136 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   return V;
 }
 
+// ---------------------------------------------------------------------------
+// tail colours: selection and the split of their columns' rows
+// ---------------------------------------------------------------------------
+constexpr int TAIL_MIN_COLOURS = 8;    // fewer tail colours: not worth the three phases
+constexpr int64_t TAIL_MAX_UNITS = 32; // units a tail colour may hold (one CTA each)
+
+__global__ void k_tail_rowcount(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
+                                int32_t* rcnt) {
+  for (int64_t u = blockIdx.x; u < n; u += gridDim.x) {
+    const int64_t j = col[u];
+    for (int64_t q = colptr[j] + threadIdx.x; q < colptr[j + 1]; q += blockDim.x) atomicAdd(&rcnt[idx_of(rowidx[q])], 1);
+  }
+}
+
+__global__ void k_tail_counts(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
+                              const int32_t* rcnt, int64_t* hc, int64_t* tc) {
+  GSTRIDE(u, n) {
+    const int64_t j = col[u];
+    int64_t t = 0;
+    for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) t += rcnt[idx_of(rowidx[q])] > 1;
+    tc[u] = t;
+    hc[u] = colptr[j + 1] - colptr[j] - t;
+  }
+}
+
+// one thread per unit, entries in column order: a deterministic split
+__global__ void k_tail_fill(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
+                            const int32_t* rcnt, const int64_t* hptr, const int64_t* tptr, uint32_t* hrow,
+                            uint32_t* trow) {
+  GSTRIDE(u, n) {
+    const int64_t j = col[u];
+    int64_t h = hptr[u], t = tptr[u];
+    for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
+      const uint32_t e = rowidx[q];
+      if (rcnt[idx_of(e)] > 1) trow[t++] = e;
+      else hrow[h++] = e;
+    }
+  }
+}
+
+// The tail: the longest run of last colours that hold no slack, no simplex
+// block and at most TAIL_MAX_UNITS singleton columns each (pattern +-1
+// matrices, single problems).
+void ensure_tail(Problem& P) {
+  if (P.tail_T >= 0) return;
+  const int C = P.ncolors;
+  P.tail_T = C;
+  if (P.nbatch > 0 || P.has_val || C < TAIL_MIN_COLOURS + 1) return;
+  int T = C;
+  while (T > 1) {
+    const ColorPlan& cp = P.plan[T - 1];
+    int64_t units = 0;
+    bool ok = cp.srow1 == cp.srow0;
+    for (auto& sg : cp.segs) {
+      ok = ok && sg.cls != UC_BLOCK;
+      units += sg.u1 - sg.u0;
+    }
+    if (!ok || units > TAIL_MAX_UNITS) break;
+    --T;
+  }
+  if (C - T < TAIL_MIN_COLOURS) return;
+  std::vector<int64_t> col, coff{0};
+  int64_t umax = 1;
+  for (int c = T; c < C; ++c) {
+    int64_t uc = 0;
+    for (auto& sg : P.plan[c].segs) uc += sg.u1 - sg.u0;
+    umax = std::max(umax, uc);
+  }
+  for (int c = T; c < C; ++c) {
+    for (auto& sg : P.plan[c].segs)
+      for (int64_t u = 0; u < sg.u1 - sg.u0; ++u) col.push_back(sg.c0 + u);
+    coff.push_back((int64_t)col.size());
+  }
+  cudaStream_t s = P.stream;
+  const int64_t n = (int64_t)col.size();
+  Arena tmp(s);
+  P.tail_col = P.mem.alloc<int64_t>(n);
+  P.tail_coff = P.mem.alloc<int64_t>(C - T + 1);
+  TH_CUDA(cudaMemcpyAsync(P.tail_col, col.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaMemcpyAsync(P.tail_coff, coff.data(), (C - T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  int32_t* rcnt = tmp.alloc<int32_t>(P.M + 1);
+  TH_CUDA(cudaMemsetAsync(rcnt, 0, (P.M + 1) * sizeof(int32_t), s));
+  k_tail_rowcount<<<grid_for(n * 256, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt);
+  TH_LAUNCHED();
+  int64_t* hc = tmp.alloc<int64_t>(n + 1);
+  int64_t* tc = tmp.alloc<int64_t>(n + 1);
+  k_tail_counts<<<grid_for(n, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, hc, tc);
+  TH_LAUNCHED();
+  P.tail_hptr = P.mem.alloc<int64_t>(n + 1);
+  P.tail_tptr = P.mem.alloc<int64_t>(n + 1);
+  exclusive_scan_i64(hc, P.tail_hptr, n, tmp, s);
+  exclusive_scan_i64(tc, P.tail_tptr, n, tmp, s);
+  int64_t tot[2];
+  TH_CUDA(cudaMemcpyAsync(&tot[0], P.tail_hptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(&tot[1], P.tail_tptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  P.tail_hrow = P.mem.alloc<uint32_t>(tot[0] + 1);
+  P.tail_trow = P.mem.alloc<uint32_t>(tot[1] + 1);
+  k_tail_fill<<<grid_for(n, 64), 64, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, P.tail_hptr, P.tail_tptr,
+                                             P.tail_hrow, P.tail_trow);
+  TH_LAUNCHED();
+  P.tail_h = P.mem.alloc<float>(n);
+  P.tail_d = P.mem.alloc<float>(n);
+  TH_CUDA(cudaStreamSynchronize(s));  // col / coff must outlive their copies
+  P.tail_T = T;
+  P.tail_n = n;
+  P.tail_ncol = C - T;
+  P.tail_ctas = (int)umax;
+}
+
+static TailView make_tail_view(const Problem& P) {
+  TailView T{};
+  if (P.tail_T < 0 || P.tail_T >= P.ncolors) return T;
+  T.n = P.tail_n;
+  T.ncol = P.tail_ncol;
+  T.col = P.tail_col;
+  T.coff = P.tail_coff;
+  T.hptr = P.tail_hptr;
+  T.hrow = P.tail_hrow;
+  T.tptr = P.tail_tptr;
+  T.trow = P.tail_trow;
+  T.h = P.tail_h;
+  T.d = P.tail_d;
+  T.ctas = P.tail_ctas;
+  return T;
+}
+
+// colours the colour-by-colour sweep runs (the rest, if any, are the tail)
+static int head_colours(const Problem& P) { return (P.tail_T >= 0 && P.tail_T < P.ncolors) ? P.tail_T : P.ncolors; }
+
 // Launches of one epoch in colour order (colored) or one launch over all
 // units (async).
 void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
@@ -780,7 +1107,9 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
     TH_CUDA(cudaGetLastError());
     return;
   }
-  for (int c = 0; c < (int)P.plan.size(); ++c) {
+  ensure_tail(P);
+  const int Ch = head_colours(P);
+  for (int c = 0; c < Ch; ++c) {
     const ColorPlan& cp = P.plan[c];
     ColorLaunch CL{};
     CL.color = c;
@@ -794,6 +1123,18 @@ void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
       tot += ctas_for(UC_COUNT, cp.srow1 - cp.srow0, P.small_g);
     }
     launch(CL, tot);
+  }
+  const TailView TV = make_tail_view(P);
+  if (TV.n > 0) {
+    const unsigned g = (unsigned)std::min<int64_t>(TV.n, 152 * 8);
+    k_tail_partial<<<g, STEP_T, 0, s>>>(V, TV);
+    TH_LAUNCHED();
+    for (int tc = 0; tc < TV.ncol; ++tc) {
+      k_tail_colour<<<TV.ctas, STEP_T, 0, s>>>(V, TV, tc);
+      TH_LAUNCHED();
+    }
+    k_tail_scatter<<<g, STEP_T, 0, s>>>(V, TV);
+    TH_LAUNCHED();
   }
   TH_CUDA(cudaGetLastError());
 }
@@ -827,10 +1168,10 @@ static void ensure_sweep_plan(Problem& P) {
   TH_CUDA(cudaMemcpyAsync(dp, h.data(), h.size() * sizeof(ColorLaunch), cudaMemcpyHostToDevice, P.stream));
   TH_CUDA(cudaMemcpyAsync(dn, nt.data(), nt.size() * sizeof(int64_t), cudaMemcpyHostToDevice, P.stream));
   if (!P.bar) {
-    P.bar = P.mem.alloc<unsigned>(2);
+    P.bar = P.mem.alloc<unsigned>(64);  // [0]: grid barrier, [32]: tail-phase barrier (its own 128-byte line)
     P.err = P.mem.alloc<int>(1);
   }
-  TH_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), P.stream));
+  TH_CUDA(cudaMemsetAsync(P.bar, 0, 64 * sizeof(unsigned), P.stream));
   TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
   TH_CUDA(cudaStreamSynchronize(P.stream));
   P.d_plan = dp;
@@ -840,20 +1181,17 @@ static void ensure_sweep_plan(Problem& P) {
 
 // The lean sweep serves problems whose colours hold only small / medium
 // columns and slacks (no long columns, no simplex blocks).
-bool sweep_lean_possible(const Problem& P) {
-  for (auto& cp : P.plan)
-    for (auto& sg : cp.segs)
+// (the tail colours run outside the colour loop: only the head colours count)
+bool sweep_lean_possible(Problem& P) {
+  ensure_tail(P);
+  const int Ch = head_colours(P);
+  for (int c = 0; c < Ch; ++c)
+    for (auto& sg : P.plan[c].segs)
       if (sg.cls == UC_HUGE || sg.cls == UC_LARGE || sg.cls == UC_BLOCK) return false;
   return true;
 }
 
-static bool sweep_lean(const Problem& P) {
-  if (P.force_full) return false;
-  for (auto& cp : P.plan)
-    for (auto& sg : cp.segs)
-      if (sg.cls == UC_HUGE || sg.cls == UC_LARGE || sg.cls == UC_BLOCK) return false;
-  return true;
-}
+static bool sweep_lean(Problem& P) { return !P.force_full && sweep_lean_possible(P); }
 
 // Grid of the cooperative sweep (0: not available on this device).
 int sweep_grid(Problem& P) {
@@ -871,7 +1209,7 @@ int sweep_grid(Problem& P) {
 
 void reset_sweep_flags(Problem& P) {
   if (!P.bar) return;
-  TH_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), P.stream));
+  TH_CUDA(cudaMemsetAsync(P.bar, 0, 64 * sizeof(unsigned), P.stream));
   TH_CUDA(cudaMemsetAsync(P.err, 0, sizeof(int), P.stream));
 }
 
@@ -977,11 +1315,14 @@ void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int
   ensure_sweep_plan(P);
   const int grid = sweep_grid(P);
   TH_CHECK(grid > 0, THETIS_E_CUDA, "cooperative launch not available");
+  ensure_tail(P);
   StepView V = make_view(P, a, use_ubar, use_xbar);
   const ColorLaunch* plan = (const ColorLaunch*)P.d_plan;
   const int64_t* nt = P.d_ntiles;
-  int C = P.ncolors;
-  void* args[] = {(void*)&V, (void*)&plan, (void*)&nt, (void*)&C, (void*)&epochs, (void*)&P.bar, (void*)&P.err};
+  int C = head_colours(P);
+  TailView TV = make_tail_view(P);
+  void* args[] = {(void*)&V,      (void*)&plan,  (void*)&nt,    (void*)&C,
+                  (void*)&epochs, (void*)&P.bar, (void*)&P.err, (void*)&TV};
   if (sweep_lean(P))
     TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep<false>, dim3(grid), dim3(STEP_T), args, 0, P.stream));
   else

@@ -289,6 +289,33 @@ def test_async_mode_converges_to_oracle_solution():
     assert np.max(np.abs(gpu_full_x(h) - x_o)) <= 1e-2
 
 
+@pytest.mark.parametrize("step_rule", [0, 1])
+def test_tail_colours_match_oracle_and_engines(step_rule):
+    """A power-law graph whose last 22 colours hold only a few columns each:
+    they run as the three tail phases (partial dots, one-CTA colour chain,
+    deferred scatter) in both engines; the iterate matches the oracle's serial
+    sweep and the engines agree bit for bit."""
+    g = is_graph(8000, 120000, 2)
+    T = gpu()
+    kw = dict(beta=100.0, epochs=30, refresh_every=10, step_rule=step_rule)
+    h0, lp = _pair("is", g, seed=0)
+    h0.solve(engine=0, **kw)
+    h1 = build_gpu("is", g, seed=0)
+    h1.solve(engine=1, **kw)
+    x0, x1 = gpu_full_x(h0), gpu_full_x(h1)
+    assert np.array_equal(x0, x1)
+    x_o, _ = lp.solve(color=lp.color(0)[0], **kw)
+    assert np.max(np.abs(x0 - x_o)) <= X_TOL
+    # with centres: xbar, ubar given
+    rng = np.random.default_rng(1)
+    ub = rng.normal(size=g.m).astype(np.float32)
+    xb = rng.random(g.n + g.m).astype(np.float32)
+    h2, _ = _pair("is", g, seed=0)
+    h2.solve(ubar=ub, xbar=xb, **kw)
+    x_o2, _ = lp.solve(color=lp.color(0)[0], ubar=ub.astype(np.float64), xbar=xb.astype(np.float64), **kw)
+    assert np.max(np.abs(gpu_full_x(h2) - x_o2)) <= X_TOL
+
+
 @pytest.mark.parametrize("ctas", [1, 4, 64])
 def test_async_mode_capped_concurrency_converges(ctas):
     """The asynchronous scheme with at most `ctas` CTAs stepping at once reaches
