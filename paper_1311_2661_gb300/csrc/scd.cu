@@ -936,7 +936,7 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
 // tail colours: selection and the split of their columns' rows
 // ---------------------------------------------------------------------------
 constexpr int TAIL_MIN_COLOURS = 8;    // fewer tail colours: not worth the three phases
-constexpr int64_t TAIL_MAX_UNITS = 32; // units a tail colour may hold (one CTA each)
+constexpr int64_t TAIL_MAX_UNITS = 152; // units a tail colour may hold (one CTA each)
 
 __global__ void k_tail_rowcount(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
                                 int32_t* rcnt) {
