@@ -394,18 +394,19 @@ thetis_status thetis_round_batch(thetis_handle* h, uint64_t seed, int32_t reps, 
 /*
  * Request server with continuous batching (deployment layer; the paper solves
  * one LP at a time).  Worker threads each own a CUDA stream; a free worker
- * takes the oldest queued request and every other queued VC / IS request with
- * the same solve parameters (up to max_batch, within the memory budget) and
- * solves them together through thetis_build_batch, so requests arriving while
+ * takes the smallest queued request (by estimated device bytes; the oldest
+ * instead once it has waited 10 s) and every other queued VC / IS request with
+ * the same solve parameters and a size within a factor 4 (up to max_batch,
+ * within the memory budget) and solves them together through
+ * thetis_build_batch, so requests arriving while
  * others run join the next batch and different workers' work overlaps on the
  * GPU.  MC requests are solved one per worker.  Admission: a request is started
  * only while the estimated device bytes of the running requests plus its own
  * stay within hbm_budget_bytes; a request larger than the whole budget is
  * refused at submit time with THETIS_E_BUDGET.
- * Within a batch, tol applies to the largest residual of its members: a request
- * solved in a batch runs the batch's epoch count (at least as many as alone);
- * with tol = 0 (a fixed epoch count) its result equals the result alone up to
- * FP32 summation order.
+ * Within a batch, tol applies to every member separately: a request stops at
+ * the check where its own rho <= tol, the check where it stops when solved
+ * alone, and its result equals the result alone up to FP32 summation order.
  */
 typedef struct {
   int32_t kind;            /* THETIS_ROUND_VC, THETIS_ROUND_IS or THETIS_ROUND_MC */

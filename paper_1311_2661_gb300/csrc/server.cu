@@ -1,8 +1,9 @@
 // Request server: LP-rounding solves submitted one by one, served with
 // continuous batching.  Worker threads ("slots") each own a CUDA stream; a free
-// worker takes the oldest queued request and every other queued vertex-cover /
-// independent-set request with the same solve parameters (up to max_batch and
-// the memory budget) and solves them as one block-diagonal batch
+// worker takes the smallest queued request (the oldest, once a request has
+// waited MAX_WAIT_MS) and every other queued vertex-cover / independent-set
+// request with the same solve parameters and a similar size (up to max_batch
+// and the memory budget) and solves them as one block-diagonal batch
 // (thetis_build_batch), so requests that arrive while others are on the GPU
 // join the next batch and the work of different slots overlaps on the device.
 // Multiway-cut requests are solved one per slot.  Admission is by an estimate
@@ -64,6 +65,9 @@ void fail(Req* r, thetis_status st) {
   r->res.status = st;
   if (r->res.message[0] == 0) std::snprintf(r->res.message, sizeof(r->res.message), "%s", thetis_last_error());
 }
+
+constexpr double MAX_WAIT_MS = 10000.0;  // a request waiting longer goes first
+constexpr size_t SIZE_RATIO = 4;         // batched requests differ in size by at most this factor
 
 bool same_params(const thetis_request& a, const thetis_request& b) {
   return a.beta == b.beta && a.epochs == b.epochs && a.tol == b.tol && a.refresh_every == b.refresh_every &&
@@ -212,17 +216,30 @@ void thetis_server::work() {
     size_t bytes = 0;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return stop || (!queue.empty() && in_flight + queue.front()->bytes <= budget); });
+      // head of the next batch: the smallest queued request (shortest job
+      // first), or the oldest once it has waited longer than MAX_WAIT_MS
+      auto pick = [&]() {
+        auto head = queue.begin();
+        if (ms_between(queue.front()->t_submit, clk::now()) < MAX_WAIT_MS)
+          for (auto it = queue.begin(); it != queue.end(); ++it)
+            if ((*it)->bytes < (*head)->bytes) head = it;
+        return head;
+      };
+      cv.wait(lk, [&] { return stop || (!queue.empty() && in_flight + (*pick())->bytes <= budget); });
       if (stop && queue.empty()) break;
-      if (queue.empty() || in_flight + queue.front()->bytes > budget) continue;
-      Req* r0 = queue.front();
-      queue.pop_front();
+      if (queue.empty()) continue;
+      auto hi = pick();
+      if (in_flight + (*hi)->bytes > budget) continue;
+      Req* r0 = *hi;
+      queue.erase(hi);
       batch.push_back(r0);
       bytes = r0->bytes;
       if (r0->q.kind != THETIS_ROUND_MC && max_batch > 1) {
+        // same parameters and a similar size (a batch ends with its slowest instance)
         for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
           Req* r = *it;
-          if (r->q.kind != THETIS_ROUND_MC && same_params(r->q, r0->q) && in_flight + bytes + r->bytes <= budget) {
+          if (r->q.kind != THETIS_ROUND_MC && same_params(r->q, r0->q) && r->bytes <= SIZE_RATIO * r0->bytes &&
+              r0->bytes <= SIZE_RATIO * r->bytes && in_flight + bytes + r->bytes <= budget) {
             batch.push_back(r);
             bytes += r->bytes;
             it = queue.erase(it);
