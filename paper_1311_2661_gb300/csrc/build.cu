@@ -654,6 +654,8 @@ __device__ __forceinline__ void row_struct_members(const JPView& V, int64_t i, i
 // its (all coloured) higher-priority neighbours do not hold and releases its
 // lower-priority neighbours.  Units of one frontier are pairwise non-adjacent.
 constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA serves a unit
+constexpr uint32_t ADJ_BIG = 0x80000000u;  // adjacency entry flag: that neighbour is served by a CTA
+constexpr uint32_t ADJ_NONE = 0xffffffffu; // no entry
 
 __global__ void k_adj_count(JPView V, int64_t Us, int64_t* acnt, int32_t* nhigh) {
   int lane = threadIdx.x & 31;
@@ -731,8 +733,10 @@ __global__ void k_adj_fill(JPView V, int64_t Us, const int64_t* aptr, const int3
         int64_t oh = hoff + warp_excl(ch, lane, &th), ol = loff + warp_excl(cl, lane, &tl);
         if (act)
           row_struct_members(V, i, u, [&](int64_t w) {
-            if (higher(V, w, u)) adj[oh++] = (uint32_t)w;
-            else adj[ol++] = (uint32_t)w;
+            // bit 31: the neighbour's own adjacency is long (a CTA serves it)
+            const uint32_t e = (uint32_t)w | ((aptr[w + 1] - aptr[w] > JP_BIG) ? ADJ_BIG : 0u);
+            if (higher(V, w, u)) adj[oh++] = e;
+            else adj[ol++] = e;
           });
         hoff += th;
         loff += tl;
@@ -757,9 +761,9 @@ __device__ __forceinline__ unsigned long long color_mask(const uint32_t* adj, co
     uint32_t e[4];
     int cw[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : 0xffffffffu;
+    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : ADJ_NONE;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) cw[t] = (e[t] != 0xffffffffu) ? __ldcg(color + e[t]) : -1;
+    for (int t = 0; t < 4; ++t) cw[t] = (e[t] != ADJ_NONE) ? __ldcg(color + (e[t] & ~ADJ_BIG)) : -1;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
@@ -768,22 +772,43 @@ __device__ __forceinline__ unsigned long long color_mask(const uint32_t* adj, co
 }
 
 // Release the lower-priority neighbours adj[a0, a1); the loop is uniform over
-// the `step` threads that run it (a warp or a CTA).
-__device__ __forceinline__ void release(const uint32_t* adj, const int64_t* aptr, int32_t* cnt, int64_t a0, int64_t a1,
-                                        int64_t start, int step, int lane, uint32_t* next_s, int64_t* nnext_s,
-                                        uint32_t* next_b, int64_t* nnext_b) {
-  for (int64_t qb = a0; qb < a1; qb += step) {
-    const int64_t q = qb + start;
-    bool pb = false, ps = false;
-    uint32_t w = 0;
-    if (q < a1) {
-      w = adj[q];
-      if (atomicSub(&cnt[w], 1) == 1) {
-        pb = aptr[w + 1] - aptr[w] > JP_BIG;
-        ps = !pb;
-      }
+// the `step` threads that run it (a warp or a CTA).  Four entries per thread
+// at a time: their counter decrements are independent, and the units they
+// release go to the next frontier with one reservation per list per warp.
+__device__ __forceinline__ void release(const uint32_t* adj, int32_t* cnt, int64_t a0, int64_t a1, int64_t start,
+                                        int step, int lane, uint32_t* next_s, int64_t* nnext_s, uint32_t* next_b,
+                                        int64_t* nnext_b) {
+  for (int64_t qb = a0; qb < a1; qb += 4 * (int64_t)step) {
+    uint32_t e[4];
+    bool rel[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t q = qb + start + (int64_t)t * step;
+      e[t] = (q < a1) ? adj[q] : ADJ_NONE;
     }
-    warp_push(pb, ps, w, lane, next_s, nnext_s, next_b, nnext_b);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) rel[t] = e[t] != ADJ_NONE && atomicSub(&cnt[e[t] & ~ADJ_BIG], 1) == 1;
+    int nb = 0, ns = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      nb += rel[t] && (e[t] & ADJ_BIG);
+      ns += rel[t] && !(e[t] & ADJ_BIG);
+    }
+    int tb, ts;
+    const int ob = warp_excl(nb, lane, &tb), os = warp_excl(ns, lane, &ts);
+    unsigned long long bb = 0, bs = 0;
+    if (lane == 0) {
+      if (tb) bb = atomicAdd((unsigned long long*)nnext_b, (unsigned long long)tb);
+      if (ts) bs = atomicAdd((unsigned long long*)nnext_s, (unsigned long long)ts);
+    }
+    bb = __shfl_sync(0xffffffffu, bb, 0) + ob;
+    bs = __shfl_sync(0xffffffffu, bs, 0) + os;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (rel[t]) {
+        if (e[t] & ADJ_BIG) next_b[bb++] = e[t] & ~ADJ_BIG;
+        else next_s[bs++] = e[t];
+      }
   }
 }
 
@@ -869,7 +894,7 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
         __syncthreads();
       }
       if (threadIdx.x == 0) R.color[u] = chosen;
-      release(R.adj, R.aptr, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+      release(R.adj, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
     }
     // the rest: one warp each
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -885,7 +910,7 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
         base += 64;
       }
       if (lane == 0) R.color[u] = chosen;
-      release(R.adj, R.aptr, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+      release(R.adj, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
     }
     if (nr > 1 && !jp_barrier(R.bar, R.err)) return;
   }
@@ -1346,6 +1371,7 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   int32_t* color = tmp.alloc<int32_t>(U + 1);
   TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));
   JPView V{raw.colptr, raw.rowidx, orowptr, csr_p, colof, unit_of_col, slack_unit, ufirst, ulen, unnz, uh, Us, slack_row};
+  TH_CHECK(Us < (int64_t)ADJ_BIG - 1, THETIS_E_INVALID, "too many coordinate units (adjacency ids are 31-bit)");
   if (Us > 0) {
     int dev = 0, sms = 0, coop = 0, per = 0;
     TH_CUDA(cudaGetDevice(&dev));
