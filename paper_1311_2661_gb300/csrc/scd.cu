@@ -1598,15 +1598,22 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
   }
 }
 
+// one warp per quantity: lane l folds partials l, l + 32, ... in order, then a
+// fixed shuffle tree (the same order every call: deterministic)
 __global__ void k_check_final(const double* red, double* out) {
-  int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= NRED) return;
-  double a = red[(int64_t)q * CHECK_BLOCKS];
-  for (int t = 1; t < CHECK_BLOCKS; ++t) {
-    double v = red[(int64_t)q * CHECK_BLOCKS + t];
-    a = (q == 0 || q == 2) ? fmax(a, v) : a + v;
+  const bool mx = q == 0 || q == 2;
+  double a = 0.0;  // maxima are of non-negative values
+  for (int t = lane; t < CHECK_BLOCKS; t += 32) {
+    const double v = red[(int64_t)q * CHECK_BLOCKS + t];
+    a = mx ? fmax(a, v) : a + v;
   }
-  out[q] = a;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double b = __shfl_xor_sync(0xffffffffu, a, o);
+    a = mx ? fmax(a, b) : a + b;
+  }
+  if (lane == 0) out[q] = a;
 }
 
 // ---------------------------------------------------------------------------
@@ -1732,7 +1739,7 @@ void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_x
     TH_CUDA(cudaMemsetAsync(P.brho, 0, P.nbatch * sizeof(unsigned long long), s));
   k_check<<<CHECK_BLOCKS, 256, 0, s>>>(make_check_view(P, a, use_ubar, use_xbar), P.red);
   TH_LAUNCHED();
-  k_check_final<<<1, 32, 0, s>>>(P.red, P.red_out);
+  k_check_final<<<1, 32 * NRED, 0, s>>>(P.red, P.red_out);
   TH_LAUNCHED();
   TH_CUDA(cudaMemcpyAsync(P.h_red, P.red_out, NRED * sizeof(double), cudaMemcpyDeviceToHost, s));
   TH_CUDA(cudaStreamSynchronize(s));
