@@ -370,6 +370,10 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
   const bool act = q < k;
   const int64_t jq = j0 + (act ? q : 0);
   const int64_t p0 = act ? V.colptr[jq] : 0, p1 = act ? V.colptr[jq + 1] : 0;
+  // lane q < k's own column: loads that do not depend on r go first
+  const float xq0 = (lane < k) ? __ldcg(V.x + j0 + lane) : 0.f;
+  const float ctq = (lane < k) ? V.ct[j0 + lane] : 0.f;
+  const float xbq = (lane < k && V.xbar) ? V.xbar[j0 + lane] : 0.f;
   uint32_t ce[CACHE];
   float cr[CACHE];
   float acc = 0.f;
@@ -400,9 +404,8 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
   float gq = __shfl_sync(0xffffffffu, acc, (lane < k ? lane : 0) * S);
   float xq = 0.f, y = -INFINITY;
   if (lane < k) {
-    xq = __ldcg(V.x + j0 + lane);
-    float xb = V.xbar ? V.xbar[j0 + lane] : 0.f;
-    float g = V.ct[j0 + lane] + V.beta * gq + (xq - xb) * V.inv_beta;
+    xq = xq0;
+    float g = ctq + V.beta * gq + (xq - xbq) * V.inv_beta;
     y = xq - g / L;
   }
   // simplex projection: for lane j, c_j = #{i: y_i >= y_j}, S_j = sum of those y_i;
