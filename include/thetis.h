@@ -294,8 +294,12 @@ thetis_status thetis_get_duals(thetis_handle* h, float* out, int32_t out_mem);
  *      larger-id end of every picked edge; best of `reps` by weight.
  *  MC: CKR region growing (App. B.3) with radius rho ~ U[0,1) and a random
  *      terminal order; best of `reps` by cut cost.
- * Random draws: U(seed, rep, stream, vertex) from splitmix64.
- * labels_out[n] (uint8, vertex order): VC/IS membership, MC label in [0,k).
+ *  SC / SC_RAND (handles of thetis_build_sc): covering repair, then the
+ *      f-threshold or the randomized rounding (see thetis_build_sc).
+ *  MAP (handles of thetis_build_map): node rounding; reps ignored.
+ * Random draws: U(seed, rep, stream, index) from splitmix64.
+ * labels_out[n] (uint8, vertex order): VC/IS membership, MC label in [0,k);
+ * for SC one byte per set (chosen), for MAP the label of every variable.
  * out_mem says where labels_out lives.  info may be NULL.
  */
 thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_t reps,
