@@ -10,6 +10,7 @@
 // of the device bytes a request needs against a fixed budget.
 #include <chrono>
 #include <cstdio>
+#include <string>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -210,7 +211,11 @@ void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
 void thetis_server::work() {
   thetis::set_coop_allowed(false);
   cudaStream_t s = nullptr;
-  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  const cudaError_t se = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (se != cudaSuccess) {
+    s = nullptr;
+    thetis::set_error(std::string("server worker: cudaStreamCreateWithFlags: ") + cudaGetErrorString(se));
+  }
   while (true) {
     std::vector<Req*> batch;
     size_t bytes = 0;
@@ -252,7 +257,11 @@ void thetis_server::work() {
     }
     const auto t0 = clk::now();
     for (Req* r : batch) r->t_start = t0;
-    run_batch(batch, s);
+    if (s) {
+      run_batch(batch, s);
+    } else {  // no stream of its own: every request fails with the reason
+      for (Req* r : batch) fail(r, THETIS_E_CUDA);
+    }
     const auto t1 = clk::now();
     {
       std::lock_guard<std::mutex> lk(mu);
