@@ -479,9 +479,8 @@ __device__ __forceinline__ void step_slacks(const StepView& V, int64_t i0, int64
 }
 
 // One tile of a colour: the CTA serves tile `tile` of the segment it falls in.
-// FULL = false compiles only the small / medium column and slack paths (for
-// problems without long columns or simplex blocks): fewer registers, more CTAs
-// per SM.
+// FULL = false compiles the paths of everything but long columns (no shared
+// memory staging): fewer registers, more CTAs per SM.
 template <bool FULL = true>
 __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch* segs, int nseg, int64_t tile,
                                              float* red_smem, unsigned char* dyn, bool staged = false) {
@@ -509,10 +508,8 @@ __device__ __forceinline__ void process_tile(const StepView& V, const SegLaunch*
     case UC_S4: small_tile_w<4>(V, S, b); break;
     case UC_S2: small_tile_w<2>(V, S, b); break;
     case UC_BLOCK: {
-      if constexpr (FULL) {
-        int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
-        if (u < S.n) step_block(V, S.c0 + u * V.k, lane);
-      }
+      int64_t u = b * (STEP_T / 32) + (threadIdx.x >> 5);
+      if (u < S.n) step_block(V, S.c0 + u * V.k, lane);
       break;
     }
     default: {  // slacks
@@ -1182,15 +1179,15 @@ static void ensure_sweep_plan(Problem& P) {
   P.d_ntiles = dn;
 }
 
-// The lean sweep serves problems whose colours hold only small / medium
-// columns and slacks (no long columns, no simplex blocks).
+// The lean sweep serves problems whose head colours hold no long column (no
+// shared-memory staging).
 // (the tail colours run outside the colour loop: only the head colours count)
 bool sweep_lean_possible(Problem& P) {
   ensure_tail(P);
   const int Ch = head_colours(P);
   for (int c = 0; c < Ch; ++c)
     for (auto& sg : P.plan[c].segs)
-      if (sg.cls == UC_HUGE || sg.cls == UC_LARGE || sg.cls == UC_BLOCK) return false;
+      if (sg.cls == UC_HUGE || sg.cls == UC_LARGE) return false;
   return true;
 }
 
