@@ -76,8 +76,8 @@ WORKLOADS = {
 DEFAULT = "is-chunglu-n2^20-m1.6e7"
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
 # DRAM bytes per epoch of the persistent sweep from one ncu capture
-# (ncu capture of one 10-epoch launch on this workload: 3.13 GB read + 2.48 GB written)
-SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 562_000_000}
+# (ncu capture of one 10-epoch launch on this workload: 3.19 GB read + 2.58 GB written)
+SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 577_000_000}
 L2_BYTES = 129 * 1024 * 1024
 SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
 
