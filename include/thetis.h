@@ -464,6 +464,20 @@ thetis_status thetis_get_colors(thetis_handle* h, int32_t* out, int64_t* n_units
 thetis_status thetis_sync(thetis_handle* h);
 thetis_status thetis_destroy(thetis_handle* h);
 
+/*
+ * Library-wide, current device: the library allocates its device memory from
+ * its own stream-ordered pool, and memory that builds and destroyed handles
+ * free stays reserved there for the next build instead of going back to the
+ * device (no new mappings per build).  thetis_cache_info reports the pool's
+ * reserved and in-use bytes (either pointer may be NULL; 0 and 0 before the
+ * first allocation).  thetis_trim_cache gives unused reserve back until at
+ * most keep_bytes stay reserved (memory in use is never touched); an
+ * allocation that fails also trims the pool once and retries.
+ * Errors: THETIS_E_CUDA.
+ */
+thetis_status thetis_cache_info(uint64_t* reserved_bytes, uint64_t* used_bytes);
+thetis_status thetis_trim_cache(uint64_t keep_bytes);
+
 #ifdef __cplusplus
 }
 #endif

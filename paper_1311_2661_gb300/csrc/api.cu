@@ -669,6 +669,27 @@ thetis_status thetis_destroy(thetis_handle* h) {
   return THETIS_OK;
 }
 
+thetis_status thetis_cache_info(uint64_t* reserved_bytes, uint64_t* used_bytes) {
+  return guard(nullptr, [&] {
+    int dev = 0;
+    TH_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = lib_pool(dev);
+    uint64_t r = 0, u = 0;
+    TH_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    TH_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    if (reserved_bytes) *reserved_bytes = r;
+    if (used_bytes) *used_bytes = u;
+  });
+}
+
+thetis_status thetis_trim_cache(uint64_t keep_bytes) {
+  return guard(nullptr, [&] {
+    int dev = 0;
+    TH_CUDA(cudaGetDevice(&dev));
+    TH_CUDA(cudaMemPoolTrimTo(lib_pool(dev), (size_t)keep_bytes));
+  });
+}
+
 namespace {
 // In-process cache of tuned launch shapes, keyed by problem shape.
 struct TuneKey {

@@ -19,14 +19,42 @@ static int bits_for(int64_t n) {
 
 #define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// Histogram increment with the lanes of a warp that share a key folded into
-// one atomic (colour histograms have only a handful of distinct keys).
-__device__ __forceinline__ void hist_add(int64_t* cnt, uint32_t key, bool valid) {
+// Colour histograms have only a handful of distinct keys per warp but every
+// warp of the grid hits the same few bins, so counts go to per-block shared
+// counters when the bins fit (HIST_SMEM_BINS), then one global atomic per bin
+// and block; otherwise the lanes of a warp that share a key fold into one
+// global atomic.
+constexpr int64_t HIST_SMEM_BINS = 8192;
+constexpr int HIST_GRID = 304;  // blocks of a shared-counter histogram kernel
+
+__device__ __forceinline__ void hist_init(int* sh, int64_t nbins, bool use_sh) {
+  if (use_sh)
+    for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void hist_add(int64_t* cnt, int* sh, bool use_sh, uint32_t key, bool valid) {
   unsigned act = __ballot_sync(0xffffffffu, valid);
   if (!valid) return;
   unsigned peers = __match_any_sync(act, key);
   int lane = threadIdx.x & 31;
-  if (lane == __ffs(peers) - 1) atomicAdd((unsigned long long*)&cnt[key], (unsigned long long)__popc(peers));
+  if (lane == __ffs(peers) - 1) {
+    if (use_sh) atomicAdd(&sh[key], __popc(peers));
+    else atomicAdd((unsigned long long*)&cnt[key], (unsigned long long)__popc(peers));
+  }
+}
+
+__device__ __forceinline__ void hist_flush(int64_t* cnt, const int* sh, int64_t nbins, bool use_sh) {
+  if (!use_sh) return;
+  __syncthreads();
+  for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (sh[b]) atomicAdd((unsigned long long*)&cnt[b], (unsigned long long)sh[b]);
+}
+
+static void hist_launch_shape(int64_t n, int64_t nbins, int* grid, size_t* smem) {
+  const bool use_sh = nbins <= HIST_SMEM_BINS;
+  *grid = use_sh ? grid_for(n, 256, HIST_GRID) : grid_for(n, 256);
+  *smem = use_sh ? (size_t)nbins * sizeof(int) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -634,15 +662,6 @@ __device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
   return a < b;
 }
 
-// Structural units conflicting with structural unit u in row i (CSR order).
-template <class F>
-__device__ __forceinline__ void row_struct_members(const JPView& V, int64_t i, int64_t u, F f) {
-  for (int64_t q = V.rowptr[i]; q < V.rowptr[i + 1]; ++q) {
-    int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
-    if (w >= 0 && w != u) f(w);
-  }
-}
-
 // Jones-Plassmann over the structural units, driven by data flow.  Slack units
 // come last in the priority order and never conflict with one another, so each
 // takes, after all structural units are coloured, the smallest colour its row
@@ -657,27 +676,47 @@ constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA se
 constexpr uint32_t ADJ_BIG = 0x80000000u;  // adjacency entry flag: that neighbour is served by a CTA
 constexpr uint32_t ADJ_NONE = 0xffffffffu; // no entry
 
-__global__ void k_adj_count(JPView V, int64_t Us, int64_t* acnt, int32_t* nhigh) {
-  int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < Us; u += nwarps) {
-    int64_t f0 = V.ufirst[u];
-    int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
-    int64_t c = 0, h = 0;
-    for (int64_t p = p0 + lane; p < p1; p += 32)
-      row_struct_members(V, V.rowidx[p], u, [&](int64_t w) {
-        ++c;
-        h += higher(V, w, u);
-      });
-    for (int o = 16; o > 0; o >>= 1) {
-      c += __shfl_xor_sync(0xffffffffu, c, o);
-      h += __shfl_xor_sync(0xffffffffu, h, o);
+// Per CSR entry: the structural unit of its column, ADJ_NONE for a fixed column.
+__global__ void k_row_units(JPView V, int64_t nnz, uint32_t* rowunit) {
+  GSTRIDE(q, nnz) {
+    const int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
+    rowunit[q] = w >= 0 ? (uint32_t)w : ADJ_NONE;
+  }
+}
+
+// Per structural unit its priority key (non-zeros, hash) as one 16-byte word.
+__global__ void k_unit_prio(JPView V, int64_t Us, ulonglong2* key) {
+  GSTRIDE(u, Us) key[u] = make_ulonglong2((unsigned long long)V.unnz[u], (unsigned long long)V.uh[u]);
+}
+
+// Structural unit a before structural unit b in the colouring order.
+__device__ __forceinline__ bool ahead(ulonglong2 ka, uint32_t a, ulonglong2 kb, uint32_t b) {
+  if (ka.x != kb.x) return ka.x > kb.x;
+  if (ka.y != kb.y) return ka.y > kb.y;
+  return a < b;
+}
+
+// One thread per non-zero p (column of unit u, row i): the occurrences in row
+// i of structural units other than u, split into those before u in the order
+// (hc[p]) and after it (lc[p]).  A thread per non-zero keeps every lane busy
+// whatever the units' sizes (MAP and set-cover units have 2-20 non-zeros).
+__global__ void k_adj_count(JPView V, const uint32_t* rowunit, const ulonglong2* key, int64_t nnz, int64_t* hc,
+                            int64_t* lc) {
+  GSTRIDE(p, nnz) {
+    const int64_t u = V.unit_of_col[V.colof[p]];
+    int64_t h = 0, l = 0;
+    if (u >= 0) {
+      const int64_t i = V.rowidx[p];
+      const ulonglong2 ku = key[u];
+      for (int64_t q = V.rowptr[i], q1 = V.rowptr[i + 1]; q < q1; ++q) {
+        const uint32_t w = rowunit[q];
+        if (w == ADJ_NONE || w == (uint32_t)u) continue;
+        if (ahead(key[w], w, ku, (uint32_t)u)) ++h;
+        else ++l;
+      }
     }
-    if (lane == 0) {
-      acnt[u] = c;
-      nhigh[u] = (int32_t)h;
-    }
+    hc[p] = h;
+    lc[p] = l;
   }
 }
 
@@ -708,46 +747,59 @@ __device__ __forceinline__ void warp_push(bool pb, bool ps, uint32_t w, int lane
   if (ps) next_s[bs + __popc(ms & lt)] = w;
 }
 
-__global__ void k_adj_fill(JPView V, int64_t Us, const int64_t* aptr, const int32_t* nhigh, uint32_t* adj,
-                           int32_t* cnt, uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
-  int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < Us; u += nwarps) {  // warp-uniform
-    const bool act_u = true;
-    {
-      int64_t hoff = aptr[u], loff = aptr[u] + nhigh[u];
-      int64_t f0 = V.ufirst[u];
-      int64_t p0 = V.colptr[f0], p1 = V.colptr[f0 + V.ulen[u]];
-      for (int64_t pb = p0; pb < p1; pb += 32) {
-        int64_t p = pb + lane;
-        bool act = p < p1;
-        int64_t i = act ? V.rowidx[p] : 0;
-        int ch = 0, cl = 0;
-        if (act)
-          row_struct_members(V, i, u, [&](int64_t w) {
-            if (higher(V, w, u)) ++ch;
-            else ++cl;
-          });
-        int th, tl;
-        int64_t oh = hoff + warp_excl(ch, lane, &th), ol = loff + warp_excl(cl, lane, &tl);
-        if (act)
-          row_struct_members(V, i, u, [&](int64_t w) {
-            // bit 31: the neighbour's own adjacency is long (a CTA serves it)
-            const uint32_t e = (uint32_t)w | ((aptr[w + 1] - aptr[w] > JP_BIG) ? ADJ_BIG : 0u);
-            if (higher(V, w, u)) adj[oh++] = e;
-            else adj[ol++] = e;
-          });
-        hoff += th;
-        loff += tl;
-      }
+// Per unit, from the exclusive scans hc, lc of the per-non-zero counts (fixed
+// columns count 0): adjacency start aptr[u] = hc[p0] + lc[p0] (p0, p1 = the
+// unit's non-zero range), nhigh[u] = hc[p1] - hc[p0], the two bases the fill
+// needs, the long-list flag, and the initial frontier (units with no
+// higher-priority neighbour).
+__global__ void k_adj_units(JPView V, int64_t Us, int64_t nnz, const int64_t* hc, const int64_t* lc, int64_t* aptr,
+                            int32_t* nhigh, int32_t* cnt, int64_t* lbase, int64_t* hend, uint8_t* ubig,
+                            uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ub = blockIdx.x * (int64_t)blockDim.x; ub < Us; ub += stride) {  // warp-uniform
+    const int64_t u = ub + threadIdx.x;
+    bool ready = false, big = false;
+    if (u < Us) {
+      const int64_t f = V.ufirst[u];
+      const int64_t p0 = V.colptr[f], p1 = V.colptr[f + V.ulen[u]];
+      const int64_t h0 = hc[p0], l0 = lc[p0], h1 = hc[p1], l1 = lc[p1];
+      const int64_t nh = h1 - h0;
+      aptr[u] = h0 + l0;
+      nhigh[u] = (int32_t)nh;
+      cnt[u] = (int32_t)nh;
+      lbase[u] = l0;
+      hend[u] = h1;
+      big = (h1 + l1) - (h0 + l0) > JP_BIG;
+      ubig[u] = big;
+      ready = nh == 0;
+      if (u == Us - 1) aptr[Us] = hc[nnz] + lc[nnz];
     }
-    // initial frontier: units without higher-priority neighbours
-    bool ready = act_u && lane == 0 && nhigh[u] == 0;
-    if (act_u && lane == 0) cnt[u] = nhigh[u];
-    bool big = ready && (aptr[u + 1] - aptr[u] > JP_BIG);
-    // one unit per warp here: the lane-0 flags suffice
-    warp_push(big, ready && !big, (uint32_t)u, lane, front_s, nfront_s, front_b, nfront_b);
+    warp_push(ready && big, ready && !big, (uint32_t)u, lane, front_s, nfront_s, front_b, nfront_b);
+  }
+}
+
+// One thread per non-zero p of unit u: writes its row's higher-priority
+// occurrences at hc[p] + lbase[u] (= aptr[u] + the ones of u's earlier
+// non-zeros) and the lower-priority ones at hend[u] + lc[p] (= aptr[u] +
+// nhigh[u] + ...).  Bit 31 of an entry: that neighbour's own list is long (a
+// CTA serves it).
+__global__ void k_adj_fill(JPView V, const uint32_t* rowunit, const ulonglong2* key, const uint8_t* ubig, int64_t nnz,
+                           const int64_t* hc, const int64_t* lc, const int64_t* lbase, const int64_t* hend,
+                           uint32_t* adj) {
+  GSTRIDE(p, nnz) {
+    const int64_t u = V.unit_of_col[V.colof[p]];
+    if (u < 0) continue;
+    int64_t oh = hc[p] + lbase[u], ol = hend[u] + lc[p];
+    const int64_t i = V.rowidx[p];
+    const ulonglong2 ku = key[u];
+    for (int64_t q = V.rowptr[i], q1 = V.rowptr[i + 1]; q < q1; ++q) {
+      const uint32_t w = rowunit[q];
+      if (w == ADJ_NONE || w == (uint32_t)u) continue;
+      const uint32_t e = w | (ubig[w] ? ADJ_BIG : 0u);
+      if (ahead(key[w], w, ku, (uint32_t)u)) adj[oh++] = e;
+      else adj[ol++] = e;
+    }
   }
 }
 
@@ -853,10 +905,103 @@ struct JPRun {
   int* err;
 };
 
+constexpr int JP_TG = 8;                // lanes per unit on the short-list path
+constexpr int64_t JP_TINY = 8 * JP_TG;  // adjacency length served by JP_TG lanes (8 entries a lane)
+
+// Colour and release up to four units whose adjacency lists hold at most
+// JP_TINY entries, one group of JP_TG lanes per unit (u = ADJ_NONE: an idle
+// group).  Control flow is uniform over the warp: every lane loads its (at
+// most 8) entries at once, the colour mask is OR-reduced inside the group, and
+// the released units are reserved on the next frontier once per warp.
+__device__ __forceinline__ void jp_tiny(const JPRun& R, uint32_t u, int lane, uint32_t* next_s, int64_t* nnext_s,
+                                        uint32_t* next_b, int64_t* nnext_b) {
+  const int sub = lane & (JP_TG - 1);
+  int64_t a0 = 0, ah = 0, a1 = 0;
+  if (u != ADJ_NONE) {
+    a0 = R.aptr[u];
+    ah = a0 + R.nhigh[u];
+    a1 = R.aptr[u + 1];
+  }
+  uint32_t e[8];
+  int cw[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t q = a0 + sub + t * JP_TG;
+    e[t] = q < ah ? R.adj[q] : ADJ_NONE;
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) cw[t] = e[t] != ADJ_NONE ? __ldcg(R.color + (e[t] & ~ADJ_BIG)) : -1;
+  // at most 64 higher-priority entries: the colour is found in the first or
+  // the second window of 64
+  int chosen = -1;
+  for (int base = 0;; base += 64) {
+    unsigned long long m = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
+    for (int o = JP_TG / 2; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    if (chosen < 0 && ~m) chosen = base + __ffsll((long long)~m) - 1;
+    if (__all_sync(0xffffffffu, chosen >= 0)) break;
+  }
+  if (u != ADJ_NONE && sub == 0) R.color[u] = chosen;
+  bool rel[8];
+  int nb = 0, ns = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t q = ah + sub + t * JP_TG;
+    e[t] = q < a1 ? R.adj[q] : ADJ_NONE;
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    rel[t] = e[t] != ADJ_NONE && atomicSub(&R.cnt[e[t] & ~ADJ_BIG], 1) == 1;
+    nb += rel[t] && (e[t] & ADJ_BIG);
+    ns += rel[t] && !(e[t] & ADJ_BIG);
+  }
+  int tb, ts;
+  const int ob = warp_excl(nb, lane, &tb), os = warp_excl(ns, lane, &ts);
+  unsigned long long bb = 0, bs = 0;
+  if (lane == 0) {
+    if (tb) bb = atomicAdd((unsigned long long*)nnext_b, (unsigned long long)tb);
+    if (ts) bs = atomicAdd((unsigned long long*)nnext_s, (unsigned long long)ts);
+  }
+  bb = __shfl_sync(0xffffffffu, bb, 0) + ob;
+  bs = __shfl_sync(0xffffffffu, bs, 0) + os;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (rel[t]) {
+      if (e[t] & ADJ_BIG) next_b[bb++] = e[t] & ~ADJ_BIG;
+      else next_s[bs++] = e[t];
+    }
+}
+
+constexpr int64_t JP_SLICE = 1024;  // lower-priority entries of a long list one CTA releases
+
+// The smallest colour not held by the entries adj[a0, ah) (all coloured),
+// computed by the whole CTA, 64 colours at a time.
+__device__ __forceinline__ int cta_colour(const JPRun& R, int64_t a0, int64_t ah, int lane, unsigned long long* smask) {
+  int base = 0, chosen = -1;
+  while (chosen < 0) {
+    if (threadIdx.x == 0) *smask = 0;
+    __syncthreads();
+    unsigned long long m = color_mask(R.adj, R.color, a0, ah, threadIdx.x, blockDim.x, base);
+    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    if (lane == 0 && m) atomicOr(smask, m);
+    __syncthreads();
+    const unsigned long long all = *smask;
+    if (~all) chosen = base + __ffsll((long long)~all) - 1;
+    base += 64;
+    __syncthreads();
+  }
+  return chosen;
+}
+
 // Rounds [r0, r0 + nr) of the data-flow colouring; with nr > 1 the launch must
 // be cooperative (a grid barrier separates the rounds).
 __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
   __shared__ unsigned long long smask;
+  __shared__ uint32_t s_u[256];
+  __shared__ int s_off[257];
+  __shared__ int s_wsum[8];
   const int lane = threadIdx.x & 31;
   for (int64_t r = r0; r < r0 + nr; ++r) {
     const int in = (int)(r % 3), out = (int)((r + 1) % 3), z = (int)((r + 2) % 3);
@@ -876,41 +1021,82 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
     uint32_t* next_b = R.fb[(r + 1) & 1];
     int64_t* nnext_s = R.fc + 2 * out;
     int64_t* nnext_b = R.fc + 2 * out + 1;
-    // long adjacency lists: one CTA each
-    for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
-      const uint32_t u = __ldcg(front_b + t);
-      const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
-      int base = 0, chosen = -1;
-      while (chosen < 0) {
-        if (threadIdx.x == 0) smask = 0;
-        __syncthreads();
-        unsigned long long m = color_mask(R.adj, R.color, a0, ah, threadIdx.x, blockDim.x, base);
-        for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-        if (lane == 0 && m) atomicOr(&smask, m);
-        __syncthreads();
-        unsigned long long all = smask;
-        if (~all) chosen = base + __ffsll((long long)~all) - 1;
-        base += 64;
-        __syncthreads();
+    if (nb > 0 && nb <= (int64_t)blockDim.x && nb < (int64_t)gridDim.x) {  // uniform
+      // few long lists (a chain of hubs): the lower-priority part of each is
+      // cut into slices of JP_SLICE entries spread over the CTAs; the CTA of
+      // a slice finds the unit's colour from its higher-priority part (short
+      // for a hub) and releases the slice.  s_off = exclusive scan of the
+      // slice counts over the frontier.
+      int nsl = 0;
+      if (threadIdx.x < nb) {
+        const uint32_t u = __ldcg(front_b + threadIdx.x);
+        const int64_t ah = R.aptr[u] + R.nhigh[u], a1 = R.aptr[u + 1];
+        nsl = (int)max((int64_t)1, (a1 - ah + JP_SLICE - 1) / JP_SLICE);
+        s_u[threadIdx.x] = u;
       }
-      if (threadIdx.x == 0) R.color[u] = chosen;
-      release(R.adj, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+      int wt;
+      const int wex = warp_excl(nsl, lane, &wt);
+      if (lane == 0) s_wsum[threadIdx.x >> 5] = wt;
+      __syncthreads();
+      int wbase = 0;
+      for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += s_wsum[w];
+      s_off[threadIdx.x] = wbase + wex;
+      if (threadIdx.x == blockDim.x - 1) s_off[blockDim.x] = wbase + wex + nsl;
+      __syncthreads();
+      const int64_t S = s_off[nb];
+      int j = 0;
+      for (int64_t g = blockIdx.x; g < S; g += gridDim.x) {
+        while (s_off[j + 1] <= g) ++j;  // uniform; g only grows
+        const uint32_t u = s_u[j];
+        const int64_t sl = g - s_off[j];
+        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
+        const int chosen = cta_colour(R, a0, ah, lane, &smask);
+        if (sl == 0 && threadIdx.x == 0) R.color[u] = chosen;
+        const int64_t b0 = ah + sl * JP_SLICE, b1 = min(a1, b0 + JP_SLICE);
+        release(R.adj, R.cnt, b0, b1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+      }
+      __syncthreads();  // s_u / s_off are rewritten next round
+    } else {
+      // long adjacency lists: one CTA each
+      for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
+        const uint32_t u = __ldcg(front_b + t);
+        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
+        const int chosen = cta_colour(R, a0, ah, lane, &smask);
+        if (threadIdx.x == 0) R.color[u] = chosen;
+        release(R.adj, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+      }
     }
-    // the rest: one warp each
+    // the rest.  A frontier larger than the warps: four units per warp, one
+    // group of JP_TG lanes each when all four lists are short, else one after
+    // the other with the whole warp.  A smaller one: one unit per warp.
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = warp; t < ns; t += nwarps) {
-      const uint32_t u = __ldcg(front_s + t);
-      const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
-      int base = 0, chosen = -1;
-      while (chosen < 0) {
-        unsigned long long m = color_mask(R.adj, R.color, a0, ah, lane, 32, base);
-        for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-        if (~m) chosen = base + __ffsll((long long)~m) - 1;
-        base += 64;
+    const int per = ns > nwarps ? 4 : 1;
+    for (int64_t tb = warp * per; tb < ns; tb += nwarps * per) {  // warp-uniform
+      uint32_t u4 = ADJ_NONE;
+      int64_t len = 0;
+      if (lane < per && tb + lane < ns) {
+        u4 = __ldcg(front_s + tb + lane);
+        len = R.aptr[u4 + 1] - R.aptr[u4];
       }
-      if (lane == 0) R.color[u] = chosen;
-      release(R.adj, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+      if (per == 4 && __all_sync(0xffffffffu, len <= JP_TINY)) {
+        jp_tiny(R, __shfl_sync(0xffffffffu, u4, lane / JP_TG), lane, next_s, nnext_s, next_b, nnext_b);
+        continue;
+      }
+      for (int j = 0; j < per; ++j) {
+        const uint32_t u = __shfl_sync(0xffffffffu, u4, j);
+        if (u == ADJ_NONE) break;  // uniform
+        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
+        int base = 0, chosen = -1;
+        while (chosen < 0) {
+          unsigned long long m = color_mask(R.adj, R.color, a0, ah, lane, 32, base);
+          for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+          if (~m) chosen = base + __ffsll((long long)~m) - 1;
+          base += 64;
+        }
+        if (lane == 0) R.color[u] = chosen;
+        release(R.adj, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+      }
     }
     if (nr > 1 && !jp_barrier(R.bar, R.err)) return;
   }
@@ -959,7 +1145,10 @@ __global__ void k_max_i32(const int32_t* a, int64_t n, int* out) {
 
 // sort keys for structural units: colour * 4 + class
 __global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const int64_t* unnz, int64_t Us,
-                              uint32_t* keys, uint32_t* vals, int64_t* cnt) {
+                              uint32_t* keys, uint32_t* vals, int64_t* cnt, int64_t nbins) {
+  extern __shared__ int sh_hist[];
+  const bool use_sh = nbins <= HIST_SMEM_BINS;
+  hist_init(sh_hist, nbins, use_sh);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t ub = blockIdx.x * (int64_t)blockDim.x; ub < Us; ub += stride) {
     const int64_t u = ub + threadIdx.x;
@@ -980,18 +1169,9 @@ __global__ void k_struct_keys(const int32_t* color, const int32_t* ulen, const i
       keys[u] = key;
       vals[u] = (uint32_t)u;
     }
-    hist_add(cnt, key, ok);
+    hist_add(cnt, sh_hist, use_sh, key, ok);
   }
-}
-
-__global__ void k_slack_keys(const int32_t* color, int64_t Us, int64_t Msl, const int64_t* slack_row,
-                             uint32_t* keys, uint32_t* vals, int64_t* cnt) {
-  GSTRIDE(s, Msl) {
-    uint32_t c = (uint32_t)color[Us + s];
-    keys[s] = c;
-    vals[s] = (uint32_t)slack_row[s];
-    atomicAdd((unsigned long long*)&cnt[c], 1ull);
-  }
+  hist_flush(cnt, sh_hist, nbins, use_sh);
 }
 
 // key = internal column of the row's highest-priority free column (0 if none)
@@ -1014,15 +1194,19 @@ __global__ void k_slack_owner_keys(JPView V, int64_t Msl, const uint32_t* col_of
 }
 
 __global__ void k_slack_color_keys(const uint32_t* rows, int64_t Msl, const int64_t* slack_unit, const int32_t* color,
-                                   uint32_t* keys, int64_t* cnt) {
+                                   uint32_t* keys, int64_t* cnt, int64_t nbins) {
+  extern __shared__ int sh_hist[];
+  const bool use_sh = nbins <= HIST_SMEM_BINS;
+  hist_init(sh_hist, nbins, use_sh);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t tb = blockIdx.x * (int64_t)blockDim.x; tb < Msl; tb += stride) {
     const int64_t t = tb + threadIdx.x;
     const bool ok = t < Msl;
     uint32_t c = ok ? (uint32_t)color[slack_unit[rows[t]]] : 0u;
     if (ok) keys[t] = c;
-    hist_add(cnt, c, ok);
+    hist_add(cnt, sh_hist, use_sh, c, ok);
   }
+  hist_flush(cnt, sh_hist, nbins, use_sh);
 }
 
 __global__ void k_pos_len(const uint32_t* unit_of_pos, const int32_t* ulen, int64_t Us, int64_t* len) {
@@ -1378,18 +1562,28 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     TH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jp, 256, 0));
-    const int fill_grid = sms * 8;
     int64_t* aptr = tmp.alloc<int64_t>(Us + 1);
     int32_t* nhigh = tmp.alloc<int32_t>(Us + 1);
-    k_adj_count<<<fill_grid, 256, 0, s>>>(V, Us, aptr, nhigh);
+    uint32_t* rowunit = tmp.alloc<uint32_t>(nnz + 1);
+    ulonglong2* ukey = tmp.alloc<ulonglong2>(Us);
+    int64_t* hc = tmp.alloc<int64_t>(nnz + 1);
+    int64_t* lc = tmp.alloc<int64_t>(nnz + 1);
+    int64_t* lbase = tmp.alloc<int64_t>(Us);
+    int64_t* hend = tmp.alloc<int64_t>(Us);
+    uint8_t* ubig = tmp.alloc<uint8_t>(Us);
+    if (nnz > 0) {
+      k_row_units<<<grid_for(nnz, 256), 256, 0, s>>>(V, nnz, rowunit);
+      TH_LAUNCHED();
+    }
+    k_unit_prio<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, ukey);
     TH_LAUNCHED();
-    exclusive_scan_i64(aptr, aptr, Us, tmp, s);
-    int64_t nadj = 0;
-    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + Us, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TH_CUDA(cudaStreamSynchronize(s));
+    if (nnz > 0) {
+      k_adj_count<<<grid_for(nnz, 256), 256, 0, s>>>(V, rowunit, ukey, nnz, hc, lc);
+      TH_LAUNCHED();
+    }
+    exclusive_scan_i64(hc, hc, nnz, tmp, s);
+    exclusive_scan_i64(lc, lc, nnz, tmp, s);
     JPRun R;
-    uint32_t* adj = tmp.alloc<uint32_t>(nadj + 1);
-    R.adj = adj;
     R.aptr = aptr;
     R.nhigh = nhigh;
     R.cnt = tmp.alloc<int32_t>(Us + 1);
@@ -1406,8 +1600,18 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     TH_CUDA(cudaMemsetAsync(R.done, 0, sizeof(unsigned long long), s));
     TH_CUDA(cudaMemsetAsync(R.bar, 0, sizeof(unsigned), s));
     TH_CUDA(cudaMemsetAsync(R.err, 0, sizeof(int), s));
-    k_adj_fill<<<fill_grid, 256, 0, s>>>(V, Us, aptr, nhigh, adj, R.cnt, R.fs[0], R.fc + 0, R.fb[0], R.fc + 1);
+    k_adj_units<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, nnz, hc, lc, aptr, nhigh, R.cnt, lbase, hend, ubig, R.fs[0],
+                                                  R.fc + 0, R.fb[0], R.fc + 1);
     TH_LAUNCHED();
+    int64_t nadj = 0;
+    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + Us, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    uint32_t* adj = tmp.alloc<uint32_t>(nadj + 1);
+    R.adj = adj;
+    if (nnz > 0) {
+      k_adj_fill<<<grid_for(nnz, 256), 256, 0, s>>>(V, rowunit, ukey, ubig, nnz, hc, lc, lbase, hend, adj);
+      TH_LAUNCHED();
+    }
     const int64_t max_rounds = Us + 2;
     if (coop && per > 0 && coop_allowed()) {
       // every round in one cooperative launch, a grid barrier between rounds
@@ -1461,7 +1665,10 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   int64_t* ccnt = tmp.alloc<int64_t>((int64_t)C * UC_COUNT + 1);
   TH_CUDA(cudaMemsetAsync(ccnt, 0, ((int64_t)C * UC_COUNT + 1) * sizeof(int64_t), s));
   if (Us > 0) {
-    k_struct_keys<<<grid_for(Us, 256), 256, 0, s>>>(color, ulen, unnz, Us, skeys, unit_of_pos, ccnt);
+    int hg;
+    size_t hsm;
+    hist_launch_shape(Us, (int64_t)C * UC_COUNT, &hg, &hsm);
+    k_struct_keys<<<hg, 256, hsm, s>>>(color, ulen, unnz, Us, skeys, unit_of_pos, ccnt, (int64_t)C * UC_COUNT);
     TH_LAUNCHED();
   }
   radix_sort_pairs(skeys, unit_of_pos, Us, bits_for((int64_t)C * UC_COUNT + 1), tmp, s);
@@ -1495,7 +1702,10 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   }
   radix_sort_pairs(slkeys, slrows, Msl, bits_for(Ns + 1), tmp, s);
   if (Msl > 0) {
-    k_slack_color_keys<<<grid_for(Msl, 256), 256, 0, s>>>(slrows, Msl, slack_unit, color, slkeys, scnt);
+    int hg;
+    size_t hsm;
+    hist_launch_shape(Msl, C, &hg, &hsm);
+    k_slack_color_keys<<<hg, 256, hsm, s>>>(slrows, Msl, slack_unit, color, slkeys, scnt, C);
     TH_LAUNCHED();
   }
   radix_sort_pairs(slkeys, slrows, Msl, bits_for(C + 1), tmp, s);

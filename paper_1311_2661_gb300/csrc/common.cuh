@@ -87,6 +87,12 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// The library's stream-ordered memory pool on device `dev`, created on first
+// use.  Freed blocks stay reserved in it (release threshold = unlimited), so a
+// build after a build reuses the same physical memory instead of mapping it
+// again; thetis_trim_cache gives the unused reserve back.
+cudaMemPool_t lib_pool(int dev);
+
 class Arena {
  public:
   explicit Arena(cudaStream_t s) : s_(s) {}
@@ -95,7 +101,16 @@ class Arena {
   T* alloc(size_t n) {
     void* p = nullptr;
     size_t b = (n ? n : 1) * sizeof(T);
-    TH_CUDA(cudaMallocAsync(&p, b, s_));
+    if (dev_ < 0) TH_CUDA(cudaStreamGetDevice(s_, &dev_));
+    cudaMemPool_t pool = lib_pool(dev_);
+    if (cudaMallocFromPoolAsync(&p, b, pool, s_) != cudaSuccess) {
+      // the reserve may hold the memory in blocks that do not fit: give the
+      // unused part back and try once more
+      (void)cudaGetLastError();
+      TH_CUDA(cudaStreamSynchronize(s_));
+      TH_CUDA(cudaMemPoolTrimTo(pool, 0));
+      TH_CUDA(cudaMallocFromPoolAsync(&p, b, pool, s_));
+    }
     bufs_.push_back({p, b});
     bytes_ += b;
     return (T*)p;
@@ -110,6 +125,7 @@ class Arena {
 
  private:
   cudaStream_t s_;
+  int dev_ = -1;
   std::vector<DevBuf> bufs_;
   size_t bytes_ = 0;
 };

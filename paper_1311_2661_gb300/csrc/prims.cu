@@ -8,6 +8,26 @@
 
 namespace thetis {
 
+cudaMemPool_t lib_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  TH_CHECK(dev >= 0 && dev < 64, THETIS_E_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    TH_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = UINT64_MAX;
+    TH_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 const char* get_error() { return g_err.c_str(); }

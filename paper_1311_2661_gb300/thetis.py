@@ -100,6 +100,8 @@ def _load():
         "thetis_batch_info": (st, [P, P, P]),
         "thetis_solve_al": (st, [P, P, i32, C.c_double, P, P, P, P]),
         "thetis_get_duals": (st, [P, P, i32]),
+        "thetis_cache_info": (st, [P, P]),
+        "thetis_trim_cache": (st, [u64]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -118,6 +120,18 @@ def thetis_last_error() -> str:
 
 def thetis_launch_count() -> int:
     return int(_lib.thetis_launch_count())
+
+
+def thetis_cache_info():
+    """(reserved, in-use) bytes of the library's device memory pool."""
+    r, u = C.c_uint64(), C.c_uint64()
+    _check(_lib.thetis_cache_info(C.byref(r), C.byref(u)))
+    return int(r.value), int(u.value)
+
+
+def thetis_trim_cache(keep_bytes=0):
+    """Give the pool's unused reserve back until at most keep_bytes stay reserved."""
+    _check(_lib.thetis_trim_cache(int(keep_bytes)))
 
 
 def _check(st, allow=(THETIS_OK,)):
