@@ -662,25 +662,33 @@ __device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
   return a < b;
 }
 
-// Jones-Plassmann over the structural units, driven by data flow.  Slack units
-// come last in the priority order and never conflict with one another, so each
-// takes, after all structural units are coloured, the smallest colour its row
-// does not hold (k_slack_color) -- the sequential greedy result.
-// adj lists, for every structural unit u, each occurrence of a conflicting
-// structural unit (once per shared row): first the nhigh[u] higher-priority
-// ones, then the lower-priority ones.  cnt[u] = higher-priority occurrences
-// still uncoloured; a unit whose count reaches zero takes the smallest colour
-// its (all coloured) higher-priority neighbours do not hold and releases its
-// lower-priority neighbours.  Units of one frontier are pairwise non-adjacent.
-constexpr int64_t JP_BIG = 1024;  // adjacency length above which a whole CTA serves a unit
-constexpr uint32_t ADJ_BIG = 0x80000000u;  // adjacency entry flag: that neighbour is served by a CTA
-constexpr uint32_t ADJ_NONE = 0xffffffffu; // no entry
+// Jones-Plassmann over the structural units, driven by data flow, with the
+// rows as the dependency structure.  Every row is a clique of the
+// column-intersection graph, so in the sequential greedy order the units of a
+// row are coloured one after the other: a unit is ready once, in each of its
+// rows, the unit just before it is coloured (cnt[u] = rows in which u has a
+// predecessor), and the colours it must avoid are those of the row prefixes
+// before it.  Per row a 128-bit mask holds the colours of the coloured prefix
+// (bit RC_OVF: some colour >= RC_OVF is among them; then, or when colours
+// 0..RC_OVF-1 are all taken, the colour is found from the prefixes
+// themselves).  Per unit a list of (row, successor) entries, the rows where
+// it has a predecessor first (npred[u] of them).  A row of exactly two units
+// needs no mask: the second reads the first one's colour directly.  Units of one frontier share
+// no row.  Slack units come last in the priority order and never conflict with
+// one another, so each takes, after all structural units are coloured, the
+// smallest colour its row does not hold (k_slack_color) -- the sequential
+// greedy result.
+constexpr int64_t JP_BIG = 1024;           // list length above which a whole CTA serves a unit
+constexpr uint32_t RC_BIG = 0x80000000u;   // successor flag: that unit's own list is long
+constexpr uint32_t RC_NONE = 0xffffffffu;  // no unit
+constexpr int RC_OVF = 127;                // mask bit: a colour >= RC_OVF in the prefix
+constexpr uint32_t RC_TWO = 0x80000000u;   // list-entry flag for a row of exactly two units (see k_row_links)
 
-// Per CSR entry: the structural unit of its column, ADJ_NONE for a fixed column.
+// Per CSR entry: the structural unit of its column, RC_NONE for a fixed column.
 __global__ void k_row_units(JPView V, int64_t nnz, uint32_t* rowunit) {
   GSTRIDE(q, nnz) {
     const int64_t w = V.unit_of_col[V.colof[V.csr_p[q]]];
-    rowunit[q] = w >= 0 ? (uint32_t)w : ADJ_NONE;
+    rowunit[q] = w >= 0 ? (uint32_t)w : RC_NONE;
   }
 }
 
@@ -696,27 +704,69 @@ __device__ __forceinline__ bool ahead(ulonglong2 ka, uint32_t a, ulonglong2 kb, 
   return a < b;
 }
 
-// One thread per non-zero p (column of unit u, row i): the occurrences in row
-// i of structural units other than u, split into those before u in the order
-// (hc[p]) and after it (lc[p]).  A thread per non-zero keeps every lane busy
-// whatever the units' sizes (MAP and set-cover units have 2-20 non-zeros).
-__global__ void k_adj_count(JPView V, const uint32_t* rowunit, const ulonglong2* key, int64_t nnz, int64_t* hc,
-                            int64_t* lc) {
-  GSTRIDE(p, nnz) {
-    const int64_t u = V.unit_of_col[V.colof[p]];
-    int64_t h = 0, l = 0;
-    if (u >= 0) {
-      const int64_t i = V.rowidx[p];
+// One thread per CSR entry q of row i: the rank of its unit in row i, i.e.
+// the occurrences in row i of units ahead of it.  A unit repeated in a row
+// (two columns of one block) keeps its first occurrence; later ones, and
+// fixed columns, get rank -1.  Distinct units get distinct ranks, so
+// sorted[rowptr[i] + rank] lists the row's units in order (with a gap where a
+// repeat was counted).
+__global__ void k_row_rank(JPView V, const uint32_t* rowof, const uint32_t* rowunit, const ulonglong2* key,
+                           int64_t nnz, int32_t* rank, uint32_t* sorted, int32_t* rowcnt) {
+  GSTRIDE(q, nnz) {
+    const uint32_t u = rowunit[q];
+    int32_t r = -1;
+    if (u != RC_NONE) {
+      const int64_t i = rowof[q];
+      const int64_t q0 = V.rowptr[i], q1 = V.rowptr[i + 1];
       const ulonglong2 ku = key[u];
-      for (int64_t q = V.rowptr[i], q1 = V.rowptr[i + 1]; q < q1; ++q) {
-        const uint32_t w = rowunit[q];
-        if (w == ADJ_NONE || w == (uint32_t)u) continue;
-        if (ahead(key[w], w, ku, (uint32_t)u)) ++h;
-        else ++l;
+      int32_t c = 0;
+      bool rep = false;
+      for (int64_t t = q0; t < q1; ++t) {
+        const uint32_t w = rowunit[t];
+        if (w == RC_NONE) continue;
+        if (w == u) {
+          rep = rep || t < q;
+          continue;
+        }
+        c += ahead(key[w], w, ku, u);
+      }
+      if (!rep) {
+        r = c;
+        sorted[q0 + c] = u;
+        atomicAdd(&rowcnt[i], 1);
       }
     }
-    hc[p] = h;
-    lc[p] = l;
+    rank[q] = r;
+  }
+}
+
+// One thread per CSR entry q: for its column non-zero p = csr_p[q], whether
+// the unit has a predecessor in the row (hc[p] = 1) or is the row's first
+// (lc[p] = 1) -- both 0 for a fixed column or a repeat --, the unit after it
+// in the row (succ[p], RC_NONE if last) and the list entry: the row id, except
+// in a row of exactly two units, where the first unit's entry is the row id
+// with RC_TWO (no mask needed) and the second unit's entry is the first
+// unit's id with RC_TWO (its colour is read directly).
+__global__ void k_row_links(JPView V, const uint32_t* rowof, const int32_t* rank, const uint32_t* sorted,
+                            const int32_t* rowcnt, int64_t nnz, int64_t* hc, int64_t* lc, uint32_t* succ,
+                            uint32_t* lval) {
+  GSTRIDE(q, nnz) {
+    const int64_t p = V.csr_p[q];
+    const int32_t r = rank[q];
+    uint32_t sv = RC_NONE, lv = 0;
+    if (r >= 0) {
+      const int64_t i = rowof[q];
+      const int64_t q0 = V.rowptr[i], q1 = V.rowptr[i + 1];
+      int64_t t = q0 + r + 1;
+      while (t < q1 && sorted[t] == RC_NONE) ++t;
+      if (t < q1) sv = sorted[t];
+      const bool two = rowcnt[i] == 2;
+      lv = !two ? (uint32_t)i : (r == 0 ? ((uint32_t)i | RC_TWO) : (sorted[q0] | RC_TWO));
+    }
+    hc[p] = r > 0;
+    lc[p] = r == 0;
+    succ[p] = sv;
+    lval[p] = lv;
   }
 }
 
@@ -747,14 +797,14 @@ __device__ __forceinline__ void warp_push(bool pb, bool ps, uint32_t w, int lane
   if (ps) next_s[bs + __popc(ms & lt)] = w;
 }
 
-// Per unit, from the exclusive scans hc, lc of the per-non-zero counts (fixed
-// columns count 0): adjacency start aptr[u] = hc[p0] + lc[p0] (p0, p1 = the
-// unit's non-zero range), nhigh[u] = hc[p1] - hc[p0], the two bases the fill
-// needs, the long-list flag, and the initial frontier (units with no
-// higher-priority neighbour).
-__global__ void k_adj_units(JPView V, int64_t Us, int64_t nnz, const int64_t* hc, const int64_t* lc, int64_t* aptr,
-                            int32_t* nhigh, int32_t* cnt, int64_t* lbase, int64_t* hend, uint8_t* ubig,
-                            uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
+// Per unit, from the exclusive scans hc, lc of the per-non-zero flags: list
+// start aptr[u] = hc[p0] + lc[p0] (p0, p1 = the unit's non-zero range),
+// npred[u] = hc[p1] - hc[p0] (also the initial count), the two bases the fill
+// needs, the long-list flag, and the initial frontier (units first in all
+// their rows).
+__global__ void k_chain_units(JPView V, int64_t Us, int64_t nnz, const int64_t* hc, const int64_t* lc, int64_t* aptr,
+                              int32_t* npred, int32_t* cnt, int64_t* lbase, int64_t* hend, uint8_t* ubig,
+                              uint32_t* front_s, int64_t* nfront_s, uint32_t* front_b, int64_t* nfront_b) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t ub = blockIdx.x * (int64_t)blockDim.x; ub < Us; ub += stride) {  // warp-uniform
@@ -766,7 +816,7 @@ __global__ void k_adj_units(JPView V, int64_t Us, int64_t nnz, const int64_t* hc
       const int64_t h0 = hc[p0], l0 = lc[p0], h1 = hc[p1], l1 = lc[p1];
       const int64_t nh = h1 - h0;
       aptr[u] = h0 + l0;
-      nhigh[u] = (int32_t)nh;
+      npred[u] = (int32_t)nh;
       cnt[u] = (int32_t)nh;
       lbase[u] = l0;
       hend[u] = h1;
@@ -779,88 +829,22 @@ __global__ void k_adj_units(JPView V, int64_t Us, int64_t nnz, const int64_t* hc
   }
 }
 
-// One thread per non-zero p of unit u: writes its row's higher-priority
-// occurrences at hc[p] + lbase[u] (= aptr[u] + the ones of u's earlier
-// non-zeros) and the lower-priority ones at hend[u] + lc[p] (= aptr[u] +
-// nhigh[u] + ...).  Bit 31 of an entry: that neighbour's own list is long (a
-// CTA serves it).
-__global__ void k_adj_fill(JPView V, const uint32_t* rowunit, const ulonglong2* key, const uint8_t* ubig, int64_t nnz,
-                           const int64_t* hc, const int64_t* lc, const int64_t* lbase, const int64_t* hend,
-                           uint32_t* adj) {
+// One thread per non-zero p of unit u: its (list entry, successor) goes to
+// hc[p] + lbase[u] (= aptr[u] + the predecessor rows of u's earlier
+// non-zeros) or, for a row u starts, to hend[u] + lc[p] (= aptr[u] + npred[u]
+// + ...).  Bit 31 of a successor: that unit's own list is long (a CTA serves
+// it).
+__global__ void k_chain_fill(JPView V, int64_t nnz, const int64_t* hc, const int64_t* lc, const int64_t* lbase,
+                             const int64_t* hend, const uint32_t* succ, const uint32_t* lval, const uint8_t* ubig,
+                             uint32_t* lrow, uint32_t* lsucc) {
   GSTRIDE(p, nnz) {
+    const bool pred = hc[p + 1] != hc[p], first = lc[p + 1] != lc[p];
+    if (!pred && !first) continue;
     const int64_t u = V.unit_of_col[V.colof[p]];
-    if (u < 0) continue;
-    int64_t oh = hc[p] + lbase[u], ol = hend[u] + lc[p];
-    const int64_t i = V.rowidx[p];
-    const ulonglong2 ku = key[u];
-    for (int64_t q = V.rowptr[i], q1 = V.rowptr[i + 1]; q < q1; ++q) {
-      const uint32_t w = rowunit[q];
-      if (w == ADJ_NONE || w == (uint32_t)u) continue;
-      const uint32_t e = w | (ubig[w] ? ADJ_BIG : 0u);
-      if (ahead(key[w], w, ku, (uint32_t)u)) adj[oh++] = e;
-      else adj[ol++] = e;
-    }
-  }
-}
-
-__device__ __forceinline__ void prefetch_l2_jp(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// window mask of the colours of the entries adj[a0, a1), strided by `step` from `start`
-__device__ __forceinline__ unsigned long long color_mask(const uint32_t* adj, const int32_t* color, int64_t a0,
-                                                         int64_t a1, int64_t start, int step, int base) {
-  unsigned long long m = 0;
-  for (int64_t qb = a0 + start; qb < a1; qb += 4 * (int64_t)step) {
-    uint32_t e[4];
-    int cw[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) e[t] = (qb + t * step < a1) ? adj[qb + t * step] : ADJ_NONE;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) cw[t] = (e[t] != ADJ_NONE) ? __ldcg(color + (e[t] & ~ADJ_BIG)) : -1;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
-  }
-  return m;
-}
-
-// Release the lower-priority neighbours adj[a0, a1); the loop is uniform over
-// the `step` threads that run it (a warp or a CTA).  Four entries per thread
-// at a time: their counter decrements are independent, and the units they
-// release go to the next frontier with one reservation per list per warp.
-__device__ __forceinline__ void release(const uint32_t* adj, int32_t* cnt, int64_t a0, int64_t a1, int64_t start,
-                                        int step, int lane, uint32_t* next_s, int64_t* nnext_s, uint32_t* next_b,
-                                        int64_t* nnext_b) {
-  for (int64_t qb = a0; qb < a1; qb += 4 * (int64_t)step) {
-    uint32_t e[4];
-    bool rel[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int64_t q = qb + start + (int64_t)t * step;
-      e[t] = (q < a1) ? adj[q] : ADJ_NONE;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) rel[t] = e[t] != ADJ_NONE && atomicSub(&cnt[e[t] & ~ADJ_BIG], 1) == 1;
-    int nb = 0, ns = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      nb += rel[t] && (e[t] & ADJ_BIG);
-      ns += rel[t] && !(e[t] & ADJ_BIG);
-    }
-    int tb, ts;
-    const int ob = warp_excl(nb, lane, &tb), os = warp_excl(ns, lane, &ts);
-    unsigned long long bb = 0, bs = 0;
-    if (lane == 0) {
-      if (tb) bb = atomicAdd((unsigned long long*)nnext_b, (unsigned long long)tb);
-      if (ts) bs = atomicAdd((unsigned long long*)nnext_s, (unsigned long long)ts);
-    }
-    bb = __shfl_sync(0xffffffffu, bb, 0) + ob;
-    bs = __shfl_sync(0xffffffffu, bs, 0) + os;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (rel[t]) {
-        if (e[t] & ADJ_BIG) next_b[bb++] = e[t] & ~ADJ_BIG;
-        else next_s[bs++] = e[t];
-      }
+    const int64_t pos = pred ? hc[p] + lbase[u] : hend[u] + lc[p];
+    const uint32_t sv = succ[p];
+    lrow[pos] = lval[p];
+    lsucc[pos] = (sv == RC_NONE) ? RC_NONE : (sv | (ubig[sv] ? RC_BIG : 0u));
   }
 }
 
@@ -892,9 +876,13 @@ __device__ __forceinline__ bool jp_barrier(unsigned* bar, int* err) {
 }
 
 struct JPRun {
-  const uint32_t* adj;
+  const uint32_t* lrow;   // per unit list: rows (RC_TWO entries: see k_row_links), predecessor rows first
+  const uint32_t* lsucc;  // successor in that row (RC_NONE: last; RC_BIG flag)
   const int64_t* aptr;
-  const int32_t* nhigh;
+  const int32_t* npred;
+  const int64_t* rowptr;  // the rows' units in priority order (slow path)
+  const uint32_t* sorted;
+  unsigned long long* rmask;  // two words per row
   int32_t* cnt;
   int32_t* color;
   uint32_t* fs[2];
@@ -905,57 +893,231 @@ struct JPRun {
   int* err;
 };
 
-constexpr int JP_TG = 8;                // lanes per unit on the short-list path
-constexpr int64_t JP_TINY = 8 * JP_TG;  // adjacency length served by JP_TG lanes (8 entries a lane)
+// colour c into the mask of row i
+__device__ __forceinline__ void mask_add(unsigned long long* rmask, uint32_t i, int c) {
+  if (c < 64) atomicOr(rmask + 2 * (int64_t)i, 1ull << c);
+  else atomicOr(rmask + 2 * (int64_t)i + 1, 1ull << (c < RC_OVF ? c - 64 : 63));
+}
 
-// Colour and release up to four units whose adjacency lists hold at most
-// JP_TINY entries, one group of JP_TG lanes per unit (u = ADJ_NONE: an idle
-// group).  Control flow is uniform over the warp: every lane loads its (at
-// most 8) entries at once, the colour mask is OR-reduced inside the group, and
-// the released units are reserved on the next frontier once per warp.
+// colour c into a 128-bit accumulator (same bits as mask_add)
+__device__ __forceinline__ void mask_set(unsigned long long& m0, unsigned long long& m1, int c) {
+  if (c < 64) m0 |= 1ull << c;
+  else m1 |= 1ull << (c < RC_OVF ? c - 64 : 63);
+}
+
+// the mask a predecessor entry contributes: its row's mask, or for the second
+// unit of a two-unit row the first unit's colour
+__device__ __forceinline__ void entry_mask(const JPRun& R, uint32_t e, unsigned long long& m0, unsigned long long& m1) {
+  if (e & RC_TWO) {
+    mask_set(m0, m1, __ldcg(R.color + (e & ~RC_TWO)));
+  } else {
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(R.rmask) + e);
+    m0 |= v.x;
+    m1 |= v.y;
+  }
+}
+
+// the smallest colour free in a 128-bit mask, or -1 when the slow path must
+// decide (bit RC_OVF set, or colours 0..RC_OVF-1 all taken)
+__device__ __forceinline__ int mask_pick(unsigned long long m0, unsigned long long m1) {
+  if (m1 >> 63) return -1;
+  if (~m0) return __ffsll((long long)~m0) - 1;
+  const unsigned long long f = ~m1 & 0x7fffffffffffffffull;
+  return f ? 64 + __ffsll((long long)f) - 1 : -1;
+}
+
+// OR of the masks of the rows lrow[a0, ah), strided by `step` from `start`
+__device__ __forceinline__ void mask_or(const JPRun& R, int64_t a0, int64_t ah, int64_t start, int step,
+                                        unsigned long long& m0, unsigned long long& m1) {
+  for (int64_t qb = a0 + start; qb < ah; qb += 4 * (int64_t)step) {
+    uint32_t rw[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) rw[t] = (qb + t * step < ah) ? R.lrow[qb + t * step] : RC_NONE;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (rw[t] != RC_NONE) entry_mask(R, rw[t], m0, m1);
+  }
+}
+
+// slow path: colours in [base, base + 64) of the units before u in the row of
+// predecessor entry i
+__device__ unsigned long long prefix_mask(const JPRun& R, uint32_t i, uint32_t u, int base) {
+  unsigned long long m = 0;
+  if (i & RC_TWO) {
+    const int c = __ldcg(R.color + (i & ~RC_TWO));
+    return (c >= base && c < base + 64) ? 1ull << (c - base) : 0ull;
+  }
+  for (int64_t t = R.rowptr[i], t1 = R.rowptr[i + 1]; t < t1; ++t) {
+    const uint32_t w = R.sorted[t];
+    if (w == u) break;
+    if (w == RC_NONE) continue;
+    const int c = __ldcg(R.color + w);
+    if (c >= base && c < base + 64) m |= 1ull << (c - base);
+  }
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long prefix_or(const JPRun& R, uint32_t u, int64_t a0, int64_t ah,
+                                                        int64_t start, int step, int base) {
+  unsigned long long m = 0;
+  for (int64_t q = a0 + start; q < ah; q += step) m |= prefix_mask(R, R.lrow[q], u, base);
+  return m;
+}
+
+// Colour c into the rows of lrow[a0, a1) that have a successor and count the
+// successors down; the loop is uniform over the `step` threads that run it (a
+// warp or a CTA).  Four entries per thread at a time; the units released go
+// to the next frontier with one reservation per list per warp.
+__device__ __forceinline__ void release(const JPRun& R, int c, int64_t a0, int64_t a1, int64_t start, int step,
+                                        int lane, uint32_t* next_s, int64_t* nnext_s, uint32_t* next_b,
+                                        int64_t* nnext_b) {
+  for (int64_t qb = a0; qb < a1; qb += 4 * (int64_t)step) {
+    uint32_t sc[4], rw[4];
+    bool rel[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t q = qb + start + (int64_t)t * step;
+      sc[t] = (q < a1) ? R.lsucc[q] : RC_NONE;
+      rw[t] = (q < a1) ? R.lrow[q] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (sc[t] != RC_NONE && !(rw[t] & RC_TWO)) mask_add(R.rmask, rw[t], c);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) rel[t] = sc[t] != RC_NONE && atomicSub(&R.cnt[sc[t] & ~RC_BIG], 1) == 1;
+    int nb = 0, ns = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      nb += rel[t] && (sc[t] & RC_BIG);
+      ns += rel[t] && !(sc[t] & RC_BIG);
+    }
+    int tb, ts;
+    const int ob = warp_excl(nb, lane, &tb), os = warp_excl(ns, lane, &ts);
+    unsigned long long bb = 0, bs = 0;
+    if (lane == 0) {
+      if (tb) bb = atomicAdd((unsigned long long*)nnext_b, (unsigned long long)tb);
+      if (ts) bs = atomicAdd((unsigned long long*)nnext_s, (unsigned long long)ts);
+    }
+    bb = __shfl_sync(0xffffffffu, bb, 0) + ob;
+    bs = __shfl_sync(0xffffffffu, bs, 0) + os;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (rel[t]) {
+        if (sc[t] & RC_BIG) next_b[bb++] = sc[t] & ~RC_BIG;
+        else next_s[bs++] = sc[t];
+      }
+  }
+}
+
+// The colour of unit u from its predecessor rows lrow[a0, ah), by one warp.
+__device__ __forceinline__ int warp_colour(const JPRun& R, uint32_t u, int64_t a0, int64_t ah, int lane) {
+  unsigned long long m0 = 0, m1 = 0;
+  mask_or(R, a0, ah, lane, 32, m0, m1);
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 |= __shfl_xor_sync(0xffffffffu, m0, o);
+    m1 |= __shfl_xor_sync(0xffffffffu, m1, o);
+  }
+  int c = mask_pick(m0, m1);
+  for (int base = 0; c < 0; base += 64) {  // uniform over the warp
+    unsigned long long m = prefix_or(R, u, a0, ah, lane, 32, base);
+    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    if (~m) c = base + __ffsll((long long)~m) - 1;
+  }
+  return c;
+}
+
+// The same by the whole CTA (sm: two shared words).
+__device__ __forceinline__ int cta_colour(const JPRun& R, uint32_t u, int64_t a0, int64_t ah, int lane,
+                                          unsigned long long* sm) {
+  if (threadIdx.x == 0) {
+    sm[0] = 0;
+    sm[1] = 0;
+  }
+  __syncthreads();
+  unsigned long long m0 = 0, m1 = 0;
+  mask_or(R, a0, ah, threadIdx.x, blockDim.x, m0, m1);
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 |= __shfl_xor_sync(0xffffffffu, m0, o);
+    m1 |= __shfl_xor_sync(0xffffffffu, m1, o);
+  }
+  if (lane == 0) {
+    if (m0) atomicOr(sm, m0);
+    if (m1) atomicOr(sm + 1, m1);
+  }
+  __syncthreads();
+  int c = mask_pick(sm[0], sm[1]);
+  __syncthreads();
+  for (int base = 0; c < 0; base += 64) {  // uniform over the CTA
+    if (threadIdx.x == 0) sm[0] = 0;
+    __syncthreads();
+    unsigned long long m = prefix_or(R, u, a0, ah, threadIdx.x, blockDim.x, base);
+    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    if (lane == 0 && m) atomicOr(sm, m);
+    __syncthreads();
+    const unsigned long long all = sm[0];
+    if (~all) c = base + __ffsll((long long)~all) - 1;
+    __syncthreads();
+  }
+  return c;
+}
+
+constexpr int64_t JP_TINY = 64;    // list length served by 8 lanes (8 entries a lane)
+constexpr int64_t JP_SLICE = 512;  // entries of a long list one CTA releases
+
+// Colour and release 32 / TG units whose lists hold at most 8 * TG entries,
+// one group of TG lanes per unit (u = RC_NONE: an idle group).  Control flow
+// is uniform over the warp: every lane loads its (at most 8) entries at once,
+// the masks are OR-reduced inside the group, and the released units are
+// reserved on the next frontier once per warp.
+template <int TG>
 __device__ __forceinline__ void jp_tiny(const JPRun& R, uint32_t u, int lane, uint32_t* next_s, int64_t* nnext_s,
                                         uint32_t* next_b, int64_t* nnext_b) {
-  const int sub = lane & (JP_TG - 1);
+  const int sub = lane & (TG - 1);
   int64_t a0 = 0, ah = 0, a1 = 0;
-  if (u != ADJ_NONE) {
+  if (u != RC_NONE) {
     a0 = R.aptr[u];
-    ah = a0 + R.nhigh[u];
+    ah = a0 + R.npred[u];
     a1 = R.aptr[u + 1];
   }
-  uint32_t e[8];
-  int cw[8];
+  uint32_t rw[8], sc[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
-    const int64_t q = a0 + sub + t * JP_TG;
-    e[t] = q < ah ? R.adj[q] : ADJ_NONE;
+    const int64_t q = a0 + sub + t * TG;
+    rw[t] = q < a1 ? R.lrow[q] : 0u;
+    sc[t] = q < a1 ? R.lsucc[q] : RC_NONE;
   }
+  unsigned long long m0 = 0, m1 = 0;
 #pragma unroll
-  for (int t = 0; t < 8; ++t) cw[t] = e[t] != ADJ_NONE ? __ldcg(R.color + (e[t] & ~ADJ_BIG)) : -1;
-  // at most 64 higher-priority entries: the colour is found in the first or
-  // the second window of 64
-  int chosen = -1;
-  for (int base = 0;; base += 64) {
-    unsigned long long m = 0;
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (cw[t] >= base && cw[t] < base + 64) m |= 1ull << (cw[t] - base);
-    for (int o = JP_TG / 2; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-    if (chosen < 0 && ~m) chosen = base + __ffsll((long long)~m) - 1;
-    if (__all_sync(0xffffffffu, chosen >= 0)) break;
+  for (int t = 0; t < 8; ++t)
+    if (a0 + sub + t * TG < ah) entry_mask(R, rw[t], m0, m1);
+  for (int o = TG / 2; o > 0; o >>= 1) {
+    m0 |= __shfl_xor_sync(0xffffffffu, m0, o);
+    m1 |= __shfl_xor_sync(0xffffffffu, m1, o);
   }
-  if (u != ADJ_NONE && sub == 0) R.color[u] = chosen;
+  int chosen = (u != RC_NONE) ? mask_pick(m0, m1) : 0;
+  if (__any_sync(0xffffffffu, chosen < 0)) {
+    const bool slow = chosen < 0;  // the same in all lanes of a group
+    for (int base = 0;; base += 64) {
+      unsigned long long m = 0;
+      if (slow)
+        for (int t = 0; t < 8; ++t)
+          if (a0 + sub + t * TG < ah) m |= prefix_mask(R, rw[t], u, base);
+      for (int o = TG / 2; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+      if (chosen < 0 && ~m) chosen = base + __ffsll((long long)~m) - 1;
+      if (__all_sync(0xffffffffu, chosen >= 0)) break;
+    }
+  }
+  if (u != RC_NONE && sub == 0) R.color[u] = chosen;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (sc[t] != RC_NONE && !(rw[t] & RC_TWO)) mask_add(R.rmask, rw[t], chosen);
   bool rel[8];
   int nb = 0, ns = 0;
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
-    const int64_t q = ah + sub + t * JP_TG;
-    e[t] = q < a1 ? R.adj[q] : ADJ_NONE;
-  }
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    rel[t] = e[t] != ADJ_NONE && atomicSub(&R.cnt[e[t] & ~ADJ_BIG], 1) == 1;
-    nb += rel[t] && (e[t] & ADJ_BIG);
-    ns += rel[t] && !(e[t] & ADJ_BIG);
+    rel[t] = sc[t] != RC_NONE && atomicSub(&R.cnt[sc[t] & ~RC_BIG], 1) == 1;
+    nb += rel[t] && (sc[t] & RC_BIG);
+    ns += rel[t] && !(sc[t] & RC_BIG);
   }
   int tb, ts;
   const int ob = warp_excl(nb, lane, &tb), os = warp_excl(ns, lane, &ts);
@@ -969,43 +1131,28 @@ __device__ __forceinline__ void jp_tiny(const JPRun& R, uint32_t u, int lane, ui
 #pragma unroll
   for (int t = 0; t < 8; ++t)
     if (rel[t]) {
-      if (e[t] & ADJ_BIG) next_b[bb++] = e[t] & ~ADJ_BIG;
-      else next_s[bs++] = e[t];
+      if (sc[t] & RC_BIG) next_b[bb++] = sc[t] & ~RC_BIG;
+      else next_s[bs++] = sc[t];
     }
-}
-
-constexpr int64_t JP_SLICE = 1024;  // lower-priority entries of a long list one CTA releases
-
-// The smallest colour not held by the entries adj[a0, ah) (all coloured),
-// computed by the whole CTA, 64 colours at a time.
-__device__ __forceinline__ int cta_colour(const JPRun& R, int64_t a0, int64_t ah, int lane, unsigned long long* smask) {
-  int base = 0, chosen = -1;
-  while (chosen < 0) {
-    if (threadIdx.x == 0) *smask = 0;
-    __syncthreads();
-    unsigned long long m = color_mask(R.adj, R.color, a0, ah, threadIdx.x, blockDim.x, base);
-    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-    if (lane == 0 && m) atomicOr(smask, m);
-    __syncthreads();
-    const unsigned long long all = *smask;
-    if (~all) chosen = base + __ffsll((long long)~all) - 1;
-    base += 64;
-    __syncthreads();
-  }
-  return chosen;
 }
 
 // Rounds [r0, r0 + nr) of the data-flow colouring; with nr > 1 the launch must
 // be cooperative (a grid barrier separates the rounds).
-__global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
-  __shared__ unsigned long long smask;
+__global__ void __launch_bounds__(256, 4) k_jp(JPRun R, int64_t r0, int64_t nr) {
+  __shared__ unsigned long long smask[2];
   __shared__ uint32_t s_u[256];
   __shared__ int s_off[257];
   __shared__ int s_wsum[8];
+  __shared__ long long s_fc[2];
   const int lane = threadIdx.x & 31;
   for (int64_t r = r0; r < r0 + nr; ++r) {
     const int in = (int)(r % 3), out = (int)((r + 1) % 3), z = (int)((r + 2) % 3);
-    const int64_t ns = __ldcg(R.fc + 2 * in), nb = __ldcg(R.fc + 2 * in + 1);
+    if (threadIdx.x == 0) {  // one read of the frontier sizes per CTA
+      s_fc[0] = __ldcg(R.fc + 2 * in);
+      s_fc[1] = __ldcg(R.fc + 2 * in + 1);
+    }
+    __syncthreads();
+    const int64_t ns = s_fc[0], nb = s_fc[1];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       // slot z is nobody's input this round; clearing it even when the
       // frontier is empty keeps rounds launched past the end (one launch per
@@ -1022,16 +1169,15 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
     int64_t* nnext_s = R.fc + 2 * out;
     int64_t* nnext_b = R.fc + 2 * out + 1;
     if (nb > 0 && nb <= (int64_t)blockDim.x && nb < (int64_t)gridDim.x) {  // uniform
-      // few long lists (a chain of hubs): the lower-priority part of each is
-      // cut into slices of JP_SLICE entries spread over the CTAs; the CTA of
-      // a slice finds the unit's colour from its higher-priority part (short
-      // for a hub) and releases the slice.  s_off = exclusive scan of the
-      // slice counts over the frontier.
+      // few long lists (a chain of hubs): each list is cut into slices of
+      // JP_SLICE entries spread over the CTAs; the CTA of a slice finds the
+      // unit's colour from its predecessor rows (few for a hub) and releases
+      // the slice.  s_off = exclusive scan of the slice counts.
       int nsl = 0;
       if (threadIdx.x < nb) {
         const uint32_t u = __ldcg(front_b + threadIdx.x);
-        const int64_t ah = R.aptr[u] + R.nhigh[u], a1 = R.aptr[u + 1];
-        nsl = (int)max((int64_t)1, (a1 - ah + JP_SLICE - 1) / JP_SLICE);
+        const int64_t a0 = R.aptr[u], a1 = R.aptr[u + 1];
+        nsl = (int)max((int64_t)1, (a1 - a0 + JP_SLICE - 1) / JP_SLICE);
         s_u[threadIdx.x] = u;
       }
       int wt;
@@ -1049,53 +1195,56 @@ __global__ void __launch_bounds__(256) k_jp(JPRun R, int64_t r0, int64_t nr) {
         while (s_off[j + 1] <= g) ++j;  // uniform; g only grows
         const uint32_t u = s_u[j];
         const int64_t sl = g - s_off[j];
-        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
-        const int chosen = cta_colour(R, a0, ah, lane, &smask);
+        const int64_t a0 = R.aptr[u], ah = a0 + R.npred[u], a1 = R.aptr[u + 1];
+        const int chosen = cta_colour(R, u, a0, ah, lane, smask);
         if (sl == 0 && threadIdx.x == 0) R.color[u] = chosen;
-        const int64_t b0 = ah + sl * JP_SLICE, b1 = min(a1, b0 + JP_SLICE);
-        release(R.adj, R.cnt, b0, b1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+        const int64_t b0 = a0 + sl * JP_SLICE, b1 = min(a1, b0 + JP_SLICE);
+        release(R, chosen, b0, b1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
       }
       __syncthreads();  // s_u / s_off are rewritten next round
     } else {
-      // long adjacency lists: one CTA each
+      // long lists: one CTA each
       for (int64_t t = blockIdx.x; t < nb; t += gridDim.x) {
         const uint32_t u = __ldcg(front_b + t);
-        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
-        const int chosen = cta_colour(R, a0, ah, lane, &smask);
+        const int64_t a0 = R.aptr[u], ah = a0 + R.npred[u], a1 = R.aptr[u + 1];
+        const int chosen = cta_colour(R, u, a0, ah, lane, smask);
         if (threadIdx.x == 0) R.color[u] = chosen;
-        release(R.adj, R.cnt, ah, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
+        release(R, chosen, a0, a1, threadIdx.x, blockDim.x, lane, next_s, nnext_s, next_b, nnext_b);
       }
     }
-    // the rest.  A frontier larger than the warps: four units per warp, one
-    // group of JP_TG lanes each when all four lists are short, else one after
+    // the rest.  A frontier larger than the warps: 16 (or 4) units per warp,
+    // 2 (or 8) lanes each when their lists are short enough, else one after
     // the other with the whole warp.  A smaller one: one unit per warp.
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int per = ns > nwarps ? 4 : 1;
+    const int per = ns > 4 * nwarps ? 16 : (ns > nwarps ? 4 : 1);
     for (int64_t tb = warp * per; tb < ns; tb += nwarps * per) {  // warp-uniform
-      uint32_t u4 = ADJ_NONE;
+      uint32_t uu = RC_NONE;
       int64_t len = 0;
       if (lane < per && tb + lane < ns) {
-        u4 = __ldcg(front_s + tb + lane);
-        len = R.aptr[u4 + 1] - R.aptr[u4];
+        uu = __ldcg(front_s + tb + lane);
+        len = R.aptr[uu + 1] - R.aptr[uu];
       }
-      if (per == 4 && __all_sync(0xffffffffu, len <= JP_TINY)) {
-        jp_tiny(R, __shfl_sync(0xffffffffu, u4, lane / JP_TG), lane, next_s, nnext_s, next_b, nnext_b);
+      if (per == 16 && __all_sync(0xffffffffu, len <= 16)) {
+        jp_tiny<2>(R, __shfl_sync(0xffffffffu, uu, lane / 2), lane, next_s, nnext_s, next_b, nnext_b);
         continue;
       }
-      for (int j = 0; j < per; ++j) {
-        const uint32_t u = __shfl_sync(0xffffffffu, u4, j);
-        if (u == ADJ_NONE) break;  // uniform
-        const int64_t a0 = R.aptr[u], ah = a0 + R.nhigh[u], a1 = R.aptr[u + 1];
-        int base = 0, chosen = -1;
-        while (chosen < 0) {
-          unsigned long long m = color_mask(R.adj, R.color, a0, ah, lane, 32, base);
-          for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-          if (~m) chosen = base + __ffsll((long long)~m) - 1;
-          base += 64;
+      for (int qd = 0; qd < per; qd += 4) {  // uniform
+        const int src = qd + (lane & 3);
+        const uint32_t uq = __shfl_sync(0xffffffffu, uu, src);  // lanes 0..3: this quad's units
+        const int64_t lq = __shfl_sync(0xffffffffu, len, src);
+        if (per > 1 && __all_sync(0xffffffffu, lane >= 4 || lq <= JP_TINY)) {
+          jp_tiny<8>(R, __shfl_sync(0xffffffffu, uq, lane / 8), lane, next_s, nnext_s, next_b, nnext_b);
+          continue;
         }
-        if (lane == 0) R.color[u] = chosen;
-        release(R.adj, R.cnt, ah, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+        for (int j = 0; j < (per > 1 ? 4 : 1); ++j) {
+          const uint32_t u = __shfl_sync(0xffffffffu, uq, j);
+          if (u == RC_NONE) break;  // uniform
+          const int64_t a0 = R.aptr[u], ah = a0 + R.npred[u], a1 = R.aptr[u + 1];
+          const int chosen = warp_colour(R, u, a0, ah, lane);
+          if (lane == 0) R.color[u] = chosen;
+          release(R, chosen, a0, a1, lane, 32, lane, next_s, nnext_s, next_b, nnext_b);
+        }
       }
     }
     if (nr > 1 && !jp_barrier(R.bar, R.err)) return;
@@ -1555,22 +1704,35 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   int32_t* color = tmp.alloc<int32_t>(U + 1);
   TH_CUDA(cudaMemsetAsync(color, 0xff, (U + 1) * sizeof(int32_t), s));
   JPView V{raw.colptr, raw.rowidx, orowptr, csr_p, colof, unit_of_col, slack_unit, ufirst, ulen, unnz, uh, Us, slack_row};
-  TH_CHECK(Us < (int64_t)ADJ_BIG - 1, THETIS_E_INVALID, "too many coordinate units (adjacency ids are 31-bit)");
+  TH_CHECK(Us < (int64_t)RC_BIG - 1, THETIS_E_INVALID, "too many coordinate units (unit ids are 31-bit)");
   if (Us > 0) {
     int dev = 0, sms = 0, coop = 0, per = 0;
     TH_CUDA(cudaGetDevice(&dev));
     TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     TH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jp, 256, 0));
-    int64_t* aptr = tmp.alloc<int64_t>(Us + 1);
-    int32_t* nhigh = tmp.alloc<int32_t>(Us + 1);
+    // row ranks, successors and per-unit (row, successor) lists; a list holds
+    // at most one entry per non-zero
     uint32_t* rowunit = tmp.alloc<uint32_t>(nnz + 1);
     ulonglong2* ukey = tmp.alloc<ulonglong2>(Us);
+    int32_t* rank = tmp.alloc<int32_t>(nnz + 1);
+    uint32_t* sorted = tmp.alloc<uint32_t>(nnz + 1);
+    uint32_t* succ = tmp.alloc<uint32_t>(nnz + 1);
+    uint32_t* lval = tmp.alloc<uint32_t>(nnz + 1);
+    int32_t* rowcnt = tmp.alloc<int32_t>(M + 1);
     int64_t* hc = tmp.alloc<int64_t>(nnz + 1);
     int64_t* lc = tmp.alloc<int64_t>(nnz + 1);
+    int64_t* aptr = tmp.alloc<int64_t>(Us + 1);
+    int32_t* npred = tmp.alloc<int32_t>(Us + 1);
     int64_t* lbase = tmp.alloc<int64_t>(Us);
     int64_t* hend = tmp.alloc<int64_t>(Us);
     uint8_t* ubig = tmp.alloc<uint8_t>(Us);
+    uint32_t* lrow = tmp.alloc<uint32_t>(nnz + 1);
+    uint32_t* lsucc = tmp.alloc<uint32_t>(nnz + 1);
+    unsigned long long* rmask = tmp.alloc<unsigned long long>(2 * (M + 1));
+    TH_CUDA(cudaMemsetAsync(sorted, 0xff, (nnz + 1) * sizeof(uint32_t), s));
+    TH_CUDA(cudaMemsetAsync(rmask, 0, 2 * (M + 1) * sizeof(unsigned long long), s));
+    TH_CUDA(cudaMemsetAsync(rowcnt, 0, (M + 1) * sizeof(int32_t), s));
     if (nnz > 0) {
       k_row_units<<<grid_for(nnz, 256), 256, 0, s>>>(V, nnz, rowunit);
       TH_LAUNCHED();
@@ -1578,14 +1740,21 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     k_unit_prio<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, ukey);
     TH_LAUNCHED();
     if (nnz > 0) {
-      k_adj_count<<<grid_for(nnz, 256), 256, 0, s>>>(V, rowunit, ukey, nnz, hc, lc);
+      k_row_rank<<<grid_for(nnz, 256), 256, 0, s>>>(V, rkeys, rowunit, ukey, nnz, rank, sorted, rowcnt);
+      TH_LAUNCHED();
+      k_row_links<<<grid_for(nnz, 256), 256, 0, s>>>(V, rkeys, rank, sorted, rowcnt, nnz, hc, lc, succ, lval);
       TH_LAUNCHED();
     }
     exclusive_scan_i64(hc, hc, nnz, tmp, s);
     exclusive_scan_i64(lc, lc, nnz, tmp, s);
     JPRun R;
+    R.lrow = lrow;
+    R.lsucc = lsucc;
     R.aptr = aptr;
-    R.nhigh = nhigh;
+    R.npred = npred;
+    R.rowptr = orowptr;
+    R.sorted = sorted;
+    R.rmask = rmask;
     R.cnt = tmp.alloc<int32_t>(Us + 1);
     R.color = color;
     for (int q = 0; q < 2; ++q) {
@@ -1600,16 +1769,11 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     TH_CUDA(cudaMemsetAsync(R.done, 0, sizeof(unsigned long long), s));
     TH_CUDA(cudaMemsetAsync(R.bar, 0, sizeof(unsigned), s));
     TH_CUDA(cudaMemsetAsync(R.err, 0, sizeof(int), s));
-    k_adj_units<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, nnz, hc, lc, aptr, nhigh, R.cnt, lbase, hend, ubig, R.fs[0],
-                                                  R.fc + 0, R.fb[0], R.fc + 1);
+    k_chain_units<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, nnz, hc, lc, aptr, npred, R.cnt, lbase, hend, ubig,
+                                                    R.fs[0], R.fc + 0, R.fb[0], R.fc + 1);
     TH_LAUNCHED();
-    int64_t nadj = 0;
-    TH_CUDA(cudaMemcpyAsync(&nadj, aptr + Us, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    TH_CUDA(cudaStreamSynchronize(s));
-    uint32_t* adj = tmp.alloc<uint32_t>(nadj + 1);
-    R.adj = adj;
     if (nnz > 0) {
-      k_adj_fill<<<grid_for(nnz, 256), 256, 0, s>>>(V, rowunit, ukey, ubig, nnz, hc, lc, lbase, hend, adj);
+      k_chain_fill<<<grid_for(nnz, 256), 256, 0, s>>>(V, nnz, hc, lc, lbase, hend, succ, lval, ubig, lrow, lsucc);
       TH_LAUNCHED();
     }
     const int64_t max_rounds = Us + 2;

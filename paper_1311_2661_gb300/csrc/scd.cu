@@ -946,28 +946,44 @@ __global__ void k_tail_rowcount(const int64_t* colptr, const uint32_t* rowidx, c
   }
 }
 
+// one warp per unit: rows shared with another tail column (T) and the rest (H)
 __global__ void k_tail_counts(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
                               const int32_t* rcnt, int64_t* hc, int64_t* tc) {
-  GSTRIDE(u, n) {
-    const int64_t j = col[u];
-    int64_t t = 0;
-    for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) t += rcnt[idx_of(rowidx[q])] > 1;
-    tc[u] = t;
-    hc[u] = colptr[j + 1] - colptr[j] - t;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    const int64_t j = col[u], q0 = colptr[j], q1 = colptr[j + 1];
+    int t = 0;
+    for (int64_t q = q0 + lane; q < q1; q += 32) t += rcnt[idx_of(rowidx[q])] > 1;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      tc[u] = t;
+      hc[u] = q1 - q0 - t;
+    }
   }
 }
 
-// one thread per unit, entries in column order: a deterministic split
+// one warp per unit, entries kept in column order (a ballot per 32 entries):
+// the same deterministic split as a serial pass
 __global__ void k_tail_fill(const int64_t* colptr, const uint32_t* rowidx, const int64_t* col, int64_t n,
                             const int32_t* rcnt, const int64_t* hptr, const int64_t* tptr, uint32_t* hrow,
                             uint32_t* trow) {
-  GSTRIDE(u, n) {
-    const int64_t j = col[u];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    const int64_t j = col[u], q0 = colptr[j], q1 = colptr[j + 1];
     int64_t h = hptr[u], t = tptr[u];
-    for (int64_t q = colptr[j]; q < colptr[j + 1]; ++q) {
-      const uint32_t e = rowidx[q];
-      if (rcnt[idx_of(e)] > 1) trow[t++] = e;
-      else hrow[h++] = e;
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane;
+      const bool in = q < q1;
+      const uint32_t e = in ? rowidx[q] : 0u;
+      const bool shared = in && rcnt[idx_of(e)] > 1;
+      const unsigned ms = __ballot_sync(0xffffffffu, shared), mh = __ballot_sync(0xffffffffu, in && !shared);
+      if (shared) trow[t + __popc(ms & lt)] = e;
+      else if (in) hrow[h + __popc(mh & lt)] = e;
+      t += __popc(ms);
+      h += __popc(mh);
     }
   }
 }
@@ -1018,7 +1034,7 @@ void ensure_tail(Problem& P) {
   TH_LAUNCHED();
   int64_t* hc = tmp.alloc<int64_t>(n + 1);
   int64_t* tc = tmp.alloc<int64_t>(n + 1);
-  k_tail_counts<<<grid_for(n, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, hc, tc);
+  k_tail_counts<<<grid_for(n * 32, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, hc, tc);
   TH_LAUNCHED();
   P.tail_hptr = P.mem.alloc<int64_t>(n + 1);
   P.tail_tptr = P.mem.alloc<int64_t>(n + 1);
@@ -1030,8 +1046,8 @@ void ensure_tail(Problem& P) {
   TH_CUDA(cudaStreamSynchronize(s));
   P.tail_hrow = P.mem.alloc<uint32_t>(tot[0] + 1);
   P.tail_trow = P.mem.alloc<uint32_t>(tot[1] + 1);
-  k_tail_fill<<<grid_for(n, 64), 64, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, P.tail_hptr, P.tail_tptr,
-                                             P.tail_hrow, P.tail_trow);
+  k_tail_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(P.colptr, P.rowidx, P.tail_col, n, rcnt, P.tail_hptr,
+                                                   P.tail_tptr, P.tail_hrow, P.tail_trow);
   TH_LAUNCHED();
   P.tail_h = P.mem.alloc<float>(n);
   P.tail_d = P.mem.alloc<float>(n);
