@@ -1365,13 +1365,17 @@ __global__ void k_refresh(const int64_t* rowptr, const uint32_t* colidx, const f
                           double* r64, float* r) {
   GSTRIDE(i, M) {
     double acc = 0.0;
-    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-      uint32_t e = colidx[q];
-      double a = rval ? (double)rval[q] : (double)sgn_of(e);
-      uint32_t j = rval ? e : idx_of(e);
-      acc += a * (double)x[j];
+    if (rval) {
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) acc += (double)rval[q] * (double)x[colidx[q]];
+    } else {
+      // +-1 coefficients: a sign flip instead of a product
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        const uint32_t e = colidx[q];
+        const double xj = x[idx_of(e)];
+        acc += (e & NEG_BIT) ? -xj : xj;
+      }
     }
-    if (i < Msl) acc += (double)sig[i] * (double)s[i];
+    if (i < Msl) acc += sig[i] > 0 ? (double)s[i] : -(double)s[i];
     acc -= (double)b[i];
     r64[i] = acc;
     r[i] = (float)acc;
@@ -1493,13 +1497,43 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
         } else {
           const int64_t base = V.ss_e0[k] + (p >> 5) * 32 * W + (p & 31);
           double acc = 0.0, sq = 0.0;
-          for (int q = 0; q < W; ++q) {
-            const uint32_t e = V.ell[base + (int64_t)q * 32];
-            if (e == ELL_PAD) break;  // slots fill from the front
-            const double a = V.ellv ? (double)V.ellv[base + (int64_t)q * 32] : (double)sgn_of(e);
-            acc += a * V.r64[V.ellv ? e : idx_of(e)];
-            sq += a * a;
+          int nslot = 0;
+          // four slots at a time (their loads overlap), summed in slot order;
+          // slots fill from the front
+          for (int qb = 0; qb < W; qb += 4) {
+            uint32_t e[4];
+            double a[4], rv[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) e[t] = (qb + t < W) ? V.ell[base + (int64_t)(qb + t) * 32] : ELL_PAD;
+            if (V.ellv) {
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (e[t] != ELL_PAD) {
+                  a[t] = (double)V.ellv[base + (int64_t)(qb + t) * 32];
+                  rv[t] = V.r64[e[t]];
+                }
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (e[t] != ELL_PAD) {
+                  acc += a[t] * rv[t];
+                  sq += a[t] * a[t];
+                }
+            } else {
+              // +-1 coefficients: a sign flip instead of a product, ||a||^2 =
+              // the slot count (FP64 instructions are scarce on this part)
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (e[t] != ELL_PAD) rv[t] = V.r64[idx_of(e[t])];
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (e[t] != ELL_PAD) {
+                  acc += (e[t] & NEG_BIT) ? -rv[t] : rv[t];
+                  ++nslot;
+                }
+            }
+            if (e[3] == ELL_PAD) break;
           }
+          if (!V.ellv) sq = (double)nslot;
           const double xj = V.x[j], xb = V.xbar ? V.xbar[j] : 0.0;
           const double g = (double)V.ct[j] + beta * acc + (xj - xb) * ib;
           const double L = beta * sq + ib;
@@ -1578,25 +1612,43 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
     obj += (double)V.c[j] * xj;
     xx += (xj - xb) * (xj - xb);
   }
-  // (d) rows and slacks
-  GSTRIDE(i, V.M) {
-    double ri = V.r64[i];
-    inf = fmax(inf, fabs(ri));
-    rr += ri * ri;
-    if (V.ubar) ur += (double)V.ubar[i] * ri;
-    if (i < V.Msl) {
-      double sv = V.s[i], sb = V.sbar ? V.sbar[i] : 0.0;
-      double sg = (double)V.sig[i];
-      double g = (V.cs ? (double)V.cs[i] : 0.0) + beta * sg * ri + (sv - sb) * ib;
-      double sn = fmax(sv - g * inv_ls, 0.0);
-      if (!V.frozen) {
-        rho = fmax(rho, fabs(sn - sv));
-      } else if (!V.frozen[V.inst_row[i]]) {
-        rho = fmax(rho, fabs(sn - sv));
-        rho_max(V.inst_rho + V.inst_row[i], fabs(sn - sv));
+  // (d) rows and slacks.  FP64 instructions are scarce on this part (a few
+  // per clock per SM): maxima of non-negative values are taken on their bit
+  // patterns (the same order), and the slack step without cs / sbar takes one
+  // fused multiply-add for its gradient.
+  {
+    unsigned long long rho_b = 0, inf_b = 0;
+    const bool plain = !V.cs && !V.sbar;
+    GSTRIDE(i, V.M) {
+      const double ri = V.r64[i];
+      inf_b = max(inf_b, (unsigned long long)__double_as_longlong(ri) & 0x7fffffffffffffffull);
+      rr = fma(ri, ri, rr);
+      if (V.ubar) ur += (double)V.ubar[i] * ri;
+      if (i < V.Msl) {
+        const double sv = V.s[i];
+        const double bsr = V.sig[i] > 0 ? beta * ri : -(beta * ri);  // beta * sign * r, sign = +-1
+        double ds, g;
+        if (plain) {
+          ds = sv;
+          g = fma(sv, ib, bsr);
+        } else {
+          ds = sv - (V.sbar ? (double)V.sbar[i] : 0.0);
+          g = fma(ds, ib, (V.cs ? (double)V.cs[i] : 0.0) + bsr);
+        }
+        double sn = fma(-g, inv_ls, sv);
+        if (__double_as_longlong(sn) < 0) sn = 0.0;  // max(., 0)
+        const unsigned long long db = (unsigned long long)__double_as_longlong(sn - sv) & 0x7fffffffffffffffull;
+        if (!V.frozen) {
+          rho_b = max(rho_b, db);
+        } else if (!V.frozen[V.inst_row[i]]) {
+          rho_b = max(rho_b, db);
+          rho_max(V.inst_rho + V.inst_row[i], __longlong_as_double((long long)db));
+        }
+        xx = fma(ds, ds, xx);
       }
-      xx += (sv - sb) * (sv - sb);
     }
+    rho = fmax(rho, __longlong_as_double((long long)rho_b));
+    inf = fmax(inf, __longlong_as_double((long long)inf_b));
   }
   // block reduction, fixed order
   __shared__ double sm[NRED][8];
