@@ -711,7 +711,7 @@ __device__ __forceinline__ bool ahead(ulonglong2 ka, uint32_t a, ulonglong2 kb, 
 // sorted[rowptr[i] + rank] lists the row's units in order (with a gap where a
 // repeat was counted).
 __global__ void k_row_rank(JPView V, const uint32_t* rowof, const uint32_t* rowunit, const ulonglong2* key,
-                           int64_t nnz, int32_t* rank, uint32_t* sorted, int32_t* rowcnt) {
+                           int64_t nnz, int32_t* rank, uint32_t* sorted, int32_t* rowcnt, int* repeat) {
   GSTRIDE(q, nnz) {
     const uint32_t u = rowunit[q];
     int32_t r = -1;
@@ -734,6 +734,8 @@ __global__ void k_row_rank(JPView V, const uint32_t* rowof, const uint32_t* rowu
         r = c;
         sorted[q0 + c] = u;
         atomicAdd(&rowcnt[i], 1);
+      } else {
+        *repeat = 1;  // a block with two columns in this row
       }
     }
     rank[q] = r;
@@ -1715,6 +1717,7 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     // at most one entry per non-zero
     uint32_t* rowunit = tmp.alloc<uint32_t>(nnz + 1);
     ulonglong2* ukey = tmp.alloc<ulonglong2>(Us);
+    int* repeat = nullptr;  // set when a block has two columns in one row
     int32_t* rank = tmp.alloc<int32_t>(nnz + 1);
     uint32_t* sorted = tmp.alloc<uint32_t>(nnz + 1);
     uint32_t* succ = tmp.alloc<uint32_t>(nnz + 1);
@@ -1733,6 +1736,8 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     TH_CUDA(cudaMemsetAsync(sorted, 0xff, (nnz + 1) * sizeof(uint32_t), s));
     TH_CUDA(cudaMemsetAsync(rmask, 0, 2 * (M + 1) * sizeof(unsigned long long), s));
     TH_CUDA(cudaMemsetAsync(rowcnt, 0, (M + 1) * sizeof(int32_t), s));
+    repeat = tmp.alloc<int>(1);
+    TH_CUDA(cudaMemsetAsync(repeat, 0, sizeof(int), s));
     if (nnz > 0) {
       k_row_units<<<grid_for(nnz, 256), 256, 0, s>>>(V, nnz, rowunit);
       TH_LAUNCHED();
@@ -1740,7 +1745,7 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     k_unit_prio<<<grid_for(Us, 256), 256, 0, s>>>(V, Us, ukey);
     TH_LAUNCHED();
     if (nnz > 0) {
-      k_row_rank<<<grid_for(nnz, 256), 256, 0, s>>>(V, rkeys, rowunit, ukey, nnz, rank, sorted, rowcnt);
+      k_row_rank<<<grid_for(nnz, 256), 256, 0, s>>>(V, rkeys, rowunit, ukey, nnz, rank, sorted, rowcnt, repeat);
       TH_LAUNCHED();
       k_row_links<<<grid_for(nnz, 256), 256, 0, s>>>(V, rkeys, rank, sorted, rowcnt, nnz, hc, lc, succ, lval);
       TH_LAUNCHED();
@@ -1799,10 +1804,12 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
       }
     }
     unsigned long long hdone = 0;
-    int herr = 0;
+    int herr = 0, hrep = 0;
     TH_CUDA(cudaMemcpyAsync(&hdone, R.done, sizeof(hdone), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(&hrep, repeat, sizeof(int), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaStreamSynchronize(s));
+    P.blk_shared = hrep != 0;
     TH_CHECK(herr == 0, THETIS_E_TIMEOUT, "colouring: grid barrier timed out");
     TH_CHECK((int64_t)hdone == Us, THETIS_E_CUDA, "colouring left units uncoloured");
   }

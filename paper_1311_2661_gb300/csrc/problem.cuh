@@ -78,6 +78,7 @@ struct Problem {
   bool bounds_uniform = false;
   float lo_u = 0.f, hi_u = 1.f;
   int slack_sign_uniform = 0;
+  bool blk_shared = false;  // some simplex block has two columns in one row
 
   // batch meta (thetis_build_batch): instance t owns vertices [bnoff[t], bnoff[t+1])
   // and edges [beoff[t], beoff[t+1]) of the union

@@ -52,6 +52,7 @@ struct StepView {
   float lfix;        // > 0: global L_max (step_rule 1)
   int k;
   int async;         // 1: atomic residual updates
+  int blk_shared;    // 1: a simplex block has two columns in one row (its scatter adds atomically)
   int small_g;       // small classes: 8 / small_g row slots per lane (small_g = 1, 2, 4 or 8, tuned)
   const uint32_t* ell;  // ELL row ids of the small classes
   const float* ellv;    // ELL values (null: +-1 encoded in ell)
@@ -430,16 +431,24 @@ __device__ __forceinline__ void step_block(const StepView& V, int64_t j0, int la
   if (lane < k) V.x[j0 + lane] = xn;
   float dq = __shfl_sync(0xffffffffu, d, act ? q : 0);
   if (act && dq != 0.f) {
+    // two columns of the block in one row (blk_shared): both changes must
+    // land, so the scatter adds atomically
+    const bool atom = V.async || V.blk_shared;
 #pragma unroll
     for (int u = 0; u < CACHE; ++u) {
       int64_t p = p0 + t + (int64_t)u * S;
-      if (p < p1) r_add(V, rowof(V, ce[u]), cr[u], coef(V, p, ce[u]) * dq);
+      if (p < p1) {
+        const uint32_t row = rowof(V, ce[u]);
+        const float delta = coef(V, p, ce[u]) * dq;
+        if (atom) atomicAdd(&V.r[row], delta);
+        else V.r[row] = cr[u] + delta;
+      }
     }
     for (int64_t p = p0 + t + (int64_t)CACHE * S; p < p1; p += S) {
       uint32_t e = V.rowidx[p];
       uint32_t row = rowof(V, e);
       float delta = coef(V, p, e) * dq;
-      if (V.async) atomicAdd(&V.r[row], delta);
+      if (atom) atomicAdd(&V.r[row], delta);
       else V.r[row] = ldr(V, row) + delta;
     }
   }
@@ -918,6 +927,7 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.lfix = (a.step_rule == 1) ? (float)(a.beta * P.lmax_sq + 1.0 / a.beta) : 0.f;
   V.k = P.k;
   V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
+  V.blk_shared = P.blk_shared ? 1 : 0;
   V.small_g = P.small_g;
   V.ell = P.ell;
   V.ellv = P.has_val ? P.ellv : nullptr;

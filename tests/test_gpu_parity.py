@@ -362,3 +362,52 @@ def test_every_small_group_matches_oracle(group):
 
 def _force_group(h, group):
     gpu().thetis_set_launch_shape(h, group, 0)
+
+
+def _general_lp_from_rows(rows, n, rng, block_first, block_k):
+    """CSC of a general LP whose rows hold the given column sets (coefficients
+    +-1 and 2), random row kinds, bounds [0, hi] with simplex blocks."""
+    M = len(rows)
+    entries = sorted((int(j), i) for i, r in enumerate(rows) for j in r)
+    colptr = np.zeros(n + 1, np.int64)
+    for j, _ in entries:
+        colptr[j + 1] += 1
+    colptr = np.cumsum(colptr)
+    rowidx = np.array([i for _, i in entries], np.int32)
+    val = rng.choice([-1.0, 1.0, 2.0], size=len(entries)).astype(np.float32)
+    b = rng.normal(0, 1, M).astype(np.float32)
+    c = rng.normal(0, 1, n).astype(np.float32)
+    lo = np.zeros(n, np.float32)
+    hi = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    for f in block_first:
+        hi[f:f + block_k] = 1
+    rk = rng.integers(0, 3, M).astype(np.uint8)
+    return M, colptr, rowidx, val, b, c, lo, hi, rk
+
+
+def test_colouring_beyond_the_row_masks():
+    """Dense rows (320 columns) force more than 300 colours, past the 127 the
+    per-row colour masks hold, so the colouring takes its slow path; rows with
+    two columns of one block, and rows of exactly two units (one of them a
+    block appearing twice), take the repeat and two-unit paths.  Colouring
+    equal to the oracle's; a short solve matches."""
+    rng = np.random.default_rng(21)
+    n, k = 700, 3
+    bf = np.array([30, 300, 600], np.int64)
+    rows = [rng.choice(n, 320, replace=False) for _ in range(3)]
+    rows += [rng.choice(n, 2, replace=False) for _ in range(200)]
+    rows += [np.array([30, 31, 300, 301, 302]), np.array([600, 601, 5]), np.array([302, 30, 32, 450])]
+    while len(rows) < 420:
+        rows.append(rng.choice(n, int(rng.integers(3, 7)), replace=False))
+    M, colptr, rowidx, val, b, c, lo, hi, rk = _general_lp_from_rows(rows, n, rng, bf, k)
+    T = gpu()
+    h = T.thetis_create(M, n, colptr, rowidx, b, c, lo, hi, rk, csc_val=val, block_k=k, block_first=bf, seed=4)
+    lp = oracle.OracleLP.general(M, colptr, rowidx, val.astype(np.float64), b.astype(np.float64),
+                                 c.astype(np.float64), lo.astype(np.float64), hi.astype(np.float64), rk, k, bf)
+    col_o, nc_o = lp.color(4)
+    assert nc_o > 300
+    assert h.sizes["ncolors"] == nc_o
+    assert np.array_equal(h.colors(), col_o)
+    h.solve(beta=5.0, epochs=20, refresh_every=10)
+    x_o, _ = lp.solve(beta=5.0, epochs=20, refresh_every=10, color=col_o)
+    assert np.max(np.abs(gpu_full_x(h) - x_o)) <= X_TOL
