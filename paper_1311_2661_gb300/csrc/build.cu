@@ -673,11 +673,11 @@ __device__ __forceinline__ bool higher(const JPView& V, int64_t a, int64_t b) {
 // 0..RC_OVF-1 are all taken, the colour is found from the prefixes
 // themselves).  Per unit a list of (row, successor) entries, the rows where
 // it has a predecessor first (npred[u] of them).  A row of exactly two units
-// needs no mask: the second reads the first one's colour directly.  Units of one frontier share
-// no row.  Slack units come last in the priority order and never conflict with
-// one another, so each takes, after all structural units are coloured, the
-// smallest colour its row does not hold (k_slack_color) -- the sequential
-// greedy result.
+// needs no mask: the second reads the first one's colour directly.  Units of
+// one frontier share no row.  Slack units come last in the priority order and
+// never conflict with one another, so each takes, after all structural units
+// are coloured, the smallest colour its row does not hold (k_slack_color) --
+// the sequential greedy result.
 constexpr int64_t JP_BIG = 1024;           // list length above which a whole CTA serves a unit
 constexpr uint32_t RC_BIG = 0x80000000u;   // successor flag: that unit's own list is long
 constexpr uint32_t RC_NONE = 0xffffffffu;  // no unit
