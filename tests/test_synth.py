@@ -56,3 +56,44 @@ def test_batch_instances_shape():
         assert 50 <= g.n <= 400 and np.all(g.eu < g.ev) and g.w.min() >= 1 and g.w.max() <= 10
         keys = g.eu.astype(np.int64) * g.n + g.ev
         assert np.unique(keys).size == keys.size  # simple graph
+
+
+def _simple(g):
+    keys = g.eu.astype(np.int64) * g.n + g.ev
+    return np.all(g.eu < g.ev) and np.unique(keys).size == keys.size and g.eu.min() >= 0 and g.ev.max() < g.n
+
+
+def test_er_graph_shape():
+    g = synth.er_graph(3000, 12000, 5)
+    assert g.m == 12000 and _simple(g)
+    deg = np.bincount(np.concatenate([g.eu, g.ev]), minlength=g.n)
+    assert deg.mean() == 8.0 and deg.max() < 30  # binomial, mean 8
+    again = synth.er_graph(3000, 12000, 5)
+    assert np.array_equal(again.eu, g.eu) and np.array_equal(again.ev, g.ev)
+
+
+def test_chung_lu_shape():
+    """m distinct edges, a heavy tail whose log-log CCDF slope is near
+    -(gamma - 1), and degrees far above the mean on a few hubs."""
+    n, m, gamma = 50_000, 400_000, 2.1
+    g = synth.chung_lu(n, m, gamma, 3)
+    assert g.m == m and _simple(g)
+    deg = np.bincount(np.concatenate([g.eu, g.ev]), minlength=n)
+    assert deg.mean() == 2 * m / n
+    assert np.median(deg) < deg.mean() < deg.max() / 20
+    # tail slope of P(D >= d) between d = 2*mean and d = 20*mean
+    d = np.array([2, 4, 8, 16]) * deg.mean()
+    ccdf = np.array([np.mean(deg >= x) for x in d])
+    slope = np.polyfit(np.log(d), np.log(ccdf), 1)[0]
+    assert -1.6 < slope < -0.7
+    again = synth.chung_lu(n, m, gamma, 3)
+    assert np.array_equal(again.eu, g.eu) and np.array_equal(again.ev, g.ev)
+
+
+def test_grid_graph_shape():
+    g = synth.grid_graph(37, 23, 4, 2)
+    assert g.n == 37 * 23 and g.m == 2 * 37 * 23 - 37 - 23 and _simple(g)
+    d = g.ev.astype(np.int64) - g.eu
+    assert np.all((d == 1) | (d == 37))  # right or down neighbour
+    assert np.all(g.eu[d == 1] % 37 != 36)  # no wrap-around
+    assert np.unique(g.terminals).size == 4 and g.ce.shape == (g.m,) and g.ce.min() > 0
