@@ -75,9 +75,11 @@ WORKLOADS = {
 }
 DEFAULT = "is-chunglu-n2^20-m1.6e7"
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
-# DRAM bytes per epoch of the persistent sweep from one ncu capture
-# (ncu capture of one 10-epoch launch on this workload: 3.19 GB read + 2.58 GB written)
-SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 577_000_000}
+# DRAM bytes per epoch of the persistent sweep from an ncu capture of the
+# current sweep kernel, per workload (none: the kernel changed since the last
+# capture -- its block scatter gained an atomic branch -- so no figure is
+# reported until it is captured again)
+SWEEP_TRAFFIC_PER_EPOCH = {}
 L2_BYTES = 129 * 1024 * 1024
 SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
 
