@@ -1,20 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the SCD + LP-rounding hot path on one GB300 (or N replicas).
 
-One step = the whole hot path over one seeded synthetic instance whose edge
-list and weights are already resident in HBM: build the standard form on the
-device, colour the column-intersection graph, 50 colour-class SCD epochs on
-eq. QP (FP32 iterate, FP64 residual refresh and checks every 10 epochs, stop
-early at rho <= 1e-3), repair, best-of-10 rounding and exact validity.
-
-Default workload: independent-set LP on a Chung-Lu power-law graph
-(exponent 2.1, n = 2^20, m = 1.6e7 edges, weights U(0,1]).  The metric is
-coordinate updates per second over whole steps; `time_to_residual` reports the
-same pipeline run to rho <= 1e-3.
+Default workload: the batched configuration -- 4096 independent vertex-cover /
+independent-set LPs (ER, n ~ U[200, 20000], average degree ~ U[4, 16], weights
+U[1, 10]) whose edge lists are already resident in HBM.  One step = build the
+batch on the device (standard form, colouring, layouts), solve every instance
+by colour-class SCD on eq. QP to rho <= 1e-3 (each instance in the shared
+memory of one CTA, checked and stopped on its own), repair, best-of-10 rounding
+and exact validity of every instance.  The metric is solved instances per
+second; the line also carries coordinate updates/s, per-instance latency
+against the plain one-at-a-time GPU solve, the sweep's roofline and, as extra
+keys, the single-instance independent-set figures (Chung-Lu power law,
+n = 2^20, m = 1.6e7: coordinate updates/s and time to residual 1e-3).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl thetis|reference]
+                  [--workload NAME]
 
-Under torchrun (N > 1) every rank solves its own instance (independent
+Under torchrun (N > 1) every rank solves its own instances (independent
 problems, weak scaling, no collective on the data path); rank 0 prints the
 JSON line.  `--impl reference` times the FP64 oracle (the serial CPU
 restatement of the method) on host cores for the same workload.
@@ -73,15 +75,48 @@ WORKLOADS = {
                             d_lo=4.0, d_hi=16.0, side_lo=64, side_hi=512, beta=100.0, epochs=5000, refresh=20,
                             tol=1e-3, reps=10, budget=120 << 30, workers=4, max_batch=64),
 }
-DEFAULT = "is-chunglu-n2^20-m1.6e7"
+DEFAULT = "batched-4096"
+SINGLE = "is-chunglu-n2^20-m1.6e7"  # the single-instance IS config reported beside the default
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
 # DRAM bytes per epoch of the persistent sweep from an ncu capture of the
 # current sweep kernel, per workload (none: the kernel changed since the last
 # capture -- its block scatter gained an atomic branch -- so no figure is
 # reported until it is captured again)
 SWEEP_TRAFFIC_PER_EPOCH = {}
+# DRAM bytes per batched step of the instance kernel from an ncu capture of the
+# current kernel (none until captured)
+BATCH_TRAFFIC = {}
 L2_BYTES = 129 * 1024 * 1024
 SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
+
+
+def host_cores():
+    """Host CPUs this process may run on (its affinity mask), not every CPU of the box."""
+    try:
+        return len(os.sched_getaffinity(0)) or 1
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU's model name, from lscpu (or /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def make_graph(wl, rank=0):
@@ -410,14 +445,19 @@ def run_gpu(args, wl, ws, rank, local):
                          if "al_infeas" in info0 else {})},
         "clocks": clk.summary(),
     }
-    if rank == 0:
-        print(json.dumps(res), flush=True)
+    return res
 
 
 # ---------------------------------------------------------------------------
 # batched workload: solves/s and latency against one-at-a-time GPU solves
 # ---------------------------------------------------------------------------
 def run_batched(args, wl, ws, rank, local):
+    """Batched workload: one step = build the batch, launch shape (tuned once per
+    shape, cached), solve every instance to rho <= tol, round every instance,
+    validate.  Value = solved instances / step time.  Per-instance latency =
+    step start -> the instance's LP solution final on the device (it stops on
+    its own in the instance-resident engine) and -> its rounded result; the
+    plain arm solves a sample of the same instances one at a time."""
     import torch
 
     import __graft_entry__
@@ -443,18 +483,23 @@ def run_batched(args, wl, ws, rank, local):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     count = wl["count"]
     bpe_inst = np.array([20 * g.n + 40 * g.m for _, g in items], np.float64)
+    coords_inst = np.array([g.n + g.m for _, g in items], np.float64)
     bpe = float(bpe_inst.sum())
     torch.cuda.synchronize()
 
     shape = {}
 
-    def step(a, out):
+    def step(a, out, t_start=None):
+        pre = torch.cuda.Event(enable_timing=True)
         h = T.thetis_build_batch(a["kinds"], a["noff"], a["eoff"], a["eu"], a["ev"], a["w"], seed=0, stream=stream)
-        shape["small_group"], shape["ctas_per_sm"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
+        shape["lanes_per_column"], shape["clusters"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
+        pre.record(stream)
         info = h.solve(beta=wl["beta"], epochs=wl["epochs"], tol=wl["tol"], refresh_every=wl["refresh"])
-        info["inst_epochs"] = T.thetis_batch_info(h)[0]
+        info["inst_epochs"], info["inst_rho"] = T.thetis_batch_info(h)
+        info["inst_done_ms"] = T.thetis_batch_latency(h)
         lab, obj, status, best = T.thetis_round_batch(h, seed=11, reps=wl["reps"], out=out)
         assert np.all(status == 1), "a rounded instance failed the validity check"
+        info["pre_solve_ms"] = t_start.elapsed_time(pre) if t_start is not None else 0.0
         h.close()
         return info
 
@@ -471,7 +516,7 @@ def run_batched(args, wl, ws, rank, local):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))
                 ev[i][0].record(stream)
-            infos.append(step(d, lab_d))
+            infos.append(step(d, lab_d, ev[i][0]))
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     barrier(ws)
@@ -479,13 +524,15 @@ def run_batched(args, wl, ws, rank, local):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), ws, dev)
     value = sum_over_ranks(float(count * args.steps), ws, dev) / (total_ms / 1e3)
+    updates = sum(float(coords_inst @ i["inst_epochs"]) for i in infos)
     ep_ms = sum(i["epoch_ms"] for i in infos)
-    ep_n = sum(i["epochs_run"] for i in infos)
-    # an instance stops being swept at the check where its rho reaches tol:
-    # only its own epochs move its bytes
+    # an instance is swept only until its own rho reaches tol: only its own
+    # epochs move its bytes
     moved = sum(float(bpe_inst @ i["inst_epochs"]) for i in infos)
     achieved = moved / (ep_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
+    # per-instance latency inside the steps: step start -> LP solution final
+    lp_done = np.concatenate([i["pre_solve_ms"] + i["inst_done_ms"] for i in infos])
 
     # e2e: host (pinned) inputs, labels back to the host
     hp = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
@@ -497,7 +544,8 @@ def run_batched(args, wl, ws, rank, local):
     b.synchronize()
     e_ms = max_over_ranks(a.elapsed_time(b), ws, dev)
 
-    # plain: the same instances one at a time through the single-instance API
+    # plain: the same instances one at a time through the single-instance API,
+    # each built, solved to the same rho and rounded (latency = its own time)
     rng = np.random.default_rng(7)
     sample = rng.choice(count, size=min(wl["plain_sample"], count), replace=False)
     lat = []
@@ -517,7 +565,7 @@ def run_batched(args, wl, ws, rank, local):
         lat.append(a.elapsed_time(b))
         h.close()
     lat = np.array(lat)
-    batch_lat = np.array(step_ms)
+    plain_total_s = float(lat.mean()) * count / 1e3  # the whole batch one at a time
 
     info0 = infos[-1]
     res = {
@@ -531,36 +579,46 @@ def run_batched(args, wl, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (FP64 refresh/checks)",
+        "dtype": "f32 (exact fixed-point refresh, FP64 checks)",
         "data": "synthetic (seeded ER instances)",
         "config": {"workload": args.workload, "instances": count, "sum_n": int(noff[-1]), "sum_m": int(eoff[-1]),
                    "colors": info0["ncolors"], "beta": wl["beta"], "tol": wl["tol"],
                    "refresh_every": wl["refresh"], "reps": wl["reps"], "parallelism": f"replicas x{ws}",
+                   "engine": "instance-resident (one CTA per instance, r and x in shared memory)",
                    "launch_shape": dict(shape),
                    "l2": "inputs larger than L2 and L2 flushed (2x129 MB write) between steps"},
+        "coord_updates_per_s": sum_over_ranks(updates, ws, dev) / (total_ms / 1e3),
         "e2e": {"value": count / (e_ms / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(sum(v.nbytes for v in host.values())), "d2h_bytes_per_step": int(noff[-1])},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "k_sweep (persistent colour sweep); unit = one epoch of the batch",
-                     "bytes_per_epoch": bpe, "bytes_per_step": moved / len(infos),
-                     "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
-        "latency": {"batched_p50_ms": float(np.percentile(batch_lat, 50)),
-                    "batched_p99_ms": float(np.percentile(batch_lat, 99)),
+                     "frac": achieved / pk["hbm_gbs"], "traffic": BATCH_TRAFFIC.get(args.workload),
+                     "kernel": "k_inst (instance-resident sweep + in-kernel checks); unit = each instance's own "
+                               "epochs, algorithmic bytes 20 n + 40 m per instance epoch",
+                     "bytes_per_epoch_all_instances": bpe, "bytes_per_step": moved / len(infos),
+                     "device_ms_per_step": ep_ms / len(infos), "peak_kind": f"{pk_kind} hbm_gbs",
+                     "note": "r and x stay in shared memory: DRAM moves far fewer bytes than the algorithmic "
+                             "count (see traffic); frac is algorithmic bytes over time, not DRAM bandwidth"},
+        "latency": {"instance_lp_done_p50_ms": float(np.percentile(lp_done, 50)),
+                    "instance_lp_done_p99_ms": float(np.percentile(lp_done, 99)),
+                    "instance_result_p50_ms": float(np.percentile(step_ms, 50)),
+                    "instance_result_p99_ms": float(np.percentile(step_ms, 99)),
                     "plain_p50_ms": float(np.percentile(lat, 50)), "plain_p99_ms": float(np.percentile(lat, 99)),
                     "plain_solves_per_s": float(1e3 / lat.mean()), "plain_sample": int(len(lat)),
-                    "note": "batched latency = whole-batch completion (every instance finishes together)"},
-        "last_step": {"epochs_run": info0["epochs_run"], "rho": info0["rho"], "converged": info0["converged"],
-                      "solve_ms": info0["solve_ms"], "step_ms": step_ms[-1]},
+                    "plain_whole_batch_s": plain_total_s,
+                    "note": "lp_done: step start -> the instance stopped on the device (instances stop "
+                            "independently); result: labels after the batch-wide rounding; plain: one "
+                            "instance at a time (build + solve + round)"},
+        "last_step": {"epochs_run_max": info0["epochs_run"], "epochs_mean": float(np.mean(info0["inst_epochs"])),
+                      "rho_max": info0["rho"], "converged": info0["converged"], "solve_ms": info0["solve_ms"],
+                      "step_ms": step_ms[-1], "pre_solve_ms": info0["pre_solve_ms"]},
         "clocks": clk.summary(),
         "cpu_baseline": None,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         order = np.random.default_rng(7).permutation(count)
         res["cpu_baseline"] = cpu_baseline_instances(wl, items, order, 15.0, "random instances of the batch")
-    if rank == 0:
-        print(json.dumps(res), flush=True)
+    return res
 
 
 def run_async_study(args, wl, ws, rank, local):
@@ -833,7 +891,7 @@ def cpu_baseline(wl, g, epochs):
     t = time.perf_counter()
     x, info = lp.solve(beta=wl["beta"], epochs=epochs, refresh_every=wl["refresh"], color=col)
     dt = time.perf_counter() - t
-    return {"value": epochs * lp.free_coords / dt, "unit": "coord_updates/s", "cores": 1, "kind": "oracle",
+    return {"value": epochs * lp.free_coords / dt, "unit": "coord_updates/s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{epochs} FP64 serial SCD epochs of {what} ({lp.free_coords} coordinates) "
                       f"incl. the final exact refresh + checks; build and colouring excluded",
             "seconds": dt}
@@ -860,7 +918,7 @@ def cpu_baseline_instances(wl, items, order, seconds, what):
     for about `seconds`.  The pool is spawned, so it is safe after GPU work."""
     import multiprocessing as mp
 
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     jobs = [(items[j][0], items[j][1], wl) for j in order]
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as P:
@@ -873,7 +931,7 @@ def cpu_baseline_instances(wl, items, order, seconds, what):
                 break
         dt = time.perf_counter() - t0
         P.terminate()
-    return {"value": done / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+    return {"value": done / dt, "unit": "solves/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{done} {what}, each built, coloured, solved to rho <= {wl['tol']} and rounded by the FP64 "
                       f"oracle, one process per core ({dt:.1f} s)"}
 
@@ -889,7 +947,7 @@ def run_reference_batch(args, wl, ws):
     items = synth.batch_instances(wl["count"], wl["n_lo"], wl["n_hi"], wl["d_lo"], wl["d_hi"], 1, 10, wl["seed"])
     rng = np.random.default_rng(7)
     order = rng.permutation(len(items))
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     jobs = [(items[j][0], items[j][1], wl) for j in order]
     per_step = 4 * cores  # one step = four instances per core, streamed so no core waits for a step's slowest
     ctx = mp.get_context("spawn")
@@ -914,7 +972,7 @@ def run_reference_batch(args, wl, ws):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(walls) / len(walls) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "instances": wl["count"]},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -943,7 +1001,7 @@ def run_reference_serving(args, wl, ws):
     pool, kinds = _serving_inputs(wl, 0)
     t_arr, idx = synth.poisson_trace(wl["rate"], 4096, kinds, wl["seed"] * 7919)
     small = [int(j) for j in idx if pool[j][1].n <= n_cap]
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     jobs = [(pool[j][0], pool[j][1], wl) for j in small]
     ctx = mp.get_context("spawn")
     walls, done = [], 0
@@ -967,7 +1025,7 @@ def run_reference_serving(args, wl, ws):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(walls) / len(walls) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_cap": n_cap},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -1008,7 +1066,7 @@ def run_reference(args, wl, ws, rank):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "kind": wl["kind"], "n": g.n, "m": g.m},
-        "cpu_baseline": {"value": value, "unit": "coord_updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "coord_updates/s", "cores": 1, "kind": "oracle", "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "coord_updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(res), flush=True)
@@ -1024,19 +1082,35 @@ def main():
     ap.add_argument("--ttr-epochs", type=int, default=3000, help="epoch cap of the time-to-residual run (0: skip)")
     ap.add_argument("--cpu-epochs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-single", action="store_true", help="batched default: skip the single-instance extra keys")
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, ws, rank)
     elif wl["kind"] == "batch":
-        run_batched(args, wl, ws, rank, local)
+        res = run_batched(args, wl, ws, rank, local)
+        if args.workload == DEFAULT and not args.no_single:
+            # the single-instance figures of the IS config (coordinate updates/s,
+            # time to residual 1e-3, its sweep roofline) ride along as extra keys
+            import copy
+
+            a1 = copy.copy(args)
+            a1.workload, a1.steps, a1.warmup = SINGLE, max(3, min(args.steps, 5)), 3
+            one = run_gpu(a1, WORKLOADS[SINGLE], ws, rank, local)
+            res["single_instance"] = {k: one[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "e2e",
+                                                          "roofline", "time_to_residual", "last_step",
+                                                          "cpu_baseline", "clocks") if k in one}
+        if rank == 0:
+            print(json.dumps(res), flush=True)
     elif wl["kind"] == "serve":
         run_serving(args, wl, ws, rank, local)
     elif wl.get("study"):
         run_async_study(args, wl, ws, rank, local)
     else:
-        run_gpu(args, wl, ws, rank, local)
+        res = run_gpu(args, wl, ws, rank, local)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
     if ws > 1:
         import torch.distributed as dist
 

@@ -107,11 +107,19 @@ typedef struct {
  *   x0[n]         structural starting point (NULL: 0 clipped to the bounds,
  *                 barycentre for simplex blocks); slacks start at 0
  *   mem           where ubar / xbar / x0 live
- *   engine        colored mode only: 0 = one persistent cooperative launch per
- *                 refresh interval with a grid barrier between colours (falls
- *                 back to 1 where cooperative launch is unavailable);
- *                 1 = one launch per colour, replayed as a CUDA graph.  Both
- *                 give the same iterates.
+ *   engine        colored mode only: 0 = default: for a single problem one
+ *                 persistent cooperative launch per refresh interval with a
+ *                 grid barrier between colours (falls back to 1 where
+ *                 cooperative launch is unavailable); for a batch of
+ *                 thetis_build_batch without ubar / xbar, the instance-resident
+ *                 engine (every instance solved, checked and stopped on its own
+ *                 by one CTA or thread-block cluster that keeps its residual
+ *                 and iterate in shared memory; see thetis_build_batch);
+ *                 1 = one launch per colour, replayed as a CUDA graph;
+ *                 2 = the persistent sweep of engine 0 for batches too (the
+ *                 whole block-diagonal LP swept colour by colour).  All give
+ *                 the same iterates up to FP32 summation order (0 and 1
+ *                 bit-identical on single problems).
  *   async_ctas    async mode only: at most this many CTAs (256 threads) step
  *                 coordinates at once, each taking tiles in turn (0 = one CTA
  *                 per tile, as many as the GPU runs); the concurrency of the
@@ -306,14 +314,38 @@ thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_
                            uint8_t* labels_out, int32_t out_mem, thetis_round_info* info);
 
 /*
+ * thetis_check_labels -- exact validity and objective of an integral solution
+ * given by the caller (the checks every rounding ends with; Sec. 2 for vertex
+ * cover, App. B.1-B.3 for set cover, independent set and multiway cut, Sec. 4.1
+ * for MAP), e.g. a rounding kept from earlier or produced elsewhere.
+ *   kind          the rounding kind of the handle's problem (as for thetis_round)
+ *   labels[n]     uint8 in vertex order (VC / IS / SC: 1 = chosen, 0 = not;
+ *                 MC / MAP: the label in [0, k)); `mem` says where it lives
+ *   valid_out     1 if VC: every edge has a chosen end; IS: no edge has both
+ *                 ends chosen; MC: terminal i has label i; SC: every element
+ *                 lies in a chosen set; and every label is in range (0/1, or
+ *                 < k); else 0.  May be NULL.
+ *   obj_out       cover / set weight, cut cost, set cost or MAP energy (FP64);
+ *                 NaN when a label is out of range.  May be NULL.
+ * THETIS_E_INVALID for a batch or general-LP handle or a kind that does not
+ * match the problem.
+ */
+thetis_status thetis_check_labels(thetis_handle* h, int32_t kind, const uint8_t* labels, int32_t mem,
+                                  int32_t* valid_out, double* obj_out);
+
+/*
  * thetis_round_is_static -- the independent-set branch of thetis_round (repair,
  * best-of-reps rounding with alterations, exact validity) for callers that
  * cannot allocate device memory when they round: serving loops that must not
- * block on cudaMalloc / cudaFree, processes whose free device memory is owned
- * by another allocator, code recording a stream capture.  The paper has no
- * counterpart; this is a deployment variant of the same kernels.
+ * block on cudaMalloc / cudaFree (either can stall every stream of the
+ * device), and processes whose free device memory is already owned by another
+ * allocator.  The paper has no counterpart; this is a deployment variant of the
+ * same kernels.
  *   n, m, eu[m], ev[m], w[n]   the graph and vertex weights, as for
- *                              thetis_build_is (DEVICE pointers)
+ *                              thetis_build_is (DEVICE pointers of the current
+ *                              device; endpoints are checked on the device
+ *                              before use: out of [0, n) or a loop gives
+ *                              THETIS_E_INVALID, as does a host pointer)
  *   x[n]                       the fractional point in vertex order (DEVICE),
  *                              e.g. from thetis_get_x
  *   labels_out[n]              DEVICE output, 1 = in the independent set
@@ -321,11 +353,14 @@ thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_
  * Scratch: one file-scope device array of 64 MiB, held by every GPU that loads
  * the library until the process exits.  Requires 2*n*reps + 131,616 bytes <=
  * 64 MiB (n * reps <= 33,488,624); larger sizes return THETIS_E_INVALID.
- * Calls no cudaMalloc / cudaFree.  The first call on a device looks the array
- * up with cudaGetSymbolAddress (once per device): make that first call before
- * any stream capture.  All calls share the array, so calls that overlap on the
- * GPU (different streams, or different threads) race; serialise them.
- * Same random streams as thetis_round: equal inputs give equal outputs.
+ * Calls no cudaMalloc / cudaFree and no allocating library routine.  It does
+ * synchronise `stream` (after the endpoint check, to pick the best repetition,
+ * and at the end) and copies a few words to host stack memory.  The first
+ * call on a device looks the array up with cudaGetSymbolAddress (once per
+ * device): make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (different streams, or different
+ * threads) race; serialise them.  Same random streams as thetis_round: equal
+ * inputs give equal outputs.
  */
 thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev,
                                      const float* w, const float* x, uint64_t seed, int32_t reps,
@@ -335,7 +370,10 @@ thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, co
  * thetis_autotune -- choose the launch shape of the colour sweep for this
  * problem: the number of lanes that serve one small column (1, 2, 4 or 8; "warps
  * per column") and the CTAs per SM of the persistent sweep (all that fit, 2 or
- * 1; the size of the colour chunk each CTA takes).  Every pair is timed over
+ * 1; the size of the colour chunk each CTA takes).  For a batch handle served
+ * by the instance-resident engine: lanes per column (1, 4, 8) and whether
+ * large instances take clusters (see thetis_set_batch_shape), returned as
+ * *small_group_out and *ctas_per_sm_out (1 = clusters).  Every pair is timed over
  * trial_epochs epochs of the real problem (beta and step_rule from p); the
  * iterate is saved before and restored after each trial, so the result of later
  * solves does not depend on tuning.  The choice is cached in the process per
@@ -346,6 +384,30 @@ thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, co
  */
 thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t trial_epochs,
                               int32_t* small_group_out, int32_t* ctas_per_sm_out);
+/*
+ * thetis_set_wait_limit -- the time limit of every bounded device wait of this
+ * handle's persistent colour sweep (the grid barriers between colours; 2000 ms
+ * by default).  A wait that runs out ends the launch and the solve returns
+ * THETIS_E_TIMEOUT; the handle stays usable (its iterate is then partly swept).
+ * missing_ctas > 0 is a test hook for that path: the barriers then wait for
+ * that many CTAs beyond the launch, which never arrive, so the first wait runs
+ * out after limit_ms.  limit_ms in (0, 600000], missing_ctas in [0, 1024].
+ * No counterpart in the paper (failure handling of the deployment).
+ */
+thetis_status thetis_set_wait_limit(thetis_handle* h, double limit_ms, int32_t missing_ctas);
+/*
+ * thetis_set_batch_shape -- the launch shape of the instance-resident engine
+ * of a batch handle (what thetis_autotune picks for it): lanes_per_column 1
+ * (one thread per short column through 32-column ELL panels, one warp per
+ * column longer than 32), 4 or 8 (that many lanes per column through the
+ * CSR); clusters 0 (an instance too large for one CTA's shared memory keeps
+ * x and the rows beyond it in global memory, i.e. L2) or 1 (such instances
+ * span a thread-block cluster of 2 or 4 CTAs whose shared memory holds r and
+ * x, reached through distributed shared memory).  Every shape gives the same
+ * iterates up to FP32 summation order.  THETIS_E_INVALID for other handles or
+ * values.  No counterpart in the paper (a launch-shape knob).
+ */
+thetis_status thetis_set_batch_shape(thetis_handle* h, int32_t lanes_per_column, int32_t clusters);
 /* Set the launch shape by hand: small_group in {1, 2, 4, 8}, ctas_per_sm >= 0
  * (0 = all that fit).  THETIS_E_INVALID otherwise. */
 thetis_status thetis_set_launch_shape(thetis_handle* h, int32_t small_group, int32_t ctas_per_sm);
@@ -381,6 +443,15 @@ thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int6
  * THETIS_E_INVALID for a handle that is not a batch.
  */
 thetis_status thetis_batch_info(const thetis_handle* h, int32_t* epochs_out, double* rho_out);
+
+/*
+ * thetis_batch_latency -- per instance, the device time in ms from the start of
+ * the last thetis_solve of a batch handle until the instance's result was
+ * final: with the instance-resident engine, when its CTA / cluster finished
+ * (instances finish independently); with the union sweep (engine 1 / 2), the
+ * check at which it stopped.  done_ms_out[count] is a HOST array.
+ */
+thetis_status thetis_batch_latency(const thetis_handle* h, double* done_ms_out);
 
 /*
  * thetis_round_batch -- repair + rounding of every instance of a batch handle,

@@ -21,7 +21,8 @@ LIB = os.path.join(HERE, "libthetis.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-SOURCES = ["prims.cu", "build.cu", "scd.cu", "round.cu", "batch.cu", "api.cu", "server.cu", "static_round.cu"]
+SOURCES = ["prims.cu", "build.cu", "scd.cu", "round.cu", "batch.cu", "inst.cu", "api.cu", "server.cu",
+           "static_round.cu"]
 
 
 def _nvcc() -> str:

@@ -14,7 +14,7 @@ struct thetis_handle {
   std::unique_ptr<Problem> P;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr, evb = nullptr;
   int64_t graph_launches = 0;  // kernels per epoch graph replay
   // key of the captured epoch graph
   double g_beta = 0;
@@ -28,6 +28,7 @@ struct thetis_handle {
     if (ev1) cudaEventDestroy(ev1);
     if (ev2) cudaEventDestroy(ev2);
     if (ev3) cudaEventDestroy(ev3);
+    if (evb) cudaEventDestroy(evb);
     if (own_stream && stream) {
       cudaStreamSynchronize(stream);
       cudaStreamDestroy(stream);
@@ -107,6 +108,7 @@ void finish_create(thetis_handle* h) {
   TH_CUDA(cudaEventCreate(&h->ev1));
   TH_CUDA(cudaEventCreate(&h->ev2));
   TH_CUDA(cudaEventCreate(&h->ev3));
+  TH_CUDA(cudaEventCreate(&h->evb));
   TH_CUDA(cudaStreamSynchronize(h->stream));
 }
 
@@ -355,12 +357,33 @@ struct SolveRun {
   int ep = 0;
   double sweep_ms = 0.0;
   int64_t sweep_launches = 0;
+  int64_t updates = -1;  // coordinate updates when not epochs * free coordinates (batches)
   CheckOut co{};
 };
 
 void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engine, SolveRun& R) {
   Problem& P = *h->P;
   cudaStream_t s = h->stream;
+  if (P.nbatch > 0 && engine == 0 && a.mode == THETIS_MODE_COLORED && !ub && !xb && inst_eligible(P)) {
+    // instance-resident engine: every instance solved and stopped on its own
+    // (inst.cu); then one FP64 check of the whole batch gives the objective,
+    // the infeasibility and every instance's rho at the iterate it stopped at
+    batch_inst_begin(P);
+    inst_solve(P, a, R.sweep_ms);
+    refresh_and_check(P, a, ub, xb, R.co);
+    batch_inst_end(P, R.ep, R.converged, R.updates);
+    R.sweep_launches = 0;
+    for (size_t c = 0; c + 1 < P.h_icls_off.size(); ++c) R.sweep_launches += P.h_icls_off[c + 1] > P.h_icls_off[c];
+    R.co.rho = 0.0;  // the largest rho any instance stopped at
+    for (double v : P.h_brho) R.co.rho = std::max(R.co.rho, v);
+    return;
+  }
+  if (engine == 2) engine = 0;  // the union sweep, asked for explicitly
+  batch_step_rule(P, a);
+  if (P.nbatch > 0) {
+    TH_CUDA(cudaEventRecord(h->evb, s));
+    P.batch_check_ms = 0.0;
+  }
   const bool persistent = a.mode == THETIS_MODE_COLORED && engine == 0 && P.ncolors > 0 && coop_allowed() &&
                           sweep_grid(P) > 0;
   if (persistent) reset_sweep_flags(P);
@@ -423,6 +446,11 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
       TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
       R.sweep_ms += t;
       checked_last = true;
+      if (P.nbatch > 0) {
+        float el = 0.f;
+        TH_CUDA(cudaEventElapsedTime(&el, h->evb, h->ev3));
+        P.batch_check_ms = el;
+      }
       // a batch converges instance by instance (each against tol)
       if (P.nbatch > 0 ? batch_after_check(P, a.tol, R.ep) : R.co.rho <= a.tol) {
         R.converged = true;
@@ -446,7 +474,7 @@ void check_params(const thetis_params* p) {
   TH_CHECK(p->epochs >= 0, THETIS_E_INVALID, "epochs must be >= 0");
   TH_CHECK(p->step_rule == 0 || p->step_rule == 1, THETIS_E_INVALID, "step_rule must be 0 or 1");
   TH_CHECK(p->mode == THETIS_MODE_COLORED || p->mode == THETIS_MODE_ASYNC, THETIS_E_INVALID, "bad mode");
-  TH_CHECK(p->engine == 0 || p->engine == 1, THETIS_E_INVALID, "engine must be 0 or 1");
+  TH_CHECK(p->engine >= 0 && p->engine <= 2, THETIS_E_INVALID, "engine must be 0, 1 or 2");
   TH_CHECK(p->async_ctas >= 0, THETIS_E_INVALID, "async_ctas must be >= 0");
 }
 
@@ -459,7 +487,7 @@ void fill_info(const Problem& P, const SolveRun& R, float ms, thetis_solve_info*
   info->obj = R.co.obj;
   info->infeas = R.co.infeas;
   info->fbeta = R.co.fbeta;
-  info->updates = (int64_t)R.ep * P.free_coords;
+  info->updates = R.updates >= 0 ? R.updates : (int64_t)R.ep * P.free_coords;
   info->solve_ms = ms;
   info->epoch_ms = R.sweep_ms;
   info->launches_per_epoch = R.ep > 0 ? (int32_t)((R.sweep_launches + R.ep - 1) / R.ep) : 0;
@@ -603,6 +631,29 @@ thetis_status thetis_round(thetis_handle* h, int32_t kind, uint64_t seed, int32_
   return THETIS_OK;
 }
 
+thetis_status thetis_check_labels(thetis_handle* h, int32_t kind, const uint8_t* labels, int32_t mem,
+                                  int32_t* valid_out, double* obj_out) {
+  if (!h || !h->P || !labels) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  int valid = 0;
+  double obj = 0.0;
+  thetis_status st = guard(h->stream, [&] {
+    Problem& P = *h->P;
+    cudaStream_t s = h->stream;
+    TH_CHECK(P.kind != KIND_BATCH && P.kind != KIND_GENERAL, THETIS_E_INVALID,
+             "thetis_check_labels needs a handle of thetis_build_vc / _is / _mc / _sc / _map");
+    Arena tmp(s);
+    const uint8_t* dl = to_dev(labels, P.nv, mem, tmp, s);
+    check_labels(P, kind, dl, valid, obj);
+  });
+  if (st != THETIS_OK) return st;
+  if (valid_out) *valid_out = valid;
+  if (obj_out) *obj_out = obj;
+  return THETIS_OK;
+}
+
 thetis_status thetis_get_x(thetis_handle* h, float* out, int32_t out_mem) {
   if (!h || !h->P || !out) {
     set_error("null argument");
@@ -726,6 +777,55 @@ thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t 
     Problem& P = *h->P;
     cudaStream_t s = h->stream;
     TH_CHECK(p->beta > 0, THETIS_E_INVALID, "beta must be > 0");
+    if (P.nbatch > 0 && inst_eligible(P)) {
+      // batches: the lanes per column of the instance-resident engine (1: one
+      // thread per short column through ELL panels; 4 or 8 through the CSR),
+      // timed on trial_epochs epochs of every instance (no stopping); iterate
+      // restored
+      TuneKey key = tune_key(P);
+      key.kind += 100;
+      int G = 0;
+      bool clusters = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+          G = it->second.small_g;
+          clusters = it->second.full;
+        }
+      }
+      if (G == 0) {
+        SolveArgs a{p->beta, std::max(1, trial_epochs), 0.0, 1 << 30, p->step_rule, THETIS_MODE_COLORED};
+        Arena tmp(s);
+        float* x0 = tmp.alloc<float>(P.Ns);
+        float* s0 = tmp.alloc<float>(P.M);
+        TH_CUDA(cudaMemcpyAsync(x0, P.x, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (P.M) TH_CUDA(cudaMemcpyAsync(s0, P.s, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        double best_ms = 1e300;
+        for (bool cl : {false, true})
+          for (int g : {1, 8, 4}) {
+            P.iml_G = g;
+            inst_set_clusters(P, cl);
+            double ms = 0.0;
+            inst_solve(P, a, ms);
+            if (ms < best_ms) {
+              best_ms = ms;
+              G = g;
+              clusters = cl;
+            }
+            TH_CUDA(cudaMemcpyAsync(P.x, x0, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            if (P.M) TH_CUDA(cudaMemcpyAsync(P.s, s0, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
+          }
+        TH_CUDA(cudaStreamSynchronize(s));
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = TuneChoice{G, 0, clusters};
+      }
+      P.iml_G = G;
+      inst_set_clusters(P, clusters);
+      if (small_group_out) *small_group_out = G;
+      if (ctas_per_sm_out) *ctas_per_sm_out = clusters ? 1 : 0;
+      return;
+    }
     const TuneKey key = tune_key(P);
     TuneChoice best{P.small_g, P.sweep_per_sm, P.force_full};
     bool cached = false;
@@ -788,6 +888,38 @@ thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t 
     if (small_group_out) *small_group_out = best.small_g;
     if (ctas_per_sm_out) *ctas_per_sm_out = best.per_sm;
   });
+}
+
+thetis_status thetis_set_wait_limit(thetis_handle* h, double limit_ms, int32_t missing_ctas) {
+  if (!h || !h->P) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  if (!(limit_ms > 0.0 && limit_ms <= 600000.0) || missing_ctas < 0 || missing_ctas > 1024) {
+    set_error("limit_ms must be in (0, 600000] and missing_ctas in [0, 1024]");
+    return THETIS_E_INVALID;
+  }
+  h->P->wait_ns = (long long)(limit_ms * 1e6);
+  h->P->wait_phantom = (unsigned)missing_ctas;
+  return THETIS_OK;
+}
+
+thetis_status thetis_set_batch_shape(thetis_handle* h, int32_t lanes_per_column, int32_t clusters) {
+  if (!h || !h->P) {
+    set_error("null handle");
+    return THETIS_E_INVALID;
+  }
+  if (h->P->kind != KIND_BATCH) {
+    set_error("thetis_set_batch_shape needs a handle from thetis_build_batch");
+    return THETIS_E_INVALID;
+  }
+  if (!(lanes_per_column == 1 || lanes_per_column == 4 || lanes_per_column == 8) || clusters < 0 || clusters > 1) {
+    set_error("lanes_per_column must be 1, 4 or 8 and clusters 0 or 1");
+    return THETIS_E_INVALID;
+  }
+  h->P->iml_G = lanes_per_column;
+  inst_set_clusters(*h->P, clusters != 0);
+  return THETIS_OK;
 }
 
 thetis_status thetis_set_launch_shape(thetis_handle* h, int32_t small_group, int32_t ctas_per_sm) {
@@ -885,6 +1017,20 @@ thetis_status thetis_batch_info(const thetis_handle* h, int32_t* epochs_out, dou
     if (epochs_out) epochs_out[t] = P.h_bepochs[t];
     if (rho_out) rho_out[t] = P.h_brho[t];
   }
+  return THETIS_OK;
+}
+
+thetis_status thetis_batch_latency(const thetis_handle* h, double* done_ms_out) {
+  if (!h || !h->P || !done_ms_out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  const Problem& P = *h->P;
+  if (P.kind != KIND_BATCH) {
+    set_error("thetis_batch_latency needs a handle from thetis_build_batch");
+    return THETIS_E_INVALID;
+  }
+  for (int64_t t = 0; t < P.nbatch; ++t) done_ms_out[t] = P.h_bdone[t];
   return THETIS_OK;
 }
 

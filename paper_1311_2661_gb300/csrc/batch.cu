@@ -293,6 +293,10 @@ __global__ void k_binst(const uint32_t* col_of_orig, const uint32_t* orig_of_row
   }
 }
 
+__global__ void k_bmaxdeg(const int64_t* colptr, const int32_t* inst_col, int64_t Ns, int32_t* maxdeg) {
+  GSTRIDE(j, Ns) atomicMax(&maxdeg[inst_col[j]], (int32_t)(colptr[j + 1] - colptr[j]));
+}
+
 void batch_index(Problem& P) {
   cudaStream_t s = P.stream;
   const int64_t count = P.nbatch;
@@ -308,9 +312,16 @@ void batch_index(Problem& P) {
                                               P.binst_col, P.binst_row);
     TH_LAUNCHED();
   }
+  P.bmaxdeg = P.mem.alloc<int32_t>(count);
+  TH_CUDA(cudaMemsetAsync(P.bmaxdeg, 0, count * sizeof(int32_t), s));
+  if (P.Ns > 0) {
+    k_bmaxdeg<<<grid_for(P.Ns, 256), 256, 0, s>>>(P.colptr, P.binst_col, P.Ns, P.bmaxdeg);
+    TH_LAUNCHED();
+  }
   P.h_bfrozen.assign(count, 0);
   P.h_bepochs.assign(count, 0);
   P.h_brho.assign(count, 0.0);
+  P.h_bdone.assign(count, 0.0);
 }
 
 void batch_begin_solve(Problem& P) {
@@ -318,6 +329,7 @@ void batch_begin_solve(Problem& P) {
   std::fill(P.h_bfrozen.begin(), P.h_bfrozen.end(), 0);
   std::fill(P.h_bepochs.begin(), P.h_bepochs.end(), 0);
   std::fill(P.h_brho.begin(), P.h_brho.end(), 0.0);
+  std::fill(P.h_bdone.begin(), P.h_bdone.end(), 0.0);
   TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, P.nbatch, P.stream));
   batch_active_tiles(P);
 }
@@ -340,6 +352,7 @@ bool batch_after_check(Problem& P, double tol, int epoch) {
     P.h_bepochs[t] = epoch;
     if (rho <= tol) {
       P.h_bfrozen[t] = 1;
+      P.h_bdone[t] = P.batch_check_ms;
       changed = true;
     } else {
       all = false;
@@ -356,7 +369,39 @@ bool batch_after_check(Problem& P, double tol, int epoch) {
 
 void batch_end_solve(Problem& P, int epoch) {
   for (int64_t t = 0; t < P.nbatch; ++t)
-    if (!P.h_bfrozen[t]) P.h_bepochs[t] = epoch;
+    if (!P.h_bfrozen[t]) {
+      P.h_bepochs[t] = epoch;
+      P.h_bdone[t] = P.batch_check_ms;
+    }
+}
+
+void batch_inst_begin(Problem& P) {
+  std::fill(P.h_bfrozen.begin(), P.h_bfrozen.end(), 0);
+  std::fill(P.h_bepochs.begin(), P.h_bepochs.end(), 0);
+  std::fill(P.h_brho.begin(), P.h_brho.end(), 0.0);
+  std::fill(P.h_bdone.begin(), P.h_bdone.end(), 0.0);
+  TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, P.nbatch, P.stream));
+}
+
+void batch_inst_end(Problem& P, int& ep_max, bool& all_converged, int64_t& updates) {
+  const int64_t count = P.nbatch;
+  std::vector<unsigned long long> bits(count);
+  TH_CUDA(cudaMemcpyAsync(bits.data(), P.brho, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  ep_max = 0;
+  all_converged = true;
+  updates = 0;
+  for (int64_t t = 0; t < count; ++t) {
+    double rho;
+    memcpy(&rho, &bits[t], sizeof(double));
+    P.h_brho[t] = rho;
+    P.h_bepochs[t] = P.h_iep[t];
+    P.h_bfrozen[t] = (uint8_t)(P.h_iconv[t] != 0);
+    P.h_bdone[t] = (double)(P.h_it[2 * t + 1] - P.h_it[2 * count]) * 1e-6;
+    ep_max = std::max(ep_max, P.h_iep[t]);
+    all_converged = all_converged && P.h_iconv[t] != 0;
+    updates += (int64_t)P.h_iep[t] * ((P.h_bnoff[t + 1] - P.h_bnoff[t]) + (P.h_beoff[t + 1] - P.h_beoff[t]));
+  }
 }
 
 }  // namespace thetis

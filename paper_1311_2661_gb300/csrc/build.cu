@@ -2079,6 +2079,7 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
 }
 
 Problem::~Problem() {
+  inst_release(*this);
   if (epoch_graph) cudaGraphExecDestroy(epoch_graph);
   if (h_red) cudaFreeHost(h_red);
 }

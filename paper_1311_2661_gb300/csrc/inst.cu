@@ -1,0 +1,1307 @@
+// Instance-resident solve of a batch of vertex-cover / independent-set LPs
+// (thetis_build_batch).
+//
+// The union sweep (scd.cu) advances every unfinished instance once per epoch,
+// so each epoch streams the residual r of the whole batch (gigabytes) through
+// HBM with scattered 4-byte accesses.  Here every instance is solved from
+// start to stop by one CTA, or by one thread-block cluster of 2 or 4 CTAs,
+// that keeps the instance's residual r and iterate x in shared memory
+// (distributed over the cluster's CTAs, reached with ld/st.shared::cluster):
+//
+//   * the colour classes of the instance are swept in order (Algorithm 1's
+//     coordinate step, re-ordered by colour as in the union sweep: no two
+//     units of a colour share a row), one CTA / cluster barrier per colour;
+//   * every R epochs the residual is recomputed exactly from x and s and the
+//     stopping test rho <= tol is made inside the kernel, so an instance stops
+//     at the same check as its solve alone and frees its SM for the next
+//     instance -- no host round trip, no grid barrier;
+//   * only the instance's non-zero structure, c and the slack values stream
+//     from memory (they stay in L2 while the instance runs).
+//
+// The exact recomputation r = Ax - b of a row x_u + x_v + sig s - 1 is done in
+// 64-bit fixed point (2^-58 units: exact for every |value| < 8 down to 2^-58,
+// with a plain FP64 fallback outside that range), then rounded once to FP32:
+// the GB300 issues about two FP64 instructions per clock per SM, the integer
+// pipes sixty-four.  The stopping test evaluates rho in FP32 from those exact
+// sums with a rigorous error bound, and only units whose bound straddles tol
+// are re-evaluated in FP64, so the decision is the FP64 decision.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <type_traits>
+
+#include "problem.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace thetis {
+
+#define GSTRIDE(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+namespace {
+
+constexpr uint32_t NO_ENTRY = 0xffffffffu;
+constexpr int FIX = 58;                              // fixed point: value * 2^58
+constexpr long long FIX_ONE = 1LL << FIX;
+constexpr int FIX_SPLIT = 18;                        // column sums: high part in 2^-40 units, low 18 bits apart
+
+// ---------------------------------------------------------------------------
+// exact arithmetic helpers
+// ---------------------------------------------------------------------------
+// |f| < 8 (exponent below 130); false for inf / nan
+__device__ __forceinline__ bool fix_ok(float f) { return ((__float_as_uint(f) >> 23) & 0xffu) < 130u; }
+
+// f * 2^58 truncated toward zero, for |f| < 8 (exact when f's lowest mantissa
+// bit is >= 2^-58, i.e. |f| >= 2^-35 or f a multiple of 2^-58)
+__device__ __forceinline__ long long fix58(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;  // zero or subnormal (< 2^-126)
+  const long long mnt = (long long)((b & 0x7fffffu) | 0x800000u);  // f = mnt * 2^(e - 150)
+  const int sh = e - 150 + FIX;
+  long long v;
+  if (sh >= 0) v = mnt << sh;
+  else v = (-sh < 24) ? (mnt >> (-sh)) : 0;
+  return (b >> 31) ? -v : v;
+}
+
+// the row value x_u + x_v + sig s - 1 in 2^-58 units (exact for |terms| < 8)
+__device__ __forceinline__ long long row_fix(float xu, float xv, float s, float sig) {
+  const long long fs = fix58(s);
+  return fix58(xu) + fix58(xv) + (sig > 0.f ? fs : -fs) - FIX_ONE;
+}
+__device__ __forceinline__ double row_f64(float xu, float xv, float s, float sig) {
+  return (((double)xu + (double)xv) + (double)sig * (double)s) - 1.0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// distributed shared memory of a cluster
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t dsm_map(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float dsm_ld(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void dsm_st(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ int dsm_ld_i(uint32_t a) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+
+// element b[i] of a small register array without dynamic indexing
+template <int K>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&b)[K], uint32_t i) {
+  uint32_t v = b[0];
+#pragma unroll
+  for (int r = 1; r < K; ++r) v = (i == (uint32_t)r) ? b[r] : v;
+  return v;
+}
+
+struct InstView {
+  const int64_t* noff;   // count + 1: first union vertex (= IML column) of every instance
+  const int64_t* eoff;   // count + 1: first union edge (= IML row) of every instance
+  const uint32_t* iend;  // per IML column: end of its entries, local to the instance
+  const uint32_t* ient;  // per entry: local row
+  const uint32_t* inb;   // per entry: local column of the other endpoint
+  const uint32_t* iru;   // per IML row: its two local columns
+  const uint32_t* irv;
+  const int32_t* coff;   // count * C: first local column of every colour
+  const int32_t* roff;   // count * 4 * C: first local slack row of every (rank, colour)
+  const int32_t* qoff;   // count * 5: first local row of every rank (rows of rank q: [qoff[q], qoff[q + 1]))
+  const int32_t* ncol;   // count: colours of the instance
+  const int32_t* cwide;  // count * C: first local column of every colour with at most 32 entries
+                         // (a colour's columns are sorted by length, longest first)
+  const int64_t* pfirst; // count * C + 1: first ELL panel of every colour (panels of 32 short columns)
+  const int64_t* pbase;  // per panel: first ELL slot (slot s of lane l at pbase + 32 s + l)
+  const uint8_t* pw;     // per panel: slots (its longest column)
+  const uint32_t* ell;   // ELL slots: local row, or NO_ENTRY
+  const int32_t* ideg;   // count: longest column of the instance
+  const uint8_t* kind;   // count: THETIS_ROUND_VC / _IS
+  const float* c;        // IML column costs
+  float* x;              // IML iterate (read at start, written at the end)
+  float* s;              // IML slack values (updated in place)
+  float* rg;             // IML rows: residual of the rows that do not fit in shared memory (one CTA)
+  int C;                 // colour-table stride
+  float beta, inv_beta, lo, hi;
+  double beta_d;
+  int step_rule;
+  int epochs, R;
+  double tol;
+  int32_t* ep_out;
+  int32_t* conv_out;
+  unsigned long long* t_out;  // 2 per instance: start, done (globaltimer ns)
+};
+
+// ---------------------------------------------------------------------------
+// the kernel: one instance per CTA (K = 1) or per cluster of K CTAs
+// ---------------------------------------------------------------------------
+// Rank q of the cluster holds the residual of its block of local rows
+// [qoff[q], qoff[q + 1]) (each row kept by a rank that steps one of its two
+// columns) and the iterate of local columns k with k % K == q at x[k / K];
+// entries name a row as (rank << 28) | position in the rank's block.  It steps
+// its slack rows (local) and, per colour, either
+//   G = 1: every K-th ELL panel of the colour's short columns, one thread per
+//          column (slot addresses follow from the panel; no index chain), and
+//          the colour's long columns one warp each, or
+//   G = 4 / 8: its own columns (k % K == q), G lanes each, through the CSR,
+// reaching the r (and x) of other ranks through distributed shared memory.
+template <int K, int NT, int G, bool SPILL>
+__global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstView V, const int32_t* order) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_over[2];
+  constexpr int GC = (G == 1) ? 8 : G;  // lanes per column of the stopping test
+  const int q = (K > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const int t = order[blockIdx.x / K];
+  const int64_t col0 = V.noff[t], row0 = V.eoff[t], ent0 = 2 * row0;
+  const int n = (int)(V.noff[t + 1] - col0), m = (int)(V.eoff[t + 1] - row0);
+  // shared memory: r of the own rows, then x of the own columns.  SPILL (one
+  // CTA, an instance that does not fit): x in global memory and the first rs
+  // rows of r in shared memory, the rest in V.rg (L2)
+  int cap = 0;
+  if constexpr (SPILL) {
+    uint32_t dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    cap = (int)(dyn_bytes / 4);
+  }
+  // this rank's block of rows, and the largest block (where x starts)
+  int qv[5] = {0, m, m, m, m};
+  int rch = m;
+  if constexpr (K > 1) {
+    rch = 0;
+#pragma unroll
+    for (int r = 0; r <= K; ++r) qv[r] = V.qoff[(int64_t)t * 5 + r];
+#pragma unroll
+    for (int r = 0; r < K; ++r) rch = max(rch, qv[r + 1] - qv[r]);
+  }
+  const int qlo = qv[q], qhi = qv[q + 1];
+  const bool xs = !SPILL || (m + n <= cap);        // x in shared memory
+  const int rs = SPILL ? min(m, cap) : rch;        // rows of r in shared memory (K = 1)
+  float* sr = smem;
+  float* sx = smem + rch;
+  float* rgl = V.rg + row0;
+  // the instance's arrays (32-bit local indices from here on)
+  float* Sx = V.x + col0;
+  const float* Cc = V.c + col0;
+  float* Ss = V.s + row0;
+  const uint32_t* Iend = V.iend + col0;
+  const uint32_t* Ient = V.ient + ent0;
+  const uint32_t* Inb = V.inb + ent0;
+  const uint32_t* Iru = V.iru + row0;
+  const uint32_t* Irv = V.irv + row0;
+  const int nc = V.ncol[t];
+  const int32_t* coff = V.coff + (int64_t)t * V.C;
+  const int32_t* roff = V.roff + ((int64_t)t * 4 + q) * V.C;
+  const float sig = (V.kind[t] == THETIS_ROUND_VC) ? -1.f : 1.f;
+  // step rule 1: the instance's own global L_max (as its solve alone uses)
+  float lfix = 0.f;
+  if (V.step_rule == 1) {
+    const int lm = max(V.ideg[t], m > 0 ? 1 : 0);
+    lfix = (float)(V.beta_d * (double)lm + 1.0 / V.beta_d);
+  }
+  const float beta = V.beta, ib = V.inv_beta;
+  const float tol32 = (float)V.tol;
+  const float bsig = beta * sig;
+  // 1 / L of a slack and of a column of every length up to 32 (the ELL path
+  // multiplies by it instead of dividing: within one rounding of the quotient)
+  __shared__ float s_invL[33];
+  const float inv_ls = 1.f / ((lfix > 0.f) ? lfix : beta + ib);
+  if (threadIdx.x <= 32) s_invL[threadIdx.x] = 1.f / ((lfix > 0.f) ? lfix : fmaf(beta, (float)threadIdx.x, ib));
+  uint32_t rb[K], xb[K];
+  if constexpr (K > 1) {
+    const uint32_t ra = smem_u32(sr), xa = smem_u32(sx);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      rb[r] = dsm_map(ra, (uint32_t)r);
+      xb[r] = dsm_map(xa, (uint32_t)r);
+    }
+  }
+  auto rget = [&](uint32_t e) -> float {
+    if constexpr (SPILL) return ((int)e < rs) ? sr[e] : rgl[e];
+    else if constexpr (K == 1) return sr[e];
+    else return dsm_ld(pick<K>(rb, e >> 28) + 4u * (e & 0x0fffffffu));
+  };
+  auto rset = [&](uint32_t e, float v) {
+    if constexpr (SPILL) {
+      if ((int)e < rs) sr[e] = v;
+      else rgl[e] = v;
+    } else if constexpr (K == 1) {
+      sr[e] = v;
+    } else {
+      dsm_st(pick<K>(rb, e >> 28) + 4u * (e & 0x0fffffffu), v);
+    }
+  };
+  // local row of an entry's encoded row id
+  auto row_of = [&](uint32_t e) -> uint32_t {
+    if constexpr (K == 1) return e;
+    else return (uint32_t)qv[e >> 28] + (e & 0x0fffffffu);
+  };
+  auto xget = [&](uint32_t k) -> float {
+    if constexpr (SPILL) return xs ? sx[k] : Sx[k];
+    else if constexpr (K == 1) return sx[k];
+    else return dsm_ld(pick<K>(xb, k % K) + 4u * (k / K));
+  };
+  auto xset = [&](uint32_t k, float v) {
+    if constexpr (SPILL) {
+      if (xs) sx[k] = v;
+      else Sx[k] = v;
+    } else if constexpr (K == 1) {
+      sx[k] = v;
+    } else {
+      dsm_st(pick<K>(xb, k % K) + 4u * (k / K), v);
+    }
+  };
+  // an own row e (local id in [qlo, qhi)) / own column k (k % K == q)
+  auto rown_get = [&](int e) -> float {
+    if constexpr (K == 1) return rget((uint32_t)e);
+    else return sr[e - qlo];
+  };
+  auto rown_set = [&](int e, float v) {
+    if constexpr (K == 1) rset((uint32_t)e, v);
+    else sr[e - qlo] = v;
+  };
+  auto xown_get = [&](int k) -> float {
+    if constexpr (K == 1) return xget((uint32_t)k);
+    else return sx[k / K];
+  };
+  auto xown_set = [&](int k, float v) {
+    if constexpr (K == 1) xset((uint32_t)k, v);
+    else sx[k / K] = v;
+  };
+  auto sync = [&]() {
+    if constexpr (K == 1) __syncthreads();
+    else cg::this_cluster().sync();
+  };
+
+  // -- start: x chunk into shared memory, exact residual of the own rows -----
+  if (xs)
+    for (int i = threadIdx.x; i * K + q < n; i += NT) sx[i] = Sx[i * K + q];
+  if (threadIdx.x < 2) s_over[threadIdx.x] = 0;
+  if (threadIdx.x == 0 && q == 0) V.t_out[2 * t] = global_ns();
+  sync();
+
+  // refresh of the own rows (and, when chk, the slack part of the stopping
+  // test into s_over[slot])
+  auto rows_pass = [&](bool chk, int slot) {
+    bool over = false;
+    for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
+      const float xu = xget(Iru[e]), xv = xget(Irv[e]);
+      const float sv = Ss[e];
+      const bool ex = fix_ok(xu) && fix_ok(xv) && fix_ok(sv);
+      long long rf = 0;
+      float r32;
+      if (ex) {
+        rf = row_fix(xu, xv, sv, sig);
+        r32 = __ll2float_rn(rf) * 0x1p-58f;
+      } else {
+        r32 = (float)row_f64(xu, xv, sv, sig);
+      }
+      rown_set(e, r32);
+      if (!chk || over) continue;
+      // slack unit: rho = |max(0, s - grad / L) - s|, L = beta + 1/beta
+      const float ls = beta + ib;
+      const float g = fmaf(beta * sig, r32, sv * ib);
+      const float qv = g / ls;
+      const float rho = fabsf(fmaxf(sv - qv, 0.f) - sv);
+      const float del = 0x1p-19f * ((beta * fabsf(r32) + sv * ib) / ls + fabsf(sv) + fabsf(qv)) + 0x1p-23f * tol32 +
+                        1e-30f;
+      if (rho - del > tol32) {
+        over = true;
+      } else if (rho + del > tol32) {  // too close to tol for FP32: decide in FP64
+        const double r64 = ex ? (double)rf * 0x1p-58 : row_f64(xu, xv, sv, sig);
+        const double bd = V.beta_d, ibd = 1.0 / bd;
+        const double bsr = sig > 0.f ? bd * r64 : -(bd * r64);
+        const double g64 = fma((double)sv, ibd, bsr);
+        double sn = fma(-g64, 1.0 / (bd + ibd), (double)sv);
+        if (sn < 0.0) sn = 0.0;
+        if (fabs(sn - (double)sv) > V.tol) over = true;
+      }
+    }
+    if (over) atomicOr(&s_over[slot], 1);
+  };
+
+  // the column part of the stopping test: a_j^T r from the exact row values
+  auto cols_check = [&](int slot) {
+    const int cnt = (n > q) ? (n - q + K - 1) / K : 0;
+    constexpr int PW = 32 / GC;
+    const int warp = threadIdx.x >> 5, lw = (threadIdx.x & 31) / GC, gl = threadIdx.x % GC;
+    bool over = false;
+    for (int ib0 = warp * PW; ib0 < cnt; ib0 += (NT / 32) * PW) {
+      const int i = ib0 + lw;
+      const bool valid = i < cnt;
+      const int k = q + i * K;
+      uint32_t p0 = 0, p1 = 0;
+      float xk = 0.f, ck = 0.f;
+      if (valid) {
+        p0 = (k == 0) ? 0u : Iend[k - 1];
+        p1 = Iend[k];
+        xk = xown_get(k);
+        ck = Cc[k];
+      }
+      long long hi = 0, lo = 0;
+      int bad = (valid && !fix_ok(xk)) ? 1 : 0;
+      const long long fk = fix58(xk);
+      for (uint32_t p = p0 + gl; p < p1; p += GC) {
+        const uint32_t e = row_of(Ient[p]);
+        const float xw = xget(Inb[p]);
+        const float sv = __ldcg(Ss + e);
+        if (!(fix_ok(xw) && fix_ok(sv))) {
+          bad = 1;
+          continue;
+        }
+        const long long fs = fix58(sv);
+        const long long rf = fk + fix58(xw) + (sig > 0.f ? fs : -fs) - FIX_ONE;
+        hi += rf >> FIX_SPLIT;
+        lo += rf & ((1LL << FIX_SPLIT) - 1);
+      }
+#pragma unroll
+      for (int o = GC / 2; o > 0; o >>= 1) {
+        hi += __shfl_xor_sync(0xffffffffu, hi, o, GC);
+        lo += __shfl_xor_sync(0xffffffffu, lo, o, GC);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o, GC);
+      }
+      if (!valid || gl != 0 || over) continue;
+      const float deg = (float)(p1 - p0);
+      const float L = fmaf(beta, deg, ib);
+      bool exact = bad != 0;
+      if (!exact) {
+        const float sum = __ll2float_rn(hi) * 0x1p-40f;  // the low parts add < deg * 2^-40
+        const float g = ck + beta * sum + xk * ib;
+        const float qv = g / L;
+        const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
+        const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
+                          0x1p-39f * (1.f + deg) + 0x1p-23f * tol32 + 1e-30f;
+        if (rho - del > tol32) over = true;
+        else if (rho + del > tol32) exact = true;
+      }
+      if (exact) {  // FP64 from the exact sum (or from FP64 row values outside the fixed-point range)
+        double sum64;
+        if (!bad) {
+          sum64 = (double)hi * 0x1p-40 + (double)lo * 0x1p-58;
+        } else {
+          sum64 = 0.0;
+          for (uint32_t p = p0; p < p1; ++p) {
+            const uint32_t e = row_of(Ient[p]);
+            sum64 += row_f64(xk, xget(Inb[p]), __ldcg(Ss + e), sig);
+          }
+        }
+        const double bd = V.beta_d, ibd = 1.0 / bd;
+        const double g64 = (double)ck + bd * sum64 + (double)xk * ibd;
+        const double L64 = bd * (double)(p1 - p0) + ibd;
+        const double xn = fmin(fmax((double)xk - g64 / L64, (double)V.lo), (double)V.hi);
+        if (fabs(xn - (double)xk) > V.tol) over = true;
+      }
+    }
+    if (over) atomicOr(&s_over[slot], 1);
+  };
+
+  // columns [ka, kb) of this rank (k % K == q) through the CSR, GG lanes each
+  auto csr_columns = [&](auto gg, int ka, int kb) {
+    constexpr int GG = decltype(gg)::value;
+    constexpr int NC = 32 / GG;  // entries a lane keeps in registers between gather and scatter
+    const int first = ka + ((q - ka % K) % K + K) % K;
+    const int cnt = (first < kb) ? (kb - first + K - 1) / K : 0;
+    constexpr int PW = 32 / GG;
+    const int warp = threadIdx.x >> 5, lw = (threadIdx.x & 31) / GG, gl = threadIdx.x % GG;
+    for (int ib0 = warp * PW; ib0 < cnt; ib0 += (NT / 32) * PW) {
+      const int i = ib0 + lw;
+      const bool valid = i < cnt;
+      const int k = first + i * K;
+      uint32_t p0 = 0, p1 = 0;
+      float xk = 0.f, ck = 0.f;
+      if (valid) {
+        p0 = (k == 0) ? 0u : Iend[k - 1];
+        p1 = Iend[k];
+        xk = xown_get(k);
+        ck = Cc[k];
+      }
+      uint32_t ce[NC];
+      float cr[NC];
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const uint32_t p = p0 + gl + (uint32_t)(u * GG);
+        ce[u] = (p < p1) ? Ient[p] : NO_ENTRY;
+      }
+#pragma unroll
+      for (int u = 0; u < NC; ++u) cr[u] = (ce[u] != NO_ENTRY) ? rget(ce[u]) : 0.f;
+      float acc = 0.f;
+#pragma unroll
+      for (int u = 0; u < NC; ++u) acc += cr[u];
+      for (uint32_t p = p0 + gl + NC * GG; p < p1; p += GG) acc += rget(Ient[p]);
+#pragma unroll
+      for (int o = GG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, GG);
+      if (!valid) continue;
+      const float g = ck + beta * acc + xk * ib;
+      const float L = (lfix > 0.f) ? lfix : fmaf(beta, (float)(p1 - p0), ib);
+      const float xn = fminf(fmaxf(xk - g / L, V.lo), V.hi);
+      const float d = xn - xk;
+      if (gl == 0) xown_set(k, xn);
+      if (d != 0.f) {
+#pragma unroll
+        for (int u = 0; u < NC; ++u)
+          if (ce[u] != NO_ENTRY) rset(ce[u], cr[u] + d);
+        for (uint32_t p = p0 + gl + NC * GG; p < p1; p += GG) {
+          const uint32_t e = Ient[p];
+          rset(e, rget(e) + d);
+        }
+      }
+    }
+  };
+
+  // the short columns of colour c in ELL panels: every K-th panel to this rank,
+  // one panel per warp, one column per lane
+  auto ell_columns = [&](int c) {
+    constexpr int NE = 8;  // slots kept in registers between gather and scatter
+    const int64_t pf = V.pfirst[(int64_t)t * V.C + c];
+    const int np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
+    const int cw = V.cwide[(int64_t)t * V.C + c], cend = coff[c + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = q + K * warp; j < np; j += K * (NT / 32)) {
+      const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
+      const int W = V.pw[pf + j];
+      const int k = cw + j * 32 + lane;
+      uint32_t ce[NE];
+      float cr[NE];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) ce[u] = (u < W) ? pe[32 * u] : NO_ENTRY;
+      const bool valid = k < cend;
+      const float xk = valid ? xget((uint32_t)k) : 0.f;
+      const float ck = valid ? Cc[k] : 0.f;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) cr[u] = (ce[u] != NO_ENTRY) ? rget(ce[u]) : 0.f;
+      float acc = 0.f;
+      int deg = 0;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        acc += cr[u];
+        deg += (ce[u] != NO_ENTRY) ? 1 : 0;
+      }
+      for (int u = NE; u < W; ++u) {
+        const uint32_t e = pe[32 * u];
+        if (e != NO_ENTRY) {
+          acc += rget(e);
+          ++deg;
+        }
+      }
+      if (!valid) continue;
+      const float g = ck + beta * acc + xk * ib;
+      const float xn = fminf(fmaxf(xk - g * s_invL[deg], V.lo), V.hi);
+      const float d = xn - xk;
+      xset((uint32_t)k, xn);
+      if (d != 0.f) {
+#pragma unroll
+        for (int u = 0; u < NE; ++u)
+          if (ce[u] != NO_ENTRY) rset(ce[u], cr[u] + d);
+        for (int u = NE; u < W; ++u) {
+          const uint32_t e = pe[32 * u];
+          if (e != NO_ENTRY) rset(e, rget(e) + d);
+        }
+      }
+    }
+  };
+
+  // one colour: its columns, then its slack rows (four per thread at a time)
+  auto sweep_colour = [&](int c) {
+    if constexpr (G == 1) {
+      const int cw = V.cwide[(int64_t)t * V.C + c];
+      if (cw > coff[c]) csr_columns(std::integral_constant<int, 32>{}, coff[c], cw);
+      ell_columns(c);
+    } else {
+      csr_columns(std::integral_constant<int, G>{}, coff[c], coff[c + 1]);
+    }
+    const int ra = roff[c], rb2 = roff[c + 1];  // this rank's slack rows of colour c
+    constexpr int SR = 4;
+    for (int e0 = ra + (int)threadIdx.x; e0 < rb2; e0 += SR * NT) {
+      float sv[SR], rv[SR];
+#pragma unroll
+      for (int u = 0; u < SR; ++u) {
+        const int e = e0 + u * NT;
+        sv[u] = (e < rb2) ? Ss[e] : 0.f;
+        rv[u] = (e < rb2) ? rown_get(e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < SR; ++u) {
+        const int e = e0 + u * NT;
+        if (e >= rb2) continue;
+        const float g = bsig * rv[u] + sv[u] * ib;
+        const float sn = fmaxf(sv[u] - g * inv_ls, 0.f);
+        const float d = sn - sv[u];
+        Ss[e] = sn;
+        if (d != 0.f) rown_set(e, rv[u] + sig * d);
+      }
+    }
+  };
+
+  // a check: exact refresh + stopping test; true when some unit has rho > tol
+  int nchk = 0;
+  auto check = [&]() -> bool {
+    const int slot = nchk & 1;
+    ++nchk;
+    rows_pass(true, slot);
+    cols_check(slot);
+    sync();
+    int over = 0;
+    if constexpr (K == 1) {
+      over = s_over[slot];
+    } else {
+      const uint32_t fa = smem_u32(&s_over[slot]);
+#pragma unroll
+      for (int r = 0; r < K; ++r) over |= dsm_ld_i(dsm_map(fa, (uint32_t)r));
+    }
+    if (threadIdx.x == 0) s_over[slot ^ 1] = 0;  // the next check's slot (no reader left: see the barriers between)
+    return over != 0;
+  };
+
+  rows_pass(false, 0);
+  sync();
+  int ep = 0;
+  bool conv = false, checked_last = false;
+  while (ep < V.epochs) {
+    for (int c = 0; c < nc; ++c) {
+      sweep_colour(c);
+      sync();
+    }
+    ++ep;
+    checked_last = false;
+    if (ep % V.R == 0 || ep == V.epochs) {
+      checked_last = true;
+      if (!check()) {
+        conv = true;
+        break;
+      }
+    }
+  }
+  if (!checked_last) conv = !check();
+  sync();  // no rank may leave while another still reads its shared memory
+  if (xs)
+    for (int i = threadIdx.x; i * K + q < n; i += NT) Sx[i * K + q] = sx[i];
+  if (threadIdx.x == 0 && q == 0) {
+    V.ep_out[t] = ep;
+    V.conv_out[t] = conv ? 1 : 0;
+    V.t_out[2 * t + 1] = global_ns();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// instance-major layout, built once from the union layout
+// ---------------------------------------------------------------------------
+__global__ void k_inst_keys(const int32_t* inst, int64_t n, uint32_t* keys, uint32_t* vals) {
+  GSTRIDE(i, n) {
+    keys[i] = (uint32_t)inst[i];
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// sort keys of the union columns: length (longest first), colour, instance
+__global__ void k_inst_key_len(const int64_t* colptr, int64_t Ns, uint32_t* keys, uint32_t* vals) {
+  GSTRIDE(j, Ns) {
+    const int64_t len = colptr[j + 1] - colptr[j];
+    keys[j] = 1023u - (uint32_t)(len < 1023 ? len : 1023);
+    vals[j] = (uint32_t)j;
+  }
+}
+__global__ void k_inst_key_of(const uint32_t* vals, const uint32_t* table, int64_t n, uint32_t* keys) {
+  GSTRIDE(k, n) keys[k] = table[vals[k]];
+}
+// colour of every union column: the colours' columns are consecutive ranges
+// cstart[c] .. cstart[c + 1] (the last c with cstart[c] <= j)
+__global__ void k_inst_ucolour(const int64_t* cstart, int C1, int64_t Ns, uint32_t* colour) {
+  GSTRIDE(j, Ns) {
+    int lo = 0, hi = C1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (cstart[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    colour[j] = (uint32_t)lo;
+  }
+}
+
+// first short column (at most 32 entries) of every colour of every instance,
+// and the ELL panels of 32 short columns each colour takes
+__global__ void k_inst_wide(const uint32_t* i_col, const int64_t* colptr, const int64_t* noff, const int32_t* coff,
+                            int64_t count, int C1, int32_t* cwide, int64_t* npan) {
+  GSTRIDE(f, count * C1) {
+    const int64_t t = f / C1;
+    const int c = (int)(f % C1);
+    if (c == C1 - 1) {
+      cwide[f] = coff[f];
+      npan[f] = 0;
+      continue;
+    }
+    int64_t lo = noff[t] + coff[f], hi = noff[t] + coff[f + 1];
+    const int64_t end = hi;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const uint32_t j = i_col[mid];
+      if (colptr[j + 1] - colptr[j] > 32) lo = mid + 1;
+      else hi = mid;
+    }
+    cwide[f] = (int32_t)(lo - noff[t]);
+    npan[f] = (end - lo + 31) / 32;
+  }
+}
+
+// per panel: its width (the length of its first, longest column) and its slot count
+__global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const uint32_t* i_col,
+                              const int64_t* colptr, const int64_t* noff, int64_t nf, int C1, int64_t npanels,
+                              uint8_t* pw, int64_t* pslots) {
+  GSTRIDE(p, npanels) {
+    int64_t lo = 0, hi = nf;  // the last f with pfirst[f] <= p (f with panels)
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (pfirst[mid] <= p) lo = mid;
+      else hi = mid;
+    }
+    while (lo + 1 < nf && pfirst[lo + 1] <= p) ++lo;
+    const int64_t t = lo / C1;
+    const int64_t k0 = noff[t] + cwide[lo] + 32 * (p - pfirst[lo]);
+    const uint32_t j = i_col[k0];
+    const int w = (int)(colptr[j + 1] - colptr[j]);
+    pw[p] = (uint8_t)w;
+    pslots[p] = 32 * (int64_t)w;
+  }
+}
+
+// ELL slots of every short column (CSR entries of the IML column, in order)
+__global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const uint32_t* ucolour,
+                           const int64_t* noff, const int64_t* eoff, const uint32_t* iend, const uint32_t* ient,
+                           const int32_t* cwide, const int64_t* pfirst, const int64_t* pbase, int64_t Ns, int C1,
+                           uint32_t* ell) {
+  GSTRIDE(k, Ns) {
+    const uint32_t j = i_col[k];
+    const int64_t t = inst_col[j];
+    const int64_t f = t * C1 + ucolour[j];
+    const int64_t loc = k - noff[t];
+    const int64_t o = loc - cwide[f];
+    if (o < 0) continue;  // a long column: served through the CSR
+    const int64_t p = pfirst[f] + o / 32;
+    const int lane = (int)(o % 32);
+    const uint32_t e1 = iend[k];
+    const uint32_t e0 = (loc == 0) ? 0u : iend[k - 1];
+    const int64_t src = 2 * eoff[t];
+    for (uint32_t q = e0; q < e1; ++q) ell[pbase[p] + 32 * (int64_t)(q - e0) + lane] = ient[src + q];
+  }
+}
+
+__global__ void k_inst_lcol(const uint32_t* i_col, const int32_t* inst_col, const int64_t* noff, int64_t Ns,
+                            uint32_t* lcol) {
+  GSTRIDE(k, Ns) {
+    const uint32_t j = i_col[k];
+    lcol[j] = (uint32_t)(k - noff[inst_col[j]]);
+  }
+}
+
+// Rank of the cluster that keeps row i in its shared memory: one of the two
+// ranks that step its columns (column k is stepped by rank k % K), chosen by a
+// hash of the row for balance -- so that column's access to the row is local.
+// 0 for instances on one CTA.
+__global__ void k_inst_rowrank(const int64_t* rowptr, const uint32_t* colidx, const uint32_t* lcol,
+                               const int32_t* inst_row, const uint8_t* iK, int64_t M, uint32_t* rank,
+                               uint32_t* vals) {
+  GSTRIDE(i, M) {
+    const uint32_t K = iK[inst_row[i]];
+    uint32_t r = 0;
+    if (K > 1) {
+      const int64_t q0 = rowptr[i];
+      const uint32_t a = lcol[idx_of(colidx[q0])], b = lcol[idx_of(colidx[q0 + 1])];
+      const uint32_t h = (uint32_t)((uint64_t)i * 0x9E3779B97F4A7C15ull >> 40);
+      r = ((h & 1u) ? a : b) & (K - 1);
+    }
+    rank[i] = r;
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// local row of every union row, and its encoded id: (rank << 28) | (position
+// inside the rank's block)
+__global__ void k_inst_lrow(const uint32_t* i_row, const int32_t* inst_row, const int64_t* eoff, const uint32_t* rank,
+                            const int32_t* qoff, int64_t M, uint32_t* lrow, uint32_t* erow) {
+  GSTRIDE(k, M) {
+    const uint32_t i = i_row[k];
+    const int32_t t = inst_row[i];
+    const uint32_t loc = (uint32_t)(k - eoff[t]);
+    const uint32_t r = rank[i];
+    lrow[i] = loc;
+    erow[i] = (r << 28) | (loc - (uint32_t)qoff[(int64_t)t * 5 + r]);
+  }
+}
+
+// first local row of every rank (5 per instance: ranks 0..3 and the end)
+__global__ void k_inst_qoff(const uint32_t* i_row, const uint32_t* rank, const int64_t* eoff, int64_t count,
+                            int32_t* qoff) {
+  GSTRIDE(f, count * 5) {
+    const int64_t t = f / 5;
+    const uint32_t q = (uint32_t)(f % 5);
+    int64_t lo = eoff[t], hi = eoff[t + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rank[i_row[mid]] < q) lo = mid + 1;
+      else hi = mid;
+    }
+    qoff[f] = (int32_t)(lo - eoff[t]);
+  }
+}
+
+__global__ void k_inst_deg(const uint32_t* i_col, const int64_t* colptr, int64_t Ns, int64_t* deg) {
+  GSTRIDE(k, Ns) {
+    const uint32_t j = i_col[k];
+    deg[k] = colptr[j + 1] - colptr[j];
+  }
+}
+
+// local end offsets, entries (encoded row, other endpoint) and the longest
+// column of every instance; err: a row without exactly two structural entries
+__global__ void k_inst_fill(const uint32_t* i_col, const int32_t* inst_col, const int64_t* pos, const int64_t* eoff,
+                            const int64_t* colptr, const uint32_t* rowidx, const int64_t* rowptr,
+                            const uint32_t* colidx, const uint32_t* lcol, const uint32_t* erow, int64_t Ns,
+                            uint32_t* iend, uint32_t* ient, uint32_t* inb, int32_t* ideg, int* err) {
+  GSTRIDE(k, Ns) {
+    const uint32_t j = i_col[k];
+    const int32_t t = inst_col[j];
+    const int64_t base = pos[k];
+    const int64_t p0 = colptr[j], p1 = colptr[j + 1];
+    iend[k] = (uint32_t)(pos[k + 1] - 2 * eoff[t]);
+    atomicMax(&ideg[t], (int32_t)(p1 - p0));
+    for (int64_t p = p0; p < p1; ++p) {
+      const uint32_t i = idx_of(rowidx[p]);
+      const int64_t q0 = rowptr[i];
+      if (rowptr[i + 1] - q0 != 2) {
+        atomicExch(err, 1);
+        ient[base + (p - p0)] = 0;
+        inb[base + (p - p0)] = 0;
+        continue;
+      }
+      const uint32_t a = idx_of(colidx[q0]), b = idx_of(colidx[q0 + 1]);
+      ient[base + (p - p0)] = erow[i];
+      inb[base + (p - p0)] = lcol[a == j ? b : a];
+    }
+  }
+}
+
+__global__ void k_inst_rows(const uint32_t* i_row, const int64_t* rowptr, const uint32_t* colidx,
+                            const uint32_t* lcol, int64_t M, uint32_t* iru, uint32_t* irv) {
+  GSTRIDE(k, M) {
+    const int64_t q0 = rowptr[i_row[k]];
+    iru[k] = lcol[idx_of(colidx[q0])];
+    irv[k] = lcol[idx_of(colidx[q0 + 1])];
+  }
+}
+
+// first local column / slack row of every colour: the instance's columns are
+// in union order, which is colour-major, so a colour starts at the first
+// column whose union position reaches the colour's first union column
+__global__ void k_inst_colours(const uint32_t* i_col, const uint32_t* i_row, const int64_t* noff, const int64_t* eoff,
+                               const int32_t* qoff, const int64_t* cstart, const int64_t* rstart, int64_t count,
+                               int C1, int32_t* coff, int32_t* roff) {
+  GSTRIDE(f, count * C1 * 5) {
+    const int64_t tq = f / C1;  // (instance, q) with q = 0 for the columns' table
+    const int c = (int)(f % C1);
+    const int64_t t = tq / 5;
+    const int q = (int)(tq % 5);
+    if (q == 4) {
+      int64_t lo = noff[t], hi = noff[t + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)i_col[mid] < cstart[c]) lo = mid + 1;
+        else hi = mid;
+      }
+      coff[t * C1 + c] = (int32_t)(lo - noff[t]);
+      continue;
+    }
+    // the rank's block of rows keeps the union's colour-major order
+    int64_t lo = eoff[t] + qoff[t * 5 + q], hi = eoff[t] + qoff[t * 5 + q + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)i_row[mid] < rstart[c]) lo = mid + 1;
+      else hi = mid;
+    }
+    roff[(t * 4 + q) * C1 + c] = (int32_t)(lo - eoff[t]);
+  }
+}
+
+// colours an instance uses: one past the last colour holding a column or a
+// slack row of any rank
+__global__ void k_inst_ncol(const int32_t* coff, const int32_t* roff, int64_t count, int C1, int32_t* ncol) {
+  GSTRIDE(t, count) {
+    int nc = 1;
+    for (int c = 0; c + 1 < C1; ++c) {
+      bool any = coff[t * C1 + c + 1] > coff[t * C1 + c];
+      for (int q = 0; q < 4; ++q) {
+        const int32_t* ro = roff + (t * 4 + q) * C1;
+        any = any || ro[c + 1] > ro[c];
+      }
+      if (any) nc = c + 1;
+    }
+    ncol[t] = nc;
+  }
+}
+
+__global__ void k_inst_gather(const uint32_t* i_col, const uint32_t* i_row, const float* x, const float* c,
+                              const float* s, int64_t Ns, int64_t M, float* ix, float* ic, float* is) {
+  GSTRIDE(k, Ns > M ? Ns : M) {
+    if (k < Ns) {
+      const uint32_t j = i_col[k];
+      ix[k] = x[j];
+      ic[k] = c[j];
+    }
+    if (k < M) is[k] = s[i_row[k]];
+  }
+}
+
+__global__ void k_inst_scatter(const uint32_t* i_col, const uint32_t* i_row, const float* ix, const float* is,
+                               int64_t Ns, int64_t M, float* x, float* s) {
+  GSTRIDE(k, Ns > M ? Ns : M) {
+    if (k < Ns) x[i_col[k]] = ix[k];
+    if (k < M) s[i_row[k]] = is[k];
+  }
+}
+
+__global__ void k_inst_stamp(unsigned long long* t) { *t = global_ns(); }
+
+int bits_for_count(int64_t n) {
+  int b = 1;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// launch classes: (cluster size, threads per CTA); an instance goes to the
+// first class whose shared-memory budget per CTA holds its chunk of r and x.
+// The last class takes what fits none: one CTA of 1024 threads with x and the
+// rows beyond its shared memory in global memory (L2).  The cluster classes
+// (r and x spread over 2 or 4 CTAs' shared memory) are used only when the
+// handle asks for them (measured slower on GB300: remote shared-memory
+// accesses cost more than L2 hits here).
+struct Cls {
+  int K, NT;
+};
+constexpr Cls CLASSES[] = {{1, 256}, {1, 512}, {1, 1024}, {2, 1024}, {4, 1024}, {1, 1024}};
+constexpr int NCLS = 6;
+constexpr int CLS_SPILL = 5;
+
+int64_t inst_smem(int64_t n, int64_t m, int K) { return 4 * ((m + K - 1) / K + (n + K - 1) / K); }
+
+struct DevLimits {
+  int64_t optin = 0, per_sm = 0;
+  bool cluster = false;
+};
+DevLimits dev_limits() {
+  DevLimits L;
+  int dev = 0, v = 0;
+  TH_CUDA(cudaGetDevice(&dev));
+  TH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  L.optin = v;
+  TH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  L.per_sm = v;
+  TH_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrClusterLaunch, dev));
+  L.cluster = v != 0;
+  return L;
+}
+
+// dynamic shared memory a CTA of class c may take (1 KB per CTA stays with the
+// system, 64 bytes of static shared memory)
+int64_t class_cap(const DevLimits& L, int c) {
+  const int per = (CLASSES[c].K == 1) ? 1024 / CLASSES[c].NT : 1;
+  return std::min<int64_t>(L.optin, L.per_sm / per - 1024) - 512;  // static shared memory stays below 512 B
+}
+
+template <int K, int NT, int G, bool SPILL = false>
+void launch_one(const InstView& V, const int32_t* order, int64_t count, size_t smem, int64_t optin, cudaStream_t st) {
+  auto kern = k_inst<K, NT, G, SPILL>;
+  cudaFuncAttributes fa;
+  TH_CUDA(cudaFuncGetAttributes(&fa, kern));
+  TH_CHECK((int64_t)smem + (int64_t)fa.sharedSizeBytes <= optin, THETIS_E_INVALID,
+           "instance engine: shared memory of a launch class exceeds the device limit");
+  TH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(optin - (int64_t)fa.sharedSizeBytes)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * K));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (K > 1) ? 1 : 0;
+  TH_CUDA(cudaLaunchKernelEx(&cfg, kern, V, order));
+  TH_LAUNCHED();
+}
+
+template <int G>
+void launch_class(int c, const InstView& V, const int32_t* order, int64_t count, size_t smem, int64_t optin,
+                  cudaStream_t st) {
+  switch (c) {
+    case 0: launch_one<1, 256, G>(V, order, count, smem, optin, st); break;
+    case 1: launch_one<1, 512, G>(V, order, count, smem, optin, st); break;
+    case 2: launch_one<1, 1024, G>(V, order, count, smem, optin, st); break;
+    case 3: launch_one<2, 1024, 8>(V, order, count, smem, optin, st); break;  // clusters: 8 lanes
+    case 4: launch_one<4, 1024, 8>(V, order, count, smem, optin, st); break;
+    default: launch_one<1, 1024, G, true>(V, order, count, smem, optin, st); break;
+  }
+}
+
+// launch classes and the order of instances in them (largest first); the
+// cluster size K of every instance (1 unless it takes a cluster)
+void inst_classes(Problem& P) {
+  cudaStream_t s = P.stream;
+  const int64_t count = P.nbatch;
+  const DevLimits L = dev_limits();
+  std::vector<std::vector<int32_t>> members(NCLS);
+  std::vector<uint8_t> iK(count, 1);
+  const bool clusters = P.iml_clusters && L.cluster;
+  for (int64_t t = 0; t < count; ++t) {
+    const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t], m = P.h_beoff[t + 1] - P.h_beoff[t];
+    // one CTA with everything in shared memory; else one CTA with x in global
+    // memory when r alone fits; else a cluster (if asked for; rows are split
+    // between ranks by a hash, so the estimate leaves 5 % + 256 rows of slack);
+    // else one CTA whose r spills to L2
+    int c = 0;
+    while (c < 3 && inst_smem(n, m, 1) > class_cap(L, c)) ++c;
+    if (c == 3) {
+      auto est = [&](int K) { return 4 * ((m * 105 / 100) / K + 256 + (n + K - 1) / K); };
+      if (4 * m <= class_cap(L, CLS_SPILL)) c = CLS_SPILL;
+      else if (clusters && est(2) <= class_cap(L, 3)) c = 3;
+      else if (clusters && est(4) <= class_cap(L, 4)) c = 4;
+      else c = CLS_SPILL;
+    }
+    members[c].push_back((int32_t)t);
+    iK[t] = (uint8_t)CLASSES[c].K;
+  }
+  std::vector<int32_t> order;
+  P.h_icls_off.assign(NCLS + 1, 0);
+  for (int c = 0; c < NCLS; ++c) {
+    auto& v = members[c];
+    std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
+      const int64_t wa = (P.h_bnoff[a + 1] - P.h_bnoff[a]) + (P.h_beoff[a + 1] - P.h_beoff[a]);
+      const int64_t wb = (P.h_bnoff[b + 1] - P.h_bnoff[b]) + (P.h_beoff[b + 1] - P.h_beoff[b]);
+      return wa > wb;
+    });
+    P.h_icls_off[c] = (int64_t)order.size();
+    order.insert(order.end(), v.begin(), v.end());
+  }
+  P.h_icls_off[NCLS] = (int64_t)order.size();
+  if (!P.i_order) P.i_order = P.mem.alloc<int32_t>(count);
+  if (!P.i_K) P.i_K = P.mem.alloc<uint8_t>(count);
+  TH_CUDA(cudaMemcpyAsync(P.i_order, order.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaMemcpyAsync(P.i_K, iK.data(), count, cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  if (iK != P.h_iK) P.iml_built = false;  // the rows' placement depends on K
+  P.h_iK = iK;
+  P.iml_classes_ok = true;
+}
+
+// shared memory of every class from the built layout: everything in shared
+// memory (K = 1), the largest rank's rows plus the rank's columns (clusters),
+// or the whole budget (spill)
+void inst_class_smem(Problem& P) {
+  const int64_t count = P.nbatch;
+  const DevLimits L = dev_limits();
+  std::vector<int32_t> qo((size_t)count * 5);
+  TH_CUDA(cudaMemcpyAsync(qo.data(), P.i_qoff, qo.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  std::vector<int32_t> order((size_t)count);
+  TH_CUDA(cudaMemcpyAsync(order.data(), P.i_order, count * sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
+  TH_CUDA(cudaStreamSynchronize(P.stream));
+  P.h_icls_smem.assign(NCLS, 0);
+  for (int c = 0; c < NCLS; ++c) {
+    int64_t need = (c == CLS_SPILL) ? class_cap(L, c) : 0;
+    for (int64_t i = P.h_icls_off[c]; i < P.h_icls_off[c + 1] && c != CLS_SPILL; ++i) {
+      const int64_t t = order[i];
+      const int K = CLASSES[c].K;
+      const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t];
+      int64_t rows = 0;
+      for (int q = 0; q < K; ++q) rows = std::max<int64_t>(rows, qo[t * 5 + q + 1] - qo[t * 5 + q]);
+      need = std::max(need, 4 * (rows + (n + K - 1) / K));
+    }
+    TH_CHECK(need <= class_cap(L, c), THETIS_E_INVALID, "instance engine: a rank's rows exceed its shared memory");
+    P.h_icls_smem[c] = (need + 15) / 16 * 16;
+  }
+}
+
+void inst_layout(Problem& P) {
+  cudaStream_t s = P.stream;
+  const int64_t count = P.nbatch, Ns = P.Ns, M = P.M;
+  TH_CHECK(P.kind == KIND_BATCH && count > 0 && P.Nfree == Ns && P.Msl == M, THETIS_E_INVALID,
+           "instance engine: not a VC / IS batch");
+  Arena tmp(s);
+  const int C = P.ncolors, C1 = C + 1;
+  auto once = [&](auto*& p, int64_t n) {
+    using T = std::remove_reference_t<decltype(*p)>;
+    if (!p) p = P.mem.alloc<T>(n);
+  };
+  once(P.i_col, Ns + 1);
+  once(P.i_row, M + 1);
+  uint32_t* keys = tmp.alloc<uint32_t>(std::max(Ns, M) + 1);
+  // colour boundaries of the union layout (colour-major columns and slack rows)
+  std::vector<int64_t> cst(C1), rst(C1);
+  {
+    int64_t col = 0;
+    for (int c = 0; c < C; ++c) {
+      cst[c] = col;
+      rst[c] = P.plan[c].srow0;
+      for (auto& sg : P.plan[c].segs) col += (sg.u1 - sg.u0) * sg.len;
+    }
+    cst[C] = col;
+    rst[C] = P.Msl;
+  }
+  int64_t* dcst = tmp.alloc<int64_t>(C1);
+  int64_t* drst = tmp.alloc<int64_t>(C1);
+  TH_CUDA(cudaMemcpyAsync(dcst, cst.data(), C1 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaMemcpyAsync(drst, rst.data(), C1 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  uint32_t* ucolour = tmp.alloc<uint32_t>(Ns + 1);
+  k_inst_ucolour<<<grid_for(Ns, 256), 256, 0, s>>>(dcst, C1, Ns, ucolour);
+  TH_LAUNCHED();
+  // columns by (instance, colour, length descending): stable LSD passes from
+  // the least significant key
+  k_inst_key_len<<<grid_for(Ns, 256), 256, 0, s>>>(P.colptr, Ns, keys, P.i_col);
+  TH_LAUNCHED();
+  radix_sort_pairs(keys, P.i_col, Ns, 10, tmp, s);
+  k_inst_key_of<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, ucolour, Ns, keys);
+  TH_LAUNCHED();
+  radix_sort_pairs(keys, P.i_col, Ns, bits_for_count(C1), tmp, s);
+  k_inst_key_of<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, (const uint32_t*)P.binst_col, Ns, keys);
+  TH_LAUNCHED();
+  radix_sort_pairs(keys, P.i_col, Ns, bits_for_count(count), tmp, s);
+  uint32_t* lcol = tmp.alloc<uint32_t>(Ns + 1);
+  k_inst_lcol<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, P.bnoff, Ns, lcol);
+  TH_LAUNCHED();
+  // rows by (instance, rank of the cluster that keeps them, union order --
+  // which is slack-colour major)
+  uint32_t* rank = tmp.alloc<uint32_t>(M + 1);
+  uint32_t* lrow = tmp.alloc<uint32_t>(M + 1);
+  uint32_t* erow = tmp.alloc<uint32_t>(M + 1);
+  once(P.i_qoff, count * 5);
+  if (M > 0) {
+    k_inst_rowrank<<<grid_for(M, 256), 256, 0, s>>>(P.rowptr, P.colidx, lcol, P.binst_row, P.i_K, M, keys, P.i_row);
+    TH_LAUNCHED();
+    TH_CUDA(cudaMemcpyAsync(rank, keys, M * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    radix_sort_pairs(keys, P.i_row, M, 2, tmp, s);
+    k_inst_key_of<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, (const uint32_t*)P.binst_row, M, keys);
+    TH_LAUNCHED();
+    radix_sort_pairs(keys, P.i_row, M, bits_for_count(count), tmp, s);
+  }
+  k_inst_qoff<<<grid_for(count * 5, 256), 256, 0, s>>>(P.i_row, rank, P.beoff, count, P.i_qoff);
+  TH_LAUNCHED();
+  if (M > 0) {
+    k_inst_lrow<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.binst_row, P.beoff, rank, P.i_qoff, M, lrow, erow);
+    TH_LAUNCHED();
+  }
+  int64_t* pos = tmp.alloc<int64_t>(Ns + 1);
+  k_inst_deg<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.colptr, Ns, pos);
+  TH_LAUNCHED();
+  exclusive_scan_i64(pos, pos, Ns, tmp, s);
+  once(P.i_end, Ns + 1);
+  once(P.i_ent, 2 * M + 1);
+  once(P.i_nb, 2 * M + 1);
+  once(P.i_ru, M + 1);
+  once(P.i_rv, M + 1);
+  once(P.i_deg, count);
+  int* err = tmp.alloc<int>(1);
+  TH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  TH_CUDA(cudaMemsetAsync(P.i_deg, 0, count * sizeof(int32_t), s));
+  k_inst_fill<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, pos, P.beoff, P.colptr, P.rowidx, P.rowptr,
+                                                P.colidx, lcol, erow, Ns, P.i_end, P.i_ent, P.i_nb, P.i_deg, err);
+  TH_LAUNCHED();
+  if (M > 0) {
+    k_inst_rows<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.rowptr, P.colidx, lcol, M, P.i_ru, P.i_rv);
+    TH_LAUNCHED();
+  }
+  P.iml_C = C1;
+  once(P.i_coff, count * C1);
+  once(P.i_roff, count * 4 * C1);
+  once(P.i_ncol, count);
+  k_inst_colours<<<grid_for(count * C1 * 5, 256), 256, 0, s>>>(P.i_col, P.i_row, P.bnoff, P.beoff, P.i_qoff, dcst,
+                                                               drst, count, C1, P.i_coff, P.i_roff);
+  TH_LAUNCHED();
+  k_inst_ncol<<<grid_for(count, 256), 256, 0, s>>>(P.i_coff, P.i_roff, count, C1, P.i_ncol);
+  TH_LAUNCHED();
+  // ELL panels of the short columns (thread-per-column sweep)
+  {
+    const int64_t nf = count * C1;
+    once(P.i_cwide, nf);
+    int64_t* npan = tmp.alloc<int64_t>(nf + 1);
+    k_inst_wide<<<grid_for(nf, 256), 256, 0, s>>>(P.i_col, P.colptr, P.bnoff, P.i_coff, count, C1, P.i_cwide, npan);
+    TH_LAUNCHED();
+    once(P.i_pfirst, nf + 1);
+    exclusive_scan_i64(npan, P.i_pfirst, nf, tmp, s);
+    int64_t npanels = 0;
+    TH_CUDA(cudaMemcpyAsync(&npanels, P.i_pfirst + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    TH_CHECK(P.i_pw == nullptr || P.i_npanels == npanels, THETIS_E_CUDA, "instance engine: panel count changed");
+    P.i_npanels = npanels;
+    once(P.i_pw, npanels + 1);
+    once(P.i_pbase, npanels + 1);
+    if (npanels > 0) {
+      k_inst_panels<<<grid_for(npanels, 256), 256, 0, s>>>(P.i_pfirst, P.i_cwide, P.i_col, P.colptr, P.bnoff, nf, C1,
+                                                           npanels, P.i_pw, P.i_pbase);
+      TH_LAUNCHED();
+    }
+    exclusive_scan_i64(P.i_pbase, P.i_pbase, npanels, tmp, s);
+    int64_t nslots = 0;
+    TH_CUDA(cudaMemcpyAsync(&nslots, P.i_pbase + npanels, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    once(P.i_ell, nslots + 1);
+    TH_CUDA(cudaMemsetAsync(P.i_ell, 0xff, (nslots + 1) * sizeof(uint32_t), s));
+    k_inst_ell<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, ucolour, P.bnoff, P.beoff, P.i_end, P.i_ent,
+                                                 P.i_cwide, P.i_pfirst, P.i_pbase, Ns, C1, P.i_ell);
+    TH_LAUNCHED();
+  }
+  once(P.i_c, Ns + 1);
+  once(P.i_x, Ns + 1);
+  once(P.i_s, M + 1);
+  once(P.i_rg, M + 1);
+  once(P.i_ep, count);
+  once(P.i_conv, count);
+  once(P.i_t, 2 * count + 1);
+  int herr = 0;
+  TH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));  // host tables above must outlive their copies
+  TH_CHECK(herr == 0, THETIS_E_INVALID, "instance engine: a row without exactly two structural entries");
+  if (P.iml_G == 0) P.iml_G = 1;  // ELL panels, one thread per column (the autotuner may pick G lanes)
+  P.iml_built = true;
+  inst_class_smem(P);
+}
+
+}  // namespace
+
+bool inst_eligible(Problem& P) {
+  if (P.kind != KIND_BATCH || P.nbatch <= 0 || P.Nfree != P.Ns || P.Msl != P.M) return false;
+  if (!P.bounds_uniform) return false;
+  for (int64_t t = 0; t < P.nbatch; ++t) {
+    const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t], m = P.h_beoff[t + 1] - P.h_beoff[t];
+    if (n >= (int64_t(1) << 30) || m >= (int64_t(1) << 30)) return false;
+  }
+  return true;
+}
+
+void inst_set_clusters(Problem& P, bool on) {
+  if (P.iml_clusters == on) return;
+  P.iml_clusters = on;
+  P.iml_classes_ok = false;  // the launch classes change on the next solve
+}
+
+void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
+  if (!P.iml_classes_ok) inst_classes(P);
+  if (!P.iml_built) inst_layout(P);
+  cudaStream_t s = P.stream;
+  const int64_t count = P.nbatch;
+  if (!P.i_events[0]) {
+    for (int c = 0; c < NCLS; ++c) TH_CUDA(cudaStreamCreateWithFlags(&P.i_streams[c], cudaStreamNonBlocking));
+    TH_CUDA(cudaEventCreate(&P.i_events[0]));
+    TH_CUDA(cudaEventCreate(&P.i_events[1]));
+    for (int c = 0; c <= NCLS; ++c) TH_CUDA(cudaEventCreateWithFlags(&P.i_events[2 + c], cudaEventDisableTiming));
+  }
+  const int64_t n2 = std::max(P.Ns, P.M);
+  k_inst_gather<<<grid_for(n2, 256), 256, 0, s>>>(P.i_col, P.i_row, P.x, P.c, P.s, P.Ns, P.M, P.i_x, P.i_c, P.i_s);
+  TH_LAUNCHED();
+  InstView V;
+  V.noff = P.bnoff;
+  V.eoff = P.beoff;
+  V.iend = P.i_end;
+  V.ient = P.i_ent;
+  V.inb = P.i_nb;
+  V.iru = P.i_ru;
+  V.irv = P.i_rv;
+  V.coff = P.i_coff;
+  V.roff = P.i_roff;
+  V.qoff = P.i_qoff;
+  V.ncol = P.i_ncol;
+  V.cwide = P.i_cwide;
+  V.pfirst = P.i_pfirst;
+  V.pbase = P.i_pbase;
+  V.pw = P.i_pw;
+  V.ell = P.i_ell;
+  V.ideg = P.i_deg;
+  V.kind = P.bkind;
+  V.c = P.i_c;
+  V.x = P.i_x;
+  V.s = P.i_s;
+  V.rg = P.i_rg;
+  V.C = P.iml_C;
+  V.beta = (float)a.beta;
+  V.inv_beta = (float)(1.0 / a.beta);
+  V.beta_d = a.beta;
+  V.lo = P.lo_u;
+  V.hi = P.hi_u;
+  V.step_rule = a.step_rule;
+  V.epochs = a.epochs;
+  V.R = a.refresh_every;
+  V.tol = a.tol;
+  V.ep_out = P.i_ep;
+  V.conv_out = P.i_conv;
+  V.t_out = P.i_t;
+  const DevLimits L = dev_limits();
+  k_inst_stamp<<<1, 1, 0, s>>>(P.i_t + 2 * count);
+  TH_LAUNCHED();
+  TH_CUDA(cudaEventRecord(P.i_events[0], s));
+  // fork: every class on its own stream, the largest clusters first so they
+  // find whole SMs free
+  TH_CUDA(cudaEventRecord(P.i_events[2 + NCLS], s));
+  for (int c = NCLS - 1; c >= 0; --c) {
+    const int64_t cnt = P.h_icls_off[c + 1] - P.h_icls_off[c];
+    if (cnt == 0) continue;
+    cudaStream_t st = P.i_streams[c];
+    TH_CUDA(cudaStreamWaitEvent(st, P.i_events[2 + NCLS], 0));
+    const int32_t* ord = P.i_order + P.h_icls_off[c];
+    const size_t smem = (size_t)P.h_icls_smem[c];
+    // clusters take 8 lanes per column through the CSR (fewer remote
+    // round trips per column than one thread per column)
+    const int g = (CLASSES[c].K > 1) ? 8 : P.iml_G;
+    if (g == 4) launch_class<4>(c, V, ord, cnt, smem, L.optin, st);
+    else if (g == 8) launch_class<8>(c, V, ord, cnt, smem, L.optin, st);
+    else launch_class<1>(c, V, ord, cnt, smem, L.optin, st);
+    TH_CUDA(cudaEventRecord(P.i_events[2 + c], st));
+    TH_CUDA(cudaStreamWaitEvent(s, P.i_events[2 + c], 0));
+  }
+  TH_CUDA(cudaEventRecord(P.i_events[1], s));
+  k_inst_scatter<<<grid_for(n2, 256), 256, 0, s>>>(P.i_col, P.i_row, P.i_x, P.i_s, P.Ns, P.M, P.x, P.s);
+  TH_LAUNCHED();
+  P.h_iep.resize(count);
+  P.h_iconv.resize(count);
+  P.h_it.resize(2 * count + 1);
+  TH_CUDA(cudaMemcpyAsync(P.h_iep.data(), P.i_ep, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(P.h_iconv.data(), P.i_conv, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(P.h_it.data(), P.i_t, (2 * count + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  TH_CUDA(cudaGetLastError());
+  float ms = 0.f;
+  TH_CUDA(cudaEventElapsedTime(&ms, P.i_events[0], P.i_events[1]));
+  sweep_ms = ms;
+}
+
+void inst_release(Problem& P) {
+  for (auto& st : P.i_streams)
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+      st = nullptr;
+    }
+  for (auto& ev : P.i_events)
+    if (ev) {
+      cudaEventDestroy(ev);
+      ev = nullptr;
+    }
+}
+
+}  // namespace thetis

@@ -94,9 +94,14 @@ struct Problem {
   int32_t* binst_row = nullptr;        // M
   uint8_t* bfrozen = nullptr;          // nbatch
   unsigned long long* brho = nullptr;  // nbatch: rho of the last check (FP64 bits, >= 0)
+  int32_t* bmaxdeg = nullptr;          // nbatch: longest column of every instance
+  float* blfix = nullptr;              // nbatch: step rule 1's L_max of every instance (for blfix_beta)
+  double blfix_beta = 0.0;
   std::vector<uint8_t> h_bfrozen;
   std::vector<int32_t> h_bepochs;      // epochs each instance ran in the last solve
   std::vector<double> h_brho;          // its rho when it stopped
+  std::vector<double> h_bdone;         // ms from the start of the solve to its stop
+  double batch_check_ms = 0.0;         // union sweep: time of the current check since the solve started
   // active tiles: per colour, the sweep tiles holding a unit of an unfinished
   // instance (built for launch shape act_g; recomputed when instances stop)
   int32_t* act_tiles = nullptr;
@@ -107,6 +112,47 @@ struct Problem {
   int64_t* tile_start = nullptr;  // per colour: first flat tile (C + 1)
   int64_t tiles_total = 0;
   int act_g = -1;
+
+  // instance-resident engine of batches (inst.cu): every instance's columns,
+  // rows and non-zeros in instance-major order ("IML": instance, then colour),
+  // built once from the union layout above
+  bool iml_built = false;
+  int iml_C = 0;                    // colour-table stride (union colours + 1)
+  uint32_t* i_col = nullptr;        // Ns: union internal column of IML column k
+  uint32_t* i_row = nullptr;        // M: union internal row of IML row k
+  uint32_t* i_end = nullptr;        // Ns: end of column k's entries, local to its instance
+  uint32_t* i_ent = nullptr;        // 2M: local row of every entry
+  uint32_t* i_nb = nullptr;         // 2M: local column of the entry's other endpoint
+  uint32_t *i_ru = nullptr, *i_rv = nullptr;  // M: local columns of every row
+  int32_t* i_coff = nullptr;        // count * iml_C: first local column of every colour
+  int32_t* i_roff = nullptr;        // count * 4 * iml_C: first local slack row of every (rank, colour)
+  int32_t* i_qoff = nullptr;        // count * 5: first local row of every cluster rank (and the end)
+  uint8_t* i_K = nullptr;           // count: cluster size of every instance (1: one CTA)
+  std::vector<uint8_t> h_iK;
+  int32_t* i_ncol = nullptr;        // count: colours of the instance
+  int32_t* i_cwide = nullptr;       // count * iml_C: first short column (<= 32 entries) of every colour
+  int64_t* i_pfirst = nullptr;      // count * iml_C + 1: first ELL panel of every colour
+  int64_t* i_pbase = nullptr;       // per panel: first ELL slot
+  uint8_t* i_pw = nullptr;          // per panel: slots per column
+  uint32_t* i_ell = nullptr;        // ELL slots of the short columns (local rows)
+  int64_t i_npanels = 0;
+  int32_t* i_deg = nullptr;         // count: largest column length of the instance
+  float *i_c = nullptr, *i_x = nullptr, *i_s = nullptr;  // c, x (Ns) and s (M) in IML order
+  float* i_rg = nullptr;            // M: residual rows kept in global memory (instances too large for one CTA)
+  bool iml_clusters = false;        // large instances on thread-block clusters instead of one CTA + L2
+  bool iml_classes_ok = false;      // launch classes computed for the current iml_clusters
+  int32_t* i_ep = nullptr;          // count: epochs the instance ran
+  int32_t* i_conv = nullptr;        // count: 1 if it stopped at rho <= tol
+  unsigned long long* i_t = nullptr;  // count: [start, done] globaltimer per instance (2 * count)
+  int32_t* i_order = nullptr;       // instances grouped by launch class, largest first
+  std::vector<int64_t> h_icls_off;  // per class: range of i_order
+  std::vector<int64_t> h_icls_smem; // per class: dynamic shared memory per CTA
+  std::vector<int32_t> h_iep;       // host copies after a solve
+  std::vector<int32_t> h_iconv;
+  std::vector<unsigned long long> h_it;
+  int iml_G = 0;                    // lanes per column of the instance kernel (1: ELL thread per column; 0: default)
+  cudaStream_t i_streams[8] = {};
+  cudaEvent_t i_events[10] = {};
 
   // set cover meta: the sets holding each element, in increasing set id
   // (elements = rows, sets = columns, original order), and f = max frequency
@@ -196,6 +242,8 @@ struct Problem {
   int64_t* d_ntiles = nullptr;  // tiles per colour
   unsigned* bar = nullptr;      // grid barrier state
   int* err = nullptr;           // barrier timeout flag
+  long long wait_ns = 2000000000LL;  // limit of every bounded grid-barrier wait
+  unsigned wait_phantom = 0;    // CTAs the barriers wait for that never arrive (timeout test)
   int sweep_grid = -1;
   // launch shape (set by thetis_autotune): lanes per SMALL unit, CTAs per SM
   int small_g = 8;
@@ -258,8 +306,25 @@ void batch_index(Problem& P);
 void batch_begin_solve(Problem& P);
 bool batch_after_check(Problem& P, double tol, int epoch);
 void batch_end_solve(Problem& P, int epoch);
+// the same around an instance-resident solve (inst.cu): clear the frozen flags;
+// after the final FP64 check, every instance's epochs, rho and convergence,
+// the largest epoch count, whether all converged, and the updates made
+void batch_inst_begin(Problem& P);
+void batch_inst_end(Problem& P, int& ep_max, bool& all_converged, int64_t& updates);
 // (scd.cu) rebuild the active-tile lists from the frozen flags
 void batch_active_tiles(Problem& P);
+// (inst.cu) instance-resident solve of a batch: every instance in the shared
+// memory of one CTA or thread-block cluster, swept colour by colour, checked
+// and stopped on its own; returns false when the batch does not fit (then the
+// union sweep serves it).  The union iterate (x, s) is read before and
+// written after.
+bool inst_eligible(Problem& P);
+struct SolveArgs;
+void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms);
+void inst_release(Problem& P);
+// large instances on 2- or 4-CTA clusters (distributed shared memory) or on one
+// CTA with the rows beyond its shared memory in L2 (the default)
+void inst_set_clusters(Problem& P, bool on);
 
 // scd.cu
 struct SolveArgs {
@@ -275,6 +340,8 @@ struct CheckOut {
   double rho, obj, infeas, fbeta;
 };
 void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const float* d_x0);
+// batches with step rule 1: the instances' own L_max (before any capture)
+void batch_step_rule(Problem& P, const SolveArgs& a);
 void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar);
 void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out);
 void refresh_only(Problem& P);
@@ -303,5 +370,7 @@ struct RoundOut {
 };
 void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out);
 void gather_x_orig(Problem& P, float* d_out);
+// exact validity (1 / 0) and objective of a caller's labels (device memory)
+void check_labels(Problem& P, int kind, const uint8_t* d_labels, int& valid, double& obj);
 
 }  // namespace thetis

@@ -318,6 +318,73 @@ __global__ void k_is_near(const float* x, int64_t n, int rep, uint64_t seed, con
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(near, c);
 }
 
+// every label below `limit` (VC / IS / SC membership: 2; MC and MAP: k)
+__global__ void k_label_range(const uint8_t* lab, int64_t n, int limit, int* bad) {
+  GSTRIDE(v, n) if (lab[v] >= limit) atomicExch(bad, 1);
+}
+
+// Exact validity and objective of a caller's integral solution (the checks
+// the roundings end with): VC every edge covered, IS no edge inside the set,
+// MC every label < k with terminal i labelled i, SC every element covered,
+// MAP every label < k; labels outside their range make the solution invalid.
+// The objective is the cover / set weight, the cut cost, the set cost or the
+// MAP energy (-score), in FP64; NaN when a label is out of range.
+void check_labels(Problem& P, int kind, const uint8_t* d_labels, int& valid, double& obj) {
+  cudaStream_t s = P.stream;
+  const bool ok_kind = (kind == THETIS_ROUND_VC && P.kind == KIND_VC) || (kind == THETIS_ROUND_IS && P.kind == KIND_IS) ||
+                       (kind == THETIS_ROUND_MC && P.kind == KIND_MC) ||
+                       ((kind == THETIS_ROUND_SC || kind == THETIS_ROUND_SC_RAND) && P.kind == KIND_SC) ||
+                       (kind == THETIS_ROUND_MAP && P.kind == KIND_MAP);
+  TH_CHECK(ok_kind, THETIS_E_INVALID, "label check: kind does not match the problem");
+  const bool sc = P.kind == KIND_SC;
+  const int64_t n = P.nv, m = P.ne;
+  const int limit = (P.kind == KIND_MC || P.kind == KIND_MAP) ? P.k : 2;
+  Arena tmp(s);
+  int* bad = tmp.alloc<int>(2);  // [0]: range, [1]: validity
+  double* part = tmp.alloc<double>(RB);
+  double* res = tmp.alloc<double>(1);
+  TH_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), s));
+  if (n > 0) {
+    k_label_range<<<grid_for(n, 256), 256, 0, s>>>(d_labels, n, limit, bad);
+    TH_LAUNCHED();
+  }
+  int hb[2] = {0, 0};
+  TH_CUDA(cudaMemcpyAsync(hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  if (hb[0]) {  // the objective kernels index by label: stop here
+    valid = 0;
+    obj = std::nan("");
+    return;
+  }
+  if (P.kind == KIND_VC || P.kind == KIND_IS) {
+    if (m > 0) {
+      k_valid_edges<<<grid_for(m, 256), 256, 0, s>>>(d_labels, P.eu, P.ev, m, P.kind, bad + 1);
+      TH_LAUNCHED();
+    }
+    k_rep_weight<<<dim3(RB, 1), 256, 0, s>>>(d_labels, P.w, n, part);
+  } else if (P.kind == KIND_MC) {
+    k_valid_mc<<<grid_for(n, 256), 256, 0, s>>>(d_labels, n, P.k, P.term, bad + 1);
+    TH_LAUNCHED();
+    k_cut_cost<<<dim3(RB, 1), 256, 0, s>>>(d_labels, P.eu, P.ev, P.ce, m, n, part);
+  } else if (sc) {
+    if (P.M > 0) {
+      k_sc_valid<<<grid_for(P.M, 256), 256, 0, s>>>(d_labels, P.sc_eptr, P.sc_esets, P.M, bad + 1);
+      TH_LAUNCHED();
+    }
+    k_rep_weight<<<dim3(RB, 1), 256, 0, s>>>(d_labels, P.w, n, part);
+  } else {  // MAP: any in-range labelling is feasible
+    k_map_energy<<<RB, 256, 0, s>>>(d_labels, P.map_tn, P.map_te, P.eu, P.ev, n, m, P.k, part);
+  }
+  TH_LAUNCHED();
+  k_rep_final<<<1, 32, 0, s>>>(part, RB, 1, res);
+  TH_LAUNCHED();
+  TH_CUDA(cudaMemcpyAsync(&hb[1], bad + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(&obj, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  TH_CUDA(cudaGetLastError());
+  valid = hb[1] ? 0 : 1;
+}
+
 void round_problem(Problem& P, int kind, uint64_t seed, int reps, uint8_t* d_labels, RoundOut& out) {
   cudaStream_t s = P.stream;
   TH_CHECK(P.kind == KIND_VC || P.kind == KIND_IS || P.kind == KIND_MC || P.kind == KIND_SC || P.kind == KIND_MAP,

@@ -50,6 +50,7 @@ struct StepView {
   const float* sbar; // null: 0
   float beta, inv_beta;
   float lfix;        // > 0: global L_max (step_rule 1)
+  const float* lfix_i;  // batches with step_rule 1: every instance's own L_max (as its solve alone)
   int k;
   int async;         // 1: atomic residual updates
   int blk_shared;    // 1: a simplex block has two columns in one row (its scatter adds atomically)
@@ -74,6 +75,13 @@ __device__ __forceinline__ bool col_frozen(const StepView& V, int64_t j) {
 }
 __device__ __forceinline__ bool row_frozen(const StepView& V, int64_t i) {
   return V.frozen && V.frozen[V.inst_row[i]];
+}
+// step rule 1: the global L_max of column j / slack row i (batches: the instance's own)
+__device__ __forceinline__ float lfix_col(const StepView& V, int64_t j) {
+  return V.lfix_i ? V.lfix_i[V.inst_col[j]] : V.lfix;
+}
+__device__ __forceinline__ float lfix_row(const StepView& V, int64_t i) {
+  return V.lfix_i ? V.lfix_i[V.inst_row[i]] : V.lfix;
 }
 
 struct SegLaunch {
@@ -181,7 +189,7 @@ __device__ __forceinline__ void step_column(const StepView& V, int64_t j, int la
   }
   const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
   const float sq = V.val ? V.csq[j] : (float)(p1 - p0);
-  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, sq, V.inv_beta);
+  const float L = (V.lfix > 0.f) ? lfix_col(V, j) : fmaf(V.beta, sq, V.inv_beta);
   const float lo = V.lo ? V.lo[j] : V.lo_u;
   const float hi = V.hi ? V.hi[j] : V.hi_u;
   const float xn = fminf(fmaxf(xj - g / L, lo), hi);
@@ -243,7 +251,7 @@ __device__ __forceinline__ void step_ell(const StepView& V, int64_t e0, int64_t 
   }
   if (!valid) return;
   const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
-  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, V.ellv ? V.csq[j] : sq, V.inv_beta);
+  const float L = (V.lfix > 0.f) ? lfix_col(V, j) : fmaf(V.beta, V.ellv ? V.csq[j] : sq, V.inv_beta);
   const float lo = V.lo ? V.lo[j] : V.lo_u;
   const float hi = V.hi ? V.hi[j] : V.hi_u;
   const float xn = fminf(fmaxf(xj - g / L, lo), hi);
@@ -348,7 +356,7 @@ __device__ __forceinline__ void step_huge(const StepView& V, int64_t j, float* r
   __syncthreads();
   acc = red_smem[32];
   const float g = ctj + V.beta * acc + (xj - xb) * V.inv_beta;
-  const float L = (V.lfix > 0.f) ? V.lfix : fmaf(V.beta, (float)n, V.inv_beta);
+  const float L = (V.lfix > 0.f) ? lfix_col(V, j) : fmaf(V.beta, (float)n, V.inv_beta);
   const float lo = V.lo ? V.lo[j] : V.lo_u;
   const float hi = V.hi ? V.hi[j] : V.hi_u;
   const float xn = fminf(fmaxf(xj - g / L, lo), hi);
@@ -467,12 +475,13 @@ __device__ __forceinline__ void step_slacks(const StepView& V, int64_t i0, int64
     sv[t] = on[t] ? __ldcg(V.s + i0 + q) : 0.f;
     rv[t] = on[t] ? __ldcg(V.r + i0 + q) : 0.f;
   }
-  const float L = (V.lfix > 0.f) ? V.lfix : V.beta + V.inv_beta;
+  const float L0 = (V.lfix > 0.f) ? V.lfix : V.beta + V.inv_beta;
 #pragma unroll
   for (int t = 0; t < SLACK_ROWS; ++t) {
     int64_t q = (int64_t)t * STEP_T + threadIdx.x;
     if (!on[t]) continue;
     const int64_t i = i0 + q;
+    const float L = (V.lfix > 0.f && V.lfix_i) ? lfix_row(V, i) : L0;
     const float sg = V.sig_u ? (float)V.sig_u : (float)V.sig[i];
     const float sb = V.sbar ? V.sbar[i] : 0.f;
     const float lin = V.cs ? V.cs[i] : 0.f;
@@ -701,25 +710,32 @@ __global__ void __launch_bounds__(STEP_T, 4) k_color_step(StepView V, ColorLaunc
 // Grid-wide barrier of a cooperative launch, split into arrive and wait so a CTA
 // can prefetch the next colour while the others finish.  One 32-bit word: CTA 0
 // adds 2^31 - (G - 1), every other CTA adds 1, so the top bit flips exactly once
-// per barrier.  The wait is bounded: after ~2 s (clock64) the CTA records
-// err = 1 and the launch gives up (the host reports THETIS_E_TIMEOUT).
-constexpr long long BARRIER_LIMIT_CYCLES = 4000000000LL;
-
-__device__ __forceinline__ unsigned bar_arrive(unsigned* bar, unsigned participants = 0) {
-  const unsigned n = participants ? participants : gridDim.x;  // CTAs 0 .. n-1 take part
+// per barrier.  The wait is bounded in time (%globaltimer, nanoseconds; 2 s by
+// default, set per handle): after the limit the CTA records err = 1 and the
+// launch gives up (the host reports THETIS_E_TIMEOUT).  `phantom` adds CTAs
+// that never arrive (a test of the timeout path: the wait then always runs
+// out).
+__device__ __forceinline__ unsigned bar_arrive(unsigned* bar, unsigned participants = 0, unsigned phantom = 0) {
+  const unsigned n = (participants ? participants : gridDim.x) + phantom;  // CTAs 0 .. n-1 take part
   unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (n - 1)) : 1u;
   unsigned old;
   asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(inc) : "memory");
   return old;
 }
 
-__device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned old, int* err) {
-  const long long t0 = clock64();
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool bar_wait(unsigned* bar, unsigned old, int* err, long long limit_ns) {
+  const unsigned long long t0 = global_ns();
   unsigned it = 0, cur;
   while (true) {
     asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
     if ((cur ^ old) & 0x80000000u) return true;
-    if ((++it & 255u) == 0 && (*(volatile int*)err || clock64() - t0 > BARRIER_LIMIT_CYCLES)) {
+    if ((++it & 255u) == 0 && (*(volatile int*)err || (long long)(global_ns() - t0) > limit_ns)) {
       atomicExch(err, 1);
       return false;
     }
@@ -792,7 +808,8 @@ constexpr int PREFETCH_TILES = 2;
 
 template <bool FULL>
 __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, const ColorLaunch* plan, const int64_t* ntiles,
-                                                     int ncolors, int epochs, unsigned* bar, int* err, TailView TV) {
+                                                     int ncolors, int epochs, unsigned* bar, int* err, TailView TV,
+                                                     long long wait_ns, unsigned phantom) {
   __shared__ float red_smem[33];
   __shared__ ColorLaunch cl[2];
   __shared__ int ok;
@@ -811,7 +828,7 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
   auto advance = [&](int cn) -> bool {
     __syncthreads();
     unsigned old = 0;
-    if (threadIdx.x == 0) old = bar_arrive(bar);
+    if (threadIdx.x == 0) old = bar_arrive(bar, 0, phantom);
     if (threadIdx.x < CLW) ((unsigned*)&cl[cur ^ 1])[threadIdx.x] = ((const unsigned*)&plan[cn])[threadIdx.x];
     __syncthreads();
     const int64_t ntn = count_of(cn);
@@ -832,7 +849,7 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
       const int64_t qq = blockIdx.x + (int64_t)q * gridDim.x;
       if (qq < ntn) prefetch_tile(V, cl[cur ^ 1].seg, cl[cur ^ 1].nseg, tile_of(cn, qq));
     }
-    if (threadIdx.x == 0) ok = bar_wait(bar, old, err) ? 1 : 0;
+    if (threadIdx.x == 0) ok = bar_wait(bar, old, err, wait_ns) ? 1 : 0;
     __syncthreads();
     cur ^= 1;
     first_staged = staged;
@@ -842,8 +859,8 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
   auto sync = [&]() -> bool {
     __syncthreads();
     if (threadIdx.x == 0) {
-      const unsigned old = bar_arrive(bar);
-      ok = bar_wait(bar, old, err) ? 1 : 0;
+      const unsigned old = bar_arrive(bar, 0, phantom);
+      ok = bar_wait(bar, old, err, wait_ns) ? 1 : 0;
     }
     __syncthreads();
     return ok != 0;
@@ -874,8 +891,8 @@ __global__ void __launch_bounds__(STEP_T, FULL ? 4 : 6) k_sweep(StepView V, cons
           if (tc + 1 < TV.ncol) {
             __syncthreads();
             if (threadIdx.x == 0) {
-              const unsigned old = bar_arrive(bar + 32, (unsigned)nT);
-              ok = bar_wait(bar + 32, old, err) ? 1 : 0;
+              const unsigned old = bar_arrive(bar + 32, (unsigned)nT, phantom);
+              ok = bar_wait(bar + 32, old, err, wait_ns) ? 1 : 0;
             }
             __syncthreads();
             if (!ok) return;
@@ -903,6 +920,25 @@ static int64_t ctas_for(int cls, int64_t n, int small_g) {
   }
 }
 
+__global__ void k_batch_lfix(const int32_t* maxdeg, const int64_t* eoff, int64_t count, double beta, float* lfix) {
+  GSTRIDE(t, count) {
+    const int lm = max(maxdeg[t], eoff[t + 1] > eoff[t] ? 1 : 0);
+    lfix[t] = (float)(beta * (double)lm + 1.0 / beta);
+  }
+}
+
+// batches with step rule 1: every instance's own L_max = beta * max(longest
+// column, 1 if it has rows) + 1/beta, as its solve alone takes (before any
+// stream capture of an epoch)
+void batch_step_rule(Problem& P, const SolveArgs& a) {
+  if (a.step_rule != 1 || P.nbatch == 0 || !P.bmaxdeg) return;
+  if (!P.blfix) P.blfix = P.mem.alloc<float>(P.nbatch);
+  if (P.blfix_beta == a.beta) return;
+  k_batch_lfix<<<grid_for(P.nbatch, 256), 256, 0, P.stream>>>(P.bmaxdeg, P.beoff, P.nbatch, a.beta, P.blfix);
+  TH_LAUNCHED();
+  P.blfix_beta = a.beta;
+}
+
 static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar) {
   StepView V;
   V.colptr = P.colptr;
@@ -925,6 +961,7 @@ static StepView make_view(Problem& P, const SolveArgs& a, bool use_ubar, bool us
   V.beta = (float)a.beta;
   V.inv_beta = (float)(1.0 / a.beta);
   V.lfix = (a.step_rule == 1) ? (float)(a.beta * P.lmax_sq + 1.0 / a.beta) : 0.f;
+  V.lfix_i = (a.step_rule == 1 && P.nbatch > 0 && P.blfix && P.blfix_beta == a.beta) ? P.blfix : nullptr;
   V.k = P.k;
   V.async = (a.mode == THETIS_MODE_ASYNC) ? 1 : 0;
   V.blk_shared = P.blk_shared ? 1 : 0;
@@ -1347,8 +1384,10 @@ void run_sweep(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, int
   const int64_t* nt = P.d_ntiles;
   int C = head_colours(P);
   TailView TV = make_tail_view(P);
-  void* args[] = {(void*)&V,      (void*)&plan,  (void*)&nt,    (void*)&C,
-                  (void*)&epochs, (void*)&P.bar, (void*)&P.err, (void*)&TV};
+  long long wait_ns = P.wait_ns;
+  unsigned phantom = P.wait_phantom;
+  void* args[] = {(void*)&V,      (void*)&plan,  (void*)&nt,    (void*)&C,       (void*)&epochs,
+                  (void*)&P.bar, (void*)&P.err, (void*)&TV,    (void*)&wait_ns, (void*)&phantom};
   if (sweep_lean(P))
     TH_CUDA(cudaLaunchCooperativeKernel((const void*)k_sweep<false>, dim3(grid), dim3(STEP_T), args, 0, P.stream));
   else

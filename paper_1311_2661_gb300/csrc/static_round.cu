@@ -2,12 +2,13 @@
 //
 // Some callers cannot allocate device memory at the moment they need a
 // rounding: a serving loop that must never block on cudaMalloc / cudaFree
-// (both can synchronise the whole device), a process whose memory pool has
-// already handed every free byte to another framework's caching allocator, or
-// code that is recording work into a CUDA stream capture, where a plain
-// cudaMalloc is not allowed.  thetis_round_is_static serves them: it runs the
-// same kernels as the independent-set branch of thetis_round, but every byte of
-// scratch comes from one file-scope device array of fixed size.
+// (both can synchronise the whole device), or a process whose memory pool has
+// already handed every free byte to another framework's caching allocator.
+// thetis_round_is_static serves them: it runs the same kernels as the
+// independent-set branch of thetis_round, but every byte of scratch comes from
+// one file-scope device array of fixed size.  It still synchronises the
+// caller's stream (up to three times) and copies a few words to the host (the
+// endpoint check, the best repetition and the info), like thetis_round.
 #include <cstring>
 #include <mutex>
 
@@ -27,6 +28,8 @@ __global__ void k_rep_final(const double* part, int nb, int reps, double* out);
 __global__ void k_valid_edges(const uint8_t* lab, const int32_t* eu, const int32_t* ev, int64_t m, int kind, int* bad);
 __global__ void k_is_near(const float* x, int64_t n, int rep, uint64_t seed, const unsigned long long* alpha_bits,
                           unsigned long long* near);
+// (build.cu) sets *err when an endpoint is outside [0, n) or an edge is a loop
+__global__ void k_check_edges(const int32_t* eu, const int32_t* ev, int64_t m, int64_t n, int* err);
 
 namespace {
 
@@ -62,6 +65,21 @@ void* scratch_on_current_device() {
   return g_addr[dev];
 }
 
+// The arrays must be device memory of the current device (or managed
+// memory): the kernels dereference them directly.
+void check_device_pointer(const void* p, const char* what) {
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error{THETIS_E_INVALID, std::string("thetis_round_is_static: ") + what + " is not a CUDA pointer"};
+  }
+  int dev = 0;
+  TH_CUDA(cudaGetDevice(&dev));
+  TH_CHECK((a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged, THETIS_E_INVALID,
+           std::string("thetis_round_is_static: ") + what + " must be device memory of the current device");
+}
+
 }  // namespace
 }  // namespace thetis
 
@@ -76,13 +94,21 @@ extern "C" thetis_status thetis_round_is_static(int64_t n, int64_t m, const int3
              "need 1 <= n < 2^31 and 0 <= m < 2^31");
     TH_CHECK(reps >= 1 && reps <= S_MAX_REPS, THETIS_E_INVALID, "reps must be in [1, 64]");
     TH_CHECK(w && x && labels_out && (m == 0 || (eu && ev)), THETIS_E_INVALID, "null array argument");
+    check_device_pointer(w, "w");
+    check_device_pointer(x, "x");
+    check_device_pointer(labels_out, "labels_out");
+    if (m > 0) {
+      check_device_pointer(eu, "eu");
+      check_device_pointer(ev, "ev");
+    }
     const size_t need = S_HEADER + 2 * (size_t)n * (size_t)reps;
     TH_CHECK(need <= S_BYTES, THETIS_E_INVALID,
              "thetis_round_is_static: n * reps = " + std::to_string((long long)n * reps) +
                  " exceeds the static scratch limit (2 * n * reps + " + std::to_string(S_HEADER) +
                  " bytes must fit in 64 MiB, i.e. n * reps <= " + std::to_string((S_BYTES - S_HEADER) / 2) + ")");
     unsigned char* base = (unsigned char*)scratch_on_current_device();
-    unsigned long long* dbits = (unsigned long long*)base;  // [violation bits, near, -, bad]
+    unsigned long long* dbits = (unsigned long long*)base;  // [violation bits, near, edge error, bad]
+    int* edge_err = (int*)(dbits + 2);
     int* bad = (int*)(dbits + 3);
     double* part = (double*)(base + 4 * sizeof(unsigned long long));
     double* repv = part + (size_t)S_RB * S_MAX_REPS;
@@ -91,6 +117,13 @@ extern "C" thetis_status thetis_round_is_static(int64_t n, int64_t m, const int3
     // the scratch keeps the previous call's contents: clear what must start at zero
     TH_CUDA(cudaMemsetAsync(dbits, 0, 4 * sizeof(unsigned long long), s));
     if (m > 0) {
+      // every endpoint in [0, n) before any kernel indexes x, keep or labels by it
+      k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(eu, ev, m, n, edge_err);
+      TH_LAUNCHED();
+      int herr = 0;
+      TH_CUDA(cudaMemcpyAsync(&herr, edge_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TH_CUDA(cudaStreamSynchronize(s));
+      TH_CHECK(herr == 0, THETIS_E_INVALID, "thetis_round_is_static: edge endpoint outside [0, n), or a loop");
       k_edge_violation<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(x, eu, ev, m, 0, dbits);
       TH_LAUNCHED();
     }

@@ -88,6 +88,10 @@ def _load():
         "thetis_sync": (st, [P]),
         "thetis_destroy": (st, [P]),
         "thetis_round_is_static": (st, [i64, i64, P, P, P, P, u64, i32, P, P, P]),
+        "thetis_check_labels": (st, [P, i32, P, i32, P, P]),
+        "thetis_set_wait_limit": (st, [P, C.c_double, i32]),
+        "thetis_batch_latency": (st, [P, P]),
+        "thetis_set_batch_shape": (st, [P, i32, i32]),
         "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
         "thetis_autotune": (st, [P, P, i32, P, P]),
         "thetis_set_launch_shape": (st, [P, i32, i32]),
@@ -221,10 +225,15 @@ class Handle:
     def duals(self):
         return thetis_get_duals(self)
 
+    @property
+    def round_kind(self):
+        return {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC, "sc": ROUND_SC, "map": ROUND_MAP}[self.kind]
+
     def round(self, kind=None, **kw):
-        if kind is None:
-            kind = {"vc": ROUND_VC, "is": ROUND_IS, "mc": ROUND_MC, "sc": ROUND_SC, "map": ROUND_MAP}[self.kind]
-        return thetis_round(self, kind, **kw)
+        return thetis_round(self, self.round_kind if kind is None else kind, **kw)
+
+    def check_labels(self, labels, kind=None):
+        return thetis_check_labels(self, labels, kind)
 
     def get_x(self, out=None):
         return thetis_get_x(self, out)
@@ -553,17 +562,58 @@ def thetis_batch_info(h: Handle):
     return ep, rho
 
 
+def thetis_set_wait_limit(h: Handle, limit_ms=2000.0, missing_ctas=0):
+    """Time limit of the persistent sweep's bounded waits; missing_ctas > 0 makes
+    them wait for CTAs that never arrive (tests the THETIS_E_TIMEOUT path)."""
+    _check(_lib.thetis_set_wait_limit(h.ptr, float(limit_ms), int(missing_ctas)))
+
+
+def thetis_check_labels(h: Handle, labels, kind=None):
+    """Exact validity and objective of a caller's integral solution: returns
+    (valid, obj).  kind defaults to the handle's own rounding kind."""
+    A = _Args()
+    ptr = A(labels, np.uint8)
+    valid, obj = C.c_int32(), C.c_double()
+    k = h.round_kind if kind is None else kind
+    _check(_lib.thetis_check_labels(h.ptr, int(k), ptr, A.memspace, C.byref(valid), C.byref(obj)))
+    return bool(valid.value), float(obj.value)
+
+
+def thetis_set_batch_shape(h: Handle, lanes_per_column=1, clusters=0):
+    """Launch shape of the instance-resident batch engine (see include/thetis.h)."""
+    _check(_lib.thetis_set_batch_shape(h.ptr, int(lanes_per_column), int(clusters)))
+
+
+def thetis_batch_latency(h: Handle):
+    """Per instance: ms from the start of the last solve until its result was final."""
+    out = np.zeros(h.count, np.float64)
+    _check(_lib.thetis_batch_latency(h.ptr, out.ctypes.data))
+    return out
+
+
 def thetis_round_is_static(n, eu, ev, w, x, labels_out, seed=0, reps=10, stream=None):
     """Independent-set rounding with no device allocation (scratch is a fixed
-    64 MiB static device array).  eu, ev, w, x and labels_out are CUDA tensors;
-    returns the info dict.  Requires n * reps <= 33,488,624."""
-    A = _Args()
-    ptrs = [A(eu, np.int32), A(ev, np.int32), A(w, np.float32), A(x, np.float32)]
-    lab_ptr = A(labels_out, np.uint8)
-    if A.memspace != MEM_DEVICE:
-        raise ValueError("thetis_round_is_static takes device arrays only")
+    64 MiB static device array).  eu, ev (int32), w, x (float32) and labels_out
+    (uint8) must already be contiguous CUDA tensors of those types: nothing is
+    converted or copied here, so the call allocates nothing and the labels land
+    in labels_out itself.  Returns the info dict.  Requires n * reps <=
+    33,488,624."""
+    import torch
+
+    want = ((eu, torch.int32, "eu"), (ev, torch.int32, "ev"), (w, torch.float32, "w"),
+            (x, torch.float32, "x"), (labels_out, torch.uint8, "labels_out"))
+    for t, dt, name in want:
+        if not (_is_torch(t) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"thetis_round_is_static: {name} must be a contiguous CUDA tensor of {dt}")
+    n = int(n)
+    if eu.shape != ev.shape or eu.dim() != 1:
+        raise ValueError("thetis_round_is_static: eu and ev must be 1-D of the same length")
+    for t, name in ((w, "w"), (x, "x"), (labels_out, "labels_out")):
+        if t.numel() < n:
+            raise ValueError(f"thetis_round_is_static: {name} holds fewer than n = {n} elements")
     info = RoundInfo()
-    st = _lib.thetis_round_is_static(int(n), int(eu.shape[0]), *ptrs, int(seed), int(reps), lab_ptr,
+    st = _lib.thetis_round_is_static(n, int(eu.shape[0]), eu.data_ptr(), ev.data_ptr(), w.data_ptr(),
+                                     x.data_ptr(), int(seed), int(reps), labels_out.data_ptr(),
                                      C.byref(info), _stream_ptr(stream))
     _check(st)
     return dict(status=st, obj=info.obj, repair=info.repair, best_rep=info.best_rep, near=info.near,

@@ -1,6 +1,8 @@
 """Batched solves (thetis_build_batch): every instance of a block-diagonal batch
 is coloured, swept and rounded as it would be alone -- checked against the
-single-instance GPU path and against the FP64 oracle instance by instance."""
+single-instance GPU path and against the FP64 oracle instance by instance.
+Engine 0 (the default) is the instance-resident engine (one CTA or cluster per
+instance); engines 1 and 2 sweep the whole block-diagonal LP."""
 import numpy as np
 import pytest
 
@@ -9,6 +11,11 @@ from paper_1311_2661_gb300 import synth
 from tests.gpu_common import OBJ_RTOL, X_TOL, gpu, rel
 
 pytestmark = pytest.mark.gpu
+
+# rho of one instance in a batch against its solve alone: the two sum every
+# column's dot product in a different FP32 order, so their iterates differ at
+# FP32 rounding level and rho (an FP64 function of the iterate) by ~1e-8
+RHO_ATOL = 1e-7
 
 
 def _batch(count=24, seed=3, nmax=600):
@@ -48,7 +55,7 @@ def test_batch_colouring_equals_alone_and_oracle():
         assert np.array_equal(mine, h.colors()), t
 
 
-@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("engine", [0, 1, 2])
 def test_batch_iterates_and_rounding_match_oracle(engine):
     T = gpu()
     items = _batch(seed=4)
@@ -122,7 +129,9 @@ def test_batch_instances_stop_where_alone_stops():
         h = b(g.n, g.eu, g.ev, g.w, seed=3)
         ia = h.solve(beta=100.0, epochs=3000, tol=1e-3, refresh_every=10)
         assert ia["epochs_run"] == ep[t], t
-        assert abs(ia["rho"] - rho[t]) <= 1e-9 + 1e-6 * rho[t], t
+        # the batch sums each column's dot in another FP32 order than the solve
+        # alone: the iterates agree to FP32 rounding, rho to ~1e-7
+        assert abs(ia["rho"] - rho[t]) <= RHO_ATOL, t
         xa = np.concatenate([h.get_x(), h.get_slack()]).astype(np.float64)
         mine = np.concatenate([x[noff[t]:noff[t + 1]], s[eoff[t]:eoff[t + 1]]])
         assert np.max(np.abs(mine - xa)) <= X_TOL, t
@@ -132,3 +141,98 @@ def test_batch_instances_stop_where_alone_stops():
         x_o, _ = lp.solve(beta=100.0, epochs=int(ep[t]), refresh_every=10, color=col)
         assert np.max(np.abs(mine - x_o)) <= X_TOL, t
         assert lp.checks(mine, 100.0)["rho"] <= 1e-3 + 1e-6
+
+
+def _sized_items(sizes, seed):
+    """One ER instance per (kind, n, m), weights U[1, 10]."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for kind, n, m in sizes:
+        g = synth.er_graph(n, m, int(rng.integers(1 << 30)))
+        g.w = synth.int_weights(n, 1, 10, rng)
+        items.append((kind, g))
+    return items
+
+
+# one instance per launch class of the instance-resident engine: r and x of
+# 4 (n + m) bytes fit one CTA of 256, 512 or 1024 threads, or span a cluster
+# of 2 or 4 CTAs (distributed shared memory), or (without clusters) one CTA
+# keeps x and part of r in global memory
+CLASS_SIZES = [("vc", 300, 1000), ("is", 3000, 20000), ("vc", 8000, 40000), ("is", 15000, 70000),
+               ("vc", 20000, 150000), ("is", 19000, 140000)]
+
+
+@pytest.mark.parametrize("step_rule,lanes,clusters", [(0, 1, 0), (1, 1, 0), (0, 1, 1), (1, 8, 1), (0, 4, 0)])
+def test_instance_engine_every_launch_class_matches_oracle(step_rule, lanes, clusters):
+    T = gpu()
+    items = _sized_items(CLASS_SIZES, 31)
+    hb = T.thetis_build_batch_graphs(items, seed=6, device=True)
+    T.thetis_set_batch_shape(hb, lanes, clusters)
+    info = hb.solve(beta=100.0, epochs=30, refresh_every=10, step_rule=step_rule)
+    assert info["epochs_run"] == 30
+    x = hb.get_x().astype(np.float64)
+    s = hb.get_slack().astype(np.float64)
+    noff, eoff = _slices(items)
+    for t, (kind, g) in enumerate(items):
+        lp = oracle.build_problem(kind, g)
+        x_o, info_o = lp.solve(beta=100.0, epochs=30, refresh_every=10, step_rule=step_rule, color=lp.color(6)[0])
+        mine = np.concatenate([x[noff[t]:noff[t + 1]], s[eoff[t]:eoff[t + 1]]])
+        assert np.max(np.abs(mine - x_o)) <= X_TOL, t
+        assert rel(lp.checks(mine, 100.0)["fbeta"], info_o["fbeta"]) <= OBJ_RTOL, t
+    # the union sweep on the same batch agrees with it to tolerance
+    hu = T.thetis_build_batch_graphs(items, seed=6, device=True)
+    hu.solve(beta=100.0, epochs=30, refresh_every=10, step_rule=step_rule, engine=2)
+    assert np.max(np.abs(hu.get_x() - hb.get_x())) <= X_TOL
+
+
+@pytest.mark.parametrize("clusters", [0, 1])
+def test_instance_engine_classes_stop_where_alone_stops(clusters):
+    T = gpu()
+    items = _sized_items(CLASS_SIZES, 32)
+    hb = T.thetis_build_batch_graphs(items, seed=1)
+    T.thetis_set_batch_shape(hb, 1, clusters)
+    info = hb.solve(beta=100.0, epochs=3000, tol=1e-3, refresh_every=20)
+    ep, rho = T.thetis_batch_info(hb)
+    done = T.thetis_batch_latency(hb)
+    assert info["converged"] and np.all(rho <= 1e-3)
+    assert np.all(done > 0) and np.all(done <= info["solve_ms"] + 1e-6)
+    x, s = hb.get_x().astype(np.float64), hb.get_slack().astype(np.float64)
+    noff, eoff = _slices(items)
+    for t, (kind, g) in enumerate(items):
+        b = T.thetis_build_vc if kind == "vc" else T.thetis_build_is
+        h = b(g.n, g.eu, g.ev, g.w, seed=1)
+        ia = h.solve(beta=100.0, epochs=3000, tol=1e-3, refresh_every=20)
+        assert ia["epochs_run"] == ep[t], t
+        assert abs(ia["rho"] - rho[t]) <= RHO_ATOL, t
+        xa = np.concatenate([h.get_x(), h.get_slack()]).astype(np.float64)
+        mine = np.concatenate([x[noff[t]:noff[t + 1]], s[eoff[t]:eoff[t + 1]]])
+        assert np.max(np.abs(mine - xa)) <= X_TOL, t
+
+
+def test_batched_workload_shape_parity_sample():
+    """The batched benchmark's distribution (ER, n ~ U[200, 20000], average
+    degree ~ U[4, 16], half VC half IS), 256 instances solved to rho <= 1e-3:
+    every instance's rho checked by the oracle at the GPU iterate, and a seeded
+    sample of 8 compared with the oracle's own solve element by element."""
+    T = gpu()
+    items = synth.batch_instances(256, 200, 20000, 4.0, 16.0, 1, 10, 77)
+    hb = T.thetis_build_batch_graphs(items, seed=0, device=True)
+    info = hb.solve(beta=100.0, epochs=4000, tol=1e-3, refresh_every=20)
+    ep, rho = T.thetis_batch_info(hb)
+    assert info["converged"] and np.all(rho <= 1e-3)
+    x, s = hb.get_x().astype(np.float64), hb.get_slack().astype(np.float64)
+    lab, obj, status, best = T.thetis_round_batch(hb, seed=4, reps=10)
+    assert np.all(status == 1)
+    noff, eoff = _slices(items)
+    sample = set(np.random.default_rng(5).choice(len(items), 8, replace=False).tolist())
+    for t, (kind, g) in enumerate(items):
+        lp = oracle.build_problem(kind, g)
+        mine = np.concatenate([x[noff[t]:noff[t + 1]], s[eoff[t]:eoff[t + 1]]])
+        chk = lp.checks(mine, 100.0)
+        assert chk["rho"] <= 1e-3 + 1e-9, t
+        assert abs(chk["rho"] - rho[t]) <= 1e-9 + 1e-6 * rho[t], t
+        assert lp.valid(lab[noff[t]:noff[t + 1]]), t
+        if t in sample:
+            x_o, info_o = lp.solve(beta=100.0, epochs=int(ep[t]), refresh_every=20, color=lp.color(0)[0])
+            assert np.max(np.abs(mine - x_o)) <= X_TOL, t
+            assert info_o["rho"] <= 1e-3 + 1e-6, t

@@ -173,41 +173,85 @@ def test_rounding_bit_exact_on_same_x(kind, mk):
 
 
 @pytest.mark.parametrize("kind,mk", [("vc", lambda: vc_graph(2000, 8000, 1)), ("is", lambda: is_graph(3000, 20000, 2)),
-                                     ("mc", lambda: synth.grid_graph(37, 23, 4, 4))])
+                                     ("mc", lambda: synth.grid_graph(37, 23, 4, 4)),
+                                     ("mc", lambda: synth.grid_graph(64, 48, 8, 9))])
 def test_rounding_end_to_end_outside_band(kind, mk):
-    """GPU solve + round vs oracle solve + round: equal labels except where a
-    decision is within 1e-4 of its threshold."""
+    """GPU solve + round vs oracle solve + round, compared element by element on
+    every vertex whose decision no draw within the band of its threshold can
+    change.  The band is 1e-4, widened to twice the largest difference of the
+    repaired points x~ of the two sides.  IS (App. B.2): a vertex's final label
+    depends on its own pick and its neighbours' (alteration), so the vertices
+    near the band and their neighbours are masked, in the repetition the GPU
+    chose; MC (App. B.3): a vertex's label depends on its own row only.  The
+    GPU's choice of repetition must be the oracle's best up to the weight / cut
+    cost the masked decisions can move."""
     g = mk()
     h, lp = _pair(kind, g)
     h.solve(beta=100.0, epochs=50)
-    lab, info = h.round(seed=5, reps=10)
+    reps, seed = 10, 5
+    lab, info = h.round(seed=seed, reps=reps)
     x_o, _ = lp.solve(beta=100.0, epochs=50, color=lp.color(0)[0])
+    x_g = h.get_x().astype(np.float64)
     n = g.n
+    assert info["valid"] and lp.valid(lab)
     if kind == "vc":
         r = lp.round_vc(x_o[:n])
         xt = np.minimum(1, x_o[:n] / (1 - r["eps"]))
-        near = np.abs(xt - 0.5) < 1e-4
+        xt_g = np.minimum(1, x_g[:n] / (1 - info["repair"]))
+        band = max(1e-4, 2 * float(np.max(np.abs(xt - xt_g))))
+        near = np.abs(xt - 0.5) < band
         assert np.array_equal(lab[~near], r["labels"][~near])
-    elif kind == "is":
-        r = lp.round_is(x_o[:n], 5, 10)
+        assert near.mean() < 0.05
+        return
+    if kind == "is":
+        r = lp.round_is(x_o[:n], seed, reps)
         xt = x_o[:n] / (1 + r["alpha"])
-        near = np.zeros(n, bool)
-        for q in range(10):
-            u = np.array([oracle.rng_uniform(5, q, 1, v) for v in range(n)])
-            near |= np.abs(u - xt) < 1e-4
-        if not near.any():
-            assert np.array_equal(lab, r["labels"])
-    else:
-        k = len(g.terminals)
-        r = lp.round_mc(x_o[: n * k], 5, 10)
-        X = x_o[: n * k].reshape(n, k)
-        near = np.zeros(n, bool)
-        for q in range(10):
-            rad = oracle.rng_uniform(5, q, 2, 0)
-            near |= np.any(np.abs(X - (1 - rad)) < 1e-4, axis=1)
-        if not near.any():
-            assert np.array_equal(lab, r["labels"])
-    assert info["valid"] and lp.valid(lab)
+        xt_g = x_g[:n] / (1 + info["repair"])
+        band = max(1e-4, 2 * float(np.max(np.abs(xt - xt_g))))
+        nbr = [[] for _ in range(n)]
+        for a, b in zip(g.eu.tolist(), g.ev.tolist()):
+            nbr[a].append(b)
+            nbr[b].append(a)
+        w = g.w.astype(np.float64)
+        wq, mq, lq = [], [], []
+        for q in range(reps):
+            u = np.array([oracle.rng_uniform(seed, q, 1, v) for v in range(n)])
+            near = np.abs(u - xt) < band
+            mask = near.copy()
+            for v in np.nonzero(near)[0]:
+                mask[nbr[v]] = True
+            l_q = lp.round_is_rep(xt, seed, q)
+            lq.append(l_q)
+            wq.append(float(w @ l_q))
+            mq.append(float(w[mask].sum()))
+            if q == info["best_rep"]:
+                b_mask = mask
+        b = info["best_rep"]
+        assert b_mask.mean() < 0.2
+        assert np.array_equal(lab[~b_mask], lq[b][~b_mask])
+        assert wq[b] + mq[b] >= max(wq[q] - mq[q] for q in range(reps))
+        if b == r["best_rep"]:
+            assert np.array_equal(lq[b], r["labels"])
+        return
+    k = len(g.terminals)
+    r = lp.round_mc(x_o[: n * k], seed, reps)
+    X = x_o[: n * k].reshape(n, k)
+    Xg = x_g[: n * k].reshape(n, k)
+    band = max(1e-4, 2 * float(np.max(np.abs(X - Xg))))
+    ce = g.ce.astype(np.float64)
+    cq, sq = [], []
+    for q in range(reps):
+        rad = oracle.rng_uniform(seed, q, 2, 0)
+        near = np.any(np.abs(X - (1 - rad)) < band, axis=1)
+        l_q = lp.round_mc_rep(x_o[: n * k], seed, q)
+        cq.append(lp.mc_cut_cost(l_q))
+        sq.append(float(ce[near[g.eu] | near[g.ev]].sum()))
+        if q == info["best_rep"]:
+            b_near, b_lab = near, l_q
+    b = info["best_rep"]
+    assert b_near.mean() < 0.2
+    assert np.array_equal(lab[~b_near], b_lab[~b_near])
+    assert cq[b] - sq[b] <= min(cq[q] + sq[q] for q in range(reps))
 
 
 def test_vc_repair_error():
