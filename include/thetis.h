@@ -445,6 +445,23 @@ thetis_status thetis_build_batch(int32_t count, const uint8_t* kinds, const int6
 thetis_status thetis_batch_info(const thetis_handle* h, int32_t* epochs_out, double* rho_out);
 
 /*
+ * thetis_solve_round_batch -- thetis_solve followed by the repair, rounding
+ * and exact validity of every instance, with the results of
+ * thetis_round_batch (same random streams, same FP64 decisions: VC threshold
+ * after the eps repair of Sec. 2; IS best of `reps` after the alpha repair of
+ * App. C.3, Algorithm 2 of App. B.2).  With the instance-resident engine
+ * every instance is rounded by its own CTA / cluster the moment it stops, so
+ * its result is final then (thetis_batch_latency); other engines round the
+ * whole batch after the solve.  Arguments as thetis_solve and
+ * thetis_round_batch (labels_out[sum n_t] in out_mem; obj_out, status_out,
+ * best_rep_out[count] HOST, each may be NULL; info may be NULL).  Returns the
+ * solve's status (THETIS_OK / THETIS_NOT_CONVERGED) or an error.
+ */
+thetis_status thetis_solve_round_batch(thetis_handle* h, const thetis_params* p, uint64_t seed, int32_t reps,
+                                       uint8_t* labels_out, int32_t out_mem, double* obj_out, int32_t* status_out,
+                                       int32_t* best_rep_out, thetis_solve_info* info);
+
+/*
  * thetis_batch_latency -- per instance, the device time in ms from the start of
  * the last thetis_solve of a batch handle until the instance's result was
  * final: with the instance-resident engine, when its CTA / cluster finished

@@ -1034,6 +1034,50 @@ thetis_status thetis_batch_latency(const thetis_handle* h, double* done_ms_out) 
   return THETIS_OK;
 }
 
+thetis_status thetis_solve_round_batch(thetis_handle* h, const thetis_params* p, uint64_t seed, int32_t reps,
+                                       uint8_t* labels_out, int32_t out_mem, double* obj_out, int32_t* status_out,
+                                       int32_t* best_rep_out, thetis_solve_info* info) {
+  if (!h || !h->P || !p || !labels_out) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  Problem& P = *h->P;
+  if (P.kind != KIND_BATCH || reps < 1 || reps > 64 || (out_mem != THETIS_MEM_HOST && out_mem != THETIS_MEM_DEVICE)) {
+    set_error("thetis_solve_round_batch needs a batch handle, 1 <= reps <= 64 and a valid out_mem");
+    return THETIS_E_INVALID;
+  }
+  // the instance kernels round every instance as it stops; other engines
+  // solve, then round the batch as thetis_round_batch
+  P.iround_on = true;
+  P.iround_done = false;
+  P.iround_seed = seed;
+  P.iround_reps = reps;
+  const thetis_status st = thetis_solve(h, p, info);
+  P.iround_on = false;
+  if (st != THETIS_OK && st != THETIS_NOT_CONVERGED) return st;
+  if (!P.iround_done) {
+    const thetis_status rs = thetis_round_batch(h, seed, reps, labels_out, out_mem, obj_out, status_out, best_rep_out);
+    return rs != THETIS_OK ? rs : st;
+  }
+  const thetis_status cs = guard(h->stream, [&] {
+    cudaStream_t s = h->stream;
+    const int64_t count = P.nbatch;
+    from_dev(labels_out, P.i_lab, P.nv, out_mem, s);
+    std::vector<double> obj(count);
+    std::vector<int32_t> status(count), best(count);
+    TH_CUDA(cudaMemcpyAsync(obj.data(), P.i_robj, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(status.data(), P.i_rstatus, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(best.data(), P.i_rbest, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    for (int64_t t = 0; t < count; ++t) {
+      if (obj_out) obj_out[t] = obj[t];
+      if (status_out) status_out[t] = status[t];
+      if (best_rep_out) best_rep_out[t] = best[t];
+    }
+  });
+  return cs != THETIS_OK ? cs : st;
+}
+
 thetis_status thetis_round_batch(thetis_handle* h, uint64_t seed, int32_t reps, uint8_t* labels_out,
                                  int32_t out_mem, double* obj_out, int32_t* status_out, int32_t* best_rep_out) {
   if (!h || !h->P || !labels_out) {

@@ -106,6 +106,20 @@ __device__ __forceinline__ int dsm_ld_i(uint32_t a) {
   return v;
 }
 
+__device__ __forceinline__ double dsm_ld_d(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t dsm_ld_u(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void dsm_and(uint32_t a, uint32_t mask) {
+  asm volatile("red.shared::cluster.and.b32 [%0], %1;" ::"r"(a), "r"(mask) : "memory");
+}
+
 // element b[i] of a small register array without dynamic indexing
 template <int K>
 __device__ __forceinline__ uint32_t pick(const uint32_t (&b)[K], uint32_t i) {
@@ -148,6 +162,17 @@ struct InstView {
   int32_t* ep_out;
   int32_t* conv_out;
   unsigned long long* t_out;  // 2 per instance: start, done (globaltimer ns)
+  // rounding inside the kernel (round != 0): repair + VC threshold / IS best
+  // of reps with alterations + exact validity, as thetis_round_batch
+  int round;
+  uint64_t seed;
+  int reps;
+  const uint32_t* vid;   // per IML column: instance-local vertex id (the random streams' index)
+  uint8_t* lab;          // labels by union vertex
+  double* r_obj;         // count: objective of the rounded solution
+  double* r_rep;         // count: repair value (eps or alpha)
+  int32_t* r_best;       // count: winning repetition
+  int32_t* r_status;     // count: 1 valid, 0 validity check failed, -1 VC repair impossible
 };
 
 // ---------------------------------------------------------------------------
@@ -192,10 +217,12 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     for (int r = 0; r < K; ++r) rch = max(rch, qv[r + 1] - qv[r]);
   }
   const int qlo = qv[q], qhi = qv[q + 1];
-  const bool xs = !SPILL || (m + n <= cap);        // x in shared memory
+  // the r region also holds the rounding's two bit words per 32 own columns
+  const int rr = max(rch, 2 * (((n + K - 1) / K + 31) / 32));
+  const bool xs = !SPILL || (rr + n <= cap);       // x in shared memory
   const int rs = SPILL ? min(m, cap) : rch;        // rows of r in shared memory (K = 1)
   float* sr = smem;
-  float* sx = smem + rch;
+  float* sx = smem + rr;
   float* rgl = V.rg + row0;
   // the instance's arrays (32-bit local indices from here on)
   float* Sx = V.x + col0;
@@ -589,6 +616,154 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     }
   }
   if (!checked_last) conv = !check();
+  sync();
+  if (V.round) {
+    // -- repair and rounding of the final iterate (Sec. 2, App. B.2, App. C) --
+    // scratch over the r region: pick and keep bits of this rank's columns
+    // (own index i = k / K of column k, k % K == q)
+    __shared__ double s_wred[32];
+    __shared__ double s_ctot;
+    const int xch = (n + K - 1) / K;
+    const int nw = (xch + 31) / 32;
+    uint32_t* pickw = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* keepw = pickw + nw;
+    uint32_t pb[K], kb[K];
+    if constexpr (K > 1) {
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        pb[r] = dsm_map(smem_u32(pickw), (uint32_t)r);
+        kb[r] = dsm_map(smem_u32(keepw), (uint32_t)r);
+      }
+    }
+    const uint32_t* Vid = V.vid + col0;
+    uint8_t* Lab = V.lab + col0;
+    const bool vc = sig < 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fixed-order reduction over the CTA, then over the cluster's ranks
+    auto reduce = [&](double v, bool mx) -> double {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = mx ? fmax(v, u) : v + u;
+      }
+      if (lane == 0) s_wred[warp] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = s_wred[0];
+        for (int w = 1; w < NT / 32; ++w) a = mx ? fmax(a, s_wred[w]) : a + s_wred[w];
+        s_ctot = a;
+      }
+      sync();
+      double tot = s_ctot;
+      if constexpr (K > 1) {
+        tot = dsm_ld_d(dsm_map(smem_u32(&s_ctot), 0));
+        for (int r = 1; r < K; ++r) {
+          const double u = dsm_ld_d(dsm_map(smem_u32(&s_ctot), (uint32_t)r));
+          tot = mx ? fmax(tot, u) : tot + u;
+        }
+      }
+      sync();
+      return tot;
+    };
+    auto bit_of = [&](const uint32_t* w, const uint32_t (&wb)[K], uint32_t k) -> uint32_t {
+      if constexpr (K == 1) return (w[k >> 5] >> (k & 31)) & 1u;
+      else {
+        const uint32_t i = k / K;
+        return (dsm_ld_u(pick<K>(wb, k % K) + 4u * (i >> 5)) >> (i & 31)) & 1u;
+      }
+    };
+    auto clear_keep = [&](uint32_t k) {
+      if constexpr (K == 1) atomicAnd(&keepw[k >> 5], ~(1u << (k & 31)));
+      else {
+        const uint32_t i = k / K;
+        dsm_and(pick<K>(kb, k % K) + 4u * (i >> 5), ~(1u << (i & 31)));
+      }
+    };
+    // repair value: VC eps = max (1 - x_u - x_v)_+, IS alpha = max (x_u + x_v - 1)_+
+    double vmax = 0.0;
+    for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
+      const double xu = (double)xget(Iru[e]), xv = (double)xget(Irv[e]);
+      const double v = vc ? (1.0 - xu) - xv : (xu + xv) - 1.0;
+      if (v > vmax) vmax = v;
+    }
+    const double a = reduce(vmax, true);
+    // the labels of this rank's columns, in bit words (and the objective)
+    auto label_words = [&](int rep, bool store) -> double {
+      double wsum = 0.0;
+      for (int i0 = warp * 32; i0 < xch; i0 += NT) {
+        const int i = i0 + lane;
+        const int k = q + i * K;
+        bool b = false;
+        if (i < xch && k < n) {
+          const double xv = (double)xown_get(k);
+          if (vc) {
+            if (a < 1.0) b = fmin(1.0, fmax(0.0, xv / (1.0 - a))) >= 0.5;
+          } else {
+            b = rng_unif(V.seed, (uint64_t)rep, STREAM_IS_PICK, Vid[k]) < xv / (1.0 + a);
+          }
+          if (store && vc) Lab[Vid[k]] = b ? 1 : 0;
+          if (b && vc) wsum += (double)Cc[k];
+        }
+        const uint32_t w = __ballot_sync(0xffffffffu, b);
+        if (lane == 0) {
+          pickw[i0 >> 5] = w;
+          keepw[i0 >> 5] = w;
+        }
+      }
+      return wsum;
+    };
+    // IS alterations: of every edge with both ends picked, the end with the
+    // larger vertex id leaves; then the kept weight
+    auto alter_weight = [&](bool store) -> double {
+      sync();
+      for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
+        const uint32_t u = Iru[e], v = Irv[e];
+        if (bit_of(pickw, pb, u) && bit_of(pickw, pb, v)) clear_keep(Vid[u] > Vid[v] ? u : v);
+      }
+      sync();
+      double wsum = 0.0;
+      for (int i = threadIdx.x; i < xch; i += NT) {
+        const int k = q + i * K;
+        if (k >= n) continue;
+        const uint32_t kb1 = (keepw[i >> 5] >> (i & 31)) & 1u;
+        if (store) Lab[Vid[k]] = (uint8_t)kb1;
+        if (kb1) wsum -= (double)Cc[k];  // IS costs are -w
+      }
+      return wsum;
+    };
+    double obj;
+    int best = 0;
+    if (vc) {
+      obj = reduce(label_words(0, true), false);
+    } else {
+      double bw = 0.0;
+      for (int rep = 0; rep < V.reps; ++rep) {
+        label_words(rep, false);
+        const double w = reduce(alter_weight(false), false);
+        if (rep == 0 || w > bw) {
+          bw = w;
+          best = rep;
+        }
+      }
+      label_words(best, false);
+      obj = reduce(alter_weight(true), false);
+    }
+    // exact validity over this rank's rows (labels are in the keep bits; for VC
+    // the pick and keep words are equal)
+    sync();
+    double bad = 0.0;
+    for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
+      const uint32_t bu = bit_of(keepw, kb, Iru[e]), bv = bit_of(keepw, kb, Irv[e]);
+      if (vc ? !(bu | bv) : (bu & bv)) bad = 1.0;
+    }
+    bad = reduce(bad, true);
+    if (threadIdx.x == 0 && q == 0) {
+      V.r_obj[t] = obj;
+      V.r_rep[t] = a;
+      V.r_best[t] = best;
+      V.r_status[t] = (vc && a >= 1.0) ? -1 : (bad != 0.0 ? 0 : 1);
+    }
+  }
   sync();  // no rank may leave while another still reads its shared memory
   if (xs)
     for (int i = threadIdx.x; i * K + q < n; i += NT) Sx[i * K + q] = sx[i];
@@ -706,6 +881,16 @@ __global__ void k_inst_lcol(const uint32_t* i_col, const int32_t* inst_col, cons
   GSTRIDE(k, Ns) {
     const uint32_t j = i_col[k];
     lcol[j] = (uint32_t)(k - noff[inst_col[j]]);
+  }
+}
+
+// instance-local vertex id of every IML column (the rounding streams' index)
+__global__ void k_inst_vid(const uint32_t* col_of_orig, const int32_t* inst_col, const int64_t* noff,
+                           const uint32_t* lcol, int64_t Ns, uint32_t* vid) {
+  GSTRIDE(j, Ns) {
+    const uint32_t ci = col_of_orig[j];
+    const int64_t t = inst_col[ci];
+    vid[noff[t] + lcol[ci]] = (uint32_t)(j - noff[t]);
   }
 }
 
@@ -896,7 +1081,12 @@ constexpr Cls CLASSES[] = {{1, 256}, {1, 512}, {1, 1024}, {2, 1024}, {4, 1024}, 
 constexpr int NCLS = 6;
 constexpr int CLS_SPILL = 5;
 
-int64_t inst_smem(int64_t n, int64_t m, int K) { return 4 * ((m + K - 1) / K + (n + K - 1) / K); }
+// shared memory of an instance on K CTAs: its r region (at least the
+// rounding's two bit words per 32 columns) and its x
+int64_t inst_smem(int64_t n, int64_t m, int K) {
+  const int64_t xch = (n + K - 1) / K;
+  return 4 * (std::max<int64_t>((m + K - 1) / K, 2 * ((xch + 31) / 32)) + xch);
+}
 
 struct DevLimits {
   int64_t optin = 0, per_sm = 0;
@@ -984,6 +1174,8 @@ void inst_classes(Problem& P) {
       else if (clusters && est(4) <= class_cap(L, 4)) c = 4;
       else c = CLS_SPILL;
     }
+    TH_CHECK(c != CLS_SPILL || 4 * 2 * ((n + 31) / 32) <= class_cap(L, CLS_SPILL), THETIS_E_INVALID,
+             "instance engine: an instance with more vertices than one CTA's rounding scratch holds");
     members[c].push_back((int32_t)t);
     iK[t] = (uint8_t)CLASSES[c].K;
   }
@@ -1031,7 +1223,8 @@ void inst_class_smem(Problem& P) {
       const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t];
       int64_t rows = 0;
       for (int q = 0; q < K; ++q) rows = std::max<int64_t>(rows, qo[t * 5 + q + 1] - qo[t * 5 + q]);
-      need = std::max(need, 4 * (rows + (n + K - 1) / K));
+      const int64_t xch = (n + K - 1) / K;
+      need = std::max(need, 4 * (std::max<int64_t>(rows, 2 * ((xch + 31) / 32)) + xch));
     }
     TH_CHECK(need <= class_cap(L, c), THETIS_E_INVALID, "instance engine: a rank's rows exceed its shared memory");
     P.h_icls_smem[c] = (need + 15) / 16 * 16;
@@ -1084,6 +1277,9 @@ void inst_layout(Problem& P) {
   radix_sort_pairs(keys, P.i_col, Ns, bits_for_count(count), tmp, s);
   uint32_t* lcol = tmp.alloc<uint32_t>(Ns + 1);
   k_inst_lcol<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, P.bnoff, Ns, lcol);
+  TH_LAUNCHED();
+  once(P.i_vid, Ns + 1);
+  k_inst_vid<<<grid_for(Ns, 256), 256, 0, s>>>(P.col_of_orig, P.binst_col, P.bnoff, lcol, Ns, P.i_vid);
   TH_LAUNCHED();
   // rows by (instance, rank of the cluster that keeps them, union order --
   // which is slack-colour major)
@@ -1173,6 +1369,11 @@ void inst_layout(Problem& P) {
   once(P.i_ep, count);
   once(P.i_conv, count);
   once(P.i_t, 2 * count + 1);
+  once(P.i_lab, Ns + 1);
+  once(P.i_robj, count);
+  once(P.i_rrep, count);
+  once(P.i_rbest, count);
+  once(P.i_rstatus, count);
   int herr = 0;
   TH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TH_CUDA(cudaStreamSynchronize(s));  // host tables above must outlive their copies
@@ -1250,6 +1451,16 @@ void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
   V.ep_out = P.i_ep;
   V.conv_out = P.i_conv;
   V.t_out = P.i_t;
+  V.round = P.iround_on ? 1 : 0;
+  P.iround_done = P.iround_on;
+  V.seed = P.iround_seed;
+  V.reps = P.iround_reps;
+  V.vid = P.i_vid;
+  V.lab = P.i_lab;
+  V.r_obj = P.i_robj;
+  V.r_rep = P.i_rrep;
+  V.r_best = P.i_rbest;
+  V.r_status = P.i_rstatus;
   const DevLimits L = dev_limits();
   k_inst_stamp<<<1, 1, 0, s>>>(P.i_t + 2 * count);
   TH_LAUNCHED();

@@ -128,6 +128,15 @@ struct Problem {
   int32_t* i_roff = nullptr;        // count * 4 * iml_C: first local slack row of every (rank, colour)
   int32_t* i_qoff = nullptr;        // count * 5: first local row of every cluster rank (and the end)
   uint8_t* i_K = nullptr;           // count: cluster size of every instance (1: one CTA)
+  uint32_t* i_vid = nullptr;        // Ns: instance-local vertex id of every IML column
+  // rounding inside the instance kernel (thetis_solve_round_batch)
+  bool iround_on = false;
+  bool iround_done = false;         // the last solve rounded in the kernel
+  uint64_t iround_seed = 0;
+  int iround_reps = 1;
+  uint8_t* i_lab = nullptr;         // Ns: labels by union vertex
+  double *i_robj = nullptr, *i_rrep = nullptr;      // count: objective, repair value
+  int32_t *i_rbest = nullptr, *i_rstatus = nullptr; // count: winning repetition, status
   std::vector<uint8_t> h_iK;
   int32_t* i_ncol = nullptr;        // count: colours of the instance
   int32_t* i_cwide = nullptr;       // count * iml_C: first short column (<= 32 entries) of every colour

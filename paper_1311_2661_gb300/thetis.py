@@ -92,6 +92,7 @@ def _load():
         "thetis_set_wait_limit": (st, [P, C.c_double, i32]),
         "thetis_batch_latency": (st, [P, P]),
         "thetis_set_batch_shape": (st, [P, i32, i32]),
+        "thetis_solve_round_batch": (st, [P, P, u64, i32, P, i32, P, P, P, P]),
         "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
         "thetis_autotune": (st, [P, P, i32, P, P]),
         "thetis_set_launch_shape": (st, [P, i32, i32]),
@@ -539,6 +540,32 @@ def thetis_build_batch_graphs(items, seed=0, stream=None, device=False) -> Handl
         dv = lambda a: torch.from_numpy(a).cuda()
         return thetis_build_batch(dv(kinds), dv(noff), dv(eoff), dv(eu), dv(ev), dv(w), seed=seed, stream=stream)
     return thetis_build_batch(kinds, noff, eoff, eu, ev, w, seed=seed, stream=stream)
+
+
+def thetis_solve_round_batch(h: Handle, seed=0, reps=10, out=None, beta=1e2, epochs=50, tol=0.0, refresh_every=10,
+                             step_rule=0, engine=0):
+    """Solve a batch and round every instance (in the instance kernel as each
+    stops).  Returns (info, labels, obj[count], status[count], best_rep[count])."""
+    A = _Args()
+    p = Params()
+    p.beta, p.epochs, p.tol = float(beta), int(epochs), float(tol)
+    p.refresh_every, p.step_rule, p.mode = int(refresh_every), int(step_rule), MODE_COLORED
+    p.mem = MEM_HOST
+    p.engine = int(engine)
+    count = h.count
+    obj = np.zeros(count, np.float64)
+    status = np.zeros(count, np.int32)
+    best = np.zeros(count, np.int32)
+    lab = np.zeros(h.n_vertices, np.uint8) if out is None else out
+    ptr, mem = _out_ptr(lab)
+    info = SolveInfo()
+    st = _check(_lib.thetis_solve_round_batch(h.ptr, C.byref(p), int(seed), int(reps), ptr, mem, obj.ctypes.data,
+                                              status.ctypes.data, best.ctypes.data, C.byref(info)),
+                allow=(THETIS_OK, THETIS_NOT_CONVERGED))
+    inf = dict(status=st, epochs_run=info.epochs_run, converged=bool(info.converged), ncolors=info.ncolors,
+               rho=info.rho, obj=info.obj, infeas=info.infeas, fbeta=info.fbeta, updates=info.updates,
+               solve_ms=info.solve_ms, epoch_ms=info.epoch_ms, launches_per_epoch=info.launches_per_epoch)
+    return inf, lab, obj, status, best
 
 
 def thetis_round_batch(h: Handle, seed=0, reps=10, out=None):

@@ -236,3 +236,38 @@ def test_batched_workload_shape_parity_sample():
             x_o, info_o = lp.solve(beta=100.0, epochs=int(ep[t]), refresh_every=20, color=lp.color(0)[0])
             assert np.max(np.abs(mine - x_o)) <= X_TOL, t
             assert info_o["rho"] <= 1e-3 + 1e-6, t
+
+
+@pytest.mark.parametrize("lanes,clusters,epochs", [(1, 0, 40), (1, 1, 40), (4, 0, 25), (1, 0, 0)])
+def test_rounding_inside_the_instance_kernel_equals_round_batch(lanes, clusters, epochs):
+    """thetis_solve_round_batch rounds every instance in its own CTA / cluster
+    the moment it stops (repair, VC threshold / IS best of reps with
+    alterations, exact validity): labels, objectives, best repetitions and
+    statuses equal thetis_round_batch on the same iterate, bit for bit --
+    including the VC repair failure of an unsolved iterate (epochs = 0)."""
+    T = gpu()
+    items = _sized_items(CLASS_SIZES, 41) + _batch(count=12, seed=9, nmax=500)
+    outs = []
+    for fused in (True, False):
+        hb = T.thetis_build_batch_graphs(items, seed=5, device=True)
+        T.thetis_set_batch_shape(hb, lanes, clusters)
+        kw = dict(beta=100.0, epochs=epochs, tol=1e-3, refresh_every=10)
+        if fused:
+            info, lab, obj, status, best = T.thetis_solve_round_batch(hb, seed=21, reps=7, **kw)
+        else:
+            info = hb.solve(**kw)
+            lab, obj, status, best = T.thetis_round_batch(hb, seed=21, reps=7)
+        outs.append((hb.get_x(), lab.copy(), obj, status, best, info["epochs_run"]))
+    (x1, l1, o1, s1, b1, e1), (x2, l2, o2, s2, b2, e2) = outs
+    assert np.array_equal(x1, x2) and e1 == e2
+    assert np.array_equal(l1, l2)
+    assert np.array_equal(o1, o2)
+    assert np.array_equal(s1, s2)
+    assert np.array_equal(b1, b2)
+    noff, _ = _slices(items)
+    for t, (kind, g) in enumerate(items):
+        if kind == "vc" and epochs == 0 and g.m > 0:
+            assert s1[t] == -1, t
+        else:
+            assert s1[t] == 1, t
+            assert oracle.build_problem(kind, g).valid(l1[noff[t]:noff[t + 1]]), t
