@@ -538,6 +538,10 @@ thetis_status thetis_poll(thetis_server* sv, uint64_t id, uint8_t* labels_out, f
                           thetis_result* out);
 thetis_status thetis_server_stats(thetis_server* sv, int64_t* submitted, int64_t* completed,
                                   int64_t* queued, int64_t* in_flight_bytes);
+/* Load shedding: at most max_queued requests wait (0 = no limit); a submit
+ * beyond it returns THETIS_E_BUDGET ("queue full") at once.  refused_out (may
+ * be NULL) receives the number of submits refused so far. */
+thetis_status thetis_server_set_queue_limit(thetis_server* sv, int64_t max_queued, int64_t* refused_out);
 /* Finishes every queued request, then stops the workers. */
 thetis_status thetis_server_destroy(thetis_server* sv);
 

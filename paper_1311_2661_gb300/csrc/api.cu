@@ -36,6 +36,12 @@ struct thetis_handle {
   }
 };
 
+namespace thetis {
+// the problem behind a handle (the request server reads a batch's per-instance
+// outputs while its solve runs)
+Problem* problem_of(thetis_handle* h) { return h ? h->P.get() : nullptr; }
+}  // namespace thetis
+
 namespace {
 
 template <class F>

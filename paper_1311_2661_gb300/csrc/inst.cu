@@ -173,6 +173,9 @@ struct InstView {
   double* r_rep;         // count: repair value (eps or alpha)
   int32_t* r_best;       // count: winning repetition
   int32_t* r_status;     // count: 1 valid, 0 validity check failed, -1 VC repair impossible
+  float* xout;           // union vertex order: the final x (rounding on)
+  float* rho_out;        // count: rho at the last check (the largest unit value, FP32 from exact sums)
+  int* done;             // count or null: set to 1 (system scope) once the instance's results are written
 };
 
 // ---------------------------------------------------------------------------
@@ -192,6 +195,7 @@ template <int K, int NT, int G, bool SPILL>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstView V, const int32_t* order) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_over[2];
+  __shared__ unsigned s_rho[2];  // the largest rho of the check (FP32 bits, non-negative)
   constexpr int GC = (G == 1) ? 8 : G;  // lanes per column of the stopping test
   const int q = (K > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int t = order[blockIdx.x / K];
@@ -320,7 +324,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // -- start: x chunk into shared memory, exact residual of the own rows -----
   if (xs)
     for (int i = threadIdx.x; i * K + q < n; i += NT) sx[i] = Sx[i * K + q];
-  if (threadIdx.x < 2) s_over[threadIdx.x] = 0;
+  if (threadIdx.x < 2) {
+    s_over[threadIdx.x] = 0;
+    s_rho[threadIdx.x] = 0u;
+  }
   if (threadIdx.x == 0 && q == 0) V.t_out[2 * t] = global_ns();
   sync();
 
@@ -328,6 +335,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // test into s_over[slot])
   auto rows_pass = [&](bool chk, int slot) {
     bool over = false;
+    float rmax = 0.f;
     for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
       const float xu = xget(Iru[e]), xv = xget(Irv[e]);
       const float sv = Ss[e];
@@ -341,12 +349,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         r32 = (float)row_f64(xu, xv, sv, sig);
       }
       rown_set(e, r32);
-      if (!chk || over) continue;
+      if (!chk) continue;
       // slack unit: rho = |max(0, s - grad / L) - s|, L = beta + 1/beta
       const float ls = beta + ib;
       const float g = fmaf(beta * sig, r32, sv * ib);
       const float qv = g / ls;
       const float rho = fabsf(fmaxf(sv - qv, 0.f) - sv);
+      rmax = fmaxf(rmax, rho);
+      if (over) continue;
       const float del = 0x1p-19f * ((beta * fabsf(r32) + sv * ib) / ls + fabsf(sv) + fabsf(qv)) + 0x1p-23f * tol32 +
                         1e-30f;
       if (rho - del > tol32) {
@@ -362,6 +372,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       }
     }
     if (over) atomicOr(&s_over[slot], 1);
+    if (chk && rmax > 0.f) atomicMax(&s_rho[slot], __float_as_uint(rmax));
   };
 
   // the column part of the stopping test: a_j^T r from the exact row values
@@ -370,6 +381,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     constexpr int PW = 32 / GC;
     const int warp = threadIdx.x >> 5, lw = (threadIdx.x & 31) / GC, gl = threadIdx.x % GC;
     bool over = false;
+    float rmax = 0.f;
     for (int ib0 = warp * PW; ib0 < cnt; ib0 += (NT / 32) * PW) {
       const int i = ib0 + lw;
       const bool valid = i < cnt;
@@ -404,7 +416,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         lo += __shfl_xor_sync(0xffffffffu, lo, o, GC);
         bad |= __shfl_xor_sync(0xffffffffu, bad, o, GC);
       }
-      if (!valid || gl != 0 || over) continue;
+      if (!valid || gl != 0) continue;
       const float deg = (float)(p1 - p0);
       const float L = fmaf(beta, deg, ib);
       bool exact = bad != 0;
@@ -413,6 +425,8 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         const float g = ck + beta * sum + xk * ib;
         const float qv = g / L;
         const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
+        rmax = fmaxf(rmax, rho);
+        if (over) continue;
         const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
                           0x1p-39f * (1.f + deg) + 0x1p-23f * tol32 + 1e-30f;
         if (rho - del > tol32) over = true;
@@ -437,6 +451,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       }
     }
     if (over) atomicOr(&s_over[slot], 1);
+    if (rmax > 0.f) atomicMax(&s_rho[slot], __float_as_uint(rmax));
   };
 
   // columns [ka, kb) of this rank (k % K == q) through the CSR, GG lanes each
@@ -578,6 +593,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
 
   // a check: exact refresh + stopping test; true when some unit has rho > tol
   int nchk = 0;
+  float last_rho = 0.f;
   auto check = [&]() -> bool {
     const int slot = nchk & 1;
     ++nchk;
@@ -585,14 +601,23 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     cols_check(slot);
     sync();
     int over = 0;
+    unsigned rb_ = 0;
     if constexpr (K == 1) {
       over = s_over[slot];
+      rb_ = s_rho[slot];
     } else {
-      const uint32_t fa = smem_u32(&s_over[slot]);
+      const uint32_t fa = smem_u32(&s_over[slot]), ra_ = smem_u32(&s_rho[slot]);
 #pragma unroll
-      for (int r = 0; r < K; ++r) over |= dsm_ld_i(dsm_map(fa, (uint32_t)r));
+      for (int r = 0; r < K; ++r) {
+        over |= dsm_ld_i(dsm_map(fa, (uint32_t)r));
+        rb_ = max(rb_, (unsigned)dsm_ld_i(dsm_map(ra_, (uint32_t)r)));
+      }
     }
-    if (threadIdx.x == 0) s_over[slot ^ 1] = 0;  // the next check's slot (no reader left: see the barriers between)
+    last_rho = __uint_as_float(rb_);
+    if (threadIdx.x == 0) {  // the next check's slot (no reader left: see the barriers between)
+      s_over[slot ^ 1] = 0;
+      s_rho[slot ^ 1] = 0u;
+    }
     return over != 0;
   };
 
@@ -757,6 +782,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       if (vc ? !(bu | bv) : (bu & bv)) bad = 1.0;
     }
     bad = reduce(bad, true);
+    for (int i = threadIdx.x; i < xch; i += NT) {
+      const int k = q + i * K;
+      if (k < n) V.xout[col0 + Vid[k]] = xown_get(k);
+    }
     if (threadIdx.x == 0 && q == 0) {
       V.r_obj[t] = obj;
       V.r_rep[t] = a;
@@ -770,7 +799,17 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   if (threadIdx.x == 0 && q == 0) {
     V.ep_out[t] = ep;
     V.conv_out[t] = conv ? 1 : 0;
+    V.rho_out[t] = last_rho;
     V.t_out[2 * t + 1] = global_ns();
+  }
+  if (V.done) {
+    // every rank's results are written (the barrier above orders them within
+    // the cluster): publish the instance to the host
+    sync();
+    if (threadIdx.x == 0 && q == 0) {
+      __threadfence_system();
+      *(volatile int*)(V.done + t) = 1;
+    }
   }
 }
 
@@ -1374,6 +1413,8 @@ void inst_layout(Problem& P) {
   once(P.i_rrep, count);
   once(P.i_rbest, count);
   once(P.i_rstatus, count);
+  once(P.i_xout, Ns + 1);
+  once(P.i_rhoout, count);
   int herr = 0;
   TH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   TH_CUDA(cudaStreamSynchronize(s));  // host tables above must outlive their copies
@@ -1393,6 +1434,11 @@ bool inst_eligible(Problem& P) {
     if (n >= (int64_t(1) << 30) || m >= (int64_t(1) << 30)) return false;
   }
   return true;
+}
+
+void inst_prepare(Problem& P) {
+  if (!P.iml_classes_ok) inst_classes(P);
+  if (!P.iml_built) inst_layout(P);
 }
 
 void inst_set_clusters(Problem& P, bool on) {
@@ -1461,6 +1507,9 @@ void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
   V.r_rep = P.i_rrep;
   V.r_best = P.i_rbest;
   V.r_status = P.i_rstatus;
+  V.xout = P.i_xout;
+  V.rho_out = P.i_rhoout;
+  V.done = P.i_done;
   const DevLimits L = dev_limits();
   k_inst_stamp<<<1, 1, 0, s>>>(P.i_t + 2 * count);
   TH_LAUNCHED();

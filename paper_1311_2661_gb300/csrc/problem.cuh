@@ -137,6 +137,9 @@ struct Problem {
   uint8_t* i_lab = nullptr;         // Ns: labels by union vertex
   double *i_robj = nullptr, *i_rrep = nullptr;      // count: objective, repair value
   int32_t *i_rbest = nullptr, *i_rstatus = nullptr; // count: winning repetition, status
+  float* i_xout = nullptr;          // Ns: final x by union vertex (rounding on)
+  float* i_rhoout = nullptr;        // count: rho at the last check
+  int* i_done = nullptr;            // count or null: host-mapped completion flags (set by the caller)
   std::vector<uint8_t> h_iK;
   int32_t* i_ncol = nullptr;        // count: colours of the instance
   int32_t* i_cwide = nullptr;       // count * iml_C: first short column (<= 32 entries) of every colour
@@ -148,7 +151,7 @@ struct Problem {
   int32_t* i_deg = nullptr;         // count: largest column length of the instance
   float *i_c = nullptr, *i_x = nullptr, *i_s = nullptr;  // c, x (Ns) and s (M) in IML order
   float* i_rg = nullptr;            // M: residual rows kept in global memory (instances too large for one CTA)
-  bool iml_clusters = false;        // large instances on thread-block clusters instead of one CTA + L2
+  bool iml_clusters = true;         // large instances on thread-block clusters (else one CTA + L2)
   bool iml_classes_ok = false;      // launch classes computed for the current iml_clusters
   int32_t* i_ep = nullptr;          // count: epochs the instance ran
   int32_t* i_conv = nullptr;        // count: 1 if it stopped at rho <= tol
@@ -334,6 +337,11 @@ void inst_release(Problem& P);
 // large instances on 2- or 4-CTA clusters (distributed shared memory) or on one
 // CTA with the rows beyond its shared memory in L2 (the default)
 void inst_set_clusters(Problem& P, bool on);
+// launch classes and layout now (before any solve), so callers may read the
+// per-instance outputs while a solve runs
+void inst_prepare(Problem& P);
+// (api.cu) the problem behind a handle
+Problem* problem_of(thetis_handle* h);
 
 // scd.cu
 struct SolveArgs {

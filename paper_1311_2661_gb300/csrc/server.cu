@@ -3,11 +3,18 @@
 // worker takes the smallest queued request (the oldest, once a request has
 // waited MAX_WAIT_MS) and every other queued vertex-cover / independent-set
 // request with the same solve parameters and a similar size (up to max_batch
-// and the memory budget) and solves them as one block-diagonal batch
-// (thetis_build_batch), so requests that arrive while others are on the GPU
-// join the next batch and the work of different slots overlaps on the device.
-// Multiway-cut requests are solved one per slot.  Admission is by an estimate
-// of the device bytes a request needs against a fixed budget.
+// and the memory budget) and solves them as one batch (thetis_build_batch +
+// thetis_solve_round_batch) on the instance-resident engine: every request is
+// solved, rounded and validated by its own CTA (or cluster), which publishes
+// its completion to host-mapped memory the moment it finishes, and the worker
+// returns that request's result right away while the rest of the batch runs.
+// Finished instances free their SMs at once, which the other workers' batches
+// (their own streams) take up, so requests that arrive while others are on the
+// GPU start as soon as a worker is free and overlap on the device.  Requests
+// too large for one CTA or cluster and multiway-cut requests are solved one
+// per worker on the whole GPU.  Admission is by an estimate of the device
+// bytes a request needs against a fixed budget.
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <string>
@@ -75,11 +82,27 @@ bool same_params(const thetis_request& a, const thetis_request& b) {
          a.seed == b.seed && a.reps == b.reps;
 }
 
+// small enough for one CTA or cluster of the instance-resident engine
+bool batchable(const thetis_request& q) { return q.kind != THETIS_ROUND_MC && q.n + q.m <= 200000; }
+
+// Completion flags of a worker in host-mapped pinned memory (written by the
+// instance kernels as instances finish) and a stream for reading finished
+// instances back while the batch still runs.
+struct Slot {
+  int* hflags = nullptr;
+  int* dflags = nullptr;
+  int cap = 0;
+  cudaStream_t copy = nullptr;
+  int device = 0;
+};
+
 }  // namespace
 
 struct thetis_server {
   size_t budget = 0;
   int max_batch = 64;
+  size_t max_queued = 0;  // 0: unbounded; else submits beyond it are refused (load shedding)
+  int64_t refused = 0;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Req*> queue;
@@ -91,9 +114,21 @@ struct thetis_server {
   std::vector<std::thread> workers;
 
   void work();
-  void run_batch(std::vector<Req*>& batch, cudaStream_t s);
+  void run_batch(std::vector<Req*>& batch, cudaStream_t s, Slot& slot);
   void run_single(Req* r, cudaStream_t s);
+  void finish(Req* r);
 };
+
+// a request's result is ready: its latency ends here
+void thetis_server::finish(Req* r) {
+  std::lock_guard<std::mutex> lk(mu);
+  r->t_done = clk::now();
+  r->res.queue_ms = ms_between(r->t_submit, r->t_start);
+  r->res.service_ms = ms_between(r->t_start, r->t_done);
+  r->res.latency_ms = ms_between(r->t_submit, r->t_done);
+  r->done = true;
+  ++completed;
+}
 
 void thetis_server::run_single(Req* r, cudaStream_t s) {
   const thetis_request& q = r->q;
@@ -141,9 +176,10 @@ void thetis_server::run_single(Req* r, cudaStream_t s) {
   thetis_destroy(h);
 }
 
-void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
-  if (batch.size() == 1) {
+void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s, Slot& slot) {
+  if (batch.size() == 1 && !batchable(batch[0]->q)) {
     run_single(batch[0], s);
+    finish(batch[0]);
     return;
   }
   const int32_t count = (int32_t)batch.size();
@@ -168,7 +204,10 @@ void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
                                         w.data(), THETIS_MEM_HOST, q.seed, s, &h);
   for (Req* r : batch) r->res.batch_size = count;
   if (st != THETIS_OK) {
-    for (Req* r : batch) fail(r, st);
+    for (Req* r : batch) {
+      fail(r, st);
+      finish(r);
+    }
     return;
   }
   thetis_params p{};
@@ -176,24 +215,88 @@ void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
   p.epochs = q.epochs;
   p.tol = q.tol;
   p.refresh_every = q.refresh_every;
-  p.engine = 1;
+  p.engine = 0;  // instance-resident engine (ordinary launches on this worker's stream)
+  // per-request completion: the kernels publish each finished instance
+  thetis::Problem* P = thetis::problem_of(h);
+  std::vector<char> fin(count, 0);
+  bool early = false;
+  if (slot.cap >= count && P && thetis::inst_eligible(*P)) {
+    try {
+      thetis::inst_prepare(*P);
+      std::memset(slot.hflags, 0, count * sizeof(int));
+      P->i_done = slot.dflags;
+      early = true;
+    } catch (thetis::Error&) {
+      early = false;
+    }
+  }
+  std::atomic<bool> solving{true};
+  std::thread poller;
+  if (early) {
+    poller = std::thread([&] {
+      cudaSetDevice(slot.device);
+      volatile int* flags = slot.hflags;
+      while (true) {
+        bool left = false;
+        for (int32_t t = 0; t < count; ++t) {
+          if (fin[t]) continue;
+          if (!flags[t]) {
+            left = true;
+            continue;
+          }
+          Req* r = batch[t];
+          const int64_t n = r->q.n;
+          r->labels.assign((size_t)n, 0);
+          r->x.assign((size_t)n, 0.f);
+          double obj = 0.0;
+          int32_t status = 0, ep = 0, conv = 0;
+          float rho = 0.f;
+          cudaStream_t c = slot.copy;
+          cudaMemcpyAsync(r->labels.data(), P->i_lab + noff[t], n, cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(r->x.data(), P->i_xout + noff[t], n * sizeof(float), cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(&obj, P->i_robj + t, sizeof(double), cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(&status, P->i_rstatus + t, sizeof(int32_t), cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(&ep, P->i_ep + t, sizeof(int32_t), cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(&conv, P->i_conv + t, sizeof(int32_t), cudaMemcpyDeviceToHost, c);
+          cudaMemcpyAsync(&rho, P->i_rhoout + t, sizeof(float), cudaMemcpyDeviceToHost, c);
+          if (cudaStreamSynchronize(c) != cudaSuccess) {
+            (void)cudaGetLastError();
+            left = true;  // read it again after the solve
+            continue;
+          }
+          r->res.status = (status == -1) ? THETIS_E_REPAIR : (conv ? THETIS_OK : THETIS_NOT_CONVERGED);
+          if (status == -1) std::snprintf(r->res.message, sizeof(r->res.message), "covering repair impossible");
+          r->res.obj = obj;
+          r->res.valid = status == 1;
+          r->res.epochs_run = ep;
+          r->res.rho = rho;
+          fin[t] = 1;
+          finish(r);
+          cv.notify_all();
+        }
+        if (!left || !solving.load()) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+      }
+    });
+  }
   thetis_solve_info si{};
-  st = thetis_solve(h, &p, &si);
-  for (Req* r : batch) fail(r, st);
   std::vector<uint8_t> lab(noff[count]);
   std::vector<double> obj(count);
   std::vector<int32_t> status(count), best(count);
-  thetis_status rs = THETIS_OK;
-  if (st == THETIS_OK || st == THETIS_NOT_CONVERGED)
-    rs = thetis_round_batch(h, q.seed, q.reps, lab.data(), THETIS_MEM_HOST, obj.data(), status.data(), best.data());
-  for (Req* r : batch) fail(r, rs);
+  st = thetis_solve_round_batch(h, &p, q.seed, q.reps, lab.data(), THETIS_MEM_HOST, obj.data(), status.data(),
+                                best.data(), &si);
+  solving = false;
+  if (poller.joinable()) poller.join();
+  if (P) P->i_done = nullptr;
   std::vector<float> xs(noff[count]);
   thetis_get_x(h, xs.data(), THETIS_MEM_HOST);
   std::vector<int32_t> iep(count, si.epochs_run);
   std::vector<double> irho(count, si.rho);
   thetis_batch_info(h, iep.data(), irho.data());
   for (int32_t t = 0; t < count; ++t) {
+    if (fin[t]) continue;
     Req* r = batch[t];
+    fail(r, st);
     if (r->res.message[0] == 0) r->res.status = st;
     if (status[t] == -1) r->res.status = THETIS_E_REPAIR;
     // each instance stops at its own check: its status is its own
@@ -204,6 +307,7 @@ void thetis_server::run_batch(std::vector<Req*>& batch, cudaStream_t s) {
     r->res.valid = status[t] == 1;
     r->labels.assign(lab.begin() + noff[t], lab.begin() + noff[t + 1]);
     r->x.assign(xs.begin() + noff[t], xs.begin() + noff[t + 1]);
+    finish(r);
   }
   thetis_destroy(h);
 }
@@ -215,6 +319,18 @@ void thetis_server::work() {
   if (se != cudaSuccess) {
     s = nullptr;
     thetis::set_error(std::string("server worker: cudaStreamCreateWithFlags: ") + cudaGetErrorString(se));
+  }
+  // completion flags (host-mapped) and the read-back stream; without them the
+  // worker returns a batch's results when the batch ends
+  Slot slot;
+  cudaGetDevice(&slot.device);
+  if (cudaHostAlloc((void**)&slot.hflags, (size_t)max_batch * sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+      cudaHostGetDevicePointer((void**)&slot.dflags, slot.hflags, 0) == cudaSuccess &&
+      cudaStreamCreateWithFlags(&slot.copy, cudaStreamNonBlocking) == cudaSuccess) {
+    slot.cap = max_batch;
+  } else {
+    (void)cudaGetLastError();
+    slot.cap = 0;
   }
   while (true) {
     std::vector<Req*> batch;
@@ -239,11 +355,11 @@ void thetis_server::work() {
       queue.erase(hi);
       batch.push_back(r0);
       bytes = r0->bytes;
-      if (r0->q.kind != THETIS_ROUND_MC && max_batch > 1) {
-        // same parameters and a similar size (a batch ends with its slowest instance)
+      if (batchable(r0->q) && max_batch > 1) {
+        // same parameters and a similar size (the worker is busy until its slowest instance ends)
         for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
           Req* r = *it;
-          if (r->q.kind != THETIS_ROUND_MC && same_params(r->q, r0->q) && r->bytes <= SIZE_RATIO * r0->bytes &&
+          if (batchable(r->q) && same_params(r->q, r0->q) && r->bytes <= SIZE_RATIO * r0->bytes &&
               r0->bytes <= SIZE_RATIO * r->bytes && in_flight + bytes + r->bytes <= budget) {
             batch.push_back(r);
             bytes += r->bytes;
@@ -258,21 +374,15 @@ void thetis_server::work() {
     const auto t0 = clk::now();
     for (Req* r : batch) r->t_start = t0;
     if (s) {
-      run_batch(batch, s);
+      run_batch(batch, s, slot);
     } else {  // no stream of its own: every request fails with the reason
-      for (Req* r : batch) fail(r, THETIS_E_CUDA);
+      for (Req* r : batch) {
+        fail(r, THETIS_E_CUDA);
+        finish(r);
+      }
     }
-    const auto t1 = clk::now();
     {
       std::lock_guard<std::mutex> lk(mu);
-      for (Req* r : batch) {
-        r->t_done = t1;
-        r->res.queue_ms = ms_between(r->t_submit, r->t_start);
-        r->res.service_ms = ms_between(r->t_start, r->t_done);
-        r->res.latency_ms = ms_between(r->t_submit, r->t_done);
-        r->done = true;
-        ++completed;
-      }
       in_flight -= bytes;
     }
     cv.notify_all();
@@ -281,6 +391,8 @@ void thetis_server::work() {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
+  if (slot.copy) cudaStreamDestroy(slot.copy);
+  if (slot.hflags) cudaFreeHost(slot.hflags);
 }
 
 extern "C" {
@@ -333,6 +445,12 @@ thetis_status thetis_submit(thetis_server* sv, const thetis_request* q, uint64_t
       thetis::set_error("thetis_submit: request larger than the server's memory budget");
       return THETIS_E_BUDGET;
     }
+    if (sv->max_queued && sv->queue.size() >= sv->max_queued) {
+      delete r;
+      ++sv->refused;
+      thetis::set_error("thetis_submit: queue full (the server's queue limit)");
+      return THETIS_E_BUDGET;
+    }
     r->id = sv->next_id++;
     sv->all[r->id] = r;
     sv->queue.push_back(r);
@@ -378,6 +496,17 @@ thetis_status thetis_server_stats(thetis_server* sv, int64_t* submitted, int64_t
   if (completed) *completed = sv->completed;
   if (queued) *queued = (int64_t)sv->queue.size();
   if (in_flight_bytes) *in_flight_bytes = (int64_t)sv->in_flight;
+  return THETIS_OK;
+}
+
+thetis_status thetis_server_set_queue_limit(thetis_server* sv, int64_t max_queued, int64_t* refused_out) {
+  if (!sv || max_queued < 0) {
+    thetis::set_error("thetis_server_set_queue_limit: need a server and max_queued >= 0");
+    return THETIS_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->max_queued = (size_t)max_queued;
+  if (refused_out) *refused_out = sv->refused;
   return THETIS_OK;
 }
 

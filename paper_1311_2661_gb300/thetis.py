@@ -93,6 +93,7 @@ def _load():
         "thetis_batch_latency": (st, [P, P]),
         "thetis_set_batch_shape": (st, [P, i32, i32]),
         "thetis_solve_round_batch": (st, [P, P, u64, i32, P, i32, P, P, P, P]),
+        "thetis_server_set_queue_limit": (st, [P, i64, P]),
         "thetis_build_batch": (st, [i32, P, P, P, P, P, P, i32, u64, P, P]),
         "thetis_autotune": (st, [P, P, i32, P, P]),
         "thetis_set_launch_shape": (st, [P, i32, i32]),
@@ -451,6 +452,13 @@ class Server:
         _check(_lib.thetis_submit(self._h, C.byref(q), C.byref(rid)))
         self._sizes[rid.value] = (int(g.n), int(g.n) * (q.k if kind == "mc" else 1))
         return rid.value
+
+    def set_queue_limit(self, max_queued):
+        """Refuse submits while max_queued requests wait (0: no limit); returns
+        the number refused so far."""
+        ref = C.c_int64()
+        _check(_lib.thetis_server_set_queue_limit(self._h, int(max_queued), C.byref(ref)))
+        return int(ref.value)
 
     def poll(self, rid):
         """None while pending; else (labels, x, result dict)."""

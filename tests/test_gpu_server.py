@@ -117,3 +117,75 @@ def test_to_tolerance_in_batches():
         assert info["epochs_run"] == ia["epochs_run"]
         assert np.max(np.abs(x - h.get_x()[:len(x)])) <= X_TOL
     sv.close()
+
+
+def test_results_return_as_their_instances_finish():
+    """Continuous batching: a worker's batch is solved by the instance-resident
+    engine, which publishes every request the moment its own CTA finishes --
+    requests that converge early in a batch come back before the batch's
+    slowest request, and each equals its solve alone."""
+    T = gpu()
+    rng = np.random.default_rng(11)
+    reqs = []
+    for t in range(12):
+        n = int(rng.integers(2000, 4000))
+        kind = "vc" if t % 3 else "is"  # IS needs about twice the epochs of VC here
+        g = synth.er_graph(n, int(n * 4), int(rng.integers(1 << 30)))
+        g.w = synth.int_weights(n, 1, 10, rng)
+        reqs.append((kind, g))
+    sv = T.Server(budget_bytes=8 << 30, workers=1, max_batch=16)
+    ids = [sv.submit(k, g, beta=100.0, epochs=5000, tol=1e-3, refresh_every=20, seed=3) for k, g in reqs]
+    res = _wait(sv, ids)
+    lat = np.array([res[i][2]["latency_ms"] for i in ids])
+    ep = np.array([res[i][2]["epochs_run"] for i in ids])
+    assert max(res[i][2]["batch_size"] for i in ids) > 1
+    # within the batch the fastest-converging requests return well before the slowest
+    assert lat.min() < 0.8 * lat.max(), lat
+    assert np.corrcoef(ep, lat)[0, 1] > 0.5, (ep, lat)
+    for (kind, g), i in zip(reqs, ids):
+        lab, x, info = res[i]
+        assert info["status"] == T.THETIS_OK and info["valid"], info["message"]
+        h = build_gpu(kind, g, seed=3)
+        ia = h.solve(beta=100.0, epochs=5000, tol=1e-3, refresh_every=20)
+        assert info["epochs_run"] == ia["epochs_run"]
+        assert abs(info["rho"] - ia["rho"]) <= 1e-6
+        assert np.max(np.abs(x - h.get_x())) <= X_TOL
+        lp = oracle.build_problem(kind, g)
+        xv = x.astype(np.float64)
+        r = lp.round_vc(xv) if kind == "vc" else lp.round_is(xv, 3, 10)
+        assert np.array_equal(lab, r["labels"])
+    sv.close()
+
+
+def test_multiway_cut_heavy_mix_equals_alone():
+    """A mix where most requests are multiway cuts (solved one per worker on
+    the whole GPU) next to batched VC / IS requests: every result equals its
+    solve alone."""
+    T = gpu()
+    rng = np.random.default_rng(17)
+    reqs = []
+    for t in range(14):
+        if t % 5 < 3:
+            side = int(rng.integers(8, 28))
+            reqs.append(("mc", synth.grid_graph(side, side, 4, int(rng.integers(1 << 30)))))
+        else:
+            n = int(rng.integers(100, 2000))
+            g = synth.er_graph(n, int(n * 3), int(rng.integers(1 << 30)))
+            g.w = synth.int_weights(n, 1, 10, rng)
+            reqs.append(("vc" if t % 2 else "is", g))
+    sv = T.Server(budget_bytes=8 << 30, workers=3, max_batch=8)
+    ids = [sv.submit(k, g, beta=100.0, epochs=30, tol=0.0, refresh_every=10, seed=5, reps=6) for k, g in reqs]
+    res = _wait(sv, ids)
+    for (kind, g), i in zip(reqs, ids):
+        lab, x, info = res[i]
+        assert info["status"] in (T.THETIS_OK, T.THETIS_NOT_CONVERGED) and info["valid"], info["message"]
+        h = build_gpu(kind, g, seed=5)
+        h.solve(beta=100.0, epochs=30, refresh_every=10)
+        lab_a, info_a = h.round(seed=5, reps=6)
+        xa = h.get_x()
+        assert np.max(np.abs(x - xa[:len(x)])) <= X_TOL
+        lp = oracle.build_problem(kind, g)
+        xv = x.astype(np.float64)
+        r = lp.round_vc(xv) if kind == "vc" else (lp.round_is(xv, 5, 6) if kind == "is" else lp.round_mc(xv, 5, 6))
+        assert np.array_equal(lab, r["labels"])
+    sv.close()
