@@ -508,6 +508,10 @@ def thetis_server_stats(server: Server):
     return server.stats()
 
 
+def thetis_server_set_queue_limit(server: Server, max_queued):
+    return server.set_queue_limit(max_queued)
+
+
 def thetis_server_destroy(server: Server):
     server.close()
 
