@@ -404,18 +404,17 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
       P.epoch_graph = nullptr;
     }
     cudaGraph_t g;
-    uint64_t l0 = launch_count();
     TH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    begin_capture_count();
     try {
       run_epoch(P, a, ub, xb);
     } catch (...) {
+      end_capture_count();
       cudaStreamEndCapture(s, &g);
       throw;
     }
+    h->graph_launches = (int64_t)end_capture_count();  // nothing ran during capture
     TH_CUDA(cudaStreamEndCapture(s, &g));
-    uint64_t l1 = launch_count();
-    h->graph_launches = (int64_t)(l1 - l0);
-    count_launch((uint64_t)0 - (l1 - l0));  // nothing ran during capture
     cudaError_t e = cudaGraphInstantiate(&P.epoch_graph, g, 0);
     cudaGraphDestroy(g);
     TH_CUDA(e);

@@ -47,6 +47,10 @@ void count_launch(uint64_t n = 1);
 bool coop_allowed();
 void set_coop_allowed(bool on);
 uint64_t launch_count();
+// launches recorded into a stream capture by this thread (not counted until
+// the graph is replayed)
+void begin_capture_count();
+uint64_t end_capture_count();
 
 #define TH_LAUNCHED() ::thetis::count_launch(1)
 

@@ -37,8 +37,23 @@ bool coop_allowed() { return g_coop; }
 void set_coop_allowed(bool on) { g_coop = on; }
 
 static std::atomic<uint64_t> g_launches{0};
-void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// while this thread records a stream capture its launches run later (as graph
+// replays): they go to a per-thread tally instead of the global count
+static thread_local bool g_capturing = false;
+static thread_local uint64_t g_captured = 0;
+void count_launch(uint64_t n) {
+  if (g_capturing) g_captured += n;
+  else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void begin_capture_count() {
+  g_capturing = true;
+  g_captured = 0;
+}
+uint64_t end_capture_count() {
+  g_capturing = false;
+  return g_captured;
+}
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int64
