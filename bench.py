@@ -493,7 +493,12 @@ def run_batched(args, wl, ws, rank, local):
     def step(a, out, t_start=None):
         pre = torch.cuda.Event(enable_timing=True)
         h = T.thetis_build_batch(a["kinds"], a["noff"], a["eoff"], a["eu"], a["ev"], a["w"], seed=0, stream=stream)
-        shape["lanes_per_column"], shape["clusters"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
+        if args.launch_shape:
+            lanes, cl = (int(v) for v in args.launch_shape.split(","))
+            T.thetis_set_batch_shape(h, lanes, cl)
+            shape["lanes_per_column"], shape["clusters"] = lanes, cl
+        else:
+            shape["lanes_per_column"], shape["clusters"] = T.thetis_autotune(h, beta=wl["beta"])  # cached per shape
         pre.record(stream)
         # solve + repair + rounding + validity; each instance is rounded by its
         # own CTA / cluster the moment it stops
@@ -1110,6 +1115,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true", help="batched default: skip the single-instance extra keys")
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="serving: seconds per load point (0: workload's)")
+    ap.add_argument("--launch-shape", default="",
+                    help="batched: 'lanes,clusters' instead of the autotuned shape (e.g. to profile the shape "
+                         "an unprofiled run chose: the tuner's timings mean nothing under a profiler)")
     args = ap.parse_args()
     ws, rank, local = dist_setup(args)
     wl = WORKLOADS[args.workload]

@@ -4,7 +4,7 @@
 // The union sweep (scd.cu) advances every unfinished instance once per epoch,
 // so each epoch streams the residual r of the whole batch (gigabytes) through
 // HBM with scattered 4-byte accesses.  Here every instance is solved from
-// start to stop by one CTA, or by one thread-block cluster of 2 or 4 CTAs,
+// start to stop by one CTA, or by one thread-block cluster of 2, 3 or 4 CTAs,
 // that keeps the instance's residual r and iterate x in shared memory
 // (distributed over the cluster's CTAs, reached with ld/st.shared::cluster):
 //
@@ -486,7 +486,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       float acc = 0.f;
 #pragma unroll
       for (int u = 0; u < NC; ++u) acc += cr[u];
-      for (uint32_t p = p0 + gl + NC * GG; p < p1; p += GG) acc += rget(Ient[p]);
+      for (uint32_t p = p0 + gl + NC * GG; p < p1; p += 4 * GG) {
+        uint32_t et[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) et[v] = (p + v * GG < p1) ? Ient[p + v * GG] : NO_ENTRY;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (et[v] != NO_ENTRY) acc += rget(et[v]);
+      }
 #pragma unroll
       for (int o = GG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, GG);
       if (!valid) continue;
@@ -499,32 +506,40 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
 #pragma unroll
         for (int u = 0; u < NC; ++u)
           if (ce[u] != NO_ENTRY) rset(ce[u], cr[u] + d);
-        for (uint32_t p = p0 + gl + NC * GG; p < p1; p += GG) {
-          const uint32_t e = Ient[p];
-          rset(e, rget(e) + d);
+        for (uint32_t p = p0 + gl + NC * GG; p < p1; p += 4 * GG) {
+          uint32_t et[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) et[v] = (p + v * GG < p1) ? Ient[p + v * GG] : NO_ENTRY;
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (et[v] != NO_ENTRY) rset(et[v], rget(et[v]) + d);
         }
       }
     }
   };
 
-  // the short columns of colour c in ELL panels: every K-th panel to this rank,
-  // one panel per warp, one column per lane
+  // the short columns of colour c in ELL panels, one panel per warp, one
+  // column per lane.  Rank q's panels (every K-th) hold its own columns of the
+  // colour (k % K == q) in stride K, so x and the rows kept by k's rank are
+  // local to it.
   auto ell_columns = [&](int c) {
-    constexpr int NE = 8;  // slots kept in registers between gather and scatter
+    constexpr int NE = (K > 1) ? 4 : 8;  // slots kept in registers between gather and scatter
+    constexpr int NB = 4;  // slots beyond NE: loaded NB at a time (independent loads in flight)
     const int64_t pf = V.pfirst[(int64_t)t * V.C + c];
     const int np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
     const int cw = V.cwide[(int64_t)t * V.C + c], cend = coff[c + 1];
+    const int first = cw + ((q - cw % K) % K + K) % K;  // this rank's first short column
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = q + K * warp; j < np; j += K * (NT / 32)) {
       const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
       const int W = V.pw[pf + j];
-      const int k = cw + j * 32 + lane;
+      const int k = first + K * (32 * (j / K) + lane);
       uint32_t ce[NE];
       float cr[NE];
 #pragma unroll
       for (int u = 0; u < NE; ++u) ce[u] = (u < W) ? pe[32 * u] : NO_ENTRY;
       const bool valid = k < cend;
-      const float xk = valid ? xget((uint32_t)k) : 0.f;
+      const float xk = valid ? xown_get(k) : 0.f;
       const float ck = valid ? Cc[k] : 0.f;
 #pragma unroll
       for (int u = 0; u < NE; ++u) cr[u] = (ce[u] != NO_ENTRY) ? rget(ce[u]) : 0.f;
@@ -535,25 +550,33 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         acc += cr[u];
         deg += (ce[u] != NO_ENTRY) ? 1 : 0;
       }
-      for (int u = NE; u < W; ++u) {
-        const uint32_t e = pe[32 * u];
-        if (e != NO_ENTRY) {
-          acc += rget(e);
-          ++deg;
-        }
+      for (int u0 = NE; u0 < W; u0 += NB) {
+        uint32_t et[NB];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) et[v] = (u0 + v < W) ? pe[32 * (u0 + v)] : NO_ENTRY;
+#pragma unroll
+        for (int v = 0; v < NB; ++v)
+          if (et[v] != NO_ENTRY) {
+            acc += rget(et[v]);
+            ++deg;
+          }
       }
       if (!valid) continue;
       const float g = ck + beta * acc + xk * ib;
       const float xn = fminf(fmaxf(xk - g * s_invL[deg], V.lo), V.hi);
       const float d = xn - xk;
-      xset((uint32_t)k, xn);
+      xown_set(k, xn);
       if (d != 0.f) {
 #pragma unroll
         for (int u = 0; u < NE; ++u)
           if (ce[u] != NO_ENTRY) rset(ce[u], cr[u] + d);
-        for (int u = NE; u < W; ++u) {
-          const uint32_t e = pe[32 * u];
-          if (e != NO_ENTRY) rset(e, rget(e) + d);
+        for (int u0 = NE; u0 < W; u0 += NB) {
+          uint32_t et[NB];
+#pragma unroll
+          for (int v = 0; v < NB; ++v) et[v] = (u0 + v < W) ? pe[32 * (u0 + v)] : NO_ENTRY;
+#pragma unroll
+          for (int v = 0; v < NB; ++v)
+            if (et[v] != NO_ENTRY) rset(et[v], rget(et[v]) + d);
         }
       }
     }
@@ -850,8 +873,16 @@ __global__ void k_inst_ucolour(const int64_t* cstart, int C1, int64_t Ns, uint32
 
 // first short column (at most 32 entries) of every colour of every instance,
 // and the ELL panels of 32 short columns each colour takes
+// ELL panels of a colour's short columns [cw, end) on K ranks: rank r's
+// columns (k % K == r) in order, 32 to a panel; panel jj of rank r is panel
+// jj * K + r of the colour, and every rank gets the same panel count (the
+// last ones may be empty).
+__device__ __forceinline__ int64_t ell_rank_first(int64_t cw, int64_t r, int64_t K) {
+  return cw + ((r - cw % K) % K + K) % K;
+}
+
 __global__ void k_inst_wide(const uint32_t* i_col, const int64_t* colptr, const int64_t* noff, const int32_t* coff,
-                            int64_t count, int C1, int32_t* cwide, int64_t* npan) {
+                            const uint8_t* iK, int64_t count, int C1, int32_t* cwide, int64_t* npan) {
   GSTRIDE(f, count * C1) {
     const int64_t t = f / C1;
     const int c = (int)(f % C1);
@@ -869,14 +900,16 @@ __global__ void k_inst_wide(const uint32_t* i_col, const int64_t* colptr, const 
       else hi = mid;
     }
     cwide[f] = (int32_t)(lo - noff[t]);
-    npan[f] = (end - lo + 31) / 32;
+    const int64_t K = iK[t], per_rank = (end - lo + K - 1) / K;
+    npan[f] = K * ((per_rank + 31) / 32);
   }
 }
 
-// per panel: its width (the length of its first, longest column) and its slot count
-__global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const uint32_t* i_col,
-                              const int64_t* colptr, const int64_t* noff, int64_t nf, int C1, int64_t npanels,
-                              uint8_t* pw, int64_t* pslots) {
+// per panel: its width (the length of its first, longest column; 0 for an
+// empty one) and its slot count
+__global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const int32_t* coff, const uint8_t* iK,
+                              const uint32_t* i_col, const int64_t* colptr, const int64_t* noff, int64_t nf, int C1,
+                              int64_t npanels, uint8_t* pw, int64_t* pslots) {
   GSTRIDE(p, npanels) {
     int64_t lo = 0, hi = nf;  // the last f with pfirst[f] <= p (f with panels)
     while (hi - lo > 1) {
@@ -885,10 +918,13 @@ __global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const
       else hi = mid;
     }
     while (lo + 1 < nf && pfirst[lo + 1] <= p) ++lo;
-    const int64_t t = lo / C1;
-    const int64_t k0 = noff[t] + cwide[lo] + 32 * (p - pfirst[lo]);
-    const uint32_t j = i_col[k0];
-    const int w = (int)(colptr[j + 1] - colptr[j]);
+    const int64_t t = lo / C1, K = iK[t], jp = p - pfirst[lo];
+    const int64_t k0 = ell_rank_first(cwide[lo], jp % K, K) + K * 32 * (jp / K);
+    int w = 0;
+    if (k0 < coff[lo + 1]) {
+      const uint32_t j = i_col[noff[t] + k0];
+      w = (int)(colptr[j + 1] - colptr[j]);
+    }
     pw[p] = (uint8_t)w;
     pslots[p] = 32 * (int64_t)w;
   }
@@ -896,18 +932,19 @@ __global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const
 
 // ELL slots of every short column (CSR entries of the IML column, in order)
 __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const uint32_t* ucolour,
-                           const int64_t* noff, const int64_t* eoff, const uint32_t* iend, const uint32_t* ient,
-                           const int32_t* cwide, const int64_t* pfirst, const int64_t* pbase, int64_t Ns, int C1,
-                           uint32_t* ell) {
+                           const uint8_t* iK, const int64_t* noff, const int64_t* eoff, const uint32_t* iend,
+                           const uint32_t* ient, const int32_t* cwide, const int64_t* pfirst, const int64_t* pbase,
+                           int64_t Ns, int C1, uint32_t* ell) {
   GSTRIDE(k, Ns) {
     const uint32_t j = i_col[k];
     const int64_t t = inst_col[j];
     const int64_t f = t * C1 + ucolour[j];
     const int64_t loc = k - noff[t];
-    const int64_t o = loc - cwide[f];
-    if (o < 0) continue;  // a long column: served through the CSR
-    const int64_t p = pfirst[f] + o / 32;
-    const int lane = (int)(o % 32);
+    if (loc < cwide[f]) continue;  // a long column: served through the CSR
+    const int64_t K = iK[t], r = loc % K;
+    const int64_t i = (loc - ell_rank_first(cwide[f], r, K)) / K;  // its place among rank r's short columns
+    const int64_t p = pfirst[f] + (i / 32) * K + r;
+    const int lane = (int)(i % 32);
     const uint32_t e1 = iend[k];
     const uint32_t e0 = (loc == 0) ? 0u : iend[k - 1];
     const int64_t src = 2 * eoff[t];
@@ -947,7 +984,7 @@ __global__ void k_inst_rowrank(const int64_t* rowptr, const uint32_t* colidx, co
       const int64_t q0 = rowptr[i];
       const uint32_t a = lcol[idx_of(colidx[q0])], b = lcol[idx_of(colidx[q0 + 1])];
       const uint32_t h = (uint32_t)((uint64_t)i * 0x9E3779B97F4A7C15ull >> 40);
-      r = ((h & 1u) ? a : b) & (K - 1);
+      r = ((h & 1u) ? a : b) % K;
     }
     rank[i] = r;
     vals[i] = (uint32_t)i;
@@ -1106,19 +1143,19 @@ int bits_for_count(int64_t n) {
   return b;
 }
 
-// launch classes: (cluster size, threads per CTA); an instance goes to the
-// first class whose shared-memory budget per CTA holds its chunk of r and x.
-// The last class takes what fits none: one CTA of 1024 threads with x and the
-// rows beyond its shared memory in global memory (L2).  The cluster classes
-// (r and x spread over 2 or 4 CTAs' shared memory) are used only when the
-// handle asks for them (measured slower on GB300: remote shared-memory
-// accesses cost more than L2 hits here).
+// launch classes: (cluster size, threads per CTA).  An instance takes one CTA
+// of 256, 512 or 1024 threads when its r and x fit that CTA's shared memory,
+// else one CTA with x in global memory when r alone fits, else the smallest
+// cluster of 2, 3 or 4 CTAs whose shared memory holds them (distributed
+// shared memory; on by default, the autotuner may switch it off), else the
+// last class: one CTA of 1024 threads with x and the rows beyond its shared
+// memory in global memory (L2), measured slower than the clusters.
 struct Cls {
   int K, NT;
 };
-constexpr Cls CLASSES[] = {{1, 256}, {1, 512}, {1, 1024}, {2, 1024}, {4, 1024}, {1, 1024}};
-constexpr int NCLS = 6;
-constexpr int CLS_SPILL = 5;
+constexpr Cls CLASSES[] = {{1, 256}, {1, 512}, {1, 1024}, {2, 1024}, {3, 1024}, {4, 1024}, {1, 1024}};
+constexpr int NCLS = 7;
+constexpr int CLS_SPILL = 6;
 
 // shared memory of an instance on K CTAs: its r region (at least the
 // rounding's two bit words per 32 columns) and its x
@@ -1183,8 +1220,10 @@ void launch_class(int c, const InstView& V, const int32_t* order, int64_t count,
     case 0: launch_one<1, 256, G>(V, order, count, smem, optin, st); break;
     case 1: launch_one<1, 512, G>(V, order, count, smem, optin, st); break;
     case 2: launch_one<1, 1024, G>(V, order, count, smem, optin, st); break;
-    case 3: launch_one<2, 1024, 8>(V, order, count, smem, optin, st); break;  // clusters: 8 lanes
-    case 4: launch_one<4, 1024, 8>(V, order, count, smem, optin, st); break;
+    // clusters: one column per lane (ELL) or 8 lanes per column
+    case 3: launch_one<2, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
+    case 4: launch_one<3, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
+    case 5: launch_one<4, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
     default: launch_one<1, 1024, G, true>(V, order, count, smem, optin, st); break;
   }
 }
@@ -1210,7 +1249,8 @@ void inst_classes(Problem& P) {
       auto est = [&](int K) { return 4 * ((m * 105 / 100) / K + 256 + (n + K - 1) / K); };
       if (4 * m <= class_cap(L, CLS_SPILL)) c = CLS_SPILL;
       else if (clusters && est(2) <= class_cap(L, 3)) c = 3;
-      else if (clusters && est(4) <= class_cap(L, 4)) c = 4;
+      else if (clusters && est(3) <= class_cap(L, 4)) c = 4;
+      else if (clusters && est(4) <= class_cap(L, 5)) c = 5;
       else c = CLS_SPILL;
     }
     TH_CHECK(c != CLS_SPILL || 4 * 2 * ((n + 31) / 32) <= class_cap(L, CLS_SPILL), THETIS_E_INVALID,
@@ -1375,30 +1415,39 @@ void inst_layout(Problem& P) {
     const int64_t nf = count * C1;
     once(P.i_cwide, nf);
     int64_t* npan = tmp.alloc<int64_t>(nf + 1);
-    k_inst_wide<<<grid_for(nf, 256), 256, 0, s>>>(P.i_col, P.colptr, P.bnoff, P.i_coff, count, C1, P.i_cwide, npan);
+    k_inst_wide<<<grid_for(nf, 256), 256, 0, s>>>(P.i_col, P.colptr, P.bnoff, P.i_coff, P.i_K, count, C1, P.i_cwide,
+                                                  npan);
     TH_LAUNCHED();
     once(P.i_pfirst, nf + 1);
     exclusive_scan_i64(npan, P.i_pfirst, nf, tmp, s);
     int64_t npanels = 0;
     TH_CUDA(cudaMemcpyAsync(&npanels, P.i_pfirst + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaStreamSynchronize(s));
-    TH_CHECK(P.i_pw == nullptr || P.i_npanels == npanels, THETIS_E_CUDA, "instance engine: panel count changed");
+    // the panels depend on the cluster sizes: a layout rebuilt for other sizes
+    // may need more of them (the handle's arena keeps the smaller arrays until
+    // it is closed)
     P.i_npanels = npanels;
-    once(P.i_pw, npanels + 1);
-    once(P.i_pbase, npanels + 1);
+    if (npanels + 1 > P.i_pcap) {
+      P.i_pw = P.mem.alloc<uint8_t>(npanels + 1);
+      P.i_pbase = P.mem.alloc<int64_t>(npanels + 1);
+      P.i_pcap = npanels + 1;
+    }
     if (npanels > 0) {
-      k_inst_panels<<<grid_for(npanels, 256), 256, 0, s>>>(P.i_pfirst, P.i_cwide, P.i_col, P.colptr, P.bnoff, nf, C1,
-                                                           npanels, P.i_pw, P.i_pbase);
+      k_inst_panels<<<grid_for(npanels, 256), 256, 0, s>>>(P.i_pfirst, P.i_cwide, P.i_coff, P.i_K, P.i_col, P.colptr,
+                                                           P.bnoff, nf, C1, npanels, P.i_pw, P.i_pbase);
       TH_LAUNCHED();
     }
     exclusive_scan_i64(P.i_pbase, P.i_pbase, npanels, tmp, s);
     int64_t nslots = 0;
     TH_CUDA(cudaMemcpyAsync(&nslots, P.i_pbase + npanels, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TH_CUDA(cudaStreamSynchronize(s));
-    once(P.i_ell, nslots + 1);
+    if (nslots + 1 > P.i_scap) {
+      P.i_ell = P.mem.alloc<uint32_t>(nslots + 1);
+      P.i_scap = nslots + 1;
+    }
     TH_CUDA(cudaMemsetAsync(P.i_ell, 0xff, (nslots + 1) * sizeof(uint32_t), s));
-    k_inst_ell<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, ucolour, P.bnoff, P.beoff, P.i_end, P.i_ent,
-                                                 P.i_cwide, P.i_pfirst, P.i_pbase, Ns, C1, P.i_ell);
+    k_inst_ell<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, ucolour, P.i_K, P.bnoff, P.beoff, P.i_end,
+                                                 P.i_ent, P.i_cwide, P.i_pfirst, P.i_pbase, Ns, C1, P.i_ell);
     TH_LAUNCHED();
   }
   once(P.i_c, Ns + 1);

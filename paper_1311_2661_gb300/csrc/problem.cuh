@@ -148,6 +148,7 @@ struct Problem {
   uint8_t* i_pw = nullptr;          // per panel: slots per column
   uint32_t* i_ell = nullptr;        // ELL slots of the short columns (local rows)
   int64_t i_npanels = 0;
+  int64_t i_pcap = 0, i_scap = 0;  // allocated panels / ELL slots
   int32_t* i_deg = nullptr;         // count: largest column length of the instance
   float *i_c = nullptr, *i_x = nullptr, *i_s = nullptr;  // c, x (Ns) and s (M) in IML order
   float* i_rg = nullptr;            // M: residual rows kept in global memory (instances too large for one CTA)

@@ -136,9 +136,13 @@ def test_results_return_as_their_instances_finish():
     sv = T.Server(budget_bytes=8 << 30, workers=1, max_batch=16)
     ids = [sv.submit(k, g, beta=100.0, epochs=5000, tol=1e-3, refresh_every=20, seed=3) for k, g in reqs]
     res = _wait(sv, ids)
-    lat = np.array([res[i][2]["latency_ms"] for i in ids])
-    ep = np.array([res[i][2]["epochs_run"] for i in ids])
-    assert max(res[i][2]["batch_size"] for i in ids) > 1
+    bs = np.array([res[i][2]["batch_size"] for i in ids])
+    # the worker may take the first requests before the rest are queued: look
+    # at the largest batch (its requests were submitted together)
+    big = bs == bs.max()
+    assert bs.max() > 1 and big.sum() >= 4, bs
+    lat = np.array([res[i][2]["latency_ms"] for i in ids])[big]
+    ep = np.array([res[i][2]["epochs_run"] for i in ids])[big]
     # within the batch the fastest-converging requests return well before the slowest
     assert lat.min() < 0.8 * lat.max(), lat
     assert np.corrcoef(ep, lat)[0, 1] > 0.5, (ep, lat)
