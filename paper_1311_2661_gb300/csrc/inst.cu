@@ -44,6 +44,11 @@ namespace thetis {
 namespace {
 
 constexpr uint32_t NO_ENTRY = 0xffffffffu;
+
+// ELL slots of 16 bits, two a word: an instance on one CTA with m < 65535
+// (every instance that fits one CTA's shared memory is one); 32-bit slots
+// otherwise
+__host__ __device__ __forceinline__ bool inst_ell16(int64_t K, int64_t m) { return K == 1 && m < 65535; }
 constexpr int FIX = 58;                              // fixed point: value * 2^58
 constexpr long long FIX_ONE = 1LL << FIX;
 constexpr int FIX_SPLIT = 18;                        // column sums: high part in 2^-40 units, low 18 bits apart
@@ -186,9 +191,10 @@ struct InstView {
 // columns) and the iterate of local columns k with k % K == q at x[k / K];
 // entries name a row as (rank << 28) | position in the rank's block.  It steps
 // its slack rows (local) and, per colour, either
-//   G = 1: every K-th ELL panel of the colour's short columns, one thread per
-//          column (slot addresses follow from the panel; no index chain), and
-//          the colour's long columns one warp each, or
+//   G = 1: every K-th ELL panel of the colour's short columns (its own ones,
+//          in stride K), one thread per column (slot addresses follow from the
+//          panel; no index chain), and the colour's long columns one warp
+//          each, or
 //   G = 4 / 8: its own columns (k % K == q), G lanes each, through the CSR,
 // reaching the r (and x) of other ranks through distributed shared memory.
 template <int K, int NT, int G, bool SPILL>
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   const int t = order[blockIdx.x / K];
   const int64_t col0 = V.noff[t], row0 = V.eoff[t], ent0 = 2 * row0;
   const int n = (int)(V.noff[t + 1] - col0), m = (int)(V.eoff[t + 1] - row0);
+  const bool ell16 = inst_ell16(K, m);
   // shared memory: r of the own rows, then x of the own columns.  SPILL (one
   // CTA, an instance that does not fit): x in global memory and the first rs
   // rows of r in shared memory, the rest in V.rg (L2)
@@ -336,6 +343,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   auto rows_pass = [&](bool chk, int slot) {
     bool over = false;
     float rmax = 0.f;
+#pragma unroll 2
     for (int e = qlo + (int)threadIdx.x; e < qhi; e += NT) {
       const float xu = xget(Iru[e]), xv = xget(Irv[e]);
       const float sv = Ss[e];
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       if (over) continue;
       const float del = 0x1p-19f * ((beta * fabsf(r32) + sv * ib) / ls + fabsf(sv) + fabsf(qv)) + 0x1p-23f * tol32 +
                         1e-30f;
-      if (rho - del > tol32) {
+      if (!(rho - del <= tol32)) {  // over tol (or not finite)
         over = true;
       } else if (rho + del > tol32) {  // too close to tol for FP32: decide in FP64
         const double r64 = ex ? (double)rf * 0x1p-58 : row_f64(xu, xv, sv, sig);
@@ -375,7 +383,11 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     if (chk && rmax > 0.f) atomicMax(&s_rho[slot], __float_as_uint(rmax));
   };
 
-  // the column part of the stopping test: a_j^T r from the exact row values
+  // the column part of the stopping test.  a_j^T r is summed in FP32 from
+  // the refreshed row values (each the exact row value rounded once), so
+  // |sum - a_j^T r| <= 2^-23 (deg + 2) sum |r_i| bounds it; rho is decided
+  // from that estimate unless it lies within the bound of tol, and then from
+  // the exact sum (2^-58 fixed point) in FP64.
   auto cols_check = [&](int slot) {
     const int cnt = (n > q) ? (n - q + K - 1) / K : 0;
     constexpr int PW = 32 / GC;
@@ -394,58 +406,57 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         xk = xown_get(k);
         ck = Cc[k];
       }
-      long long hi = 0, lo = 0;
-      int bad = (valid && !fix_ok(xk)) ? 1 : 0;
-      const long long fk = fix58(xk);
-      for (uint32_t p = p0 + gl; p < p1; p += GC) {
-        const uint32_t e = row_of(Ient[p]);
-        const float xw = xget(Inb[p]);
-        const float sv = __ldcg(Ss + e);
-        if (!(fix_ok(xw) && fix_ok(sv))) {
-          bad = 1;
-          continue;
-        }
-        const long long fs = fix58(sv);
-        const long long rf = fk + fix58(xw) + (sig > 0.f ? fs : -fs) - FIX_ONE;
-        hi += rf >> FIX_SPLIT;
-        lo += rf & ((1LL << FIX_SPLIT) - 1);
+      float sum = 0.f, sabs = 0.f;
+      for (uint32_t p = p0 + gl; p < p1; p += 4 * GC) {
+        uint32_t et[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) et[v] = (p + v * GC < p1) ? Ient[p + v * GC] : NO_ENTRY;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (et[v] != NO_ENTRY) {
+            const float rv = rget(et[v]);
+            sum += rv;
+            sabs += fabsf(rv);
+          }
       }
 #pragma unroll
       for (int o = GC / 2; o > 0; o >>= 1) {
-        hi += __shfl_xor_sync(0xffffffffu, hi, o, GC);
-        lo += __shfl_xor_sync(0xffffffffu, lo, o, GC);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o, GC);
+        sum += __shfl_xor_sync(0xffffffffu, sum, o, GC);
+        sabs += __shfl_xor_sync(0xffffffffu, sabs, o, GC);
       }
       if (!valid || gl != 0) continue;
-      const float deg = (float)(p1 - p0);
-      const float L = fmaf(beta, deg, ib);
-      bool exact = bad != 0;
-      if (!exact) {
-        const float sum = __ll2float_rn(hi) * 0x1p-40f;  // the low parts add < deg * 2^-40
-        const float g = ck + beta * sum + xk * ib;
-        const float qv = g / L;
-        const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
-        rmax = fmaxf(rmax, rho);
-        if (over) continue;
-        const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
-                          0x1p-39f * (1.f + deg) + 0x1p-23f * tol32 + 1e-30f;
-        if (rho - del > tol32) over = true;
-        else if (rho + del > tol32) exact = true;
-      }
-      if (exact) {  // FP64 from the exact sum (or from FP64 row values outside the fixed-point range)
-        double sum64;
-        if (!bad) {
-          sum64 = (double)hi * 0x1p-40 + (double)lo * 0x1p-58;
-        } else {
-          sum64 = 0.0;
-          for (uint32_t p = p0; p < p1; ++p) {
-            const uint32_t e = row_of(Ient[p]);
-            sum64 += row_f64(xk, xget(Inb[p]), __ldcg(Ss + e), sig);
-          }
+      const int deg = (int)(p1 - p0);
+      const float L = fmaf(beta, (float)deg, ib);
+      const float g = ck + beta * sum + xk * ib;
+      const float qv = g / L;
+      const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
+      rmax = fmaxf(rmax, rho);
+      if (over) continue;
+      const float esum = 0x1p-22f * (float)(deg + 2) * sabs;  // twice the bound above
+      const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
+                        beta * esum / L + 0x1p-23f * tol32 + 1e-30f;
+      if (!(rho - del <= tol32)) {  // over tol (or not finite)
+        over = true;
+      } else if (rho + del > tol32) {  // too close to tol for FP32: the exact sum, FP64
+        long long hi = 0, lo = 0;
+        bool bad = !fix_ok(xk);
+        const long long fk = fix58(xk);
+        double sum64 = 0.0;
+        for (uint32_t p = p0; p < p1; ++p) {
+          const uint32_t e = row_of(Ient[p]);
+          const float xw = xget(Inb[p]);
+          const float sv = __ldcg(Ss + e);
+          sum64 += row_f64(xk, xw, sv, sig);  // used when some value is outside the fixed-point range
+          if (!(fix_ok(xw) && fix_ok(sv))) bad = true;
+          const long long fs = fix58(sv);
+          const long long rf = fk + fix58(xw) + (sig > 0.f ? fs : -fs) - FIX_ONE;
+          hi += rf >> FIX_SPLIT;
+          lo += rf & ((1LL << FIX_SPLIT) - 1);
         }
+        if (!bad) sum64 = (double)hi * 0x1p-40 + (double)lo * 0x1p-58;
         const double bd = V.beta_d, ibd = 1.0 / bd;
         const double g64 = (double)ck + bd * sum64 + (double)xk * ibd;
-        const double L64 = bd * (double)(p1 - p0) + ibd;
+        const double L64 = bd * (double)deg + ibd;
         const double xn = fmin(fmax((double)xk - g64 / L64, (double)V.lo), (double)V.hi);
         if (fabs(xn - (double)xk) > V.tol) over = true;
       }
@@ -582,12 +593,89 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     }
   };
 
+  // the same for an instance on one CTA with fewer than 65535 rows: two
+  // 16-bit row ids a word, so twice the slots per load and per register (the
+  // scatter re-reads r: no other column of the colour touches the row)
+  auto ell_columns16 = [&](int c) {
+    constexpr int NW = 7;  // words (14 slots) kept in registers between gather and scatter
+    constexpr int NB = 4;  // words beyond NW: loaded NB at a time
+    constexpr uint32_t NO16 = 0xffffu;
+    const int64_t pf = V.pfirst[(int64_t)t * V.C + c];
+    const int np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
+    const int cw = V.cwide[(int64_t)t * V.C + c], cend = coff[c + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < np; j += NT / 32) {
+      const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
+      const int WW = (V.pw[pf + j] + 1) >> 1;
+      const int k = cw + j * 32 + lane;
+      uint32_t ce[NW];
+#pragma unroll
+      for (int u = 0; u < NW; ++u) ce[u] = (u < WW) ? pe[32 * u] : NO_ENTRY;
+      const bool valid = k < cend;
+      const float xk = valid ? xget((uint32_t)k) : 0.f;
+      const float ck = valid ? Cc[k] : 0.f;
+      float acc = 0.f;
+      int deg = 0;
+      auto take = [&](uint32_t e) {
+        if (e != NO16) {
+          acc += rget(e);
+          ++deg;
+        }
+      };
+#pragma unroll
+      for (int u = 0; u < NW; ++u) {
+        take(ce[u] & 0xffffu);
+        take(ce[u] >> 16);
+      }
+      for (int u0 = NW; u0 < WW; u0 += NB) {
+        uint32_t et[NB];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) et[v] = (u0 + v < WW) ? pe[32 * (u0 + v)] : NO_ENTRY;
+#pragma unroll
+        for (int v = 0; v < NB; ++v) {
+          take(et[v] & 0xffffu);
+          take(et[v] >> 16);
+        }
+      }
+      if (!valid) continue;
+      const float g = ck + beta * acc + xk * ib;
+      const float xn = fminf(fmaxf(xk - g * s_invL[deg], V.lo), V.hi);
+      const float d = xn - xk;
+      xset((uint32_t)k, xn);
+      if (d != 0.f) {
+        auto put = [&](uint32_t e) {
+          if (e != NO16) rset(e, rget(e) + d);
+        };
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+          put(ce[u] & 0xffffu);
+          put(ce[u] >> 16);
+        }
+        for (int u0 = NW; u0 < WW; u0 += NB) {
+          uint32_t et[NB];
+#pragma unroll
+          for (int v = 0; v < NB; ++v) et[v] = (u0 + v < WW) ? pe[32 * (u0 + v)] : NO_ENTRY;
+#pragma unroll
+          for (int v = 0; v < NB; ++v) {
+            put(et[v] & 0xffffu);
+            put(et[v] >> 16);
+          }
+        }
+      }
+    }
+  };
+
   // one colour: its columns, then its slack rows (four per thread at a time)
   auto sweep_colour = [&](int c) {
     if constexpr (G == 1) {
       const int cw = V.cwide[(int64_t)t * V.C + c];
       if (cw > coff[c]) csr_columns(std::integral_constant<int, 32>{}, coff[c], cw);
-      ell_columns(c);
+      if constexpr (K == 1) {
+        if (SPILL && !ell16) ell_columns(c);
+        else ell_columns16(c);
+      } else {
+        ell_columns(c);
+      }
     } else {
       csr_columns(std::integral_constant<int, G>{}, coff[c], coff[c + 1]);
     }
@@ -617,11 +705,21 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // a check: exact refresh + stopping test; true when some unit has rho > tol
   int nchk = 0;
   float last_rho = 0.f;
-  auto check = [&]() -> bool {
+  // (last: no epoch follows, so rho itself is reported; otherwise the column
+  // part is skipped once a slack row is over tol)
+  auto check = [&](bool last) -> bool {
     const int slot = nchk & 1;
     ++nchk;
     rows_pass(true, slot);
-    cols_check(slot);
+    sync();  // every rank's rows refreshed before the columns read them
+    bool skip = false;
+    if constexpr (K == 1) {
+      skip = !last && s_over[slot] != 0;
+    } else if (!last) {
+#pragma unroll
+      for (int r = 0; r < K; ++r) skip |= dsm_ld_i(dsm_map(smem_u32(&s_over[slot]), (uint32_t)r)) != 0;
+    }
+    if (!skip) cols_check(slot);
     sync();
     int over = 0;
     unsigned rb_ = 0;
@@ -657,13 +755,13 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     checked_last = false;
     if (ep % V.R == 0 || ep == V.epochs) {
       checked_last = true;
-      if (!check()) {
+      if (!check(ep == V.epochs)) {
         conv = true;
         break;
       }
     }
   }
-  if (!checked_last) conv = !check();
+  if (!checked_last) conv = !check(true);
   sync();
   if (V.round) {
     // -- repair and rounding of the final iterate (Sec. 2, App. B.2, App. C) --
@@ -839,13 +937,6 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
 // ---------------------------------------------------------------------------
 // instance-major layout, built once from the union layout
 // ---------------------------------------------------------------------------
-__global__ void k_inst_keys(const int32_t* inst, int64_t n, uint32_t* keys, uint32_t* vals) {
-  GSTRIDE(i, n) {
-    keys[i] = (uint32_t)inst[i];
-    vals[i] = (uint32_t)i;
-  }
-}
-
 // sort keys of the union columns: length (longest first), colour, instance
 __global__ void k_inst_key_len(const int64_t* colptr, int64_t Ns, uint32_t* keys, uint32_t* vals) {
   GSTRIDE(j, Ns) {
@@ -908,8 +999,8 @@ __global__ void k_inst_wide(const uint32_t* i_col, const int64_t* colptr, const 
 // per panel: its width (the length of its first, longest column; 0 for an
 // empty one) and its slot count
 __global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const int32_t* coff, const uint8_t* iK,
-                              const uint32_t* i_col, const int64_t* colptr, const int64_t* noff, int64_t nf, int C1,
-                              int64_t npanels, uint8_t* pw, int64_t* pslots) {
+                              const uint32_t* i_col, const int64_t* colptr, const int64_t* noff, const int64_t* eoff,
+                              int64_t nf, int C1, int64_t npanels, uint8_t* pw, int64_t* pslots) {
   GSTRIDE(p, npanels) {
     int64_t lo = 0, hi = nf;  // the last f with pfirst[f] <= p (f with panels)
     while (hi - lo > 1) {
@@ -926,7 +1017,7 @@ __global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const
       w = (int)(colptr[j + 1] - colptr[j]);
     }
     pw[p] = (uint8_t)w;
-    pslots[p] = 32 * (int64_t)w;
+    pslots[p] = 32 * (int64_t)(inst_ell16(K, eoff[t + 1] - eoff[t]) ? (w + 1) / 2 : w);  // in 32-bit words
   }
 }
 
@@ -948,7 +1039,14 @@ __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const
     const uint32_t e1 = iend[k];
     const uint32_t e0 = (loc == 0) ? 0u : iend[k - 1];
     const int64_t src = 2 * eoff[t];
-    for (uint32_t q = e0; q < e1; ++q) ell[pbase[p] + 32 * (int64_t)(q - e0) + lane] = ient[src + q];
+    if (inst_ell16(K, eoff[t + 1] - eoff[t])) {  // slots 2w, 2w + 1 in word w (low half first)
+      for (uint32_t q = e0; q < e1; q += 2) {
+        const uint32_t lo = ient[src + q], hi = (q + 1 < e1) ? ient[src + q + 1] : 0xffffu;
+        ell[pbase[p] + 32 * (int64_t)((q - e0) / 2) + lane] = lo | (hi << 16);
+      }
+    } else {
+      for (uint32_t q = e0; q < e1; ++q) ell[pbase[p] + 32 * (int64_t)(q - e0) + lane] = ient[src + q];
+    }
   }
 }
 
@@ -1255,6 +1353,8 @@ void inst_classes(Problem& P) {
     }
     TH_CHECK(c != CLS_SPILL || 4 * 2 * ((n + 31) / 32) <= class_cap(L, CLS_SPILL), THETIS_E_INVALID,
              "instance engine: an instance with more vertices than one CTA's rounding scratch holds");
+    // the kernels of classes 0-2 read 16-bit ELL slots only
+    TH_CHECK(c > 2 || inst_ell16(1, m), THETIS_E_INVALID, "instance engine: a one-CTA instance with 65535 rows or more");
     members[c].push_back((int32_t)t);
     iK[t] = (uint8_t)CLASSES[c].K;
   }
@@ -1434,7 +1534,7 @@ void inst_layout(Problem& P) {
     }
     if (npanels > 0) {
       k_inst_panels<<<grid_for(npanels, 256), 256, 0, s>>>(P.i_pfirst, P.i_cwide, P.i_coff, P.i_K, P.i_col, P.colptr,
-                                                           P.bnoff, nf, C1, npanels, P.i_pw, P.i_pbase);
+                                                           P.bnoff, P.beoff, nf, C1, npanels, P.i_pw, P.i_pbase);
       TH_LAUNCHED();
     }
     exclusive_scan_i64(P.i_pbase, P.i_pbase, npanels, tmp, s);
