@@ -45,10 +45,10 @@ namespace {
 
 constexpr uint32_t NO_ENTRY = 0xffffffffu;
 
-// ELL slots of 16 bits, two a word: an instance on one CTA with m < 65535
-// (every instance that fits one CTA's shared memory is one); 32-bit slots
-// otherwise
-__host__ __device__ __forceinline__ bool inst_ell16(int64_t K, int64_t m) { return K == 1 && m < 65535; }
+// ELL slots of 16 bits, two a word, holding a shared-memory index: every
+// cluster instance, and a one-CTA instance with m < 65535 (every instance
+// that fits one CTA's shared memory is one); 32-bit local rows otherwise
+__host__ __device__ __forceinline__ bool inst_ell16(int64_t K, int64_t m) { return K > 1 || m < 65535; }
 constexpr int FIX = 58;                              // fixed point: value * 2^58
 constexpr long long FIX_ONE = 1LL << FIX;
 constexpr int FIX_SPLIT = 18;                        // column sums: high part in 2^-40 units, low 18 bits apart
@@ -94,7 +94,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint32_t dsm_map(uint32_t a, uint32_t rank) {
   uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));  // pure: the compiler may reuse it
   return r;
 }
 __device__ __forceinline__ float dsm_ld(uint32_t a) {
@@ -151,7 +151,19 @@ struct InstView {
   const int64_t* pfirst; // count * C + 1: first ELL panel of every colour (panels of 32 short columns)
   const int64_t* pbase;  // per panel: first ELL slot (slot s of lane l at pbase + 32 s + l)
   const uint8_t* pw;     // per panel: slots (its longest column)
-  const uint32_t* ell;   // ELL slots: local row, or NO_ENTRY
+  const uint32_t* ell;   // ELL slots: shared-memory index of the row (16 bits, two a word; a cluster
+                         // instance's rows of other ranks: their halo copies), or all ones; 32-bit local
+                         // rows for a one-CTA instance of 65535 rows or more
+  // cluster instances (K > 1): rank q keeps its rows in halo-group order --
+  // first those no other rank's short column reads, then per (accessor rank
+  // A, accessor colour c) the contiguous segment R(q, A, c)
+  const uint32_t* rpos;  // per local row: its place in its rank's block of r
+  const uint32_t* rrow;  // per place (rank block starts at qoff[q]): the local row
+  const int32_t* hs;     // count * 4 * 4 * C: start of R(q, A, c) in rank q's block
+  const int32_t* hl;     // count * 4 * 4 * C: its length
+  const int32_t* hoff;   // count * 4 * C * 4: where R(A, q, c) sits in rank q's halo buffer of colour c
+  const int32_t* hH;     // count: halo buffer length
+  const uint8_t* hnb;    // count: halo buffers (2: colour parity, one barrier a colour; 1: two barriers)
   const int32_t* ideg;   // count: longest column of the instance
   const uint8_t* kind;   // count: THETIS_ROUND_VC / _IS
   const float* c;        // IML column costs
@@ -188,17 +200,21 @@ struct InstView {
 // ---------------------------------------------------------------------------
 // Rank q of the cluster holds the residual of its block of local rows
 // [qoff[q], qoff[q + 1]) (each row kept by a rank that steps one of its two
-// columns) and the iterate of local columns k with k % K == q at x[k / K];
-// entries name a row as (rank << 28) | position in the rank's block.  It steps
-// its slack rows (local) and, per colour, either
+// columns; in halo-group order, V.rpos) and the iterate of local columns k
+// with k % K == q at x[k / K]; CSR entries name a row as (rank << 28) |
+// place in the rank's block.  It steps its slack rows (local) and, per
+// colour, either
 //   G = 1: every K-th ELL panel of the colour's short columns (its own ones,
 //          in stride K), one thread per column (slot addresses follow from the
 //          panel; no index chain), and the colour's long columns one warp
 //          each, or
-//   G = 4 / 8: its own columns (k % K == q), G lanes each, through the CSR,
-// reaching the r (and x) of other ranks through distributed shared memory.
+//   G = 4 / 8 (one CTA only): its columns, G lanes each, through the CSR.
+// A cluster's short columns read other ranks' rows from halo copies that the
+// ranks exchange between colours (see halo); its long columns and the checks
+// reach other ranks' r and x through distributed shared memory.
 template <int K, int NT, int G, bool SPILL>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstView V, const int32_t* order) {
+  static_assert(K == 1 || (G == 1 && !SPILL), "a cluster steps its short columns through ELL panels and halos");
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_over[2];
   __shared__ unsigned s_rho[2];  // the largest rho of the check (FP32 bits, non-negative)
@@ -235,6 +251,11 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   float* sr = smem;
   float* sx = smem + rr;
   float* rgl = V.rg + row0;
+  // cluster: the halo buffer(s) after x
+  const int hb = rr + (n + K - 1) / K;
+  const int H = (K > 1) ? V.hH[t] : 0;
+  const int nbuf = (K > 1) ? V.hnb[t] : 0;  // the halo buffer of colour c: hb + (nbuf == 2 ? (c & 1) H : 0)
+  const uint32_t* Rpos = V.rpos + row0;
   // the instance's arrays (32-bit local indices from here on)
   float* Sx = V.x + col0;
   const float* Cc = V.c + col0;
@@ -262,19 +283,13 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   __shared__ float s_invL[33];
   const float inv_ls = 1.f / ((lfix > 0.f) ? lfix : beta + ib);
   if (threadIdx.x <= 32) s_invL[threadIdx.x] = 1.f / ((lfix > 0.f) ? lfix : fmaf(beta, (float)threadIdx.x, ib));
-  uint32_t rb[K], xb[K];
-  if constexpr (K > 1) {
-    const uint32_t ra = smem_u32(sr), xa = smem_u32(sx);
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-      rb[r] = dsm_map(ra, (uint32_t)r);
-      xb[r] = dsm_map(xa, (uint32_t)r);
-    }
-  }
+  // rank r's copy of a shared-memory word of this CTA (mapped on use: no
+  // registers held for the other ranks' bases)
+  const uint32_t ra = smem_u32(sr), xa = smem_u32(sx);
   auto rget = [&](uint32_t e) -> float {
     if constexpr (SPILL) return ((int)e < rs) ? sr[e] : rgl[e];
     else if constexpr (K == 1) return sr[e];
-    else return dsm_ld(pick<K>(rb, e >> 28) + 4u * (e & 0x0fffffffu));
+    else return dsm_ld(dsm_map(ra + 4u * (e & 0x0fffffffu), e >> 28));
   };
   auto rset = [&](uint32_t e, float v) {
     if constexpr (SPILL) {
@@ -283,18 +298,18 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     } else if constexpr (K == 1) {
       sr[e] = v;
     } else {
-      dsm_st(pick<K>(rb, e >> 28) + 4u * (e & 0x0fffffffu), v);
+      dsm_st(dsm_map(ra + 4u * (e & 0x0fffffffu), e >> 28), v);
     }
   };
   // local row of an entry's encoded row id
   auto row_of = [&](uint32_t e) -> uint32_t {
     if constexpr (K == 1) return e;
-    else return (uint32_t)qv[e >> 28] + (e & 0x0fffffffu);
+    else return V.rrow[row0 + qv[e >> 28] + (e & 0x0fffffffu)];
   };
   auto xget = [&](uint32_t k) -> float {
     if constexpr (SPILL) return xs ? sx[k] : Sx[k];
     else if constexpr (K == 1) return sx[k];
-    else return dsm_ld(pick<K>(xb, k % K) + 4u * (k / K));
+    else return dsm_ld(dsm_map(xa + 4u * (k / K), k % K));
   };
   auto xset = [&](uint32_t k, float v) {
     if constexpr (SPILL) {
@@ -303,17 +318,17 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     } else if constexpr (K == 1) {
       sx[k] = v;
     } else {
-      dsm_st(pick<K>(xb, k % K) + 4u * (k / K), v);
+      dsm_st(dsm_map(xa + 4u * (k / K), k % K), v);
     }
   };
   // an own row e (local id in [qlo, qhi)) / own column k (k % K == q)
   auto rown_get = [&](int e) -> float {
     if constexpr (K == 1) return rget((uint32_t)e);
-    else return sr[e - qlo];
+    else return sr[Rpos[e]];
   };
   auto rown_set = [&](int e, float v) {
     if constexpr (K == 1) rset((uint32_t)e, v);
-    else sr[e - qlo] = v;
+    else sr[Rpos[e]] = v;
   };
   auto xown_get = [&](int k) -> float {
     if constexpr (K == 1) return xget((uint32_t)k);
@@ -593,9 +608,11 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     }
   };
 
-  // the same for an instance on one CTA with fewer than 65535 rows: two
-  // 16-bit row ids a word, so twice the slots per load and per register (the
-  // scatter re-reads r: no other column of the colour touches the row)
+  // the same with 16-bit slots, two a word, so twice the slots per load and
+  // per register (the scatter re-reads r: no other column of the colour
+  // touches the row).  A slot is the row's index in shared memory: for a
+  // cluster rank its own row or the halo copy of another rank's row, so the
+  // sweep makes no remote access.
   auto ell_columns16 = [&](int c) {
     constexpr int NW = 7;  // words (14 slots) kept in registers between gather and scatter
     constexpr int NB = 4;  // words beyond NW: loaded NB at a time
@@ -603,22 +620,31 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     const int64_t pf = V.pfirst[(int64_t)t * V.C + c];
     const int np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
     const int cw = V.cwide[(int64_t)t * V.C + c], cend = coff[c + 1];
+    const int first = cw + ((q - cw % K) % K + K) % K;  // this rank's first short column
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < np; j += NT / 32) {
+    auto lr = [&](uint32_t e) -> float {
+      if constexpr (SPILL) return rget(e);
+      else return smem[e];
+    };
+    auto lw = [&](uint32_t e, float v) {
+      if constexpr (SPILL) rset(e, v);
+      else smem[e] = v;
+    };
+    for (int j = q + K * warp; j < np; j += K * (NT / 32)) {
       const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
       const int WW = (V.pw[pf + j] + 1) >> 1;
-      const int k = cw + j * 32 + lane;
+      const int k = first + K * (32 * (j / K) + lane);
       uint32_t ce[NW];
 #pragma unroll
       for (int u = 0; u < NW; ++u) ce[u] = (u < WW) ? pe[32 * u] : NO_ENTRY;
       const bool valid = k < cend;
-      const float xk = valid ? xget((uint32_t)k) : 0.f;
+      const float xk = valid ? xown_get(k) : 0.f;
       const float ck = valid ? Cc[k] : 0.f;
       float acc = 0.f;
       int deg = 0;
       auto take = [&](uint32_t e) {
         if (e != NO16) {
-          acc += rget(e);
+          acc += lr(e);
           ++deg;
         }
       };
@@ -641,10 +667,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       const float g = ck + beta * acc + xk * ib;
       const float xn = fminf(fmaxf(xk - g * s_invL[deg], V.lo), V.hi);
       const float d = xn - xk;
-      xset((uint32_t)k, xn);
+      xown_set(k, xn);
       if (d != 0.f) {
         auto put = [&](uint32_t e) {
-          if (e != NO16) rset(e, rget(e) + d);
+          if (e != NO16) lw(e, lr(e) + d);
         };
 #pragma unroll
         for (int u = 0; u < NW; ++u) {
@@ -670,12 +696,8 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     if constexpr (G == 1) {
       const int cw = V.cwide[(int64_t)t * V.C + c];
       if (cw > coff[c]) csr_columns(std::integral_constant<int, 32>{}, coff[c], cw);
-      if constexpr (K == 1) {
-        if (SPILL && !ell16) ell_columns(c);
-        else ell_columns16(c);
-      } else {
-        ell_columns(c);
-      }
+      if (SPILL && !ell16) ell_columns(c);
+      else ell_columns16(c);
     } else {
       csr_columns(std::integral_constant<int, G>{}, coff[c], coff[c + 1]);
     }
@@ -698,6 +720,37 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         const float d = sn - sv[u];
         Ss[e] = sn;
         if (d != 0.f) rown_set(e, rv[u] + sig * d);
+      }
+    }
+  };
+
+  // halo exchange of a cluster instance, between the colour's sweep and its
+  // cluster barrier: the halo copies of other ranks' rows that this rank's
+  // colour-c short columns changed go back to their keepers (c >= 0), and
+  // this rank's rows that other ranks' colour-cin short columns read go to
+  // their halo buffers (cin >= 0).  Each is one contiguous segment per pair
+  // of ranks (distributed shared memory moves those an order of magnitude
+  // faster than scattered words).  Neither touches a row any rank steps in
+  // colour c, so the copies overlap the other ranks' sweeps.
+  auto halo = [&](int c, int cin) {
+    if constexpr (K > 1) {
+      const int64_t C1 = V.C;
+#pragma unroll
+      for (int A = 0; A < K; ++A) {
+        if (A == q) continue;
+        if (c >= 0) {
+          const int len = V.hl[(((int64_t)t * 4 + A) * 4 + q) * C1 + c];
+          const float* src = smem + hb + ((nbuf == 2) ? (c & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + q) * C1 + c) * 4 + A];
+          const uint32_t dst = dsm_map(ra + 4u * (uint32_t)V.hs[(((int64_t)t * 4 + A) * 4 + q) * C1 + c], (uint32_t)A);
+          for (int i = threadIdx.x; i < len; i += NT) dsm_st(dst + 4u * i, src[i]);
+        }
+        if (cin >= 0) {
+          const int len = V.hl[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
+          const float* src = sr + V.hs[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
+          const int at = hb + ((nbuf == 2) ? (cin & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + A) * C1 + cin) * 4 + q];
+          const uint32_t dst = dsm_map(smem_u32(smem + at), (uint32_t)A);
+          for (int i = threadIdx.x; i < len; i += NT) dsm_st(dst + 4u * i, src[i]);
+        }
       }
     }
   };
@@ -744,11 +797,26 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
 
   rows_pass(false, 0);
   sync();
+  if constexpr (K > 1) {  // the first colour's halo
+    halo(-1, 0);
+    sync();
+  }
   int ep = 0;
   bool conv = false, checked_last = false;
   while (ep < V.epochs) {
     for (int c = 0; c < nc; ++c) {
       sweep_colour(c);
+      if constexpr (K > 1) {
+        __syncthreads();  // this rank's writes of colour c done
+        const int next = (c + 1 < nc) ? c + 1 : -1;
+        if (nbuf == 2) {  // the next colour's halo goes to the other buffer at once
+          halo(c, next);
+        } else {  // one buffer: emptied before it is filled again
+          halo(c, -1);
+          sync();
+          if (next >= 0) halo(-1, next);
+        }
+      }
       sync();
     }
     ++ep;
@@ -759,6 +827,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         conv = true;
         break;
       }
+    }
+    if constexpr (K > 1) {  // the next epoch's first colour reads the rows as they are now (refreshed by a check)
+      halo(-1, 0);
+      sync();
     }
   }
   if (!checked_last) conv = !check(true);
@@ -1025,11 +1097,13 @@ __global__ void k_inst_panels(const int64_t* pfirst, const int32_t* cwide, const
 __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const uint32_t* ucolour,
                            const uint8_t* iK, const int64_t* noff, const int64_t* eoff, const uint32_t* iend,
                            const uint32_t* ient, const int32_t* cwide, const int64_t* pfirst, const int64_t* pbase,
-                           int64_t Ns, int C1, uint32_t* ell) {
+                           const int32_t* qoff, const int32_t* hs, const int32_t* hoff, const int32_t* hH,
+                           const uint8_t* hnb, int64_t Ns, int C1, uint32_t* ell, int* err) {
   GSTRIDE(k, Ns) {
     const uint32_t j = i_col[k];
     const int64_t t = inst_col[j];
-    const int64_t f = t * C1 + ucolour[j];
+    const int c = (int)ucolour[j];
+    const int64_t f = t * C1 + c;
     const int64_t loc = k - noff[t];
     if (loc < cwide[f]) continue;  // a long column: served through the CSR
     const int64_t K = iK[t], r = loc % K;
@@ -1040,8 +1114,27 @@ __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const
     const uint32_t e0 = (loc == 0) ? 0u : iend[k - 1];
     const int64_t src = 2 * eoff[t];
     if (inst_ell16(K, eoff[t + 1] - eoff[t])) {  // slots 2w, 2w + 1 in word w (low half first)
+      // the shared-memory index of an entry's row: for a cluster rank, its own
+      // row, or the halo copy of another rank's row (after r and x)
+      int64_t hb = 0, H = 0;
+      if (K > 1) {
+        int64_t rch = 0;
+        for (int a = 0; a < K; ++a) rch = max(rch, (int64_t)(qoff[t * 5 + a + 1] - qoff[t * 5 + a]));
+        const int64_t xch = (noff[t + 1] - noff[t] + K - 1) / K;
+        hb = max(rch, 2 * ((xch + 31) / 32)) + xch;
+        H = (hnb[t] == 2) ? hH[t] : 0;  // the buffer of colour c at hb + (c & 1) H
+      }
+      auto slot = [&](uint32_t e) -> uint32_t {
+        if (K == 1) return e;
+        const int64_t er = e >> 28, pos = e & 0x0fffffffu;
+        const int64_t a = (er == r) ? pos
+                                    : hb + (c & 1) * H + hoff[((t * 4 + r) * C1 + c) * 4 + er] +
+                                          (pos - hs[((t * 4 + er) * 4 + r) * C1 + c]);
+        if (a >= 0xffff) atomicExch(err + 1, 1);
+        return (uint32_t)a & 0xffffu;
+      };
       for (uint32_t q = e0; q < e1; q += 2) {
-        const uint32_t lo = ient[src + q], hi = (q + 1 < e1) ? ient[src + q + 1] : 0xffffu;
+        const uint32_t lo = slot(ient[src + q]), hi = (q + 1 < e1) ? slot(ient[src + q + 1]) : 0xffffu;
         ell[pbase[p] + 32 * (int64_t)((q - e0) / 2) + lane] = lo | (hi << 16);
       }
     } else {
@@ -1092,14 +1185,108 @@ __global__ void k_inst_rowrank(const int64_t* rowptr, const uint32_t* colidx, co
 // local row of every union row, and its encoded id: (rank << 28) | (position
 // inside the rank's block)
 __global__ void k_inst_lrow(const uint32_t* i_row, const int32_t* inst_row, const int64_t* eoff, const uint32_t* rank,
-                            const int32_t* qoff, int64_t M, uint32_t* lrow, uint32_t* erow) {
+                            const uint32_t* rpos, int64_t M, uint32_t* lrow, uint32_t* erow) {
   GSTRIDE(k, M) {
     const uint32_t i = i_row[k];
     const int32_t t = inst_row[i];
-    const uint32_t loc = (uint32_t)(k - eoff[t]);
-    const uint32_t r = rank[i];
-    lrow[i] = loc;
-    erow[i] = (r << 28) | (loc - (uint32_t)qoff[(int64_t)t * 5 + r]);
+    lrow[i] = (uint32_t)(k - eoff[t]);
+    erow[i] = (rank[i] << 28) | rpos[k];
+  }
+}
+
+// halo group of every row (at its place k in the rows' (instance, rank)
+// order): 0 unless the row's other endpoint is a short column stepped by
+// another rank A, then 1 + A * C1 + that column's colour
+__global__ void k_inst_hkey(const uint32_t* i_row, const int32_t* inst_row, const uint8_t* iK, const uint32_t* rank,
+                            const int64_t* rowptr, const uint32_t* colidx, const int64_t* colptr,
+                            const uint32_t* lcol, const uint32_t* ucolour, int C1, int64_t M, uint32_t* keys,
+                            uint32_t* vals, uint32_t* hkey) {
+  GSTRIDE(k, M) {
+    const uint32_t i = i_row[k];
+    const uint32_t K = iK[inst_row[i]];
+    uint32_t key = 0;
+    if (K > 1) {
+      const uint32_t r = rank[i];
+      const int64_t q0 = rowptr[i];
+      const uint32_t a = idx_of(colidx[q0]), b = idx_of(colidx[q0 + 1]);
+      const uint32_t w = (lcol[a] % K == r) ? b : a;  // the endpoint the keeper does not step, if any
+      const uint32_t A = lcol[w] % K;
+      if (A != r && colptr[w + 1] - colptr[w] <= 32) key = 1 + A * (uint32_t)C1 + ucolour[w];
+    }
+    keys[k] = key;
+    vals[k] = (uint32_t)k;
+    hkey[k] = key;
+  }
+}
+
+// sort key of the rows' (instance, rank) block
+__global__ void k_inst_hblock(const uint32_t* perm, const uint32_t* i_row, const int32_t* inst_row,
+                              const uint32_t* rank, int64_t M, uint32_t* keys) {
+  GSTRIDE(p, M) {
+    const uint32_t i = i_row[perm[p]];
+    keys[p] = (uint32_t)inst_row[i] * 4u + rank[i];
+  }
+}
+
+// place of every row in its rank's block of r (perm: the rows by (instance,
+// rank, halo group), as places k of the (instance, rank) order; null: that
+// order itself), the inverse, and the halo groups in the new order
+__global__ void k_inst_rpos(const uint32_t* perm, const uint32_t* i_row, const int32_t* inst_row,
+                            const uint32_t* rank, const int64_t* eoff, const int32_t* qoff, const uint32_t* hkey,
+                            int64_t M, uint32_t* rpos, uint32_t* rrow, uint32_t* hsorted) {
+  GSTRIDE(p, M) {
+    const uint32_t k = perm ? perm[p] : (uint32_t)p;
+    const uint32_t i = i_row[k];
+    const int64_t t = inst_row[i];
+    const int64_t base = eoff[t] + qoff[t * 5 + rank[i]];
+    rpos[k] = (uint32_t)(p - base);
+    rrow[p] = (uint32_t)(k - eoff[t]);
+    if (hsorted) hsorted[p] = hkey[k];
+  }
+}
+
+// the segment R(q, A, c) of rank q's block: its rows read by rank A's short
+// columns of colour c (f = ((t * 4 + q) * 4 + A) * C1 + c)
+__global__ void k_inst_hseg(const uint32_t* hsorted, const int64_t* eoff, const int32_t* qoff, const uint8_t* iK,
+                            int64_t count, int C1, int32_t* hs, int32_t* hl) {
+  GSTRIDE(f, count * 16 * C1) {
+    const int64_t t = f / (16 * C1);
+    const int qa = (int)((f / C1) % 16), c = (int)(f % C1);
+    const int q = qa / 4, A = qa % 4, K = iK[t];
+    int32_t start = 0, len = 0;
+    if (q < K && A < K && q != A && hsorted) {
+      const int64_t b0 = eoff[t] + qoff[t * 5 + q], b1 = eoff[t] + qoff[t * 5 + q + 1];
+      const uint32_t key = 1u + (uint32_t)A * (uint32_t)C1 + (uint32_t)c;
+      auto lower = [&](uint32_t v) {
+        int64_t lo = b0, hi = b1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (hsorted[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        return lo;
+      };
+      const int64_t a = lower(key), b = lower(key + 1);
+      start = (int32_t)(a - b0);
+      len = (int32_t)(b - a);
+    }
+    hs[f] = start;
+    hl[f] = len;
+  }
+}
+
+// rank q's halo buffer of colour c: R(A, q, c) for A = 0, 1, ... one after
+// another (hoff[((t * 4 + q) * C1 + c) * 4 + A]); hH[t]: the largest buffer
+__global__ void k_inst_hoff(const int32_t* hl, int64_t count, int C1, int32_t* hoff, int32_t* hH) {
+  GSTRIDE(f, count * 4 * C1) {
+    const int64_t t = f / (4 * C1);
+    const int q = (int)((f / C1) % 4), c = (int)(f % C1);
+    int32_t acc = 0;
+    for (int A = 0; A < 4; ++A) {
+      hoff[f * 4 + A] = acc;
+      acc += hl[((t * 4 + A) * 4 + q) * C1 + c];
+    }
+    atomicMax(&hH[t], acc);
   }
 }
 
@@ -1318,10 +1505,10 @@ void launch_class(int c, const InstView& V, const int32_t* order, int64_t count,
     case 0: launch_one<1, 256, G>(V, order, count, smem, optin, st); break;
     case 1: launch_one<1, 512, G>(V, order, count, smem, optin, st); break;
     case 2: launch_one<1, 1024, G>(V, order, count, smem, optin, st); break;
-    // clusters: one column per lane (ELL) or 8 lanes per column
-    case 3: launch_one<2, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
-    case 4: launch_one<3, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
-    case 5: launch_one<4, 1024, (G == 1) ? 1 : 8>(V, order, count, smem, optin, st); break;
+    // clusters: one column per lane through ELL panels and halo buffers
+    case 3: launch_one<2, 1024, 1>(V, order, count, smem, optin, st); break;
+    case 4: launch_one<3, 1024, 1>(V, order, count, smem, optin, st); break;
+    case 5: launch_one<4, 1024, 1>(V, order, count, smem, optin, st); break;
     default: launch_one<1, 1024, G, true>(V, order, count, smem, optin, st); break;
   }
 }
@@ -1335,20 +1522,29 @@ void inst_classes(Problem& P) {
   std::vector<std::vector<int32_t>> members(NCLS);
   std::vector<uint8_t> iK(count, 1);
   const bool clusters = P.iml_clusters && L.cluster;
+  if ((int64_t)P.h_iKmin.size() != count) P.h_iKmin.assign(count, 1);
   for (int64_t t = 0; t < count; ++t) {
     const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t], m = P.h_beoff[t + 1] - P.h_beoff[t];
     // one CTA with everything in shared memory; else one CTA with x in global
     // memory when r alone fits; else a cluster (if asked for; rows are split
     // between ranks by a hash, so the estimate leaves 5 % + 256 rows of slack);
     // else one CTA whose r spills to L2
+    const int kmin = P.h_iKmin[t];
     int c = 0;
     while (c < 3 && inst_smem(n, m, 1) > class_cap(L, c)) ++c;
     if (c == 3) {
-      auto est = [&](int K) { return 4 * ((m * 105 / 100) / K + 256 + (n + K - 1) / K); };
+      // a rank: its rows, x, and a halo buffer of (at a guess) a fifth of the
+      // rows the other ranks keep and its short columns read (the layout
+      // measures it, takes a second buffer where that fits, and raises kmin
+      // of an instance that misses)
+      auto est = [&](int K) {
+        const int64_t halo = (m * (K - 1)) / (5 * K * K) + 64;
+        return 4 * ((m * 105 / 100) / K + 256 + (n + K - 1) / K + halo);
+      };
       if (4 * m <= class_cap(L, CLS_SPILL)) c = CLS_SPILL;
-      else if (clusters && est(2) <= class_cap(L, 3)) c = 3;
-      else if (clusters && est(3) <= class_cap(L, 4)) c = 4;
-      else if (clusters && est(4) <= class_cap(L, 5)) c = 5;
+      else if (clusters && kmin <= 2 && est(2) <= class_cap(L, 3)) c = 3;
+      else if (clusters && kmin <= 3 && est(3) <= class_cap(L, 4)) c = 4;
+      else if (clusters && kmin <= 4 && est(4) <= class_cap(L, 5)) c = 5;
       else c = CLS_SPILL;
     }
     TH_CHECK(c != CLS_SPILL || 4 * 2 * ((n + 31) / 32) <= class_cap(L, CLS_SPILL), THETIS_E_INVALID,
@@ -1381,10 +1577,12 @@ void inst_classes(Problem& P) {
   P.iml_classes_ok = true;
 }
 
-// shared memory of every class from the built layout: everything in shared
-// memory (K = 1), the largest rank's rows plus the rank's columns (clusters),
-// or the whole budget (spill)
-void inst_class_smem(Problem& P) {
+// dynamic shared memory of every launch class from the built layout:
+// everything in shared memory (K = 1); the largest rank's rows, the rank's
+// columns and its halo buffers (clusters); the whole budget (spill).  False
+// (with the minimum cluster size of the instances at fault raised) when a
+// cluster instance does not fit its class even with one halo buffer.
+bool inst_class_smem(Problem& P) {
   const int64_t count = P.nbatch;
   const DevLimits L = dev_limits();
   std::vector<int32_t> qo((size_t)count * 5);
@@ -1394,6 +1592,7 @@ void inst_class_smem(Problem& P) {
   TH_CUDA(cudaMemcpyAsync(order.data(), P.i_order, count * sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
   TH_CUDA(cudaStreamSynchronize(P.stream));
   P.h_icls_smem.assign(NCLS, 0);
+  bool fits = true;
   for (int c = 0; c < NCLS; ++c) {
     int64_t need = (c == CLS_SPILL) ? class_cap(L, c) : 0;
     for (int64_t i = P.h_icls_off[c]; i < P.h_icls_off[c + 1] && c != CLS_SPILL; ++i) {
@@ -1403,11 +1602,19 @@ void inst_class_smem(Problem& P) {
       int64_t rows = 0;
       for (int q = 0; q < K; ++q) rows = std::max<int64_t>(rows, qo[t * 5 + q + 1] - qo[t * 5 + q]);
       const int64_t xch = (n + K - 1) / K;
-      need = std::max(need, 4 * (std::max<int64_t>(rows, 2 * ((xch + 31) / 32)) + xch));
+      const int64_t halo = (K > 1) ? (int64_t)std::max<uint8_t>(P.h_ihnb[t], 1) * P.h_iH[t] : 0;
+      const int64_t own = 4 * (std::max<int64_t>(rows, 2 * ((xch + 31) / 32)) + xch + halo);
+      if (K > 1 && own > class_cap(L, c)) {
+        P.h_iKmin[t] = (uint8_t)(K + 1);  // 5: the spill class
+        fits = false;
+      }
+      need = std::max(need, own);
     }
+    if (!fits) continue;
     TH_CHECK(need <= class_cap(L, c), THETIS_E_INVALID, "instance engine: a rank's rows exceed its shared memory");
     P.h_icls_smem[c] = (need + 15) / 16 * 16;
   }
+  return fits;
 }
 
 void inst_layout(Problem& P) {
@@ -1477,9 +1684,69 @@ void inst_layout(Problem& P) {
   }
   k_inst_qoff<<<grid_for(count * 5, 256), 256, 0, s>>>(P.i_row, rank, P.beoff, count, P.i_qoff);
   TH_LAUNCHED();
+  // a cluster rank's block of r in halo-group order: first the rows no other
+  // rank's short column reads, then the segments R(q, A, c) by (A, c)
+  const bool any_cluster = std::any_of(P.h_iK.begin(), P.h_iK.end(), [](uint8_t k) { return k > 1; });
+  once(P.i_rpos, M + 1);
+  once(P.i_rrow, M + 1);
+  uint32_t* hsorted = nullptr;
   if (M > 0) {
-    k_inst_lrow<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.binst_row, P.beoff, rank, P.i_qoff, M, lrow, erow);
+    if (any_cluster) {
+      uint32_t* perm = tmp.alloc<uint32_t>(M + 1);
+      uint32_t* hkey = tmp.alloc<uint32_t>(M + 1);
+      hsorted = tmp.alloc<uint32_t>(M + 1);
+      k_inst_hkey<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.binst_row, P.i_K, rank, P.rowptr, P.colidx, P.colptr,
+                                                   lcol, ucolour, C1, M, keys, perm, hkey);
+      TH_LAUNCHED();
+      radix_sort_pairs(keys, perm, M, bits_for_count(4 * (int64_t)C1 + 2), tmp, s);
+      k_inst_hblock<<<grid_for(M, 256), 256, 0, s>>>(perm, P.i_row, P.binst_row, rank, M, keys);
+      TH_LAUNCHED();
+      radix_sort_pairs(keys, perm, M, bits_for_count(count * 4), tmp, s);
+      k_inst_rpos<<<grid_for(M, 256), 256, 0, s>>>(perm, P.i_row, P.binst_row, rank, P.beoff, P.i_qoff, hkey, M,
+                                                   P.i_rpos, P.i_rrow, hsorted);
+    } else {
+      k_inst_rpos<<<grid_for(M, 256), 256, 0, s>>>(nullptr, P.i_row, P.binst_row, rank, P.beoff, P.i_qoff, nullptr, M,
+                                                   P.i_rpos, P.i_rrow, nullptr);
+    }
     TH_LAUNCHED();
+    k_inst_lrow<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.binst_row, P.beoff, rank, P.i_rpos, M, lrow, erow);
+    TH_LAUNCHED();
+  }
+  // the segments, where they sit in the halo buffers, and each instance's
+  // buffer length
+  once(P.i_hs, count * 16 * C1);
+  once(P.i_hl, count * 16 * C1);
+  once(P.i_hoff, count * 16 * C1);
+  once(P.i_hH, count);
+  k_inst_hseg<<<grid_for(count * 16 * C1, 256), 256, 0, s>>>(hsorted, P.beoff, P.i_qoff, P.i_K, count, C1, P.i_hs,
+                                                             P.i_hl);
+  TH_LAUNCHED();
+  TH_CUDA(cudaMemsetAsync(P.i_hH, 0, count * sizeof(int32_t), s));
+  k_inst_hoff<<<grid_for(count * 4 * C1, 256), 256, 0, s>>>(P.i_hl, count, C1, P.i_hoff, P.i_hH);
+  TH_LAUNCHED();
+  // halo buffers of a cluster instance: two (colour parity, one cluster
+  // barrier a colour) when they fit its class beside r and x, else one (two
+  // barriers a colour)
+  {
+    std::vector<int32_t> qo((size_t)count * 5);
+    P.h_iH.resize(count);
+    TH_CUDA(cudaMemcpyAsync(qo.data(), P.i_qoff, qo.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaMemcpyAsync(P.h_iH.data(), P.i_hH, count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    const DevLimits L = dev_limits();
+    P.h_ihnb.assign(count, 0);
+    for (int64_t t = 0; t < count; ++t) {
+      const int K = P.h_iK[t];
+      if (K == 1) continue;
+      int64_t rch = 0;
+      for (int q = 0; q < K; ++q) rch = std::max<int64_t>(rch, qo[t * 5 + q + 1] - qo[t * 5 + q]);
+      const int64_t xch = (P.h_bnoff[t + 1] - P.h_bnoff[t] + K - 1) / K;
+      const int64_t own = std::max<int64_t>(rch, 2 * ((xch + 31) / 32)) + xch;
+      P.h_ihnb[t] = (4 * (own + 2 * (int64_t)P.h_iH[t]) <= class_cap(L, K + 1)) ? 2 : 1;
+    }
+    once(P.i_hnb, count);
+    TH_CUDA(cudaMemcpyAsync(P.i_hnb, P.h_ihnb.data(), count, cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaStreamSynchronize(s));  // the host vector is read by the copy
   }
   int64_t* pos = tmp.alloc<int64_t>(Ns + 1);
   k_inst_deg<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.colptr, Ns, pos);
@@ -1491,8 +1758,8 @@ void inst_layout(Problem& P) {
   once(P.i_ru, M + 1);
   once(P.i_rv, M + 1);
   once(P.i_deg, count);
-  int* err = tmp.alloc<int>(1);
-  TH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  int* err = tmp.alloc<int>(2);  // [0]: a malformed row; [1]: a halo index past 16 bits
+  TH_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
   TH_CUDA(cudaMemsetAsync(P.i_deg, 0, count * sizeof(int32_t), s));
   k_inst_fill<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, pos, P.beoff, P.colptr, P.rowidx, P.rowptr,
                                                 P.colidx, lcol, erow, Ns, P.i_end, P.i_ent, P.i_nb, P.i_deg, err);
@@ -1547,7 +1814,8 @@ void inst_layout(Problem& P) {
     }
     TH_CUDA(cudaMemsetAsync(P.i_ell, 0xff, (nslots + 1) * sizeof(uint32_t), s));
     k_inst_ell<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, ucolour, P.i_K, P.bnoff, P.beoff, P.i_end,
-                                                 P.i_ent, P.i_cwide, P.i_pfirst, P.i_pbase, Ns, C1, P.i_ell);
+                                                 P.i_ent, P.i_cwide, P.i_pfirst, P.i_pbase, P.i_qoff, P.i_hs,
+                                                 P.i_hoff, P.i_hH, P.i_hnb, Ns, C1, P.i_ell, err);
     TH_LAUNCHED();
   }
   once(P.i_c, Ns + 1);
@@ -1564,13 +1832,20 @@ void inst_layout(Problem& P) {
   once(P.i_rstatus, count);
   once(P.i_xout, Ns + 1);
   once(P.i_rhoout, count);
-  int herr = 0;
-  TH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int herr[2] = {0, 0};
+  TH_CUDA(cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   TH_CUDA(cudaStreamSynchronize(s));  // host tables above must outlive their copies
-  TH_CHECK(herr == 0, THETIS_E_INVALID, "instance engine: a row without exactly two structural entries");
+  TH_CHECK(herr[0] == 0, THETIS_E_INVALID, "instance engine: a row without exactly two structural entries");
   if (P.iml_G == 0) P.iml_G = 1;  // ELL panels, one thread per column (the autotuner may pick G lanes)
   P.iml_built = true;
-  inst_class_smem(P);
+  // an instance whose halo does not fit its class takes a larger cluster (or
+  // the spill class) and the layout is built again
+  if (!inst_class_smem(P)) {
+    P.iml_classes_ok = false;
+    P.iml_built = false;
+    return;
+  }
+  TH_CHECK(herr[1] == 0, THETIS_E_CUDA, "instance engine: a halo index past 16 bits in a class that fits");
 }
 
 }  // namespace
@@ -1585,10 +1860,18 @@ bool inst_eligible(Problem& P) {
   return true;
 }
 
-void inst_prepare(Problem& P) {
-  if (!P.iml_classes_ok) inst_classes(P);
-  if (!P.iml_built) inst_layout(P);
+// launch classes and the layout, again while an instance's halo pushes it
+// to a larger cluster (at most three times)
+void inst_ready(Problem& P) {
+  for (int it = 0; it < 5; ++it) {
+    if (!P.iml_classes_ok) inst_classes(P);
+    if (!P.iml_built) inst_layout(P);
+    if (P.iml_classes_ok && P.iml_built) return;
+  }
+  TH_CHECK(false, THETIS_E_CUDA, "instance engine: no launch class settled");
 }
+
+void inst_prepare(Problem& P) { inst_ready(P); }
 
 void inst_set_clusters(Problem& P, bool on) {
   if (P.iml_clusters == on) return;
@@ -1597,8 +1880,7 @@ void inst_set_clusters(Problem& P, bool on) {
 }
 
 void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
-  if (!P.iml_classes_ok) inst_classes(P);
-  if (!P.iml_built) inst_layout(P);
+  inst_ready(P);
   cudaStream_t s = P.stream;
   const int64_t count = P.nbatch;
   if (!P.i_events[0]) {
@@ -1627,6 +1909,13 @@ void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
   V.pbase = P.i_pbase;
   V.pw = P.i_pw;
   V.ell = P.i_ell;
+  V.rpos = P.i_rpos;
+  V.rrow = P.i_rrow;
+  V.hs = P.i_hs;
+  V.hl = P.i_hl;
+  V.hoff = P.i_hoff;
+  V.hH = P.i_hH;
+  V.hnb = P.i_hnb;
   V.ideg = P.i_deg;
   V.kind = P.bkind;
   V.c = P.i_c;

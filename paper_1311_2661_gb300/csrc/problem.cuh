@@ -149,6 +149,17 @@ struct Problem {
   uint32_t* i_ell = nullptr;        // ELL slots of the short columns (local rows)
   int64_t i_npanels = 0;
   int64_t i_pcap = 0, i_scap = 0;  // allocated panels / ELL slots
+  // cluster instances: rows of a rank in halo-group order and the halo segments
+  uint32_t* i_rpos = nullptr;       // M: place of every IML row in its rank's block of r
+  uint32_t* i_rrow = nullptr;       // M: the IML row at every place
+  int32_t* i_hs = nullptr;          // count * 16 * iml_C: start of segment R(q, A, c) in rank q's block
+  int32_t* i_hl = nullptr;          // count * 16 * iml_C: its length
+  int32_t* i_hoff = nullptr;        // count * 4 * iml_C * 4: where R(A, q, c) sits in q's halo buffer
+  int32_t* i_hH = nullptr;          // count: halo buffer length
+  uint8_t* i_hnb = nullptr;         // count: halo buffers (1 or 2)
+  std::vector<int32_t> h_iH;        // host copy of i_hH
+  std::vector<uint8_t> h_ihnb;      // host copy of i_hnb
+  std::vector<uint8_t> h_iKmin;     // count: smallest cluster an instance may take (5: the spill class)
   int32_t* i_deg = nullptr;         // count: largest column length of the instance
   float *i_c = nullptr, *i_x = nullptr, *i_s = nullptr;  // c, x (Ns) and s (M) in IML order
   float* i_rg = nullptr;            // M: residual rows kept in global memory (instances too large for one CTA)
