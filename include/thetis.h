@@ -371,9 +371,9 @@ thetis_status thetis_round_is_static(int64_t n, int64_t m, const int32_t* eu, co
  * problem: the number of lanes that serve one small column (1, 2, 4 or 8; "warps
  * per column") and the CTAs per SM of the persistent sweep (all that fit, 2 or
  * 1; the size of the colour chunk each CTA takes).  For a batch handle served
- * by the instance-resident engine: lanes per column (1, 4, 8) and whether
- * large instances take clusters (see thetis_set_batch_shape), returned as
- * *small_group_out and *ctas_per_sm_out (1 = clusters).  Every pair is timed over
+ * by the instance-resident engine: one of (1 lane, clusters), (1 lane, no
+ * clusters), (8 lanes, clusters) (see thetis_set_batch_shape), returned as
+ * *small_group_out and *ctas_per_sm_out (1 = clusters).  Every choice is timed over
  * trial_epochs epochs of the real problem (beta and step_rule from p); the
  * iterate is saved before and restored after each trial, so the result of later
  * solves does not depend on tuning.  The choice is cached in the process per

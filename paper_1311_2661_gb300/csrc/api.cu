@@ -783,10 +783,9 @@ thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t 
     cudaStream_t s = h->stream;
     TH_CHECK(p->beta > 0, THETIS_E_INVALID, "beta must be > 0");
     if (P.nbatch > 0 && inst_eligible(P)) {
-      // batches: the lanes per column of the instance-resident engine (1: one
-      // thread per short column through ELL panels; 4 or 8 through the CSR),
-      // timed on trial_epochs epochs of every instance (no stopping); iterate
-      // restored
+      // batches: clusters on or off (one thread per short column through ELL
+      // panels; the CSR with 8 lanes a column as a third choice), timed on
+      // trial_epochs epochs of every instance (no stopping); iterate restored
       TuneKey key = tune_key(P);
       key.kind += 100;
       int G = 0;
@@ -807,8 +806,11 @@ thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t 
         TH_CUDA(cudaMemcpyAsync(x0, P.x, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
         if (P.M) TH_CUDA(cudaMemcpyAsync(s0, P.s, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
         double best_ms = 1e300;
-        for (bool cl : {false, true})
-          for (int g : {1, 8, 4}) {
+        const std::pair<int, bool> shapes[3] = {{1, true}, {1, false}, {8, true}};
+        for (const auto& sh : shapes) {
+          {  // one trial
+            const int g = sh.first;
+            const bool cl = sh.second;
             P.iml_G = g;
             inst_set_clusters(P, cl);
             double ms = 0.0;
@@ -821,6 +823,7 @@ thetis_status thetis_autotune(thetis_handle* h, const thetis_params* p, int32_t 
             TH_CUDA(cudaMemcpyAsync(P.x, x0, P.Ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
             if (P.M) TH_CUDA(cudaMemcpyAsync(P.s, s0, P.M * sizeof(float), cudaMemcpyDeviceToDevice, s));
           }
+        }
         TH_CUDA(cudaStreamSynchronize(s));
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = TuneChoice{G, 0, clusters};

@@ -218,6 +218,13 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_over[2];
   __shared__ unsigned s_rho[2];  // the largest rho of the check (FP32 bits, non-negative)
+  __shared__ int s_q[2];         // work counters of the colour sweep (colour parity)
+  // the instance's colour table in shared memory (up to CM colours): first
+  // panel (relative), first short column, first column, this rank's first
+  // slack row
+  constexpr int CM = 64;
+  __shared__ int s_cm[4][CM + 1];
+  __shared__ long long s_pf0;
   constexpr int GC = (G == 1) ? 8 : G;  // lanes per column of the stopping test
   const int q = (K > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int t = order[blockIdx.x / K];
@@ -268,6 +275,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   const int nc = V.ncol[t];
   const int32_t* coff = V.coff + (int64_t)t * V.C;
   const int32_t* roff = V.roff + ((int64_t)t * 4 + q) * V.C;
+  const bool cm_ok = nc < CM;
   const float sig = (V.kind[t] == THETIS_ROUND_VC) ? -1.f : 1.f;
   // step rule 1: the instance's own global L_max (as its solve alone uses)
   float lfix = 0.f;
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // local row of an entry's encoded row id
   auto row_of = [&](uint32_t e) -> uint32_t {
     if constexpr (K == 1) return e;
-    else return V.rrow[row0 + qv[e >> 28] + (e & 0x0fffffffu)];
+    else return V.rrow[row0 + V.qoff[(int64_t)t * 5 + (e >> 28)] + (e & 0x0fffffffu)];
   };
   auto xget = [&](uint32_t k) -> float {
     if constexpr (SPILL) return xs ? sx[k] : Sx[k];
@@ -349,6 +357,16 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   if (threadIdx.x < 2) {
     s_over[threadIdx.x] = 0;
     s_rho[threadIdx.x] = 0u;
+    s_q[threadIdx.x] = 0;
+  }
+  if (cm_ok && threadIdx.x <= nc) {
+    const int c = threadIdx.x;
+    const int64_t f = (int64_t)t * V.C;
+    if (c == 0) s_pf0 = V.pfirst[f];
+    s_cm[0][c] = (int)(V.pfirst[f + c] - V.pfirst[f]);
+    s_cm[1][c] = V.cwide[f + c];
+    s_cm[2][c] = coff[c];
+    s_cm[3][c] = roff[c];
   }
   if (threadIdx.x == 0 && q == 0) V.t_out[2 * t] = global_ns();
   sync();
@@ -403,16 +421,53 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // |sum - a_j^T r| <= 2^-23 (deg + 2) sum |r_i| bounds it; rho is decided
   // from that estimate unless it lies within the bound of tol, and then from
   // the exact sum (2^-58 fixed point) in FP64.
-  auto cols_check = [&](int slot) {
-    const int cnt = (n > q) ? (n - q + K - 1) / K : 0;
+  auto col_decide = [&](int k, float xk, float ck, float sum, float sabs, int deg, bool& over, float& rmax) {
+    const float L = fmaf(beta, (float)deg, ib);
+    const float g = ck + beta * sum + xk * ib;
+    const float qv = g / L;
+    const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
+    rmax = fmaxf(rmax, rho);
+    if (over) return;
+    const float esum = 0x1p-22f * (float)(deg + 2) * sabs;  // twice the bound above
+    const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
+                      beta * esum / L + 0x1p-23f * tol32 + 1e-30f;
+    if (!(rho - del <= tol32)) {  // over tol (or not finite)
+      over = true;
+    } else if (rho + del > tol32) {  // too close to tol for FP32: the exact sum, FP64
+      const uint32_t p0 = (k == 0) ? 0u : Iend[k - 1], p1 = Iend[k];
+      long long hi = 0, lo = 0;
+      bool bad = !fix_ok(xk);
+      const long long fk = fix58(xk);
+      double sum64 = 0.0;
+      for (uint32_t p = p0; p < p1; ++p) {
+        const uint32_t e = row_of(Ient[p]);
+        const float xw = xget(Inb[p]);
+        const float sv = __ldcg(Ss + e);
+        sum64 += row_f64(xk, xw, sv, sig);  // used when some value is outside the fixed-point range
+        if (!(fix_ok(xw) && fix_ok(sv))) bad = true;
+        const long long fs = fix58(sv);
+        const long long rf = fk + fix58(xw) + (sig > 0.f ? fs : -fs) - FIX_ONE;
+        hi += rf >> FIX_SPLIT;
+        lo += rf & ((1LL << FIX_SPLIT) - 1);
+      }
+      if (!bad) sum64 = (double)hi * 0x1p-40 + (double)lo * 0x1p-58;
+      const double bd = V.beta_d, ibd = 1.0 / bd;
+      const double g64 = (double)ck + bd * sum64 + (double)xk * ibd;
+      const double L64 = bd * (double)deg + ibd;
+      const double xn = fmin(fmax((double)xk - g64 / L64, (double)V.lo), (double)V.hi);
+      if (fabs(xn - (double)xk) > V.tol) over = true;
+    }
+  };
+  // the columns [ka, kb) of this rank through the CSR, GC lanes each
+  auto cols_csr = [&](int ka, int kb, bool& over, float& rmax) {
+    const int first = ka + ((q - ka % K) % K + K) % K;
+    const int cnt = (first < kb) ? (kb - first + K - 1) / K : 0;
     constexpr int PW = 32 / GC;
     const int warp = threadIdx.x >> 5, lw = (threadIdx.x & 31) / GC, gl = threadIdx.x % GC;
-    bool over = false;
-    float rmax = 0.f;
     for (int ib0 = warp * PW; ib0 < cnt; ib0 += (NT / 32) * PW) {
       const int i = ib0 + lw;
       const bool valid = i < cnt;
-      const int k = q + i * K;
+      const int k = first + i * K;
       uint32_t p0 = 0, p1 = 0;
       float xk = 0.f, ck = 0.f;
       if (valid) {
@@ -440,41 +495,69 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
         sabs += __shfl_xor_sync(0xffffffffu, sabs, o, GC);
       }
       if (!valid || gl != 0) continue;
-      const int deg = (int)(p1 - p0);
-      const float L = fmaf(beta, (float)deg, ib);
-      const float g = ck + beta * sum + xk * ib;
-      const float qv = g / L;
-      const float rho = fabsf(fminf(fmaxf(xk - qv, V.lo), V.hi) - xk);
-      rmax = fmaxf(rmax, rho);
-      if (over) continue;
-      const float esum = 0x1p-22f * (float)(deg + 2) * sabs;  // twice the bound above
-      const float del = 0x1p-19f * ((fabsf(ck) + beta * fabsf(sum) + fabsf(xk) * ib) / L + fabsf(xk) + fabsf(qv)) +
-                        beta * esum / L + 0x1p-23f * tol32 + 1e-30f;
-      if (!(rho - del <= tol32)) {  // over tol (or not finite)
-        over = true;
-      } else if (rho + del > tol32) {  // too close to tol for FP32: the exact sum, FP64
-        long long hi = 0, lo = 0;
-        bool bad = !fix_ok(xk);
-        const long long fk = fix58(xk);
-        double sum64 = 0.0;
-        for (uint32_t p = p0; p < p1; ++p) {
-          const uint32_t e = row_of(Ient[p]);
-          const float xw = xget(Inb[p]);
-          const float sv = __ldcg(Ss + e);
-          sum64 += row_f64(xk, xw, sv, sig);  // used when some value is outside the fixed-point range
-          if (!(fix_ok(xw) && fix_ok(sv))) bad = true;
-          const long long fs = fix58(sv);
-          const long long rf = fk + fix58(xw) + (sig > 0.f ? fs : -fs) - FIX_ONE;
-          hi += rf >> FIX_SPLIT;
-          lo += rf & ((1LL << FIX_SPLIT) - 1);
+      col_decide(k, xk, ck, sum, sabs, (int)(p1 - p0), over, rmax);
+    }
+  };
+  // one CTA with 16-bit ELL panels: per colour its long columns through the
+  // CSR and its short ones a thread each through the panels (the sweep's
+  // gather without the step; a cluster reads the other ranks' rows through
+  // the CSR, its halo copies being stale here)
+  auto cols_check = [&](int slot) {
+    bool over = false;
+    float rmax = 0.f;
+    if constexpr (K == 1 && G == 1) {
+      if (!ell16) {
+        cols_csr(0, n, over, rmax);
+      } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        constexpr uint32_t NO16 = 0xffffu;
+        for (int c = 0; c < nc; ++c) {
+          int64_t pf;
+          int np, cw, cend, cst;
+          if (cm_ok) {
+            pf = s_pf0 + s_cm[0][c];
+            np = s_cm[0][c + 1] - s_cm[0][c];
+            cw = s_cm[1][c];
+            cst = s_cm[2][c];
+            cend = s_cm[2][c + 1];
+          } else {
+            pf = V.pfirst[(int64_t)t * V.C + c];
+            np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
+            cw = V.cwide[(int64_t)t * V.C + c];
+            cst = coff[c];
+            cend = coff[c + 1];
+          }
+          if (cw > cst) cols_csr(cst, cw, over, rmax);
+          for (int j = warp; j < np; j += NT / 32) {
+            const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
+            const int WW = (V.pw[pf + j] + 1) >> 1;
+            const int k = cw + 32 * j + lane;
+            float sum = 0.f, sabs = 0.f;
+            int deg = 0;
+            auto take = [&](uint32_t e) {
+              if (e != NO16) {
+                const float rv = rget(e);
+                sum += rv;
+                sabs += fabsf(rv);
+                ++deg;
+              }
+            };
+            for (int u0 = 0; u0 < WW; u0 += 4) {
+              uint32_t et[4];
+#pragma unroll
+              for (int v = 0; v < 4; ++v) et[v] = (u0 + v < WW) ? pe[32 * (u0 + v)] : NO_ENTRY;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                take(et[v] & 0xffffu);
+                take(et[v] >> 16);
+              }
+            }
+            if (k < cend) col_decide(k, xget((uint32_t)k), Cc[k], sum, sabs, deg, over, rmax);
+          }
         }
-        if (!bad) sum64 = (double)hi * 0x1p-40 + (double)lo * 0x1p-58;
-        const double bd = V.beta_d, ibd = 1.0 / bd;
-        const double g64 = (double)ck + bd * sum64 + (double)xk * ibd;
-        const double L64 = bd * (double)deg + ibd;
-        const double xn = fmin(fmax((double)xk - g64 / L64, (double)V.lo), (double)V.hi);
-        if (fabs(xn - (double)xk) > V.tol) over = true;
       }
+    } else {
+      cols_csr(0, n, over, rmax);
     }
     if (over) atomicOr(&s_over[slot], 1);
     if (rmax > 0.f) atomicMax(&s_rho[slot], __float_as_uint(rmax));
@@ -608,20 +691,69 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     }
   };
 
-  // the same with 16-bit slots, two a word, so twice the slots per load and
-  // per register (the scatter re-reads r: no other column of the colour
-  // touches the row).  A slot is the row's index in shared memory: for a
-  // cluster rank its own row or the halo copy of another rank's row, so the
-  // sweep makes no remote access.
-  auto ell_columns16 = [&](int c) {
-    constexpr int NW = 7;  // words (14 slots) kept in registers between gather and scatter
+  // one slack row: its projected step (the row is this rank's)
+  auto slack_row = [&](int e, float sv, float rv) {
+    const float g = bsig * rv + sv * ib;
+    const float sn = fmaxf(sv - g * inv_ls, 0.f);
+    const float d = sn - sv;
+    Ss[e] = sn;
+    if (d != 0.f) rown_set(e, rv + sig * d);
+  };
+  // the slack rows [ra, rb2) of a colour, four per thread at a time
+  auto slack_rows = [&](int ra, int rb2) {
+    constexpr int SR = 4;
+    for (int e0 = ra + (int)threadIdx.x; e0 < rb2; e0 += SR * NT) {
+      float sv[SR], rv[SR];
+#pragma unroll
+      for (int u = 0; u < SR; ++u) {
+        const int e = e0 + u * NT;
+        sv[u] = (e < rb2) ? Ss[e] : 0.f;
+        rv[u] = (e < rb2) ? rown_get(e) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < SR; ++u)
+        if (e0 + u * NT < rb2) slack_row(e0 + u * NT, sv[u], rv[u]);
+    }
+  };
+
+  // a colour through 16-bit ELL panels, two slots a word, so twice the slots
+  // per load and per register (the scatter re-reads r: no other column of the
+  // colour touches the row).  A slot is the row's index in shared memory: for
+  // a cluster rank its own row or the halo copy of another rank's row, so the
+  // sweep makes no remote access.  The warps pull the work -- this rank's
+  // panels (widest first), then chunks of 128 slack rows -- from a counter in
+  // shared memory, so a warp with a narrow panel goes on to the next item
+  // instead of waiting at the colour's barrier.
+  int seq = 0;  // colours swept so far: the counter of colour step seq is s_q[seq & 1]
+  auto colour16 = [&](int c) {
+    constexpr int NW = 5;  // words (10 slots) kept in registers between gather and scatter
     constexpr int NB = 4;  // words beyond NW: loaded NB at a time
+    constexpr int CH = 128;  // slack rows an item
     constexpr uint32_t NO16 = 0xffffu;
-    const int64_t pf = V.pfirst[(int64_t)t * V.C + c];
-    const int np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
-    const int cw = V.cwide[(int64_t)t * V.C + c], cend = coff[c + 1];
+    int64_t pf;
+    int np, cw, cend, ra, rb2;
+    if (cm_ok) {
+      pf = s_pf0 + s_cm[0][c];
+      np = s_cm[0][c + 1] - s_cm[0][c];
+      cw = s_cm[1][c];
+      cend = s_cm[2][c + 1];
+      ra = s_cm[3][c];
+      rb2 = s_cm[3][c + 1];
+    } else {
+      pf = V.pfirst[(int64_t)t * V.C + c];
+      np = (int)(V.pfirst[(int64_t)t * V.C + c + 1] - pf);
+      cw = V.cwide[(int64_t)t * V.C + c];
+      cend = coff[c + 1];
+      ra = roff[c];
+      rb2 = roff[c + 1];
+    }
     const int first = cw + ((q - cw % K) % K + K) % K;  // this rank's first short column
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int npq = (np > q) ? (np - q + K - 1) / K : 0;  // this rank's panels: q + K jj
+    const int nit = npq + (rb2 - ra + CH - 1) / CH;
+    const int lane = threadIdx.x & 31;
+    int* ctr = &s_q[seq & 1];
+    if (threadIdx.x == 0) s_q[(seq + 1) & 1] = 0;  // the next colour's counter (last used a barrier ago)
+    ++seq;
     auto lr = [&](uint32_t e) -> float {
       if constexpr (SPILL) return rget(e);
       else return smem[e];
@@ -630,10 +762,47 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       if constexpr (SPILL) rset(e, v);
       else smem[e] = v;
     };
-    for (int j = q + K * warp; j < np; j += K * (NT / 32)) {
-      const uint32_t* pe = V.ell + V.pbase[pf + j] + lane;
-      const int WW = (V.pw[pf + j] + 1) >> 1;
-      const int k = first + K * (32 * (j / K) + lane);
+    // a warp holds the next item it will take, and that panel's slot base
+    // and width, while it works on the current one
+    auto pull = [&]() {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(ctr, 1);
+      return __shfl_sync(0xffffffffu, v, 0);
+    };
+    int nx = pull();
+    int64_t nx_base = 0;
+    int nx_w = 0;
+    if (nx < npq) {
+      nx_base = V.pbase[pf + q + K * nx];
+      nx_w = V.pw[pf + q + K * nx];
+    }
+    for (;;) {
+      const int it = nx;
+      if (it >= nit) break;
+      const int64_t pbase = nx_base;
+      const int pw = nx_w;
+      nx = pull();
+      if (nx < npq) {
+        nx_base = V.pbase[pf + q + K * nx];
+        nx_w = V.pw[pf + q + K * nx];
+      }
+      if (it >= npq) {  // slack rows
+        const int e0 = ra + (it - npq) * CH + lane;
+        float sv[CH / 32], rv[CH / 32];
+#pragma unroll
+        for (int u = 0; u < CH / 32; ++u) {
+          const int e = e0 + 32 * u;
+          sv[u] = (e < rb2) ? Ss[e] : 0.f;
+          rv[u] = (e < rb2) ? rown_get(e) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < CH / 32; ++u)
+          if (e0 + 32 * u < rb2) slack_row(e0 + 32 * u, sv[u], rv[u]);
+        continue;
+      }
+      const uint32_t* pe = V.ell + pbase + lane;
+      const int WW = (pw + 1) >> 1;
+      const int k = first + K * (32 * it + lane);
       uint32_t ce[NW];
 #pragma unroll
       for (int u = 0; u < NW; ++u) ce[u] = (u < WW) ? pe[32 * u] : NO_ENTRY;
@@ -691,36 +860,21 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     }
   };
 
-  // one colour: its columns, then its slack rows (four per thread at a time)
+  // one colour: its long columns (a warp each), then its short columns and
+  // slack rows
   auto sweep_colour = [&](int c) {
     if constexpr (G == 1) {
       const int cw = V.cwide[(int64_t)t * V.C + c];
       if (cw > coff[c]) csr_columns(std::integral_constant<int, 32>{}, coff[c], cw);
-      if (SPILL && !ell16) ell_columns(c);
-      else ell_columns16(c);
+      if (SPILL && !ell16) {
+        ell_columns(c);
+        slack_rows(roff[c], roff[c + 1]);
+      } else {
+        colour16(c);
+      }
     } else {
       csr_columns(std::integral_constant<int, G>{}, coff[c], coff[c + 1]);
-    }
-    const int ra = roff[c], rb2 = roff[c + 1];  // this rank's slack rows of colour c
-    constexpr int SR = 4;
-    for (int e0 = ra + (int)threadIdx.x; e0 < rb2; e0 += SR * NT) {
-      float sv[SR], rv[SR];
-#pragma unroll
-      for (int u = 0; u < SR; ++u) {
-        const int e = e0 + u * NT;
-        sv[u] = (e < rb2) ? Ss[e] : 0.f;
-        rv[u] = (e < rb2) ? rown_get(e) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < SR; ++u) {
-        const int e = e0 + u * NT;
-        if (e >= rb2) continue;
-        const float g = bsig * rv[u] + sv[u] * ib;
-        const float sn = fmaxf(sv[u] - g * inv_ls, 0.f);
-        const float d = sn - sv[u];
-        Ss[e] = sn;
-        if (d != 0.f) rown_set(e, rv[u] + sig * d);
-      }
+      slack_rows(roff[c], roff[c + 1]);
     }
   };
 
@@ -1467,10 +1621,12 @@ DevLimits dev_limits() {
 }
 
 // dynamic shared memory a CTA of class c may take (1 KB per CTA stays with the
-// system, 64 bytes of static shared memory)
+// system; the kernel's static shared memory -- flags, 1/L table, colour
+// table, rounding scratch -- stays below 2 KB)
+constexpr int64_t INST_STATIC_SMEM = 2048;
 int64_t class_cap(const DevLimits& L, int c) {
   const int per = (CLASSES[c].K == 1) ? 1024 / CLASSES[c].NT : 1;
-  return std::min<int64_t>(L.optin, L.per_sm / per - 1024) - 512;  // static shared memory stays below 512 B
+  return std::min<int64_t>(L.optin, L.per_sm / per - 1024) - INST_STATIC_SMEM;
 }
 
 template <int K, int NT, int G, bool SPILL = false>
@@ -1478,8 +1634,8 @@ void launch_one(const InstView& V, const int32_t* order, int64_t count, size_t s
   auto kern = k_inst<K, NT, G, SPILL>;
   cudaFuncAttributes fa;
   TH_CUDA(cudaFuncGetAttributes(&fa, kern));
-  TH_CHECK((int64_t)smem + (int64_t)fa.sharedSizeBytes <= optin, THETIS_E_INVALID,
-           "instance engine: shared memory of a launch class exceeds the device limit");
+  TH_CHECK((int64_t)fa.sharedSizeBytes <= INST_STATIC_SMEM && (int64_t)smem + (int64_t)fa.sharedSizeBytes <= optin,
+           THETIS_E_INVALID, "instance engine: shared memory of a launch class exceeds the device limit");
   TH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(optin - (int64_t)fa.sharedSizeBytes)));
   cudaLaunchConfig_t cfg = {};

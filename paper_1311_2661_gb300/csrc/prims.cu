@@ -144,70 +144,162 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& tmp, 
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 4-bit digits, one item per thread, 512-item tiles
+// stable LSD radix sort, 8-bit digits, 4096-item tiles (512 threads x 8):
+// per pass a tile histogram, a digit-major scan of all tiles' counts, and a
+// scatter in which each tile first sorts itself by the digit in shared memory
+// (two stable 4-bit splits) so that its items of one digit leave as one
+// contiguous run
 // ---------------------------------------------------------------------------
-constexpr int RS_T = 512;
-constexpr int RS_W = RS_T / 32;
-constexpr int RS_D = 16;
+constexpr int R8_T = 512;
+constexpr int R8_I = 8;
+constexpr int R8_TILE = R8_T * R8_I;
+constexpr int R8_D = 256;
+constexpr size_t R8_SMEM = (4 * R8_TILE + 16 * R8_T) * sizeof(uint32_t);
 
-__global__ void k_rs_count(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
-                           int64_t* __restrict__ counts) {
-  __shared__ int c[RS_D];
-  if (threadIdx.x < RS_D) c[threadIdx.x] = 0;
+__global__ void __launch_bounds__(R8_T) k_r8_count(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                   int64_t ntiles, int64_t* __restrict__ counts) {
+  __shared__ int c[R8_D];
+  for (int i = threadIdx.x; i < R8_D; i += R8_T) c[i] = 0;
   __syncthreads();
-  int64_t i = (int64_t)blockIdx.x * RS_T + threadIdx.x;
-  if (i < n) atomicAdd(&c[(keys[i] >> shift) & (RS_D - 1)], 1);
-  __syncthreads();
-  if (threadIdx.x < RS_D) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c[threadIdx.x];
-}
-
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                             int shift, int64_t ntiles, const int64_t* __restrict__ offs) {
-  __shared__ int wc[RS_W][RS_D];
-  __shared__ int wp[RS_W][RS_D];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int t = threadIdx.x; t < RS_W * RS_D; t += RS_T) (&wc[0][0])[t] = 0;
-  __syncthreads();
-  int64_t i = (int64_t)blockIdx.x * RS_T + threadIdx.x;
-  bool valid = i < n;
-  uint32_t k = valid ? kin[i] : 0u;
-  uint32_t v = valid ? vin[i] : 0u;
-  int d = valid ? (int)((k >> shift) & (RS_D - 1)) : RS_D;
-  unsigned peers = __match_any_sync(0xffffffffu, d);
-  int rank = __popc(peers & ((1u << lane) - 1u));
-  if (valid && rank == 0) wc[w][d] = __popc(peers);
-  __syncthreads();
-  if (threadIdx.x < RS_D) {
-    int acc = 0;
-    for (int q = 0; q < RS_W; ++q) {
-      wp[q][threadIdx.x] = acc;
-      acc += wc[q][threadIdx.x];
-    }
+  const int64_t base = (int64_t)blockIdx.x * R8_TILE;
+#pragma unroll
+  for (int u = 0; u < R8_I; ++u) {
+    const int64_t i = base + u * R8_T + threadIdx.x;
+    if (i < n) atomicAdd(&c[(keys[i] >> shift) & (R8_D - 1)], 1);
   }
   __syncthreads();
-  if (valid) {
-    int64_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + wp[w][d] + rank;
-    kout[pos] = k;
-    vout[pos] = v;
+  for (int d = threadIdx.x; d < R8_D; d += R8_T) counts[(int64_t)d * ntiles + blockIdx.x] = c[d];
+}
+
+__global__ void __launch_bounds__(R8_T) k_r8_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                     int64_t n, int shift, int64_t ntiles,
+                                                     const int64_t* __restrict__ offs) {
+  extern __shared__ __align__(16) uint32_t r8[];
+  uint32_t* ka = r8;                 // the tile's keys and values, two buffers
+  uint32_t* va = r8 + R8_TILE;
+  uint32_t* kb = r8 + 2 * R8_TILE;
+  uint32_t* vb = r8 + 3 * R8_TILE;
+  int* cnt = reinterpret_cast<int*>(r8 + 4 * R8_TILE);  // [16][R8_T]: per 4-bit bin and thread
+  __shared__ int tstart[R8_D];
+  __shared__ int wsum[R8_T / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * R8_TILE;
+  const int nv = (n - base < (int64_t)R8_TILE) ? (int)(n - base) : R8_TILE;
+  // the tile in its order; the padding past n takes the largest key, so it
+  // sorts behind every item of the last digit and is never written
+#pragma unroll
+  for (int u = 0; u < R8_I; ++u) {
+    const int i = u * R8_T + tid;
+    ka[i] = (i < nv) ? kin[base + i] : 0xffffffffu;
+    va[i] = (i < nv) ? vin[base + i] : 0u;
+  }
+  __syncthreads();
+  for (int half = 0; half < 2; ++half) {
+    const int sh = shift + 4 * half;
+    uint32_t* kc = half ? kb : ka;
+    uint32_t* vc = half ? vb : va;
+    uint32_t* kn = half ? ka : kb;
+    uint32_t* vn = half ? va : vb;
+    // thread t holds items [8t, 8t + 8) of the current order
+    uint32_t k[R8_I], v[R8_I];
+    {
+      const uint4* k4 = reinterpret_cast<const uint4*>(kc) + 2 * tid;
+      const uint4* v4 = reinterpret_cast<const uint4*>(vc) + 2 * tid;
+      const uint4 k0 = k4[0], k1 = k4[1], v0 = v4[0], v1 = v4[1];
+      k[0] = k0.x; k[1] = k0.y; k[2] = k0.z; k[3] = k0.w; k[4] = k1.x; k[5] = k1.y; k[6] = k1.z; k[7] = k1.w;
+      v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w; v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+    }
+#pragma unroll
+    for (int b = 0; b < 16; ++b) cnt[b * R8_T + tid] = 0;
+#pragma unroll
+    for (int j = 0; j < R8_I; ++j) cnt[((k[j] >> sh) & 15u) * R8_T + tid] += 1;
+    __syncthreads();
+    // exclusive scan of cnt in (bin, thread) order: thread t takes entries
+    // [16 t, 16 t + 16), then a scan over the threads' totals
+    int loc[16];
+    int tot = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      loc[i] = tot;
+      tot += cnt[16 * tid + i];
+    }
+    int inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      int w = (lane < R8_T / 32) ? wsum[lane] : 0;
+      int wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      if (lane < R8_T / 32) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const int pre = wsum[warp] + inc - tot;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) cnt[16 * tid + i] = pre + loc[i];
+    __syncthreads();
+    // every item to its place in the order by the 4 bits, stably
+#pragma unroll
+    for (int j = 0; j < R8_I; ++j) {
+      int* slot = &cnt[((k[j] >> sh) & 15u) * R8_T + tid];
+      const int pos = *slot;
+      *slot = pos + 1;
+      kn[pos] = k[j];
+      vn[pos] = v[j];
+    }
+    __syncthreads();
+  }
+  // ka / va: the tile sorted by the digit; where every digit's run starts
+#pragma unroll
+  for (int u = 0; u < R8_I; ++u) {
+    const int p = u * R8_T + tid;
+    const uint32_t d = (ka[p] >> shift) & (R8_D - 1);
+    if (p == 0 || ((ka[p - 1] >> shift) & (R8_D - 1)) != d) tstart[d] = p;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < R8_I; ++u) {
+    const int p = u * R8_T + tid;
+    if (p < nv) {
+      const uint32_t d = (ka[p] >> shift) & (R8_D - 1);
+      const int64_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + (p - tstart[d]);
+      kout[pos] = ka[p];
+      vout[pos] = va[p];
+    }
   }
 }
 
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, Arena& tmp,
                       cudaStream_t s) {
   if (n <= 1 || bits <= 0) return;
-  int64_t ntiles = (n + RS_T - 1) / RS_T;
-  int64_t* counts = tmp.alloc<int64_t>(RS_D * ntiles + 1);
+  static thread_local int attr_dev = -1;
+  int dev = 0;
+  TH_CUDA(cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    TH_CUDA(cudaFuncSetAttribute(k_r8_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R8_SMEM));
+    attr_dev = dev;
+  }
+  const int64_t ntiles = (n + R8_TILE - 1) / R8_TILE;
+  int64_t* counts = tmp.alloc<int64_t>(R8_D * ntiles + 1);
   uint32_t* k2 = tmp.alloc<uint32_t>(n);
   uint32_t* v2 = tmp.alloc<uint32_t>(n);
   uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
-  int passes = (bits + 3) / 4;
+  const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
-    int shift = 4 * p;
-    k_rs_count<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, n, shift, ntiles, counts);
+    const int shift = 8 * p;
+    k_r8_count<<<(unsigned)ntiles, R8_T, 0, s>>>(ka, n, shift, ntiles, counts);
     TH_LAUNCHED();
-    exclusive_scan_i64(counts, counts, RS_D * ntiles, tmp, s);
-    k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, counts);
+    exclusive_scan_i64(counts, counts, R8_D * ntiles, tmp, s);
+    k_r8_scatter<<<(unsigned)ntiles, R8_T, R8_SMEM, s>>>(ka, va, kb, vb, n, shift, ntiles, counts);
     TH_LAUNCHED();
     std::swap(ka, kb);
     std::swap(va, vb);
