@@ -225,6 +225,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   constexpr int CM = 64;
   __shared__ int s_cm[4][CM + 1];
   __shared__ long long s_pf0;
+  // a cluster rank's halo copies of the coming exchange: per direction (0:
+  // changed copies back to their keepers, 1: the next colour's copies out)
+  // and other rank, (length, source index, destination index)
+  __shared__ int s_hd[2][4][3];
   constexpr int GC = (G == 1) ? 8 : G;  // lanes per column of the stopping test
   const int q = (K > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int t = order[blockIdx.x / K];
@@ -886,23 +890,47 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   // of ranks (distributed shared memory moves those an order of magnitude
   // faster than scattered words).  Neither touches a row any rank steps in
   // colour c, so the copies overlap the other ranks' sweeps.
-  auto halo = [&](int c, int cin) {
+  // The descriptors are read from global memory into s_hd by halo_desc at
+  // the start of the colour, so their latency hides behind the sweep (the
+  // barrier before the exchange publishes them).
+  auto halo_desc = [&](int c, int cin) {
     if constexpr (K > 1) {
-      const int64_t C1 = V.C;
+      if (threadIdx.x < 8) {
+        const int dir = threadIdx.x >> 2, A = threadIdx.x & 3;
+        const int64_t C1 = V.C;
+        int len = 0, src = 0, dst = 0;
+        if (A < K && A != q) {
+          if (dir == 0 && c >= 0) {
+            len = V.hl[(((int64_t)t * 4 + A) * 4 + q) * C1 + c];
+            src = hb + ((nbuf == 2) ? (c & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + q) * C1 + c) * 4 + A];
+            dst = V.hs[(((int64_t)t * 4 + A) * 4 + q) * C1 + c];
+          } else if (dir == 1 && cin >= 0) {
+            len = V.hl[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
+            src = V.hs[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
+            dst = hb + ((nbuf == 2) ? (cin & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + A) * C1 + cin) * 4 + q];
+          }
+        }
+        s_hd[dir][A][0] = len;
+        s_hd[dir][A][1] = src;
+        s_hd[dir][A][2] = dst;
+      }
+    }
+  };
+  auto halo = [&](bool out, bool in) {
+    if constexpr (K > 1) {
 #pragma unroll
       for (int A = 0; A < K; ++A) {
         if (A == q) continue;
-        if (c >= 0) {
-          const int len = V.hl[(((int64_t)t * 4 + A) * 4 + q) * C1 + c];
-          const float* src = smem + hb + ((nbuf == 2) ? (c & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + q) * C1 + c) * 4 + A];
-          const uint32_t dst = dsm_map(ra + 4u * (uint32_t)V.hs[(((int64_t)t * 4 + A) * 4 + q) * C1 + c], (uint32_t)A);
+        if (out) {  // halo copies (after r and x) -> rank A's rows
+          const int len = s_hd[0][A][0];
+          const float* src = smem + s_hd[0][A][1];
+          const uint32_t dst = dsm_map(ra + 4u * (uint32_t)s_hd[0][A][2], (uint32_t)A);
           for (int i = threadIdx.x; i < len; i += NT) dsm_st(dst + 4u * i, src[i]);
         }
-        if (cin >= 0) {
-          const int len = V.hl[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
-          const float* src = sr + V.hs[(((int64_t)t * 4 + q) * 4 + A) * C1 + cin];
-          const int at = hb + ((nbuf == 2) ? (cin & 1) * H : 0) + V.hoff[(((int64_t)t * 4 + A) * C1 + cin) * 4 + q];
-          const uint32_t dst = dsm_map(smem_u32(smem + at), (uint32_t)A);
+        if (in) {  // own rows -> rank A's halo buffer
+          const int len = s_hd[1][A][0];
+          const float* src = sr + s_hd[1][A][1];
+          const uint32_t dst = dsm_map(smem_u32(smem + s_hd[1][A][2]), (uint32_t)A);
           for (int i = threadIdx.x; i < len; i += NT) dsm_st(dst + 4u * i, src[i]);
         }
       }
@@ -952,23 +980,26 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   rows_pass(false, 0);
   sync();
   if constexpr (K > 1) {  // the first colour's halo
-    halo(-1, 0);
+    halo_desc(-1, 0);
+    __syncthreads();
+    halo(false, true);
     sync();
   }
   int ep = 0;
   bool conv = false, checked_last = false;
   while (ep < V.epochs) {
     for (int c = 0; c < nc; ++c) {
+      const bool more = c + 1 < nc;
+      halo_desc(c, more ? c + 1 : -1);
       sweep_colour(c);
       if constexpr (K > 1) {
-        __syncthreads();  // this rank's writes of colour c done
-        const int next = (c + 1 < nc) ? c + 1 : -1;
+        __syncthreads();  // this rank's writes of colour c (and the descriptors) done
         if (nbuf == 2) {  // the next colour's halo goes to the other buffer at once
-          halo(c, next);
+          halo(true, more);
         } else {  // one buffer: emptied before it is filled again
-          halo(c, -1);
+          halo(true, false);
           sync();
-          if (next >= 0) halo(-1, next);
+          if (more) halo(false, true);
         }
       }
       sync();
@@ -983,7 +1014,9 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
       }
     }
     if constexpr (K > 1) {  // the next epoch's first colour reads the rows as they are now (refreshed by a check)
-      halo(-1, 0);
+      halo_desc(-1, 0);
+      __syncthreads();
+      halo(false, true);
       sync();
     }
   }
