@@ -79,14 +79,14 @@ WORKLOADS = {
 DEFAULT = "batched-4096"
 SINGLE = "is-chunglu-n2^20-m1.6e7"  # the single-instance IS config reported beside the default
 METRIC = "SCD coord updates/s & time to residual 1e-3; batched solves/s + p99 vs plain"
-# DRAM bytes per epoch of the persistent sweep from an ncu capture of the
-# current sweep kernel, per workload (none: the kernel changed since the last
-# capture -- its block scatter gained an atomic branch -- so no figure is
-# reported until it is captured again)
-SWEEP_TRAFFIC_PER_EPOCH = {}
-# DRAM bytes per batched step of the instance kernel from an ncu capture of the
-# current kernel (none until captured)
-BATCH_TRAFFIC = {}
+# DRAM bytes per epoch of the persistent sweep, from an ncu capture of the
+# current kernel (profiles/k_sweep_is-chunglu-n2e20.md: one launch of ten
+# epochs moved 5.78 GB)
+SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 578.0e6}
+# DRAM bytes per batched step of the instance kernels (all launch classes),
+# from an ncu capture of the current kernels at full size
+# (profiles/k_inst_batched-4096_dram.md)
+BATCH_TRAFFIC = {"batched-4096": 174.6e9}
 L2_BYTES = 129 * 1024 * 1024
 SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
 
@@ -434,6 +434,7 @@ def run_gpu(args, wl, ws, rank, local):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": SWEEP_TRAFFIC_PER_EPOCH.get(args.workload),
+                     "traffic_unit": "DRAM bytes per epoch",
                      "kernel": "k_sweep (persistent colour sweep); unit = one epoch", "bytes_per_epoch": bpe,
                      "epoch_us": ep_ms / ep_n * 1e3, "peak_kind": f"{pk_kind} hbm_gbs"},
         "cpu_baseline": cpu,
@@ -603,6 +604,7 @@ def run_batched(args, wl, ws, rank, local):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": BATCH_TRAFFIC.get(args.workload),
+                     "traffic_unit": "DRAM bytes per step (all launch classes)",
                      "kernel": "k_inst (instance-resident sweep + in-kernel checks); unit = each instance's own "
                                "epochs, algorithmic bytes 20 n + 40 m per instance epoch",
                      "bytes_per_epoch_all_instances": bpe, "bytes_per_step": moved / len(infos),
