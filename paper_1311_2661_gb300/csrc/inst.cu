@@ -164,6 +164,7 @@ struct InstView {
   const int32_t* hoff;   // count * 4 * C * 4: where R(A, q, c) sits in rank q's halo buffer of colour c
   const int32_t* hH;     // count: halo buffer length
   const uint8_t* hnb;    // count: halo buffers (2: colour parity, one barrier a colour; 1: two barriers)
+  const uint8_t* xg;     // count: 1 when a cluster instance keeps x in global memory (so fewer CTAs hold r)
   const int32_t* ideg;   // count: longest column of the instance
   const uint8_t* kind;   // count: THETIS_ROUND_VC / _IS
   const float* c;        // IML column costs
@@ -257,13 +258,13 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   const int qlo = qv[q], qhi = qv[q + 1];
   // the r region also holds the rounding's two bit words per 32 own columns
   const int rr = max(rch, 2 * (((n + K - 1) / K + 31) / 32));
-  const bool xs = !SPILL || (rr + n <= cap);       // x in shared memory
+  const bool xs = SPILL ? (rr + n <= cap) : (K == 1 || V.xg[t] == 0);  // x in shared memory
   const int rs = SPILL ? min(m, cap) : rch;        // rows of r in shared memory (K = 1)
   float* sr = smem;
   float* sx = smem + rr;
   float* rgl = V.rg + row0;
-  // cluster: the halo buffer(s) after x
-  const int hb = rr + (n + K - 1) / K;
+  // cluster: the halo buffer(s) after x (after r when x is in global memory)
+  const int hb = rr + (xs ? (n + K - 1) / K : 0);
   const int H = (K > 1) ? V.hH[t] : 0;
   const int nbuf = (K > 1) ? V.hnb[t] : 0;  // the halo buffer of colour c: hb + (nbuf == 2 ? (c & 1) H : 0)
   const uint32_t* Rpos = V.rpos + row0;
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   auto xget = [&](uint32_t k) -> float {
     if constexpr (SPILL) return xs ? sx[k] : Sx[k];
     else if constexpr (K == 1) return sx[k];
-    else return dsm_ld(dsm_map(xa + 4u * (k / K), k % K));
+    else return xs ? dsm_ld(dsm_map(xa + 4u * (k / K), k % K)) : __ldcg(Sx + k);  // L2: other ranks write it
   };
   auto xset = [&](uint32_t k, float v) {
     if constexpr (SPILL) {
@@ -330,7 +331,8 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
     } else if constexpr (K == 1) {
       sx[k] = v;
     } else {
-      dsm_st(dsm_map(xa + 4u * (k / K), k % K), v);
+      if (xs) dsm_st(dsm_map(xa + 4u * (k / K), k % K), v);
+      else Sx[k] = v;
     }
   };
   // an own row e (local id in [qlo, qhi)) / own column k (k % K == q)
@@ -344,11 +346,15 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 1024 / NT) k_inst(InstV
   };
   auto xown_get = [&](int k) -> float {
     if constexpr (K == 1) return xget((uint32_t)k);
-    else return sx[k / K];
+    else return xs ? sx[k / K] : Sx[k];
   };
   auto xown_set = [&](int k, float v) {
-    if constexpr (K == 1) xset((uint32_t)k, v);
-    else sx[k / K] = v;
+    if constexpr (K == 1) {
+      xset((uint32_t)k, v);
+    } else {
+      if (xs) sx[k / K] = v;
+      else Sx[k] = v;
+    }
   };
   auto sync = [&]() {
     if constexpr (K == 1) __syncthreads();
@@ -1285,7 +1291,7 @@ __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const
                            const uint8_t* iK, const int64_t* noff, const int64_t* eoff, const uint32_t* iend,
                            const uint32_t* ient, const int32_t* cwide, const int64_t* pfirst, const int64_t* pbase,
                            const int32_t* qoff, const int32_t* hs, const int32_t* hoff, const int32_t* hH,
-                           const uint8_t* hnb, int64_t Ns, int C1, uint32_t* ell, int* err) {
+                           const uint8_t* hnb, const uint8_t* xg, int64_t Ns, int C1, uint32_t* ell, int* err) {
   GSTRIDE(k, Ns) {
     const uint32_t j = i_col[k];
     const int64_t t = inst_col[j];
@@ -1308,7 +1314,7 @@ __global__ void k_inst_ell(const uint32_t* i_col, const int32_t* inst_col, const
         int64_t rch = 0;
         for (int a = 0; a < K; ++a) rch = max(rch, (int64_t)(qoff[t * 5 + a + 1] - qoff[t * 5 + a]));
         const int64_t xch = (noff[t + 1] - noff[t] + K - 1) / K;
-        hb = max(rch, 2 * ((xch + 31) / 32)) + xch;
+        hb = max(rch, 2 * ((xch + 31) / 32)) + (xg[t] ? 0 : xch);
         H = (hnb[t] == 2) ? hH[t] : 0;  // the buffer of colour c at hb + (c & 1) H
       }
       auto slot = [&](uint32_t e) -> uint32_t {
@@ -1709,32 +1715,41 @@ void inst_classes(Problem& P) {
   const int64_t count = P.nbatch;
   const DevLimits L = dev_limits();
   std::vector<std::vector<int32_t>> members(NCLS);
-  std::vector<uint8_t> iK(count, 1);
+  std::vector<uint8_t> iK(count, 1), xg(count, 0);
   const bool clusters = P.iml_clusters && L.cluster;
-  if ((int64_t)P.h_iKmin.size() != count) P.h_iKmin.assign(count, 1);
+  if ((int64_t)P.h_iKmin.size() != count) P.h_iKmin.assign(count, 0);
   for (int64_t t = 0; t < count; ++t) {
     const int64_t n = P.h_bnoff[t + 1] - P.h_bnoff[t], m = P.h_beoff[t + 1] - P.h_beoff[t];
     // one CTA with everything in shared memory; else one CTA with x in global
     // memory when r alone fits; else a cluster (if asked for; rows are split
     // between ranks by a hash, so the estimate leaves 5 % + 256 rows of slack);
     // else one CTA whose r spills to L2
-    const int kmin = P.h_iKmin[t];
+    const int lmin = P.h_iKmin[t];
     int c = 0;
+    uint8_t g = 0;
     while (c < 3 && inst_smem(n, m, 1) > class_cap(L, c)) ++c;
     if (c == 3) {
-      // a rank: its rows, x, and a halo buffer of (at a guess) a fifth of the
-      // rows the other ranks keep and its short columns read (the layout
-      // measures it, takes a second buffer where that fits, and raises kmin
-      // of an instance that misses)
-      auto est = [&](int K) {
+      // a rank: its rows, x (unless in global memory), and a halo buffer of
+      // (at a guess) a fifth of the rows the other ranks keep and its short
+      // columns read (the layout measures it, takes a second buffer where
+      // that fits, and moves an instance that misses to the next level).
+      // Levels: 2 CTAs with x in shared memory, 2 CTAs with x in global
+      // memory (measured cheaper than a third CTA), 3, 3 global, 4, 4 global.
+      auto est = [&](int K, int xg) {
         const int64_t halo = (m * (K - 1)) / (5 * K * K) + 64;
-        return 4 * ((m * 105 / 100) / K + 256 + (n + K - 1) / K + halo);
+        return 4 * ((m * 102 / 100) / K + 512 + (xg ? 0 : (n + K - 1) / K) + halo);
       };
-      if (4 * m <= class_cap(L, CLS_SPILL)) c = CLS_SPILL;
-      else if (clusters && kmin <= 2 && est(2) <= class_cap(L, 3)) c = 3;
-      else if (clusters && kmin <= 3 && est(3) <= class_cap(L, 4)) c = 4;
-      else if (clusters && kmin <= 4 && est(4) <= class_cap(L, 5)) c = 5;
-      else c = CLS_SPILL;
+      c = CLS_SPILL;
+      if (4 * m > class_cap(L, CLS_SPILL) && clusters) {
+        for (int lv = lmin; lv < 6; ++lv) {
+          const int K = 2 + lv / 2, xg = lv & 1;
+          if (est(K, xg) <= class_cap(L, K + 1)) {
+            c = K + 1;
+            g = (uint8_t)xg;
+            break;
+          }
+        }
+      }
     }
     TH_CHECK(c != CLS_SPILL || 4 * 2 * ((n + 31) / 32) <= class_cap(L, CLS_SPILL), THETIS_E_INVALID,
              "instance engine: an instance with more vertices than one CTA's rounding scratch holds");
@@ -1742,6 +1757,7 @@ void inst_classes(Problem& P) {
     TH_CHECK(c > 2 || inst_ell16(1, m), THETIS_E_INVALID, "instance engine: a one-CTA instance with 65535 rows or more");
     members[c].push_back((int32_t)t);
     iK[t] = (uint8_t)CLASSES[c].K;
+    xg[t] = g;
   }
   std::vector<int32_t> order;
   P.h_icls_off.assign(NCLS + 1, 0);
@@ -1761,8 +1777,12 @@ void inst_classes(Problem& P) {
   TH_CUDA(cudaMemcpyAsync(P.i_order, order.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   TH_CUDA(cudaMemcpyAsync(P.i_K, iK.data(), count, cudaMemcpyHostToDevice, s));
   TH_CUDA(cudaStreamSynchronize(s));
-  if (iK != P.h_iK) P.iml_built = false;  // the rows' placement depends on K
+  if (iK != P.h_iK || xg != P.h_ixg) P.iml_built = false;  // the rows' placement depends on K, the halo on x
   P.h_iK = iK;
+  P.h_ixg = xg;
+  if (!P.i_xg) P.i_xg = P.mem.alloc<uint8_t>(count);
+  TH_CUDA(cudaMemcpyAsync(P.i_xg, xg.data(), count, cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaStreamSynchronize(s));
   P.iml_classes_ok = true;
 }
 
@@ -1791,10 +1811,11 @@ bool inst_class_smem(Problem& P) {
       int64_t rows = 0;
       for (int q = 0; q < K; ++q) rows = std::max<int64_t>(rows, qo[t * 5 + q + 1] - qo[t * 5 + q]);
       const int64_t xch = (n + K - 1) / K;
+      const bool xsm = K == 1 || P.h_ixg[t] == 0;
       const int64_t halo = (K > 1) ? (int64_t)std::max<uint8_t>(P.h_ihnb[t], 1) * P.h_iH[t] : 0;
-      const int64_t own = 4 * (std::max<int64_t>(rows, 2 * ((xch + 31) / 32)) + xch + halo);
+      const int64_t own = 4 * (std::max<int64_t>(rows, 2 * ((xch + 31) / 32)) + (xsm ? xch : 0) + halo);
       if (K > 1 && own > class_cap(L, c)) {
-        P.h_iKmin[t] = (uint8_t)(K + 1);  // 5: the spill class
+        P.h_iKmin[t] = (uint8_t)(2 * (K - 2) + P.h_ixg[t] + 1);  // the next level (6: the spill class)
         fits = false;
       }
       need = std::max(need, own);
@@ -1930,7 +1951,7 @@ void inst_layout(Problem& P) {
       int64_t rch = 0;
       for (int q = 0; q < K; ++q) rch = std::max<int64_t>(rch, qo[t * 5 + q + 1] - qo[t * 5 + q]);
       const int64_t xch = (P.h_bnoff[t + 1] - P.h_bnoff[t] + K - 1) / K;
-      const int64_t own = std::max<int64_t>(rch, 2 * ((xch + 31) / 32)) + xch;
+      const int64_t own = std::max<int64_t>(rch, 2 * ((xch + 31) / 32)) + (P.h_ixg[t] ? 0 : xch);
       P.h_ihnb[t] = (4 * (own + 2 * (int64_t)P.h_iH[t]) <= class_cap(L, K + 1)) ? 2 : 1;
     }
     once(P.i_hnb, count);
@@ -2004,7 +2025,7 @@ void inst_layout(Problem& P) {
     TH_CUDA(cudaMemsetAsync(P.i_ell, 0xff, (nslots + 1) * sizeof(uint32_t), s));
     k_inst_ell<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, ucolour, P.i_K, P.bnoff, P.beoff, P.i_end,
                                                  P.i_ent, P.i_cwide, P.i_pfirst, P.i_pbase, P.i_qoff, P.i_hs,
-                                                 P.i_hoff, P.i_hH, P.i_hnb, Ns, C1, P.i_ell, err);
+                                                 P.i_hoff, P.i_hH, P.i_hnb, P.i_xg, Ns, C1, P.i_ell, err);
     TH_LAUNCHED();
   }
   once(P.i_c, Ns + 1);
@@ -2105,6 +2126,7 @@ void inst_solve(Problem& P, const SolveArgs& a, double& sweep_ms) {
   V.hoff = P.i_hoff;
   V.hH = P.i_hH;
   V.hnb = P.i_hnb;
+  V.xg = P.i_xg;
   V.ideg = P.i_deg;
   V.kind = P.bkind;
   V.c = P.i_c;

@@ -159,7 +159,10 @@ struct Problem {
   uint8_t* i_hnb = nullptr;         // count: halo buffers (1 or 2)
   std::vector<int32_t> h_iH;        // host copy of i_hH
   std::vector<uint8_t> h_ihnb;      // host copy of i_hnb
-  std::vector<uint8_t> h_iKmin;     // count: smallest cluster an instance may take (5: the spill class)
+  uint8_t* i_xg = nullptr;          // count: 1 when a cluster instance keeps x in global memory
+  std::vector<uint8_t> h_ixg;       // host copy of i_xg
+  std::vector<uint8_t> h_iKmin;     // count: lowest cluster level an instance may take (2 (K - 2) + x in
+                                    // global memory; 6: the spill class)
   int32_t* i_deg = nullptr;         // count: largest column length of the instance
   float *i_c = nullptr, *i_x = nullptr, *i_s = nullptr;  // c, x (Ns) and s (M) in IML order
   float* i_rg = nullptr;            // M: residual rows kept in global memory (instances too large for one CTA)

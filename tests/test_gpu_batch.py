@@ -156,12 +156,13 @@ def _sized_items(sizes, seed):
 
 # instances for every launch class of the instance-resident engine: r and x
 # of 4 (n + m) bytes fit one CTA of 256, 512 or 1024 threads, or span a
-# cluster of 2, 3 or 4 CTAs (distributed shared memory; two instances each
-# for 3 and 4), or (without clusters) one CTA keeps x and part of r in global
-# memory
+# cluster of 2, 3 or 4 CTAs (distributed shared memory and halo buffers; x in
+# shared memory, or in global memory where that saves a CTA: the (20000,
+# 100000) and (19000, 140000) instances), or (without clusters) one CTA keeps
+# x and part of r in global memory
 CLASS_SIZES = [("vc", 300, 1000), ("is", 3000, 20000), ("vc", 8000, 40000), ("is", 15000, 70000),
                ("vc", 20000, 150000), ("is", 19000, 140000), ("vc", 18000, 130000),
-               ("is", 21000, 160000)]
+               ("is", 21000, 160000), ("vc", 20000, 100000)]
 
 
 @pytest.mark.parametrize("step_rule,lanes,clusters", [(0, 1, 0), (1, 1, 0), (0, 1, 1), (1, 8, 1), (0, 4, 0)])
