@@ -445,7 +445,7 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
     R.ep += chunk;
     checked_last = false;
     if (R.ep % a.refresh_every == 0 || R.ep == a.epochs) {
-      refresh_and_check(P, a, ub, xb, R.co);  // synchronises the stream
+      refresh_and_check(P, a, ub, xb, R.co, false);  // rho only; synchronises the stream
       if (persistent && sweep_error(P)) throw Error{THETIS_E_TIMEOUT, "grid barrier of the persistent sweep timed out"};
       float t = 0.f;
       TH_CUDA(cudaEventElapsedTime(&t, h->ev2, h->ev3));
@@ -466,6 +466,14 @@ void solve_run(thetis_handle* h, const SolveArgs& a, bool ub, bool xb, int engin
   if (!checked_last) {
     refresh_and_check(P, a, ub, xb, R.co);
     R.converged = (P.nbatch > 0) ? batch_after_check(P, a.tol, R.ep) : R.co.rho <= a.tol;
+  } else {
+    // the last check took rho only: the objective, infeasibility and f_beta
+    // of the same (already refreshed) iterate
+    CheckOut full{};
+    refresh_and_check(P, a, ub, xb, full, true, false);
+    R.co.obj = full.obj;
+    R.co.infeas = full.infeas;
+    R.co.fbeta = full.fbeta;
   }
   if (P.nbatch > 0) {
     batch_end_solve(P, R.ep);

@@ -375,7 +375,11 @@ void prepare_solve(Problem& P, const float* d_ubar, const float* d_xbar, const f
 // batches with step rule 1: the instances' own L_max (before any capture)
 void batch_step_rule(Problem& P, const SolveArgs& a);
 void run_epoch(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar);
-void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out);
+// FP64 refresh of r (unless refresh is false: r is already exact) and the
+// check: rho (per instance for batches), and with full also the objective,
+// the infeasibility and f_beta (intermediate checks need only rho)
+void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out, bool full = true,
+                       bool refresh = true);
 void refresh_only(Problem& P);
 // Sec. 3.4 multiplier step: ubar <- ubar - beta (A x - b) from the last FP64
 // refresh, xbar <- x (slacks included); c - A'ubar and the slack terms follow

@@ -1450,6 +1450,7 @@ struct CheckView {
   const float* sbar;
   const float* ubar;  // internal row order, or null
   double beta;
+  int full;           // 0: rho only (an intermediate check); 1: also the objective, infeasibility and f_beta terms
   int k;
   int64_t Ncol;   // all internal structural columns
   int64_t Nfree;
@@ -1656,7 +1657,7 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
     if (lane < V.k) rho = fmax(rho, fabs(fmax(yq - th, 0.0) - xq));
   }
   // (c) objective and proximal term over all structural columns
-  GSTRIDE(j, V.Ncol) {
+  if (V.full) GSTRIDE(j, V.Ncol) {
     double xj = V.x[j], xb = (V.xbar) ? V.xbar[j] : 0.0;
     obj += (double)V.c[j] * xj;
     xx += (xj - xb) * (xj - xb);
@@ -1670,9 +1671,11 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
     const bool plain = !V.cs && !V.sbar;
     GSTRIDE(i, V.M) {
       const double ri = V.r64[i];
-      inf_b = max(inf_b, (unsigned long long)__double_as_longlong(ri) & 0x7fffffffffffffffull);
-      rr = fma(ri, ri, rr);
-      if (V.ubar) ur += (double)V.ubar[i] * ri;
+      if (V.full) {
+        inf_b = max(inf_b, (unsigned long long)__double_as_longlong(ri) & 0x7fffffffffffffffull);
+        rr = fma(ri, ri, rr);
+        if (V.ubar) ur += (double)V.ubar[i] * ri;
+      }
       if (i < V.Msl) {
         const double sv = V.s[i];
         const double bsr = V.sig[i] > 0 ? beta * ri : -(beta * ri);  // beta * sign * r, sign = +-1
@@ -1693,7 +1696,7 @@ __global__ void __launch_bounds__(256) k_check(CheckView V, double* red) {
           rho_b = max(rho_b, db);
           rho_max(V.inst_rho + V.inst_row[i], __longlong_as_double((long long)db));
         }
-        xx = fma(ds, ds, xx);
+        if (V.full) xx = fma(ds, ds, xx);
       }
     }
     rho = fmax(rho, __longlong_as_double((long long)rho_b));
@@ -1845,16 +1848,19 @@ static CheckView make_check_view(Problem& P, const SolveArgs& a, bool use_ubar, 
   return V;
 }
 
-void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out) {
+void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_xbar, CheckOut& out, bool full,
+                       bool refresh) {
   cudaStream_t s = P.stream;
-  if (P.M > 0) {
+  if (refresh && P.M > 0) {
     k_refresh<<<grid_for(P.M, 256, 152 * 64), 256, 0, s>>>(P.rowptr, P.colidx, P.has_val ? P.rval : nullptr, P.x,
                                                           P.s, P.sig, P.b, P.M, P.Msl, P.r64, P.r);
     TH_LAUNCHED();
   }
-  if (P.nbatch > 0 && P.brho)
+  if (refresh && P.nbatch > 0 && P.brho)
     TH_CUDA(cudaMemsetAsync(P.brho, 0, P.nbatch * sizeof(unsigned long long), s));
-  k_check<<<CHECK_BLOCKS, 256, 0, s>>>(make_check_view(P, a, use_ubar, use_xbar), P.red);
+  CheckView V = make_check_view(P, a, use_ubar, use_xbar);
+  V.full = full ? 1 : 0;
+  k_check<<<CHECK_BLOCKS, 256, 0, s>>>(V, P.red);
   TH_LAUNCHED();
   k_check_final<<<1, 32 * NRED, 0, s>>>(P.red, P.red_out);
   TH_LAUNCHED();
@@ -1862,9 +1868,11 @@ void refresh_and_check(Problem& P, const SolveArgs& a, bool use_ubar, bool use_x
   TH_CUDA(cudaStreamSynchronize(s));
   const double* h = P.h_red;
   out.rho = h[0];
-  out.obj = h[1];
-  out.infeas = h[2];
-  out.fbeta = h[1] - h[4] + 0.5 * a.beta * h[3] + 0.5 / a.beta * h[5];
+  if (full) {
+    out.obj = h[1];
+    out.infeas = h[2];
+    out.fbeta = h[1] - h[4] + 0.5 * a.beta * h[3] + 0.5 / a.beta * h[5];
+  }
 }
 
 // FP64 recompute of r only (start of a solve)
