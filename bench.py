@@ -86,7 +86,7 @@ SWEEP_TRAFFIC_PER_EPOCH = {"is-chunglu-n2^20-m1.6e7": 578.0e6}
 # DRAM bytes per batched step of the instance kernels (all launch classes),
 # from an ncu capture of the current kernels at full size
 # (profiles/k_inst_batched-4096_dram.md)
-BATCH_TRAFFIC = {"batched-4096": 174.6e9}
+BATCH_TRAFFIC = {"batched-4096": 343.3e9}
 L2_BYTES = 129 * 1024 * 1024
 SERVE_ORACLE_N_CAP = 20000  # serving requests the oracle baseline samples
 
