@@ -402,10 +402,11 @@ thetis_status thetis_set_wait_limit(thetis_handle* h, double limit_ms, int32_t m
  * column longer than 32), 4 or 8 (that many lanes per column through the
  * CSR); clusters 0 (an instance too large for one CTA's shared memory keeps
  * x and the rows beyond it in global memory, i.e. L2) or 1 (such instances
- * span a thread-block cluster of 2, 3 or 4 CTAs whose shared memory holds r and
- * x, reached through distributed shared memory; their columns take one lane
- * each with lanes_per_column 1, else 8).  Every shape gives the same iterates
- * up to FP32 summation order.  THETIS_E_INVALID for other handles or
+ * span a thread-block cluster of 2, 3 or 4 CTAs whose shared memory holds r --
+ * and x, unless keeping x in global memory lets fewer CTAs hold r -- the ranks
+ * exchanging the rows their short columns share as contiguous halo copies
+ * between colours; a cluster's short columns always take one lane each).
+ * Every shape gives the same iterates up to FP32 summation order.  THETIS_E_INVALID for other handles or
  * values.  No counterpart in the paper (a launch-shape knob).
  */
 thetis_status thetis_set_batch_shape(thetis_handle* h, int32_t lanes_per_column, int32_t clusters);
