@@ -2071,9 +2071,10 @@ bool inst_eligible(Problem& P) {
 }
 
 // launch classes and the layout, again while an instance's halo pushes it
-// to a larger cluster (at most three times)
+// to the next cluster level (six levels up to the spill class, so at most
+// seven rounds)
 void inst_ready(Problem& P) {
-  for (int it = 0; it < 5; ++it) {
+  for (int it = 0; it < 8; ++it) {
     if (!P.iml_classes_ok) inst_classes(P);
     if (!P.iml_built) inst_layout(P);
     if (P.iml_classes_ok && P.iml_built) return;
