@@ -1624,10 +1624,11 @@ int bits_for_count(int64_t n) {
 // launch classes: (cluster size, threads per CTA).  An instance takes one CTA
 // of 256, 512 or 1024 threads when its r and x fit that CTA's shared memory,
 // else one CTA with x in global memory when r alone fits, else the smallest
-// cluster of 2, 3 or 4 CTAs whose shared memory holds them (distributed
-// shared memory; on by default, the autotuner may switch it off), else the
-// last class: one CTA of 1024 threads with x and the rows beyond its shared
-// memory in global memory (L2), measured slower than the clusters.
+// cluster of 2, 3 or 4 CTAs whose shared memory holds its rows and halo
+// buffers -- with x there too, or in global memory where that saves a CTA
+// (on by default, the autotuner may switch clusters off) -- else the last
+// class: one CTA of 1024 threads with x and the rows beyond its shared memory
+// in global memory (L2), measured slower than the clusters.
 struct Cls {
   int K, NT;
 };
@@ -1709,7 +1710,8 @@ void launch_class(int c, const InstView& V, const int32_t* order, int64_t count,
 }
 
 // launch classes and the order of instances in them (largest first); the
-// cluster size K of every instance (1 unless it takes a cluster)
+// cluster size K of every instance (1 unless it takes a cluster) and whether
+// a cluster instance keeps x in global memory
 void inst_classes(Problem& P) {
   cudaStream_t s = P.stream;
   const int64_t count = P.nbatch;
