@@ -473,6 +473,17 @@ thetis_status thetis_solve_round_batch(thetis_handle* h, const thetis_params* p,
 thetis_status thetis_batch_latency(const thetis_handle* h, double* done_ms_out);
 
 /*
+ * thetis_batch_placement -- where the last thetis_solve of a batch handle ran
+ * every instance.  start_ms_out[count] (HOST, may be NULL): with the
+ * instance-resident engine, the device time in ms from the start of the solve
+ * until the instance's CTA / cluster began (with thetis_batch_latency, the
+ * span it held its SMs); 0 with the union sweep.  ctas_out[count] (HOST, may
+ * be NULL): the CTAs of the CTA / thread-block cluster that solved it (1-4;
+ * one SM each), 0 with the union sweep.
+ */
+thetis_status thetis_batch_placement(const thetis_handle* h, double* start_ms_out, int32_t* ctas_out);
+
+/*
  * thetis_round_batch -- repair + rounding of every instance of a batch handle,
  * exactly as thetis_round does for one instance (VC threshold, IS best of `reps`
  * with the instance-local vertex ids in the random streams).

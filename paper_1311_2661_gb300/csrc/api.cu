@@ -1050,6 +1050,23 @@ thetis_status thetis_batch_latency(const thetis_handle* h, double* done_ms_out) 
   return THETIS_OK;
 }
 
+thetis_status thetis_batch_placement(const thetis_handle* h, double* start_ms_out, int32_t* ctas_out) {
+  if (!h || !h->P) {
+    set_error("null argument");
+    return THETIS_E_INVALID;
+  }
+  const Problem& P = *h->P;
+  if (P.kind != KIND_BATCH) {
+    set_error("thetis_batch_placement needs a handle from thetis_build_batch");
+    return THETIS_E_INVALID;
+  }
+  for (int64_t t = 0; t < P.nbatch; ++t) {
+    if (start_ms_out) start_ms_out[t] = P.h_bstart[t];
+    if (ctas_out) ctas_out[t] = P.h_bctas[t];
+  }
+  return THETIS_OK;
+}
+
 thetis_status thetis_solve_round_batch(thetis_handle* h, const thetis_params* p, uint64_t seed, int32_t reps,
                                        uint8_t* labels_out, int32_t out_mem, double* obj_out, int32_t* status_out,
                                        int32_t* best_rep_out, thetis_solve_info* info) {

@@ -87,6 +87,13 @@ void build_batch_raw(int64_t count, const uint8_t* d_kind, const int64_t* d_noff
     k_batch_edges<<<grid_for(Ne, 256), 256, 0, s>>>(d_eu, d_ev, d_noff, d_eoff, count, Ne, geu, gev, prow, err);
     TH_LAUNCHED();
   }
+  {  // the endpoints index the incidence counters below: checked first
+    int h = 0;
+    TH_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    TH_CHECK(h != 1, THETIS_E_INVALID, "batch: edge endpoint out of its instance's range, or a loop");
+    TH_CHECK(h != 3, THETIS_E_INVALID, "batch: kinds must be THETIS_ROUND_VC or THETIS_ROUND_IS");
+  }
   raw.M = Ne;
   raw.Ns = Nv;
   raw.nnz = 2 * Ne;
@@ -322,6 +329,8 @@ void batch_index(Problem& P) {
   P.h_bepochs.assign(count, 0);
   P.h_brho.assign(count, 0.0);
   P.h_bdone.assign(count, 0.0);
+  P.h_bstart.assign(count, 0.0);
+  P.h_bctas.assign(count, 0);
 }
 
 void batch_begin_solve(Problem& P) {
@@ -330,6 +339,8 @@ void batch_begin_solve(Problem& P) {
   std::fill(P.h_bepochs.begin(), P.h_bepochs.end(), 0);
   std::fill(P.h_brho.begin(), P.h_brho.end(), 0.0);
   std::fill(P.h_bdone.begin(), P.h_bdone.end(), 0.0);
+  std::fill(P.h_bstart.begin(), P.h_bstart.end(), 0.0);
+  std::fill(P.h_bctas.begin(), P.h_bctas.end(), 0);
   TH_CUDA(cudaMemsetAsync(P.bfrozen, 0, P.nbatch, P.stream));
   batch_active_tiles(P);
 }
@@ -398,6 +409,8 @@ void batch_inst_end(Problem& P, int& ep_max, bool& all_converged, int64_t& updat
     P.h_bepochs[t] = P.h_iep[t];
     P.h_bfrozen[t] = (uint8_t)(P.h_iconv[t] != 0);
     P.h_bdone[t] = (double)(P.h_it[2 * t + 1] - P.h_it[2 * count]) * 1e-6;
+    P.h_bstart[t] = (double)(P.h_it[2 * t] - P.h_it[2 * count]) * 1e-6;
+    P.h_bctas[t] = (int32_t)P.h_iK[t];
     ep_max = std::max(ep_max, P.h_iep[t]);
     all_converged = all_converged && P.h_iconv[t] != 0;
     updates += (int64_t)P.h_iep[t] * ((P.h_bnoff[t + 1] - P.h_bnoff[t]) + (P.h_beoff[t + 1] - P.h_beoff[t]));

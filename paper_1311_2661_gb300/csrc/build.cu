@@ -60,18 +60,18 @@ static void hist_launch_shape(int64_t n, int64_t nbins, int* grid, size_t* smem)
 // ---------------------------------------------------------------------------
 // graph builders
 // ---------------------------------------------------------------------------
-__global__ void k_pairs_from_edges(const int32_t* eu, const int32_t* ev, int64_t m, uint32_t* keys,
-                                   uint32_t* vals) {
+// the vertex of every endpoint slot: eu of edge e at e, ev at m + e
+__global__ void k_slot_vertices(const int32_t* eu, const int32_t* ev, int64_t m, uint32_t* keys) {
   GSTRIDE(e, m) {
     keys[e] = (uint32_t)eu[e];
-    vals[e] = (uint32_t)e;
     keys[m + e] = (uint32_t)ev[e];
-    vals[m + e] = (uint32_t)e;
   }
 }
-
-__global__ void k_count_keys(const uint32_t* keys, int64_t n, int64_t* cnt) {
-  GSTRIDE(i, n) atomicAdd((unsigned long long*)&cnt[keys[i]], 1ull);
+__global__ void k_slot_edges(uint32_t* slots, int64_t m) {
+  GSTRIDE(i, 2 * m) {
+    const uint32_t p = slots[i];
+    slots[i] = (p >= (uint64_t)m) ? (uint32_t)(p - m) : p;
+  }
 }
 
 __global__ void k_check_edges(const int32_t* eu, const int32_t* ev, int64_t m, int64_t n, int* err) {
@@ -110,22 +110,22 @@ static int read_flag(int* d, cudaStream_t s) {
 }
 
 // vertex -> incident edges (stable: edges where v = eu in edge order, then v = ev)
+// (the 2m endpoint slots p -- eu of edge p, then ev of edge p - m -- grouped by
+// vertex in slot order, then each slot replaced by its edge)
 static void incidence(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, int64_t*& ptr,
                       uint32_t*& edges, Arena& tmp, cudaStream_t s) {
   uint32_t* keys = tmp.alloc<uint32_t>(2 * m);
   edges = tmp.alloc<uint32_t>(2 * m);
   if (m > 0) {
-    k_pairs_from_edges<<<grid_for(m, 256), 256, 0, s>>>(eu, ev, m, keys, edges);
+    k_slot_vertices<<<grid_for(m, 256), 256, 0, s>>>(eu, ev, m, keys);
     TH_LAUNCHED();
   }
-  radix_sort_pairs(keys, edges, 2 * m, bits_for(n), tmp, s);
   ptr = tmp.alloc<int64_t>(n + 1);
-  TH_CUDA(cudaMemsetAsync(ptr, 0, (n + 1) * sizeof(int64_t), s));
+  group_by_key(keys, nullptr, 2 * m, n, edges, ptr, tmp, s);
   if (m > 0) {
-    k_count_keys<<<grid_for(2 * m, 256), 256, 0, s>>>(keys, 2 * m, ptr);
+    k_slot_edges<<<grid_for(2 * m, 256), 256, 0, s>>>(edges, m);
     TH_LAUNCHED();
   }
-  exclusive_scan_i64(ptr, ptr, n, tmp, s);
 }
 
 // vertex -> incident edges as an int32 CSC (used by the batch builder)
@@ -581,31 +581,30 @@ __global__ void k_slack_flags(const uint8_t* rk, int64_t M, int64_t* has) {
   GSTRIDE(i, M) has[i] = (rk[i] != THETIS_ROW_EQ) ? 1 : 0;
 }
 
-// (row, p) pairs for the CSC -> CSR transpose
-__global__ void k_row_pairs(const int32_t* rowidx, int64_t nnz, uint32_t* keys, uint32_t* vals) {
-  GSTRIDE(p, nnz) {
-    keys[p] = (uint32_t)rowidx[p];
-    vals[p] = (uint32_t)p;
+// the segment of every position (the column of a CSC entry, the row of a CSR
+// entry): a segment of up to 32 positions written by its thread, a longer one
+// by its whole warp
+__global__ void k_seg_ids(const int64_t* colptr, int64_t Ns, uint32_t* colof) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < Ns; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    int64_t p0 = 0, p1 = 0;
+    if (j < Ns) {
+      p0 = colptr[j];
+      p1 = colptr[j + 1];
+    }
+    const bool longc = p1 - p0 > 32;
+    if (!longc)
+      for (int64_t p = p0; p < p1; ++p) colof[p] = (uint32_t)j;
+    unsigned mb = __ballot_sync(0xffffffffu, longc);
+    while (mb) {
+      const int l = __ffs(mb) - 1;
+      mb &= mb - 1;
+      const int64_t a = __shfl_sync(0xffffffffu, p0, l), e = __shfl_sync(0xffffffffu, p1, l);
+      const uint32_t jj = (uint32_t)__shfl_sync(0xffffffffu, j, l);
+      for (int64_t p = a + lane; p < e; p += 32) colof[p] = jj;
+    }
   }
-}
-
-__device__ __forceinline__ int64_t upper_col(const int64_t* colptr, int64_t Ns, int64_t p) {
-  // column j with colptr[j] <= p < colptr[j+1]
-  int64_t lo = 0, hi = Ns;  // invariant colptr[lo] <= p < colptr[hi]
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (colptr[mid] <= p) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-__global__ void k_col_of_p(const int64_t* colptr, int64_t Ns, int64_t nnz, uint32_t* colof) {
-  GSTRIDE(p, nnz) colof[p] = (uint32_t)upper_col(colptr, Ns, p);
-}
-
-__global__ void k_count_rows(const int32_t* rowidx, int64_t nnz, int64_t* cnt) {
-  GSTRIDE(p, nnz) atomicAdd((unsigned long long*)&cnt[rowidx[p]], 1ull);
 }
 
 // csr_p: positions p sorted by row (stable); check for a repeated (row, col)
@@ -1413,52 +1412,59 @@ __global__ void k_int_col_counts(const uint32_t* orig_of_col, const int64_t* col
   }
 }
 
-// one warp per internal column
-__global__ void k_int_csc_fill(const uint32_t* orig_of_col, const int64_t* ocolptr, const int32_t* orow,
-                               const float* oval, const uint32_t* row_of_orig, const int64_t* icolptr,
-                               int64_t N, bool keep_val, uint32_t* irow, float* ival, float* csq) {
-  int lane = threadIdx.x & 31;
-  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp; j < N; j += nwarps) {
-    int64_t o = orig_of_col[j];
-    int64_t p0 = ocolptr[o], p1 = ocolptr[o + 1], q0 = icolptr[j];
-    float sq = 0.f;
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-      float v = oval ? oval[p] : 1.f;
-      uint32_t r = row_of_orig[orow[p]];
-      if (keep_val) {
-        irow[q0 + (p - p0)] = r;
-        ival[q0 + (p - p0)] = v;
-      } else {
-        irow[q0 + (p - p0)] = r | (v < 0.f ? NEG_BIT : 0u);
-      }
-      sq += v * v;
-    }
-    for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
-    if (csq && lane == 0) csq[j] = sq;
-  }
-}
-
-__global__ void k_icsc_rowkeys(const int32_t* orow, const uint32_t* row_of_orig, int64_t nnz, uint32_t* key,
-                               uint32_t* ord) {
+// the entries of every internal column at its place, in the original
+// column's order: key the internal row, ord the original position.  One
+// thread per entry (colof: the original column of every entry) where columns
+// are long on average; else one thread per column, a column of more than 32
+// entries taken by its whole warp.
+__global__ void k_icsc_gather(const uint32_t* colof, const uint32_t* col_of_orig, const int64_t* ocolptr,
+                              const int32_t* orow, const uint32_t* row_of_orig, const int64_t* icolptr, int64_t nnz,
+                              uint32_t* key, uint32_t* ord) {
   GSTRIDE(p, nnz) {
-    key[p] = row_of_orig[orow[p]];
-    ord[p] = (uint32_t)p;
+    const uint32_t o = colof[p];
+    const int64_t q = icolptr[col_of_orig[o]] + (p - ocolptr[o]);
+    key[q] = row_of_orig[orow[p]];
+    ord[q] = (uint32_t)p;
+  }
+}
+__global__ void k_icsc_gather_cols(const uint32_t* orig_of_col, const int64_t* ocolptr, const int32_t* orow,
+                                   const uint32_t* row_of_orig, const int64_t* icolptr, int64_t N, uint32_t* key,
+                                   uint32_t* ord) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    int64_t p0 = 0, p1 = 0, q0 = 0;
+    if (j < N) {
+      const int64_t o = orig_of_col[j];
+      p0 = ocolptr[o];
+      p1 = ocolptr[o + 1];
+      q0 = icolptr[j];
+    }
+    const bool longc = p1 - p0 > 32;
+    if (!longc)
+      for (int64_t p = p0; p < p1; ++p) {
+        key[q0 + (p - p0)] = row_of_orig[orow[p]];
+        ord[q0 + (p - p0)] = (uint32_t)p;
+      }
+    unsigned mb = __ballot_sync(0xffffffffu, longc);
+    while (mb) {
+      const int l = __ffs(mb) - 1;
+      mb &= mb - 1;
+      const int64_t a = __shfl_sync(0xffffffffu, p0, l), e = __shfl_sync(0xffffffffu, p1, l);
+      const int64_t q = __shfl_sync(0xffffffffu, q0, l);
+      for (int64_t p = a + lane; p < e; p += 32) {
+        key[q + (p - a)] = row_of_orig[orow[p]];
+        ord[q + (p - a)] = (uint32_t)p;
+      }
+    }
   }
 }
 
-__global__ void k_icsc_colkeys(const uint32_t* ord, const uint32_t* colof, const uint32_t* col_of_orig, int64_t nnz,
-                               uint32_t* key) {
-  GSTRIDE(t, nnz) key[t] = col_of_orig[colof[ord[t]]];
-}
-
-__global__ void k_icsc_fill(const uint32_t* ord, const int32_t* orow, const float* oval, const uint32_t* row_of_orig,
-                            int64_t nnz, bool keep_val, uint32_t* irow, float* ival) {
+__global__ void k_icsc_fill(const uint32_t* ord, const uint32_t* key, const float* oval, int64_t nnz, bool keep_val,
+                            uint32_t* irow, float* ival) {
   GSTRIDE(t, nnz) {
-    uint32_t p = ord[t];
-    float v = oval ? oval[p] : 1.f;
-    uint32_t r = row_of_orig[orow[p]];
+    const float v = oval ? oval[ord[t]] : 1.f;
+    const uint32_t r = key[t];
     if (keep_val) {
       irow[t] = r;
       ival[t] = v;
@@ -1674,23 +1680,19 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   }
 
   // -- CSR transpose (stable by row, columns ascending inside a row) -------
-  uint32_t* rkeys = tmp.alloc<uint32_t>(nnz);
+  // (the entry positions p grouped by row, ascending inside a row; rkeys: the
+  // row of every CSR position, colof: the column of every entry)
   uint32_t* csr_p = tmp.alloc<uint32_t>(nnz);
-  if (nnz > 0) {
-    k_row_pairs<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, nnz, rkeys, csr_p);
-    TH_LAUNCHED();
-  }
-  radix_sort_pairs(rkeys, csr_p, nnz, bits_for(M), tmp, s);
   int64_t* orowptr = tmp.alloc<int64_t>(M + 1);
-  TH_CUDA(cudaMemsetAsync(orowptr, 0, (M + 1) * sizeof(int64_t), s));
+  group_by_key(reinterpret_cast<const uint32_t*>(raw.rowidx), nullptr, nnz, M, csr_p, orowptr, tmp, s);
+  uint32_t* rkeys = tmp.alloc<uint32_t>(nnz);
   uint32_t* colof = tmp.alloc<uint32_t>(nnz);
   if (nnz > 0) {
-    k_count_rows<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, nnz, orowptr);
+    k_seg_ids<<<grid_for(M, 256), 256, 0, s>>>(orowptr, M, rkeys);
     TH_LAUNCHED();
-    k_col_of_p<<<grid_for(nnz, 256), 256, 0, s>>>(raw.colptr, Ns, nnz, colof);
+    k_seg_ids<<<grid_for(Ns, 256), 256, 0, s>>>(raw.colptr, Ns, colof);
     TH_LAUNCHED();
   }
-  exclusive_scan_i64(orowptr, orowptr, M, tmp, s);
   if (M > 0) {
     k_csr_dupcheck<<<grid_for(M, 256), 256, 0, s>>>(orowptr, csr_p, colof, M, err);
     TH_LAUNCHED();
@@ -1864,14 +1866,18 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
   // its highest-priority column, so the rows a column owns -- nearly all rows of
   // a hub -- are consecutive and its gather / scatter of r is coalesced.
   uint32_t* slkeys = tmp.alloc<uint32_t>(Msl + 1);
+  uint32_t* slrows0 = tmp.alloc<uint32_t>(Msl + 1);
   uint32_t* slrows = tmp.alloc<uint32_t>(Msl + 1);
   int64_t* scnt = tmp.alloc<int64_t>(C + 1);
   TH_CUDA(cudaMemsetAsync(scnt, 0, (C + 1) * sizeof(int64_t), s));
   if (Msl > 0) {
-    k_slack_owner_keys<<<grid_for(Msl, 256), 256, 0, s>>>(V, Msl, P.col_of_orig, slkeys, slrows);
+    k_slack_owner_keys<<<grid_for(Msl, 256), 256, 0, s>>>(V, Msl, P.col_of_orig, slkeys, slrows0);
     TH_LAUNCHED();
   }
-  radix_sort_pairs(slkeys, slrows, Msl, bits_for(Ns + 1), tmp, s);
+  {  // by owner column (the rows ascend within an owner's group)
+    int64_t* optr = tmp.alloc<int64_t>(Ns + 2);
+    group_by_key(slkeys, slrows0, Msl, Ns + 1, slrows, optr, tmp, s);
+  }
   if (Msl > 0) {
     int hg;
     size_t hsm;
@@ -1904,23 +1910,24 @@ std::unique_ptr<Problem> build_problem(RawLP& raw, int kind, uint64_t seed, cuda
     P.val = P.mem.alloc<float>(nnz);
     P.csq = P.mem.alloc<float>(Ns);
   }
-  // entries sorted by (internal column, internal row): two stable radix passes
+  // entries sorted by (internal column, internal row): every internal
+  // column's entries gathered in place, then sorted by internal row
   {
     uint32_t* k1 = tmp.alloc<uint32_t>(nnz + 1);
     uint32_t* ord = tmp.alloc<uint32_t>(nnz + 1);
     if (nnz > 0) {
-      k_icsc_rowkeys<<<grid_for(nnz, 256), 256, 0, s>>>(raw.rowidx, P.row_of_orig, nnz, k1, ord);
+      if (nnz > 16 * Ns) {
+        k_icsc_gather<<<grid_for(nnz, 256), 256, 0, s>>>(colof, P.col_of_orig, raw.colptr, raw.rowidx, P.row_of_orig,
+                                                         P.colptr, nnz, k1, ord);
+      } else {
+        k_icsc_gather_cols<<<grid_for(Ns, 256), 256, 0, s>>>(orig_of_col, raw.colptr, raw.rowidx, P.row_of_orig,
+                                                             P.colptr, Ns, k1, ord);
+      }
       TH_LAUNCHED();
     }
-    radix_sort_pairs(k1, ord, nnz, bits_for(M + 1), tmp, s);
+    segsort_pairs(P.colptr, Ns, k1, ord, nnz, tmp, s);
     if (nnz > 0) {
-      k_icsc_colkeys<<<grid_for(nnz, 256), 256, 0, s>>>(ord, colof, P.col_of_orig, nnz, k1);
-      TH_LAUNCHED();
-    }
-    radix_sort_pairs(k1, ord, nnz, bits_for(Ns + 1), tmp, s);
-    if (nnz > 0) {
-      k_icsc_fill<<<grid_for(nnz, 256), 256, 0, s>>>(ord, raw.rowidx, raw.val, P.row_of_orig, nnz, P.has_val, P.rowidx,
-                                                     P.val);
+      k_icsc_fill<<<grid_for(nnz, 256), 256, 0, s>>>(ord, k1, raw.val, nnz, P.has_val, P.rowidx, P.val);
       TH_LAUNCHED();
     }
     if (P.has_val) {

@@ -149,6 +149,15 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& tmp, 
 // stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, Arena& tmp,
                       cudaStream_t s);
+// every segment [ptr[i], ptr[i + 1]) of (keys, vals) sorted by key, stably, in
+// place (vals may be null); n = ptr[nseg] < 2^32.  Synchronises the stream.
+void segsort_pairs(const int64_t* ptr, int64_t nseg, uint32_t* keys, uint32_t* vals, int64_t n, Arena& tmp,
+                   cudaStream_t s);
+// out_vals: vals grouped by key (keys < nkeys), ascending inside a group (the
+// stable sort by key when vals ascend with position; null vals: the positions
+// 0..n-1); out_ptr[nkeys + 1] the groups' starts.  Synchronises the stream.
+void group_by_key(const uint32_t* keys, const uint32_t* vals, int64_t n, int64_t nkeys, uint32_t* out_vals,
+                  int64_t* out_ptr, Arena& tmp, cudaStream_t s);
 void fill_iota_u32(uint32_t* p, int64_t n, cudaStream_t s);
 void fill_f32(float* p, float v, int64_t n, cudaStream_t s);
 

@@ -101,6 +101,8 @@ struct Problem {
   std::vector<int32_t> h_bepochs;      // epochs each instance ran in the last solve
   std::vector<double> h_brho;          // its rho when it stopped
   std::vector<double> h_bdone;         // ms from the start of the solve to its stop
+  std::vector<double> h_bstart;        // instance engine: ms from the start of the solve to its CTA's start
+  std::vector<int32_t> h_bctas;        // instance engine: CTAs of the CTA / cluster that solved it (0: union sweep)
   double batch_check_ms = 0.0;         // union sweep: time of the current check since the solve started
   // active tiles: per colour, the sweep tiles holding a unit of an unfinished
   // instance (built for launch shape act_g; recomputed when instances stop)

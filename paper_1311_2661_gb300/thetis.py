@@ -91,6 +91,7 @@ def _load():
         "thetis_check_labels": (st, [P, i32, P, i32, P, P]),
         "thetis_set_wait_limit": (st, [P, C.c_double, i32]),
         "thetis_batch_latency": (st, [P, P]),
+        "thetis_batch_placement": (st, [P, P, P]),
         "thetis_set_batch_shape": (st, [P, i32, i32]),
         "thetis_solve_round_batch": (st, [P, P, u64, i32, P, i32, P, P, P, P]),
         "thetis_server_set_queue_limit": (st, [P, i64, P]),
@@ -628,6 +629,15 @@ def thetis_batch_latency(h: Handle):
     out = np.zeros(h.count, np.float64)
     _check(_lib.thetis_batch_latency(h.ptr, out.ctypes.data))
     return out
+
+
+def thetis_batch_placement(h: Handle):
+    """Per instance: (ms from the start of the last solve until its CTA /
+    cluster began, CTAs of that CTA / cluster); zeros after a union sweep."""
+    start = np.zeros(h.count, np.float64)
+    ctas = np.zeros(h.count, np.int32)
+    _check(_lib.thetis_batch_placement(h.ptr, start.ctypes.data, ctas.ctypes.data))
+    return start, ctas
 
 
 def thetis_round_is_static(n, eu, ev, w, x, labels_out, seed=0, reps=10, stream=None):

@@ -185,6 +185,8 @@ def test_instance_engine_every_launch_class_matches_oracle(step_rule, lanes, clu
     # the union sweep on the same batch agrees with it to tolerance
     hu = T.thetis_build_batch_graphs(items, seed=6, device=True)
     hu.solve(beta=100.0, epochs=30, refresh_every=10, step_rule=step_rule, engine=2)
+    start, ctas = T.thetis_batch_placement(hu)
+    assert not start.any() and not ctas.any()
     assert np.max(np.abs(hu.get_x() - hb.get_x())) <= X_TOL
 
 
@@ -199,6 +201,12 @@ def test_instance_engine_classes_stop_where_alone_stops(clusters):
     done = T.thetis_batch_latency(hb)
     assert info["converged"] and np.all(rho <= 1e-3)
     assert np.all(done > 0) and np.all(done <= info["solve_ms"] + 1e-6)
+    start, ctas = T.thetis_batch_placement(hb)
+    assert np.all(start >= 0) and np.all(start < done)
+    # one CTA unless r does not fit one CTA's shared memory (clusters on)
+    assert np.all(ctas[:3 if clusters else len(items)] == 1)
+    if clusters:
+        assert np.all((ctas[3:] >= 2) & (ctas[3:] <= 4))
     x, s = hb.get_x().astype(np.float64), hb.get_slack().astype(np.float64)
     noff, eoff = _slices(items)
     for t, (kind, g) in enumerate(items):
