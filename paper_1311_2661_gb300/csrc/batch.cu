@@ -300,8 +300,19 @@ __global__ void k_binst(const uint32_t* col_of_orig, const uint32_t* orig_of_row
   }
 }
 
+// (one atomic per warp where its lanes share the instance)
 __global__ void k_bmaxdeg(const int64_t* colptr, const int32_t* inst_col, int64_t Ns, int32_t* maxdeg) {
-  GSTRIDE(j, Ns) atomicMax(&maxdeg[inst_col[j]], (int32_t)(colptr[j + 1] - colptr[j]));
+  GSTRIDE(j, Ns) {
+    const int32_t t = inst_col[j], d = (int32_t)(colptr[j + 1] - colptr[j]);
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1;
+    if (__all_sync(act, t == __shfl_sync(act, t, leader))) {
+      const int32_t dmax = __reduce_max_sync(act, d);
+      if ((int)(threadIdx.x & 31) == leader) atomicMax(&maxdeg[t], dmax);
+    } else {
+      atomicMax(&maxdeg[t], d);
+    }
+  }
 }
 
 void batch_index(Problem& P) {

@@ -1506,11 +1506,26 @@ __global__ void k_inst_deg(const uint32_t* i_col, const int64_t* colptr, int64_t
   }
 }
 
+// per union row: its two columns, their local ids and the row's encoded id
+// (x = 0xffffffff: the row has not exactly two structural entries), so the
+// fill below reads one 16-byte record per entry instead of four scattered words
+__global__ void k_inst_rowinfo(const int64_t* rowptr, const uint32_t* colidx, const uint32_t* lcol, const uint32_t* erow,
+                               int64_t M, uint4* rinfo) {
+  GSTRIDE(i, M) {
+    const int64_t q0 = rowptr[i];
+    uint4 v = make_uint4(0xffffffffu, 0u, 0u, 0u);
+    if (rowptr[i + 1] - q0 == 2) {
+      const uint32_t a = idx_of(colidx[q0]), b = idx_of(colidx[q0 + 1]);
+      v = make_uint4(a, lcol[a], lcol[b], erow[i]);
+    }
+    rinfo[i] = v;
+  }
+}
+
 // local end offsets, entries (encoded row, other endpoint) and the longest
 // column of every instance; err: a row without exactly two structural entries
 __global__ void k_inst_fill(const uint32_t* i_col, const int32_t* inst_col, const int64_t* pos, const int64_t* eoff,
-                            const int64_t* colptr, const uint32_t* rowidx, const int64_t* rowptr,
-                            const uint32_t* colidx, const uint32_t* lcol, const uint32_t* erow, int64_t Ns,
+                            const int64_t* colptr, const uint32_t* rowidx, const uint4* rinfo, int64_t Ns,
                             uint32_t* iend, uint32_t* ient, uint32_t* inb, int32_t* ideg, int* err) {
   GSTRIDE(k, Ns) {
     const uint32_t j = i_col[k];
@@ -1518,29 +1533,36 @@ __global__ void k_inst_fill(const uint32_t* i_col, const int32_t* inst_col, cons
     const int64_t base = pos[k];
     const int64_t p0 = colptr[j], p1 = colptr[j + 1];
     iend[k] = (uint32_t)(pos[k + 1] - 2 * eoff[t]);
-    atomicMax(&ideg[t], (int32_t)(p1 - p0));
+    // the longest column: one atomic per warp where its lanes share the instance
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1;
+    const int32_t t0 = __shfl_sync(act, t, leader);
+    const int32_t d = (int32_t)(p1 - p0);
+    if (__all_sync(act, t == t0)) {
+      const int32_t dmax = __reduce_max_sync(act, d);
+      if ((int)(threadIdx.x & 31) == leader) atomicMax(&ideg[t], dmax);
+    } else {
+      atomicMax(&ideg[t], d);
+    }
     for (int64_t p = p0; p < p1; ++p) {
-      const uint32_t i = idx_of(rowidx[p]);
-      const int64_t q0 = rowptr[i];
-      if (rowptr[i + 1] - q0 != 2) {
+      const uint4 ri = rinfo[idx_of(rowidx[p])];
+      if (ri.x == 0xffffffffu) {
         atomicExch(err, 1);
         ient[base + (p - p0)] = 0;
         inb[base + (p - p0)] = 0;
         continue;
       }
-      const uint32_t a = idx_of(colidx[q0]), b = idx_of(colidx[q0 + 1]);
-      ient[base + (p - p0)] = erow[i];
-      inb[base + (p - p0)] = lcol[a == j ? b : a];
+      ient[base + (p - p0)] = ri.w;
+      inb[base + (p - p0)] = (ri.x == j) ? ri.z : ri.y;
     }
   }
 }
 
-__global__ void k_inst_rows(const uint32_t* i_row, const int64_t* rowptr, const uint32_t* colidx,
-                            const uint32_t* lcol, int64_t M, uint32_t* iru, uint32_t* irv) {
+__global__ void k_inst_rows(const uint32_t* i_row, const uint4* rinfo, int64_t M, uint32_t* iru, uint32_t* irv) {
   GSTRIDE(k, M) {
-    const int64_t q0 = rowptr[i_row[k]];
-    iru[k] = lcol[idx_of(colidx[q0])];
-    irv[k] = lcol[idx_of(colidx[q0 + 1])];
+    const uint4 ri = rinfo[i_row[k]];
+    iru[k] = ri.y;
+    irv[k] = ri.z;
   }
 }
 
@@ -1973,11 +1995,16 @@ void inst_layout(Problem& P) {
   int* err = tmp.alloc<int>(2);  // [0]: a malformed row; [1]: a halo index past 16 bits
   TH_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
   TH_CUDA(cudaMemsetAsync(P.i_deg, 0, count * sizeof(int32_t), s));
-  k_inst_fill<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, pos, P.beoff, P.colptr, P.rowidx, P.rowptr,
-                                                P.colidx, lcol, erow, Ns, P.i_end, P.i_ent, P.i_nb, P.i_deg, err);
+  uint4* rinfo = tmp.alloc<uint4>(M + 1);
+  if (M > 0) {
+    k_inst_rowinfo<<<grid_for(M, 256), 256, 0, s>>>(P.rowptr, P.colidx, lcol, erow, M, rinfo);
+    TH_LAUNCHED();
+  }
+  k_inst_fill<<<grid_for(Ns, 256), 256, 0, s>>>(P.i_col, P.binst_col, pos, P.beoff, P.colptr, P.rowidx, rinfo, Ns,
+                                                P.i_end, P.i_ent, P.i_nb, P.i_deg, err);
   TH_LAUNCHED();
   if (M > 0) {
-    k_inst_rows<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, P.rowptr, P.colidx, lcol, M, P.i_ru, P.i_rv);
+    k_inst_rows<<<grid_for(M, 256), 256, 0, s>>>(P.i_row, rinfo, M, P.i_ru, P.i_rv);
     TH_LAUNCHED();
   }
   P.iml_C = C1;
