@@ -43,6 +43,29 @@ def hub_graph(n, m, hub_deg, seed):
     return g
 
 
+def multi_hub_graph(n, m, hubs, seed):
+    """ER graph plus hubs {vertex: degree} at scattered vertex ids: columns and
+    vertex lists long enough for every per-group sort tier of the build (more
+    than 8, 32, 128 and 4096 entries) in warps other than the first."""
+    g = synth.er_graph(n, m, seed)
+    rng = np.random.default_rng(seed + 11)
+    key = set(zip(g.eu.tolist(), g.ev.tolist()))
+    extra = []
+    for hub, deg in hubs.items():
+        nb = rng.choice(np.delete(np.arange(n), hub), size=deg, replace=False)
+        for v in nb.tolist():
+            e = (min(hub, v), max(hub, v))
+            if e not in key:
+                key.add(e)
+                extra.append(e)
+    eu = np.concatenate([g.eu, np.array([e[0] for e in extra], np.int32)])
+    ev = np.concatenate([g.ev, np.array([e[1] for e in extra], np.int32)])
+    o = np.lexsort((ev, eu))
+    g.eu, g.ev = eu[o].astype(np.int32), ev[o].astype(np.int32)
+    g.w = synth.int_weights(n, 1, 10, rng)
+    return g
+
+
 def build_gpu(kind, g, seed=0, device=False, stream=None):
     T = gpu()
     if device:

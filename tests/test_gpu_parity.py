@@ -7,8 +7,8 @@ import pytest
 
 import oracle
 from paper_1311_2661_gb300 import synth
-from tests.gpu_common import (OBJ_RTOL, X_TOL, build_gpu, gpu, gpu_full_x, hub_graph, is_graph, rel,
-                              vc_graph)
+from tests.gpu_common import (OBJ_RTOL, X_TOL, build_gpu, gpu, gpu_full_x, hub_graph, is_graph, multi_hub_graph,
+                              rel, vc_graph)
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,7 @@ CASES = [
     ("is", lambda: is_graph(3000, 20000, 2)),
     ("vc", lambda: hub_graph(5000, 12000, 2600, 3)),
     ("is", lambda: hub_graph(6000, 9000, 4500, 6)),
+    ("vc", lambda: multi_hub_graph(9000, 30000, {37: 60, 1413: 300, 2900: 1500, 5071: 4700, 8999: 20}, 8)),
     ("mc", lambda: synth.grid_graph(37, 23, 4, 4)),
     ("mc", lambda: synth.grid_graph(16, 16, 8, 5)),
 ]
